@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Trace-ratio throughput of the Krylov local-trace engine on one or more GB300s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (five-orbital model, Sec. IV-V parameters): n=5, U=4, J=1, U'=U-2J,
+crystal field Uniform[-0.05, 0.05], mu = 4.5U - 10J, beta = 50, Krylov
+tolerance 1e-12; 4,096 walkers with per-flavor orders Poisson(6) (capped at
+40); one proposed insert/remove move per walker per step (rounds of moves with
+seeds 1000 + r; the walkers' configurations are not advanced). A step is one
+trace-ratio evaluation of every walker's move: validation and move editing,
+structural pruning, the Krylov trace of every surviving (walker, kept state)
+pair and the reduction to sign and log-ratio. Inputs are resident in HBM; L2
+is flushed (256 MiB write) before every timed step. Each rank runs its own
+4,096 walkers (weak scaling); there is no data-path collective.
+
+Prints one JSON line (rank 0). The FP32-Krylov path is the headline; the plain
+FP64 GPU path is timed on the same rounds (key "fp64_gpu").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "5-orbital trace-ratio evals/s (batched FP32) vs plain FP64 GPU; rel err ≤1e-5"
+UNIT = "evals/s"
+N_WALKERS = 4096
+N_ROUNDS = 200
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM_CLK = 2  # 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz x 2 flops)
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--fp64-steps", type=int, default=0, help="steps for the FP64 comparator (default min(K, 100))")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("kt_kernels.cu", "kt_model.cpp", "kt_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_0908_0681_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(sha: str):
+    """dram read+write bytes per items-kernel launch from a committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "items_kernel_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    return d.get("dram_bytes_per_launch") if d.get("source_sha") == sha else None
+
+
+def make_workload(rank: int, rounds: int):
+    from paper_0908_0681_gb300 import workloads
+    w = workloads.five_orbital()
+    seqs = workloads.generate_sequences(w, N_WALKERS, seed=1 + 7919 * rank)
+    moves = [workloads.generate_moves(w, seqs, seed=1000 + r + 100000 * rank) for r in range(rounds)]
+    return w, seqs, moves
+
+
+def cpu_baseline(w, seqs, moves_list, gpu_ratio_round0, seconds: float):
+    """Time the oracle (as it stands) on a bounded sample of the same workload on the host cores."""
+    import numpy as np
+    from oracle.oracle import Model, Params, SeqBatch, classify, ratio
+
+    spec = w.model
+    P = Params(spec.n_orb, spec.U, spec.J, Up=spec.up, mu=spec.mu, delta=spec.delta, beta=spec.beta,
+               trunc_eps=spec.trunc_eps, deg_tol=spec.deg_tol)
+    o = Model(P)
+    sb = SeqBatch(seqs.offsets, seqs.tau, seqs.flavor, seqs.dagger)
+    cs, cl, _ = o.trace(sb)
+    done, t_used, evals = 0, 0.0, 0
+    errs = []
+    r = 0
+    while t_used < seconds and r < len(moves_list):
+        mv = moves_list[r].as_dict()
+        t0 = time.perf_counter()
+        sgn, lr, ns, nl = ratio(o, sb, cs, cl, mv)
+        t_used += time.perf_counter() - t0
+        evals += seqs.n
+        if r == 0 and gpu_ratio_round0 is not None:
+            gs, gl = gpu_ratio_round0
+            ok = (sgn != 0) & np.isfinite(lr)
+            errs = np.abs(np.expm1(gl[ok] - lr[ok])).tolist()
+            sign_ok = bool((gs == sgn).all())
+        r += 1
+    out = {"value": evals / t_used, "unit": UNIT, "cores": int(o.threads_used), "kind": "oracle",
+           "sample": f"{r} round(s) x {seqs.n} walkers of the same workload (FP64 dense-block oracle, OpenMP)"}
+    if errs:
+        out["max_rel_err_fp32_vs_oracle"] = float(max(errs))
+        out["signs_equal"] = sign_ok
+    return out
+
+
+def reference_arm(a):
+    """Oracle timed on the host cores, on bounded samples of the same workload."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle.oracle import Model, Params, SeqBatch, ratio
+
+    w, seqs, moves = make_workload(0, min(N_ROUNDS, a.warmup + a.steps))
+    spec = w.model
+    P = Params(spec.n_orb, spec.U, spec.J, Up=spec.up, mu=spec.mu, delta=spec.delta, beta=spec.beta,
+               trunc_eps=spec.trunc_eps, deg_tol=spec.deg_tol)
+    o = Model(P)
+    sample = 256
+    sub = seqs.subset(range(sample))
+    sb = SeqBatch(sub.offsets, sub.tau, sub.flavor, sub.dagger)
+    cs, cl, _ = o.trace(sb)
+
+    def mv_sub(m):
+        return {k: v[:sample] for k, v in m.as_dict().items()}
+
+    for i in range(a.warmup):
+        ratio(o, sb, cs, cl, mv_sub(moves[i % len(moves)]))
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        ratio(o, sb, cs, cl, mv_sub(moves[(a.warmup + i) % len(moves)]))
+    dt = time.perf_counter() - t0
+    v = sample * a.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "five_orbital_4096_walkers", "n_orb": 5, "walkers": N_WALKERS, "beta": 50.0,
+                       "sample_walkers_per_step": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(o.threads_used), "kind": "oracle",
+                             "sample": f"{sample} of {N_WALKERS} walkers per step, FP64 dense-block oracle, OpenMP"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        reference_arm(a)
+        return
+    import numpy as np
+    import torch
+
+    from paper_0908_0681_gb300 import engine, kt
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    n_rounds = min(N_ROUNDS, a.warmup + a.steps)
+    w, seqs, moves = make_workload(rank, n_rounds)
+    dseq = engine.DeviceSeqs.from_host(seqs, dev)
+    dmoves = [engine.DeviceMoves.from_host(m, dev) for m in moves]
+    m32 = engine.model_from_spec(w.model, precision=kt.KT_FP32_KRYLOV)
+    m64 = engine.model_from_spec(w.model, precision=kt.KT_FP64)
+    info = kt.kt_model_query(m32)
+    ws = engine.workspace(m32, seqs.n, dev)
+    stream = torch.cuda.current_stream()
+    n = seqs.n
+    out_s = torch.empty(n, dtype=torch.int8, device=dev)
+    out_l = torch.empty(n, dtype=torch.float64, device=dev)
+    out_st = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MiB > 129 MB L2
+
+    def current(model):
+        s, l, st = engine.trace(model, dseq, ws=ws)
+        return s, l
+
+    cur32 = current(m32)
+    cur64 = current(m64)
+    torch.cuda.synchronize()
+
+    def step(model, cur, r, stats=None):
+        kt.kt_trace_ratio(model, dseq.batch(), cur[0], cur[1], dmoves[r % n_rounds].batch(), out_s, out_l, out_st,
+                          stats, ws, stream)
+
+    def timed_loop(model, cur, K, start_round):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        kt.kt_timing_begin(model, K)
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step(model, cur, start_round + k)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        stage_ms, nl = kt.kt_timing_end(model)
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        return ms, stage_ms, nl
+
+    # warm-up
+    for k in range(a.warmup):
+        step(m32, cur32, k)
+        step(m64, cur64, k)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms32, stage32, nl32 = timed_loop(m32, cur32, a.steps, a.warmup)
+    clocks = sampler.stop()
+    if st_bad := int((out_st != 0).sum().item()):
+        print(f"warning: {st_bad} walkers with non-OK status in the last step", file=sys.stderr)
+
+    K64 = a.fp64_steps if a.fp64_steps > 0 else min(a.steps, 100)
+    ms64, stage64, _ = timed_loop(m64, cur64, K64, a.warmup)
+
+    # algorithmic work of the timed FP32 steps (untimed stats pass over the same rounds)
+    stats = engine.new_stats(dev)
+    for k in range(a.steps):
+        step(m32, cur32, a.warmup + k, stats)
+    torch.cuda.synchronize()
+    st = kt.stats_from_tensor(stats)
+
+    # end to end through the C ABI from pinned host buffers
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+            dict(off=seqs.offsets, tau=seqs.tau, fl=seqs.flavor, dg=seqs.dagger).items()}
+    cs_h, cl_h = cur32[0].cpu().pin_memory(), cur32[1].cpu().pin_memory()
+    mv_h = [{k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in m.as_dict().items()}
+            for m in moves]
+    res_h = (torch.empty(n, dtype=torch.int8).pin_memory(), torch.empty(n, dtype=torch.float64).pin_memory(),
+             torch.empty(n, dtype=torch.int32).pin_memory())
+    d_cs, d_cl = torch.empty_like(cur32[0]), torch.empty_like(cur32[1])
+    d_mv = engine.DeviceMoves.from_host(moves[0], dev)
+    h2d = sum(t.numel() * t.element_size() for t in host.values()) + n * 9 + d_mv.nbytes()
+    d2h = n * (1 + 8 + 4)
+    K_e2e = min(a.steps, 200)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(K_e2e):
+        r = (a.warmup + k) % n_rounds
+        dseq.offsets.copy_(host["off"], non_blocking=True)
+        dseq.tau.copy_(host["tau"], non_blocking=True)
+        dseq.flavor.copy_(host["fl"], non_blocking=True)
+        dseq.dagger.copy_(host["dg"], non_blocking=True)
+        d_cs.copy_(cs_h, non_blocking=True)
+        d_cl.copy_(cl_h, non_blocking=True)
+        for name in ("kind", "flavor", "t_dag", "t_ann", "rem_idx"):
+            getattr(d_mv, name).copy_(mv_h[r][name], non_blocking=True)
+        kt.kt_trace_ratio(m32, dseq.batch(), d_cs, d_cl, d_mv.batch(), out_s, out_l, out_st, None, ws, stream)
+        res_h[0].copy_(out_s, non_blocking=True)
+        res_h[1].copy_(out_l, non_blocking=True)
+        res_h[2].copy_(out_st, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / K_e2e
+    barrier()
+
+    # aggregate over ranks: max time
+    tot32 = sum(ms32)
+    tot64 = sum(ms64)
+    if world > 1:
+        t = torch.tensor([tot32, tot64, e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot32, tot64, e2e_ms = t.tolist()
+    value = world * n * a.steps / (tot32 / 1000.0)
+    value64 = world * n * K64 / (tot64 / 1000.0)
+    e2e_value = world * n / (e2e_ms / 1000.0)
+
+    # roofline of the dominant kernel (Krylov items)
+    items_ms = stage32["items"] / max(nl32, 1)
+    sha = source_sha()
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak32 = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    peak64 = SM_COUNT_GB300 * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+    f32_per_launch = st["flops_vec"] / a.steps
+    f64_per_launch = st["flops_tri"] / a.steps
+    ach32 = f32_per_launch / (items_ms / 1000.0) / 1e12
+    ach64 = f64_per_launch / (items_ms / 1000.0) / 1e12
+    fp32_dom = ach32 / peak32 >= ach64 / peak64
+    roofline = {"bound": "alu", "achieved": ach32 if fp32_dom else ach64, "peak": peak32 if fp32_dom else peak64,
+                "unit": "TFLOP/s", "frac": (ach32 / peak32) if fp32_dom else (ach64 / peak64),
+                "traffic": measured_traffic(sha), "kernel": "items_kernel",
+                "pipe": "fp32" if fp32_dom else "fp64",
+                "fp32": {"achieved": ach32, "peak": peak32, "frac": ach32 / peak32},
+                "fp64": {"achieved": ach64, "peak": peak64, "frac": ach64 / peak64},
+                "items_ms_per_launch": items_ms,
+                "stage_ms_per_step": {k: v / max(nl32, 1) for k, v in stage32.items()},
+                "peak_source": "derived: 152 SMs x (128 FP32 | 2 FP64) FMA lanes/clk x 2 flops x max SM clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        # GPU ratios of the first timed round, for the sampled error statement
+        step(m32, cur32, a.warmup)
+        torch.cuda.synchronize()
+        g = (out_s.cpu().numpy(), out_l.cpu().numpy())
+        cpu = cpu_baseline(w, seqs, moves[a.warmup % n_rounds:] + moves[:a.warmup % n_rounds], g, a.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": tot32 / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "five_orbital_4096_walkers", "n_orb": 5, "U": 4.0, "J": 1.0, "beta": 50.0,
+                       "walkers_per_gpu": n, "mean_ops_per_walker": float(seqs.offsets[-1]) / n,
+                       "krylov_tol": 1e-12, "precision": "fp32-krylov (fp64 tridiagonal exp, norms, log-weights)",
+                       "blocks": "(n_up, n_dn, singly-occupied mask)", "n_blocks": info["n_blocks"],
+                       "d_max": info["d_max"], "n_kept": info["n_kept"], "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": tot64 / K64, "steps": K64,
+                         "stage_ms_per_step": {k: v / max(K64, 1) for k, v in stage64.items()},
+                         "speedup_fp32_over_fp64": value / value64},
+            "work": {"items_alive_per_step": st["items_alive"] / a.steps, "intervals_per_step": st["intervals"] / a.steps,
+                     "mean_krylov_dim": st["krylov_iters"] / max(st["intervals"], 1), "p_max": st["p_max"],
+                     "noconv": st["noconv"], "flops_vec_per_step": f32_per_launch, "flops_tri_per_step": f64_per_launch},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clocks,
+            "gpu_launches": 4 * a.steps,
+            "kernel_source_sha": sha,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * kt.h - C ABI of the GB300 Krylov local-trace engine for the hybridization
+ * expansion (Laeuchli & Werner, "Krylov-implementation of the hybridization
+ * expansion impurity solver and application to 5-orbital models").
+ *
+ * The engine evaluates, for a batch of Monte Carlo walkers, the local trace of
+ * Eq. (weight_strong) truncated to the low-energy eigenstates of H_loc
+ * (Sec. II, truncation type (i); Sec. III, steps 3-8):
+ *
+ *   T = sum_{n kept} <n| e^{-(beta-tau_K) H} O_K e^{-(tau_K - tau_{K-1}) H} ... O_1 e^{-tau_1 H} |n>
+ *
+ * with H = H_loc of Eq. (H_loc) (Sec. IV.A), O_k = c_f or c_f^+, every inner
+ * interval propagated by a Lanczos approximation of exp(-dtau H) v (Sec. III,
+ * step 5), and the trace ratio of a local update (insertion or removal of a
+ * c^+/c pair, Sec. II) against the walker's current trace.
+ *
+ * Conventions fixed by this library (the paper leaves them open):
+ *   - flavor f = 2a + s for orbital a in [0, n_orb) and spin s (0 up, 1 down);
+ *     bit f of a Fock bitstring is the occupation n_f;
+ *   - c_f and c_f^+ carry the Jordan-Wigner sign (-1)^popcount(x & ((1<<f)-1));
+ *   - a sequence is sorted by time (non-decreasing), tau in [0, beta), and its
+ *     operators act in increasing array index; at equal times array order
+ *     decides and a zero-length interval is the identity;
+ *   - the spin-flip and pair-hopping terms of Eq. (H_loc) are read with each
+ *     ordered orbital pair a != b counted once (this keeps H_loc SU(2)
+ *     invariant at U' = U - 2J);
+ *   - results are (sign, log|T|); internally every propagation is shifted by
+ *     the global ground energy E0 so that log|T| = log|T~| - beta E0 with
+ *     |T~| <= N_tr.
+ *
+ * Memory and streams: every batch, move and output pointer below is a DEVICE
+ * pointer owned by the caller. The model's tables are device memory owned by
+ * the model (allocated by kt_model_create on the current device, freed by
+ * kt_model_destroy). Per-call scratch is a caller-owned device workspace of
+ * at least kt_workspace_size() bytes. Trace calls enqueue kernels on the given
+ * cudaStream_t (NULL = legacy default stream) and return without
+ * synchronising; their return value reports only argument and launch errors,
+ * while per-walker outcomes land in the device array `status`.
+ * No call throws; no call falls back to the CPU.
+ */
+#ifndef KT_H
+#define KT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KT_OK = 0,
+  KT_EINVAL = 1,       /* malformed argument, sequence or move */
+  KT_ENOMEM = 2,       /* host or device allocation failed, or workspace too small */
+  KT_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  KT_ENOCONV = 4,      /* a Krylov propagation reached its dimension cap unconverged */
+  KT_ENUMERIC = 5,     /* NaN or Inf met in a log-weight */
+  KT_EZEROWEIGHT = 6,  /* trace ratio requested against a current weight of 0 */
+  KT_ETIMEOUT = 7,     /* a bounded device-side wait gave up */
+  KT_EUNSUPPORTED = 8  /* model outside what the compiled kernels handle */
+} kt_status;
+
+/* precision */
+#define KT_FP64 0         /* FP64 Krylov vectors and scalars (plain FP64 path) */
+#define KT_FP32_KRYLOV 1  /* FP32 SpMV and Krylov vectors; FP64 tridiagonal exponential,
+                             Lanczos norms and log-weights */
+
+/* flags */
+#define KT_DENSITY_ONLY 1u   /* drop spin-flip and pair-hopping (density-density H_loc) */
+#define KT_SECTOR_BLOCKS 2u  /* propagate in whole (n_up, n_dn) sectors instead of the
+                                finer blocks that also fix the set of singly occupied orbitals */
+#define KT_HOST_ONLY 256u    /* build and check the model on the host only: no device upload;
+                                trace calls on such a model return KT_EINVAL */
+
+/* Model parameters of Eq. (H_loc) (Sec. IV.A) and of the trace truncation
+ * (Sec. III, setup steps 1-2). */
+typedef struct {
+  int32_t n_orb;        /* orbitals, 1..7 (2*n_orb flavors, 4^n_orb Fock states) */
+  double U;             /* intra-orbital repulsion */
+  double J;             /* Hund coupling (spin-flip and pair hopping carry -J) */
+  double Up;            /* inter-orbital U'; NaN selects U - 2J */
+  double mu;            /* chemical potential, enters as -(mu + delta_a) n_{a,s} */
+  const double *delta;  /* HOST pointer, [n_orb] crystal-field shifts, or NULL for zeros */
+  double beta;          /* inverse temperature */
+  double trunc_eps;     /* keep whole multiplets with exp(-beta (E - E0)) >= trunc_eps;
+                           <= 0 keeps every eigenstate (untruncated trace) */
+  double deg_tol;       /* eigenvalues within deg_tol * max(1, |E|) form one multiplet */
+  double krylov_tol;    /* relative a-posteriori error target per propagation */
+  int32_t krylov_pmax;  /* cap on the Krylov dimension (<= 0: the compiled maximum) */
+  int32_t precision;    /* KT_FP64 or KT_FP32_KRYLOV */
+  uint32_t flags;       /* KT_DENSITY_ONLY | KT_SECTOR_BLOCKS */
+} kt_model_params;
+
+typedef struct kt_model kt_model;
+
+typedef struct {
+  int32_t n_orb, n_flavors, n_states;
+  int32_t n_blocks;     /* invariant blocks of H_loc used for propagation */
+  int32_t d_max;        /* largest block dimension */
+  int32_t nnz_max;      /* most off-diagonal entries in one row */
+  int32_t n_kept;       /* N_tr: kept eigenstates in the outer trace */
+  int32_t precision;
+  int32_t krylov_pmax;  /* effective Krylov cap */
+  int32_t kernel_dmax;  /* row capacity of the kernel variant chosen for this model */
+  double E0;            /* global ground energy of H_loc */
+  double e_kept_max;    /* highest kept energy minus E0 */
+  size_t device_bytes;  /* device memory held by the model's tables */
+} kt_model_info;
+
+/* Per-call counters, accumulated on the device with atomics into a caller-owned
+ * DEVICE struct (zero it before the call; pass NULL to skip counting). */
+typedef struct {
+  unsigned long long walkers;        /* walkers evaluated */
+  unsigned long long items;          /* (walker, kept state) pairs */
+  unsigned long long items_alive;    /* pairs that survived structural pruning */
+  unsigned long long items_vanished; /* alive pairs whose vector became exactly zero */
+  unsigned long long ops_applied;    /* c / c^+ applications */
+  unsigned long long intervals;      /* Krylov propagations */
+  unsigned long long krylov_iters;   /* sum of Krylov dimensions p */
+  unsigned long long p_max;          /* largest p seen */
+  unsigned long long noconv;         /* propagations that stopped at the cap unconverged */
+  unsigned long long flops_vec;      /* algorithmic vector flops (SpMV, dots, axpys, assembly) */
+  unsigned long long flops_tri;      /* FP64 flops of the small tridiagonal exponentials */
+  unsigned long long bytes_apply;    /* bytes moved by c / c^+ gathers */
+} kt_stats;
+
+/* CSR batch of operator sequences (Eq. (weight_strong): the time-ordered
+ * product of hybridization events). All DEVICE pointers. */
+typedef struct {
+  int32_t n;               /* walkers */
+  const int32_t *offsets;  /* [n+1], offsets[0] = 0; ops of walker i: offsets[i] .. offsets[i+1]-1 */
+  const double *tau;       /* [offsets[n]] times in [0, beta), non-decreasing per walker */
+  const uint8_t *flavor;   /* [offsets[n]] flavor f in [0, 2 n_orb) */
+  const uint8_t *dagger;   /* [offsets[n]] 1 = c_f^+, 0 = c_f */
+} kt_seq_batch;
+
+/* One proposed local update per walker (Sec. II: insertion or removal of a
+ * pair of c^+ and c). All DEVICE pointers, [n] each. */
+typedef struct {
+  const uint8_t *kind;     /* 0 insert, 1 remove */
+  const uint8_t *flavor;   /* flavor of the pair */
+  const double *t_dag;     /* insert: time of the new c^+ */
+  const double *t_ann;     /* insert: time of the new c; each new operator goes after all
+                              existing operators at an equal time; if t_dag == t_ann the c
+                              is placed first */
+  const int32_t *rem_idx;  /* remove: index (inside the walker's sequence) of the c^+ to drop;
+                              the next operator of the same flavor after it, cyclically,
+                              must be a c and is dropped with it */
+} kt_move_batch;
+
+/* Human-readable name of a status code (static storage). */
+const char *kt_status_string(kt_status s);
+
+/* Sec. III, setup steps 1-2: enumerate the Fock space, build the blocks of
+ * H_loc (Eq. (H_loc)) and the c / c^+ maps with Jordan-Wigner signs,
+ * diagonalise every block, pick the kept multiplets, and upload the tables to
+ * the current CUDA device. *out is owned by the caller and released with
+ * kt_model_destroy. Errors: KT_EINVAL (parameters), KT_ENOMEM, KT_ECUDA,
+ * KT_EUNSUPPORTED (a block larger than every compiled kernel variant). */
+kt_status kt_model_create(const kt_model_params *params, kt_model **out);
+
+/* Sizes and energies of a model (host struct). */
+kt_status kt_model_query(const kt_model *m, kt_model_info *out);
+
+/* Kept eigenstates (HOST arrays of length n_kept, any may be NULL): energy
+ * E - E0, and the (n_up, n_dn) and singly-occupied-orbital mask of the block
+ * that holds each one. */
+kt_status kt_model_kept(const kt_model *m, double *e_minus_e0, int32_t *n_up, int32_t *n_dn,
+                        int32_t *single_mask);
+
+/* All eigenvalues of H_loc (HOST array of length n_states), ascending: the
+ * spectrum of Sec. III setup step 1. */
+kt_status kt_model_spectrum(const kt_model *m, double *energies);
+
+/* Free the model and its device tables (no-op on NULL). Not stream-ordered:
+ * call it after all work using the model has completed. */
+void kt_model_destroy(kt_model *m);
+
+/* Device workspace (bytes) that kt_trace / kt_trace_ratio need for n walkers. */
+kt_status kt_workspace_size(const kt_model *m, int32_t n_walkers, size_t *bytes);
+
+/* Sec. III steps 3-8 for every walker of the batch: the truncated local trace.
+ * Outputs (DEVICE, [n] each): sign in {-1, 0, +1}; logabs = log|T| (-inf when
+ * sign = 0); status = kt_status of that walker (KT_EINVAL for an unsorted
+ * sequence, a flavor out of range or a time outside [0, beta); KT_ENOCONV if a
+ * propagation stopped at the Krylov cap; KT_ENUMERIC for a NaN/Inf weight).
+ * stats may be NULL. workspace: DEVICE, >= kt_workspace_size(m, batch->n).
+ * stream: a cudaStream_t. Returns KT_EINVAL/KT_ENOMEM/KT_ECUDA on bad
+ * arguments or launch failure, else KT_OK (asynchronous). */
+kt_status kt_trace(kt_model *m, const kt_seq_batch *batch, int8_t *sign, double *logabs, int32_t *status,
+                   kt_stats *stats, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Trace ratio of one local update per walker (Sec. II local updates; the
+ * trace factor of the Metropolis ratio of Eq. (weight_strong)): the trace of
+ * the edited sequence divided by the caller's current trace (cur_sign,
+ * cur_logabs, DEVICE, [n]), as sign = sign_new * cur_sign and
+ * logratio = log|T_new| - cur_logabs (-inf when the new trace is 0).
+ * A walker with cur_sign == 0 gets status KT_EZEROWEIGHT, sign 0 and logratio
+ * NaN; a malformed move gets KT_EINVAL. Other arguments as kt_trace. */
+kt_status kt_trace_ratio(kt_model *m, const kt_seq_batch *cur, const int8_t *cur_sign, const double *cur_logabs,
+                         const kt_move_batch *moves, int8_t *sign, double *logratio, int32_t *status,
+                         kt_stats *stats, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Per-stage timing with CUDA events (profiling aid, not part of the method).
+ * After kt_timing_begin(m, max_launches), each of the next max_launches trace
+ * or trace-ratio calls on m records CUDA events on its own stream around its
+ * four kernels: 0 validation/edit, 1 structural pruning, 2 Krylov items,
+ * 3 reduction. kt_timing_end waits for those events, writes the summed
+ * durations in milliseconds to ms_per_stage[4] and the number of recorded calls
+ * to *launches, and stops recording. Calls beyond max_launches run untimed.
+ * Not thread-safe: do not share a model between host threads while timing. */
+kt_status kt_timing_begin(kt_model *m, int32_t max_launches);
+kt_status kt_timing_end(kt_model *m, double *ms_per_stage, int32_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KT_H */

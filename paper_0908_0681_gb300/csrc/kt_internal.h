@@ -1,0 +1,92 @@
+// Internal declarations shared by the host setup (kt_model.cpp) and the CUDA
+// kernels (kt_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/kt.h"
+
+namespace kt {
+
+// Device tables of one model (plain pointers into a single device allocation).
+//
+// Blocks: H_loc is block diagonal in the occupation basis. A block is the set
+// of bitstrings with the same (n_up, n_dn) and, unless KT_SECTOR_BLOCKS is
+// set, the same mask of singly occupied orbitals (spin flip and pair hopping
+// of Eq. (H_loc) never change which orbitals hold exactly one electron).
+// Inside a block, rows are the bitstrings in ascending order.
+struct DevModel {
+  int n_orb, nf, n_states, n_blocks, n_kept, d_max, pmax;
+  double beta, E0, tol, brk_rel;
+
+  const int32_t *blk_off;     // [n_blocks] first global row of the block
+  const int32_t *blk_dim;     // [n_blocks]
+  const int32_t *blk_nnz;     // [n_blocks] ELL width (max off-diagonal entries per row)
+  const int32_t *blk_ell;     // [n_blocks] first ELL slot of the block (row-major rows x width)
+  const double *blk_shift;    // [n_blocks] lowest eigenvalue s_b of the block
+  const double *blk_norm;     // [n_blocks] 1-norm of H_b - s_b
+  const int32_t *blk_target;  // [n_blocks * nf * 2] block reached by c_f (dag 0) / c_f^+ (dag 1), -1 if none
+
+  const uint16_t *st_bits;    // [n_states] bitstring of each global row
+  const double *st_diag64;    // [n_states] diagonal of H - s_b
+  const float *st_diag32;
+  const int16_t *ell_col;     // [n_ell] column inside the block, -1 = padding
+  const double *ell_val64;    // [n_ell] off-diagonal values
+  const float *ell_val32;
+  const uint16_t *partner;    // [n_states * nf] rank of (x ^ 1<<f) in its block | 0x8000 if the
+                              //   Jordan-Wigner sign of c_f / c_f^+ on x is negative
+
+  const int32_t *kept_blk;    // [n_kept]
+  const double *kept_e;       // [n_kept] E - E0
+  const int32_t *kept_off;    // [n_kept] offset into kept_vec (block dimension entries)
+  const double *kept_vec64;
+  const float *kept_vec32;
+};
+
+struct SeqView {
+  int n;
+  const int32_t *offsets;
+  const double *tau;
+  const uint8_t *flavor;
+  const uint8_t *dagger;
+};
+
+struct MoveView {
+  const uint8_t *kind;
+  const uint8_t *flavor;
+  const double *t_dag;
+  const double *t_ann;
+  const int32_t *rem_idx;
+};
+
+// Workspace layout (device), sized for n walkers and n_kept kept states.
+struct Workspace {
+  int32_t *counters;   // [4]: 0 = number of alive items, 1 = next item to claim
+  int4 *desc;          // [n] per-walker edit descriptor {kind, p1, p2, K_new}
+  int32_t *wstatus;    // [n] per-walker status from validation
+  int32_t *worklist;   // [n * n_kept] alive items (walker * n_kept + kept)
+  int8_t *item_sign;   // [n * n_kept]
+  double *item_log;    // [n * n_kept] log|contribution| (relative to exp(-beta E0))
+  int32_t *item_status;// [n * n_kept]
+};
+
+size_t workspace_bytes(int n_walkers, int n_kept);
+Workspace carve_workspace(void *base, int n_walkers, int n_kept);
+
+// Kernel variants compiled for sm_103a: rows per block (DMAX) and Krylov cap (PMAX).
+int kernel_dmax_for(int d_max);    // 0 if no variant fits
+int kernel_pmax_for(int kernel_dmax);
+
+// Optional CUDA events recorded at the 5 stage boundaries of one pipeline call.
+struct StageEvents {
+  void *ev[5];  // cudaEvent_t
+};
+
+// Launch the full pipeline (validation/edit, pruning, Krylov items, reduction).
+// moves == nullptr: plain traces. Returns a CUDA error code (0 = success).
+int launch_pipeline(const DevModel &m, int precision, int kernel_dmax, const SeqView &seq, const MoveView *moves,
+                    const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv, int32_t *status,
+                    kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing);
+
+}  // namespace kt

@@ -1,0 +1,101 @@
+"""Convenience layer over the binding: device-resident batches and one-call traces.
+
+Moves arrays to the GPU with torch, sizes the workspace and calls the C ABI;
+it computes nothing itself.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import kt
+
+
+@dataclass
+class DeviceSeqs:
+    offsets: torch.Tensor
+    tau: torch.Tensor
+    flavor: torch.Tensor
+    dagger: torch.Tensor
+
+    @staticmethod
+    def from_host(seqs, device="cuda") -> "DeviceSeqs":
+        return DeviceSeqs(torch.as_tensor(np.asarray(seqs.offsets, np.int32), device=device),
+                          torch.as_tensor(np.asarray(seqs.tau, np.float64), device=device),
+                          torch.as_tensor(np.asarray(seqs.flavor, np.uint8), device=device),
+                          torch.as_tensor(np.asarray(seqs.dagger, np.uint8), device=device))
+
+    @property
+    def n(self) -> int:
+        return self.offsets.numel() - 1
+
+    def batch(self) -> kt.kt_seq_batch:
+        return kt.seq_batch(self.offsets, self.tau, self.flavor, self.dagger)
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.offsets, self.tau, self.flavor, self.dagger))
+
+
+@dataclass
+class DeviceMoves:
+    kind: torch.Tensor
+    flavor: torch.Tensor
+    t_dag: torch.Tensor
+    t_ann: torch.Tensor
+    rem_idx: torch.Tensor
+
+    @staticmethod
+    def from_host(mv, device="cuda") -> "DeviceMoves":
+        return DeviceMoves(torch.as_tensor(np.asarray(mv.kind, np.uint8), device=device),
+                           torch.as_tensor(np.asarray(mv.flavor, np.uint8), device=device),
+                           torch.as_tensor(np.asarray(mv.t_dag, np.float64), device=device),
+                           torch.as_tensor(np.asarray(mv.t_ann, np.float64), device=device),
+                           torch.as_tensor(np.asarray(mv.rem_idx, np.int32), device=device))
+
+    def batch(self) -> kt.kt_move_batch:
+        return kt.move_batch(self.kind, self.flavor, self.t_dag, self.t_ann, self.rem_idx)
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.kind, self.flavor, self.t_dag, self.t_ann, self.rem_idx))
+
+
+def model_from_spec(spec, precision=kt.KT_FP32_KRYLOV, flags=0, krylov_pmax=0, trunc_eps=None) -> kt.KtModel:
+    return kt.kt_model_create(spec.n_orb, spec.U, spec.J, spec.mu, spec.beta, delta=spec.delta,
+                              Up=spec.up, trunc_eps=spec.trunc_eps if trunc_eps is None else trunc_eps,
+                              deg_tol=spec.deg_tol, krylov_tol=spec.krylov_tol, krylov_pmax=krylov_pmax,
+                              precision=precision, flags=flags)
+
+
+def new_stats(device="cuda") -> torch.Tensor:
+    return torch.zeros(len(kt.STATS_FIELDS), dtype=torch.int64, device=device)
+
+
+def workspace(model: kt.KtModel, n: int, device="cuda") -> torch.Tensor:
+    return torch.empty(max(kt.kt_workspace_size(model, n), 1), dtype=torch.uint8, device=device)
+
+
+def trace(model: kt.KtModel, seqs: DeviceSeqs, stats: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+    """(sign int8, log|T| float64, status int32) device tensors for every walker."""
+    n = seqs.n
+    dev = seqs.offsets.device
+    sign = torch.empty(n, dtype=torch.int8, device=dev)
+    la = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = workspace(model, n, dev) if ws is None else ws
+    kt.kt_trace(model, seqs.batch(), sign, la, st, stats, ws)
+    return sign, la, st
+
+
+def trace_ratio(model: kt.KtModel, seqs: DeviceSeqs, cur_sign: torch.Tensor, cur_logabs: torch.Tensor,
+                moves: DeviceMoves, stats: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+    """(sign int8, log|ratio| float64, status int32) device tensors for every walker."""
+    n = seqs.n
+    dev = seqs.offsets.device
+    sign = torch.empty(n, dtype=torch.int8, device=dev)
+    lr = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = workspace(model, n, dev) if ws is None else ws
+    kt.kt_trace_ratio(model, seqs.batch(), cur_sign, cur_logabs, moves.batch(), sign, lr, st, stats, ws)
+    return sign, lr, st

@@ -1,0 +1,229 @@
+"""Thin Python binding of the C ABI in include/kt.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of its own: all work runs in libkt.so's CUDA kernels. PyTorch is
+used for device memory (tensors) and streams. If the shared library is
+missing and cannot be built, importing the engine raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KT_OK, KT_EINVAL, KT_ENOMEM, KT_ECUDA, KT_ENOCONV, KT_ENUMERIC, KT_EZEROWEIGHT, KT_ETIMEOUT, KT_EUNSUPPORTED = range(9)
+KT_FP64, KT_FP32_KRYLOV = 0, 1
+KT_DENSITY_ONLY, KT_SECTOR_BLOCKS, KT_HOST_ONLY = 1, 2, 256
+
+
+class kt_model_params(ctypes.Structure):
+    _fields_ = [("n_orb", ctypes.c_int32), ("U", ctypes.c_double), ("J", ctypes.c_double), ("Up", ctypes.c_double),
+                ("mu", ctypes.c_double), ("delta", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.c_double),
+                ("trunc_eps", ctypes.c_double), ("deg_tol", ctypes.c_double), ("krylov_tol", ctypes.c_double),
+                ("krylov_pmax", ctypes.c_int32), ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class kt_model_info(ctypes.Structure):
+    _fields_ = [("n_orb", ctypes.c_int32), ("n_flavors", ctypes.c_int32), ("n_states", ctypes.c_int32),
+                ("n_blocks", ctypes.c_int32), ("d_max", ctypes.c_int32), ("nnz_max", ctypes.c_int32),
+                ("n_kept", ctypes.c_int32), ("precision", ctypes.c_int32), ("krylov_pmax", ctypes.c_int32),
+                ("kernel_dmax", ctypes.c_int32), ("E0", ctypes.c_double), ("e_kept_max", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+STATS_FIELDS = ["walkers", "items", "items_alive", "items_vanished", "ops_applied", "intervals", "krylov_iters",
+                "p_max", "noconv", "flops_vec", "flops_tri", "bytes_apply"]
+
+
+class kt_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_ulonglong) for f in STATS_FIELDS]
+
+
+class kt_seq_batch(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("offsets", ctypes.c_void_p), ("tau", ctypes.c_void_p),
+                ("flavor", ctypes.c_void_p), ("dagger", ctypes.c_void_p)]
+
+
+class kt_move_batch(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_void_p), ("flavor", ctypes.c_void_p), ("t_dag", ctypes.c_void_p),
+                ("t_ann", ctypes.c_void_p), ("rem_idx", ctypes.c_void_p)]
+
+
+# Every function the header declares (checked by the CPU test suite).
+ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_model_kept", "kt_model_spectrum",
+                 "kt_model_destroy", "kt_workspace_size", "kt_trace", "kt_trace_ratio", "kt_timing_begin",
+                 "kt_timing_end"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libkt.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libkt.so is missing: build it with paper_0908_0681_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.kt_status_string.argtypes = [ctypes.c_int]
+    lib.kt_status_string.restype = ctypes.c_char_p
+    lib.kt_model_create.argtypes = [ctypes.POINTER(kt_model_params), ctypes.POINTER(vp)]
+    lib.kt_model_query.argtypes = [vp, ctypes.POINTER(kt_model_info)]
+    lib.kt_model_kept.argtypes = [vp, vp, vp, vp, vp]
+    lib.kt_model_spectrum.argtypes = [vp, vp]
+    lib.kt_model_destroy.argtypes = [vp]
+    lib.kt_model_destroy.restype = None
+    lib.kt_workspace_size.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t)]
+    lib.kt_trace.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    lib.kt_trace_ratio.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
+                                   vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    lib.kt_timing_begin.argtypes = [vp, i32]
+    lib.kt_timing_end.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+    for f in ABI_FUNCTIONS:
+        if f not in ("kt_status_string", "kt_model_destroy"):
+            getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class KtError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {kt_status_string(code)} ({code})")
+        self.code = code
+
+
+def _check(code: int, what: str):
+    if code != KT_OK:
+        raise KtError(code, what)
+
+
+def kt_status_string(code: int) -> str:
+    return load().kt_status_string(int(code)).decode()
+
+
+class KtModel:
+    """Owning handle of a kt_model* (kt_model_destroy on close/garbage collection)."""
+
+    def __init__(self, handle, params: dict):
+        self.handle = handle
+        self.params = params
+
+    def close(self):
+        if self.handle:
+            load().kt_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kt_model_create(n_orb: int, U: float, J: float, mu: float, beta: float, delta=None, Up: float = math.nan,
+                    trunc_eps: float = 1e-10, deg_tol: float = 1e-9, krylov_tol: float = 1e-12,
+                    krylov_pmax: int = 0, precision: int = KT_FP32_KRYLOV, flags: int = 0) -> KtModel:
+    lib = load()
+    d = np.zeros(n_orb, dtype=np.float64)
+    if delta is not None:
+        d[:] = np.asarray(delta, dtype=np.float64)
+    p = kt_model_params(int(n_orb), float(U), float(J), float(Up), float(mu),
+                        d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(beta), float(trunc_eps),
+                        float(deg_tol), float(krylov_tol), int(krylov_pmax), int(precision), int(flags))
+    h = ctypes.c_void_p()
+    _check(lib.kt_model_create(ctypes.byref(p), ctypes.byref(h)), "kt_model_create")
+    return KtModel(h, dict(n_orb=n_orb, U=U, J=J, mu=mu, beta=beta, delta=d.tolist(), Up=Up, trunc_eps=trunc_eps,
+                           deg_tol=deg_tol, krylov_tol=krylov_tol, krylov_pmax=krylov_pmax, precision=precision,
+                           flags=flags))
+
+
+def kt_model_query(m: KtModel) -> dict:
+    info = kt_model_info()
+    _check(load().kt_model_query(m.handle, ctypes.byref(info)), "kt_model_query")
+    return {f: getattr(info, f) for f, _ in kt_model_info._fields_}
+
+
+def kt_model_kept(m: KtModel) -> dict:
+    nk = kt_model_query(m)["n_kept"]
+    e = np.zeros(nk, np.float64); nu = np.zeros(nk, np.int32); nd = np.zeros(nk, np.int32); mk = np.zeros(nk, np.int32)
+    _check(load().kt_model_kept(m.handle, e.ctypes.data, nu.ctypes.data, nd.ctypes.data, mk.ctypes.data), "kt_model_kept")
+    return {"e_minus_e0": e, "n_up": nu, "n_dn": nd, "single_mask": mk}
+
+
+def kt_model_spectrum(m: KtModel) -> np.ndarray:
+    ns = kt_model_query(m)["n_states"]
+    e = np.zeros(ns, np.float64)
+    _check(load().kt_model_spectrum(m.handle, e.ctypes.data), "kt_model_spectrum")
+    return e
+
+
+def kt_workspace_size(m: KtModel, n: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().kt_workspace_size(m.handle, int(n), ctypes.byref(b)), "kt_workspace_size")
+    return int(b.value)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def seq_batch(offsets, tau, flavor, dagger) -> kt_seq_batch:
+    """kt_seq_batch over device tensors (int32 offsets, float64 tau, uint8 flavor/dagger)."""
+    return kt_seq_batch(int(offsets.numel() - 1), _ptr(offsets), _ptr(tau), _ptr(flavor), _ptr(dagger))
+
+
+def move_batch(kind, flavor, t_dag, t_ann, rem_idx) -> kt_move_batch:
+    return kt_move_batch(_ptr(kind), _ptr(flavor), _ptr(t_dag), _ptr(t_ann), _ptr(rem_idx))
+
+
+def kt_trace(m: KtModel, batch: kt_seq_batch, sign, logabs, status, stats=None, workspace=None, stream=None) -> None:
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load().kt_trace(m.handle, ctypes.byref(batch), _ptr(sign), _ptr(logabs), _ptr(status), _ptr(stats),
+                           _ptr(workspace), ws_bytes, _stream_handle(stream)), "kt_trace")
+
+
+def kt_trace_ratio(m: KtModel, cur: kt_seq_batch, cur_sign, cur_logabs, moves: kt_move_batch, sign, logratio, status,
+                   stats=None, workspace=None, stream=None) -> None:
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load().kt_trace_ratio(m.handle, ctypes.byref(cur), _ptr(cur_sign), _ptr(cur_logabs), ctypes.byref(moves),
+                                 _ptr(sign), _ptr(logratio), _ptr(status), _ptr(stats), _ptr(workspace), ws_bytes,
+                                 _stream_handle(stream)), "kt_trace_ratio")
+
+
+def kt_timing_begin(m: KtModel, max_launches: int) -> None:
+    _check(load().kt_timing_begin(m.handle, int(max_launches)), "kt_timing_begin")
+
+
+STAGES = ["prep", "prune", "items", "reduce"]
+
+
+def kt_timing_end(m: KtModel):
+    """(dict stage -> summed ms, number of timed calls)."""
+    ms = np.zeros(4, np.float64)
+    n = ctypes.c_int32()
+    _check(load().kt_timing_end(m.handle, ms.ctypes.data, ctypes.byref(n)), "kt_timing_end")
+    return dict(zip(STAGES, ms.tolist())), int(n.value)
+
+
+def stats_from_tensor(t) -> dict:
+    """Decode a kt_stats held in a uint64 tensor of len(STATS_FIELDS)."""
+    v = t.cpu().numpy().astype(np.uint64)
+    return {f: int(v[i]) for i, f in enumerate(STATS_FIELDS)}

@@ -1,0 +1,115 @@
+"""CPU tests of the C-ABI library: symbols, argument checks and the host-side setup.
+
+No GPU is touched: models are built with KT_HOST_ONLY (no device upload) and
+compared with the oracle's spectrum and kept multiplets.
+"""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Model, Params
+from paper_0908_0681_gb300 import kt, workloads
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "kt.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kt_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = kt.load()
+    names = declared_functions()
+    assert set(names) == set(kt.ABI_FUNCTIONS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings():
+    for code in range(9):
+        assert kt.kt_status_string(code) != "unknown status"
+    assert kt.kt_status_string(99) == "unknown status"
+
+
+def test_rejects_bad_parameters():
+    with pytest.raises(kt.KtError) as e:
+        kt.kt_model_create(8, 4.0, 1.0, 1.0, 10.0, flags=kt.KT_HOST_ONLY)
+    assert e.value.code == kt.KT_EINVAL
+    with pytest.raises(kt.KtError):
+        kt.kt_model_create(3, 4.0, 1.0, 1.0, -1.0, flags=kt.KT_HOST_ONLY)
+    with pytest.raises(kt.KtError):
+        kt.kt_model_create(3, 4.0, 1.0, 1.0, 1.0, precision=7, flags=kt.KT_HOST_ONLY)
+
+
+def host_model(spec, flags=0, trunc_eps=None):
+    return kt.kt_model_create(spec.n_orb, spec.U, spec.J, spec.mu, spec.beta, delta=spec.delta, Up=spec.up,
+                              trunc_eps=spec.trunc_eps if trunc_eps is None else trunc_eps, deg_tol=spec.deg_tol,
+                              krylov_tol=spec.krylov_tol, flags=flags | kt.KT_HOST_ONLY)
+
+
+def oracle_model(spec, trunc_eps=None, density_only=False):
+    return Model(Params(spec.n_orb, spec.U, spec.J, Up=spec.up, mu=spec.mu, delta=spec.delta, beta=spec.beta,
+                        trunc_eps=spec.trunc_eps if trunc_eps is None else trunc_eps, deg_tol=spec.deg_tol,
+                        density_only=density_only))
+
+
+@pytest.mark.parametrize("name", ["three_orbital", "five_orbital"])
+@pytest.mark.parametrize("flags", [0, kt.KT_SECTOR_BLOCKS, kt.KT_DENSITY_ONLY])
+def test_host_spectrum_and_kept_set_match_oracle(name, flags):
+    spec = workloads.WORKLOADS[name]().model
+    m = host_model(spec, flags)
+    o = oracle_model(spec, density_only=bool(flags & kt.KT_DENSITY_ONLY))
+    info = kt.kt_model_query(m)
+    assert info["n_states"] == 4 ** spec.n_orb
+    np.testing.assert_allclose(kt.kt_model_spectrum(m), o.spectrum(), atol=1e-10)
+    assert abs(info["E0"] - o.E0) < 1e-10
+    kept = kt.kt_model_kept(m)
+    assert info["n_kept"] == o.nkept
+    np.testing.assert_allclose(np.sort(kept["e_minus_e0"]), np.sort(o.kept_E - o.E0), atol=1e-10)
+    # kept blocks: (n_up, n_dn) agree with the oracle's kept sectors as a multiset
+    n1 = spec.n_orb + 1
+    ours = sorted(zip(kept["n_up"].tolist(), kept["n_dn"].tolist()))
+    theirs = sorted((int(s) // n1, int(s) % n1) for s in o.kept_sec)
+    assert ours == theirs
+
+
+def test_block_structure_counts():
+    """(n_up, n_dn, singly-occupied mask) blocks: counts follow from combinatorics."""
+    for n in (1, 2, 3, 5):
+        m = kt.kt_model_create(n, 4.0, 1.0, 2.0, 5.0, flags=kt.KT_HOST_ONLY)
+        info = kt.kt_model_query(m)
+        # a block is fixed by the mask m (which orbitals are single), the number D of doubly
+        # occupied among the rest, and n_up of the singles: sum over |m|=s of (n-s+1)(s+1)
+        expect = sum(math.comb(n, s) * (n - s + 1) * (s + 1) for s in range(n + 1))
+        assert info["n_blocks"] == expect
+        ms = kt.kt_model_create(n, 4.0, 1.0, 2.0, 5.0, flags=kt.KT_HOST_ONLY | kt.KT_SECTOR_BLOCKS)
+        assert kt.kt_model_query(ms)["n_blocks"] == (n + 1) ** 2
+        assert kt.kt_model_query(ms)["d_max"] == math.comb(n, n // 2) ** 2
+
+
+def test_five_orbital_paper_degeneracies_host():
+    """The product's own setup reproduces N_tr = 6, 31, 25 near the level crossing (Sec. IV.C)."""
+    U, J = 6.0, 1.0
+    mh = (5 - 0.5) * U - 4 * 2.5 * J
+    for dmu, ntr in zip([4.98, 5.0, 5.02], [6, 31, 25]):
+        m = kt.kt_model_create(5, U, J, mh + dmu, 50.0, trunc_eps=1.0, flags=kt.KT_HOST_ONLY)
+        assert kt.kt_model_query(m)["n_kept"] == ntr
+
+
+def test_trace_on_host_only_model_is_rejected():
+    m = kt.kt_model_create(2, 4.0, 1.0, 2.0, 5.0, flags=kt.KT_HOST_ONLY)
+    b = kt.kt_seq_batch(0, None, None, None, None)
+    code = kt.load().kt_trace(m.handle, ctypes.byref(b), 1, 1, 1, None, None, 0, None)
+    assert code == kt.KT_EINVAL
+
+
+def test_workspace_size_grows_with_walkers():
+    m = kt.kt_model_create(3, 4.0, 1.0, 5.0, 10.0, flags=kt.KT_HOST_ONLY)
+    a, b = kt.kt_workspace_size(m, 10), kt.kt_workspace_size(m, 1000)
+    assert 0 < a < b
