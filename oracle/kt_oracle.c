@@ -18,7 +18,10 @@
  *    (Householder reduction to tridiagonal form, then implicit symmetric QR
  *    with Wilkinson shifts; Golub & Van Loan, Sec. 8.3), used for the
  *    low-energy spectrum (Sec. III, setup step 1) and for exact block
- *    exponentials V diag(exp(-dtau (w - E0))) V^T.
+ *    exponentials V diag(exp(-dtau (w - E0))) V^T. Each sector is
+ *    diagonalised one connected component of H's nonzero pattern at a time
+ *    (H is exactly block diagonal in them, so this is the same exponential),
+ *    which keeps rounding from coupling subspaces that H never couples.
  *  - Truncation of the outer trace to whole multiplets with
  *    exp(-beta (E - E0)) >= trunc_eps (Sec. II, truncation type (i);
  *    Sec. III, setup step 2).
@@ -248,6 +251,72 @@ static int sym_eig(int d, real *A, real *w, real *Q) {
   return OR_OK;
 }
 
+/* Eigendecomposition of one sector matrix H (d x d) into w (ascending) and
+ * the columns of V. The sector is first split into the connected components
+ * of the graph of H's nonzero entries: H is exactly block diagonal in them,
+ * so each component is diagonalised on its own and V is zero across
+ * components. (A joint FP64 decomposition would couple the decoupled
+ * components at rounding level, and exp(dtau dE) growth over an imaginary-time
+ * path can amplify that coupling beyond the true trace.) */
+static int sector_eig(int d, const real *H, real *w, real *V) {
+  int *comp = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
+  int *stack = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
+  int *idx = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
+  real *wv = (real *)malloc(sizeof(real) * (size_t)(d > 0 ? d : 1));
+  real *A = (real *)malloc(sizeof(real) * (size_t)(d * d > 0 ? d * d : 1));
+  real *Q = (real *)malloc(sizeof(real) * (size_t)(d * d > 0 ? d * d : 1));
+  int *perm = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
+  real *Vt = (real *)malloc(sizeof(real) * (size_t)(d * d > 0 ? d * d : 1));
+  int rc = OR_OK;
+  if (!comp || !stack || !idx || !wv || !A || !Q || !perm || !Vt) rc = OR_ENOMEM;
+  int ncomp = 0, col = 0;
+  if (rc == OR_OK) {
+    for (int i = 0; i < d; ++i) comp[i] = -1;
+    for (int i = 0; i < d * d; ++i) Vt[i] = 0;
+    for (int i0 = 0; i0 < d && rc == OR_OK; ++i0) {
+      if (comp[i0] >= 0) continue;
+      /* depth-first search over nonzero couplings */
+      int top = 0, n = 0;
+      stack[top++] = i0;
+      comp[i0] = ncomp;
+      while (top > 0) {
+        int i = stack[--top];
+        idx[n++] = i;
+        for (int j = 0; j < d; ++j)
+          if (comp[j] < 0 && (H[i * d + j] != 0 || H[j * d + i] != 0)) { comp[j] = ncomp; stack[top++] = j; }
+      }
+      for (int a = 1; a < n; ++a) { /* ascending row order inside the component */
+        int t = idx[a], b = a;
+        while (b > 0 && idx[b - 1] > t) { idx[b] = idx[b - 1]; --b; }
+        idx[b] = t;
+      }
+      for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) A[a * n + b] = H[idx[a] * d + idx[b]];
+      rc = sym_eig(n, A, wv, Q);
+      for (int k = 0; k < n && rc == OR_OK; ++k, ++col) {
+        w[col] = wv[k];
+        for (int a = 0; a < n; ++a) Vt[idx[a] * d + col] = Q[a * n + k];
+      }
+      ++ncomp;
+    }
+  }
+  if (rc == OR_OK) { /* order all columns by eigenvalue */
+    for (int i = 0; i < d; ++i) perm[i] = i;
+    for (int i = 1; i < d; ++i) {
+      int t = perm[i], j = i;
+      while (j > 0 && w[perm[j - 1]] > w[t]) { perm[j] = perm[j - 1]; --j; }
+      perm[j] = t;
+    }
+    for (int j = 0; j < d; ++j) wv[j] = w[perm[j]];
+    for (int j = 0; j < d; ++j) {
+      w[j] = wv[j];
+      for (int i = 0; i < d; ++i) V[i * d + j] = Vt[i * d + perm[j]];
+    }
+  }
+  free(comp); free(stack); free(idx); free(wv); free(A); free(Q); free(perm); free(Vt);
+  return rc;
+}
+
 /* ---------------------------------------------------------------------- */
 
 void FN(model_free)(void *hm) {
@@ -321,11 +390,7 @@ int FN(model_create)(int n, double U_, double J_, double Up_, double mu_, const 
           if (apply_string(x, f2, g2, 4, &y, &sg)) H[m->rank[y] * d + i] += -J * (real)sg;
         }
     }
-    real *A = (real *)malloc(sizeof(real) * (size_t)(d * d > 0 ? d * d : 1));
-    if (!A) { FN(model_free)(m); return OR_ENOMEM; }
-    memcpy(A, H, sizeof(real) * (size_t)d * (size_t)d);
-    int rc = sym_eig(d, A, m->w[s], m->V[s]);
-    free(A);
+    int rc = sector_eig(d, H, m->w[s], m->V[s]);
     if (rc) { FN(model_free)(m); return rc; }
   }
   /* global ground energy */
@@ -430,23 +495,28 @@ static int apply_vec(const or_model *m, int s, const real *v, int f, int dag, re
   return t;
 }
 
-/* v <- exp(-dtau (H_s - wmin)) v through the eigenbasis; returns the log of
- * the scalar exp(-dtau (wmin - E0)) taken out. */
+/* v <- exp(-dtau (H_s - w_ref)) v through the eigenbasis, where w_ref is
+ * the lowest eigenvalue whose eigenvector overlaps v; returns the log of the
+ * scalar exp(-dtau (w_ref - E0)) taken out. Eigenvectors without overlap
+ * contribute exactly nothing. */
 static real propagate(const or_model *m, int s, real dtau, real *v, real *tmp) {
   int d = m->sec_dim[s];
   const real *V = m->V[s], *w = m->w[s];
-  real wmin = w[0];
+  real wref = INFINITY;
   for (int j = 0; j < d; ++j) {
     real u = 0;
     for (int i = 0; i < d; ++i) u += V[i * d + j] * v[i];
-    tmp[j] = u * exp(-dtau * (w[j] - wmin));
+    tmp[j] = u;
+    if (u != 0 && w[j] < wref) wref = w[j];
   }
+  if (!(wref < INFINITY)) return 0;
+  for (int j = 0; j < d; ++j) tmp[j] = (tmp[j] != 0) ? tmp[j] * exp(-dtau * (w[j] - wref)) : 0;
   for (int i = 0; i < d; ++i) {
     real u = 0;
     for (int j = 0; j < d; ++j) u += V[i * d + j] * tmp[j];
     v[i] = u;
   }
-  return -dtau * (wmin - m->E0);
+  return -dtau * (wref - m->E0);
 }
 
 /* One sequence. Writes sign (-1, 0, +1), log|T| and log|T~|. */
