@@ -102,6 +102,7 @@ typedef struct {
   int32_t precision;
   int32_t krylov_pmax;  /* effective Krylov cap */
   int32_t kernel_dmax;  /* row capacity of the kernel variant chosen for this model */
+  int32_t group_lanes;  /* lanes that cooperate on one (walker, kept state) item (1..32) */
   double E0;            /* global ground energy of H_loc */
   double e_kept_max;    /* highest kept energy minus E0 */
   size_t device_bytes;  /* device memory held by the model's tables */
@@ -200,6 +201,17 @@ kt_status kt_trace(kt_model *m, const kt_seq_batch *batch, int8_t *sign, double 
 kt_status kt_trace_ratio(kt_model *m, const kt_seq_batch *cur, const int8_t *cur_sign, const double *cur_logabs,
                          const kt_move_batch *moves, int8_t *sign, double *logratio, int32_t *status,
                          kt_stats *stats, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Kernel tiling: every (walker, kept state) item of the Krylov stage is
+ * processed by a group of group_lanes lanes of one warp (32 / group_lanes items
+ * per warp). kt_model_set_tiling picks one of the compiled group sizes
+ * (KT_EINVAL if it is not compiled for this model's block size).
+ * kt_autotune times kt_trace on the caller's batch (DEVICE buffers as in
+ * kt_trace) for every compiled group size, keeps the fastest and writes it to
+ * *group_lanes. It synchronises on the stream. */
+kt_status kt_model_set_tiling(kt_model *m, int32_t group_lanes);
+kt_status kt_autotune(kt_model *m, const kt_seq_batch *batch, int8_t *sign, double *logabs, int32_t *status,
+                      void *workspace, size_t workspace_bytes, void *stream, int32_t *group_lanes);
 
 /* Per-stage timing with CUDA events (profiling aid, not part of the method).
  * After kt_timing_begin(m, max_launches), each of the next max_launches trace

@@ -77,6 +77,8 @@ Workspace carve_workspace(void *base, int n_walkers, int n_kept);
 // Kernel variants compiled for sm_103a: rows per block (DMAX) and Krylov cap (PMAX).
 int kernel_dmax_for(int d_max);    // 0 if no variant fits
 int kernel_pmax_for(int kernel_dmax);
+int kernel_groups_for(int kernel_dmax, int *out, int cap);  // lane-group sizes compiled for this row capacity
+int default_group_for(int kernel_dmax);
 
 // Optional CUDA events recorded at the 5 stage boundaries of one pipeline call.
 struct StageEvents {
@@ -85,7 +87,8 @@ struct StageEvents {
 
 // Launch the full pipeline (validation/edit, pruning, Krylov items, reduction).
 // moves == nullptr: plain traces. Returns a CUDA error code (0 = success).
-int launch_pipeline(const DevModel &m, int precision, int kernel_dmax, const SeqView &seq, const MoveView *moves,
+int launch_pipeline(const DevModel &m, int precision, int kernel_dmax, int group_lanes, const SeqView &seq,
+                    const MoveView *moves,
                     const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv, int32_t *status,
                     kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing);
 

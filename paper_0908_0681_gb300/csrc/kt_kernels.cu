@@ -201,16 +201,22 @@ __global__ void prune_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, 
 
 // ---------------------------------------------------------------------------
 // 3. Krylov items
+//
+// G lanes cooperate on one (walker, kept state) item; a warp holds 32/G items.
+// Vector rows are spread over the G lanes of the item (row r on lane r % G).
+// With small G every FP64 instruction of the scalar part (tridiagonal
+// exponential, norms, log-weights) serves several items at once, which
+// matters on GB300 where an FP64 warp instruction occupies the SM's FP64 pipe
+// for 16 cycles however many lanes are active.
+// Shared memory is interleaved item-minor: element e of item g of a warp lives
+// at e * IPW + g, so lanes of different items touch consecutive words.
 // ---------------------------------------------------------------------------
-template <typename VT, int DMAX, int PMAX>
-struct WarpSmem {
-  VT q[PMAX + 1][DMAX];  // Lanczos basis; q[0] carries the state between intervals
-  VT t[DMAX];            // gather target
-  double alpha[PMAX], beta[PMAX];
-  double dd[PMAX], ee[PMAX];  // tridiagonal working copy -> Ritz values
-  double ex[PMAX];            // exp(-dtau (lambda_k - lambda_min))
-  double y[PMAX];             // exp(-dtau T) e_1 (scaled)
-  double S[PMAX][PMAX];       // S[k][i]: component i of Ritz vector k
+template <typename VT, int G, int DMAX, int PMAX>
+struct WarpTile {
+  static constexpr int IPW = 32 / G;
+  VT q[(PMAX + 1) * DMAX * IPW];  // Lanczos basis; basis vector 0 carries the state between intervals
+  double a[PMAX * IPW], b[PMAX * IPW], dd[PMAX * IPW], ee[PMAX * IPW], ex[PMAX * IPW], y[PMAX * IPW];
+  double S[PMAX * PMAX * IPW];    // S(k, i): component i of Ritz vector k
 };
 
 template <typename VT>
@@ -228,119 +234,234 @@ struct Tab<double> {
   static __device__ __forceinline__ const double *kept(const DevModel &M) { return M.kept_vec64; }
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <int G>
+__device__ __forceinline__ double gsum(double v, unsigned mask) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+template <int G>
+__device__ __forceinline__ int gsum_int(int v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
   return v;
 }
 
-// y = exp(-dt T_p) e_1 / exp(-dt lambda_min) for the symmetric tridiagonal T_p
-// (diagonal alpha[0..p), off-diagonal beta[0..p-1)). Writes y to smem and
-// returns log of the factor taken out (-dt lambda_min). p = 1 and p = 2 use
-// closed forms; p >= 3 an implicit QL iteration with shifts from the leading
-// 2x2 block, the Ritz vectors kept one component per lane. All FP64.
-// Returns false if the QL iteration did not converge.
-template <typename VT, int DMAX, int PMAX>
-__device__ bool tri_exp(WarpSmem<VT, DMAX, PMAX> &s, int p, double dt, int lane, double &logfac) {
+// Dot-product accumulator. FP32 vectors: products and sums are carried as
+// unevaluated (hi, lo) pairs of floats with error-free transformations
+// (Dekker/Knuth TwoProduct via fmaf, TwoSum), so the result has FP64-class
+// accuracy while running on the FP32 pipe; it is handed over as a double.
+// FP64 vectors: plain FP64 fused multiply-adds.
+template <typename VT>
+struct Dot;
+template <>
+struct Dot<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x, float y) {
+    const float p = x * y;
+    const float pe = fmaf(x, y, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float se = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += se + pe;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct Dot<double> {
+  double acc = 0.0;
+  __device__ __forceinline__ void add(double x, double y) { acc = fma(x, y, acc); }
+  __device__ __forceinline__ double value() const { return acc; }
+};
+
+// Rotation (c, s) with c x - s z = r, s x + c z = 0.
+__device__ __forceinline__ void givens(double x, double z, double &c, double &s, double &r) {
+  const double r2 = x * x + z * z;
+  if (r2 == 0.0) {
+    c = 1.0; s = 0.0; r = 0.0;
+    return;
+  }
+  const double inv = rsqrt(r2);
+  c = x * inv;
+  s = -z * inv;
+  r = r2 * inv;
+}
+
+// Product of positive factors kept as mantissa * 2^exponent (no log per step).
+struct LogScale {
+  double m = 1.0;
+  int e = 0;
+  __device__ __forceinline__ void mul(double f) {
+    int k;
+    m = frexp(m * f, &k);
+    e += k;
+  }
+  __device__ __forceinline__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
+};
+
+
+// Scale the item's rows v to unit norm. The rows are first multiplied by a
+// power of two that brings the largest entry to [1, 2) (exact), so the sum of
+// squares can neither underflow nor overflow; the factor actually applied is
+// multiplied into `applied` (exact bookkeeping of what was taken out).
+// Returns false if the rows are all zero.
+template <typename VT, int G, int R>
+__device__ __forceinline__ bool normalize_rows(VT (&v)[R], int gl, int dim, unsigned gm, LogScale &applied) {
+  VT m = VT(0);
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (gl + G * j < dim) m = fmax(m, fabs(v[j]));
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(gm, m, o));
+  if (!(m > VT(0))) return false;
+  const VT s1 = scalbn(VT(1), -ilogb(m));
+  VT n2 = VT(0);
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (gl + G * j < dim) {
+      const VT t = v[j] * s1;
+      n2 += t * t;
+    }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) n2 += __shfl_xor_sync(gm, n2, o);
+  const VT sc = s1 * rsqrt(n2);
+#pragma unroll
+  for (int j = 0; j < R; ++j) v[j] *= sc;
+  applied.mul((double)sc);
+  return true;
+}
+
+// y = exp(-dt T_p) e_1 / exp(-dt lambda_min) for the symmetric tridiagonal
+// T_p (diagonal a, off-diagonal b) of one item; returns -dt lambda_min in
+// logfac. p = 1, 2 in closed form; p >= 3 by implicit QL sweeps with the shift
+// from the leading 2x2 block, the Ritz vectors spread over the group's lanes.
+// All FP64. Returns false if the QL iteration did not converge.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ bool tri_exp(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
+                        double &logfac) {
+  constexpr int IPW = 32 / G;
+#define A_(k) s.a[(k) * IPW + grp]
+#define B_(k) s.b[(k) * IPW + grp]
+#define D_(k) s.dd[(k) * IPW + grp]
+#define E_(k) s.ee[(k) * IPW + grp]
+#define X_(k) s.ex[(k) * IPW + grp]
+#define Y_(k) s.y[(k) * IPW + grp]
+#define S_(k, i) s.S[((k) * PMAX + (i)) * IPW + grp]
   if (p == 1) {
-    if (lane == 0) s.y[0] = 1.0;
-    logfac = -dt * s.alpha[0];
-    __syncwarp();
+    if (gl == 0) Y_(0) = 1.0;
+    logfac = -dt * A_(0);
+    __syncwarp(gm);
     return true;
   }
   if (p == 2) {
-    const double a = s.alpha[0], c = s.alpha[1], b = s.beta[0];
+    const double a = A_(0), c = A_(1), b = B_(0);
     const double m = 0.5 * (a + c), h = 0.5 * (a - c);
-    const double r = hypot(h, b);
+    const double r = sqrt(h * h + b * b);
     const double E = exp(-2.0 * dt * r);
     const double g = (r > 0.0) ? -expm1(-2.0 * dt * r) / (2.0 * r) : dt;
-    if (lane == 0) {
-      s.y[0] = 0.5 * (1.0 + E) - g * h;
-      s.y[1] = -g * b;
+    if (gl == 0) {
+      Y_(0) = 0.5 * (1.0 + E) - g * h;
+      Y_(1) = -g * b;
     }
     logfac = -dt * (m - r);
-    __syncwarp();
+    __syncwarp(gm);
     return true;
   }
-  // ---- p >= 3: implicit QL ----
-  for (int i = lane; i < p; i += 32) {
-    s.dd[i] = s.alpha[i];
-    s.ee[i] = (i + 1 < p) ? s.beta[i] : 0.0;
-    for (int k = 0; k < p; ++k) s.S[k][i] = (i == k) ? 1.0 : 0.0;
+  for (int i = gl; i < p; i += G) {
+    D_(i) = A_(i);
+    E_(i) = (i + 1 < p) ? B_(i) : 0.0;
+    for (int k = 0; k < p; ++k) S_(k, i) = (i == k) ? 1.0 : 0.0;
   }
-  __syncwarp();
+  __syncwarp(gm);
   const double eps = 2.3e-16;
   int lo = 0, guard = 0;
   bool ok = true;
   while (lo < p - 1) {
-    // deflate from the top
-    if (fabs(s.ee[lo]) <= eps * (fabs(s.dd[lo]) + fabs(s.dd[lo + 1]))) {
+    if (fabs(E_(lo)) <= eps * (fabs(D_(lo)) + fabs(D_(lo + 1)))) {
       ++lo;
       continue;
     }
     int hi = lo + 1;
-    while (hi < p - 1 && fabs(s.ee[hi]) > eps * (fabs(s.dd[hi]) + fabs(s.dd[hi + 1]))) ++hi;
+    while (hi < p - 1 && fabs(E_(hi)) > eps * (fabs(D_(hi)) + fabs(D_(hi + 1)))) ++hi;
     if (++guard > 40 * p) {
       ok = false;
       break;
     }
-    // shift: eigenvalue of the leading 2x2 of [lo, hi] closest to dd[lo]
-    const double b0 = s.ee[lo];
-    const double dm = 0.5 * (s.dd[lo + 1] - s.dd[lo]);
-    const double mu = s.dd[lo] - b0 * b0 / (dm + copysign(hypot(dm, b0), dm));
-    double x = s.dd[hi] - mu, z = s.ee[hi - 1];
+    // shift: eigenvalue of the leading 2x2 of [lo, hi] closest to D(lo)
+    const double b0 = E_(lo);
+    const double dm = 0.5 * (D_(lo + 1) - D_(lo));
+    const double mu = D_(lo) - b0 * b0 / (dm + copysign(sqrt(dm * dm + b0 * b0), dm));
+    double x = D_(hi) - mu, z = E_(hi - 1);
     for (int k = hi; k > lo; --k) {
-      // rotation in the (k-1, k) plane that zeroes z against x
-      const double r = hypot(x, z);
-      const double c = (r == 0.0) ? 1.0 : x / r, sn = (r == 0.0) ? 0.0 : -z / r;
-      const double a11 = s.dd[k], a22 = s.dd[k - 1], a12 = s.ee[k - 1];
-      const double ek2 = (k - 1 > lo) ? s.ee[k - 2] : 0.0;
-      __syncwarp();
-      if (lane == 0) {
-        if (k < hi) s.ee[k] = r;
-        s.dd[k] = c * c * a11 - 2.0 * c * sn * a12 + sn * sn * a22;
-        s.dd[k - 1] = sn * sn * a11 + 2.0 * c * sn * a12 + c * c * a22;
-        s.ee[k - 1] = c * sn * (a11 - a22) + (c * c - sn * sn) * a12;
-        if (k - 1 > lo) s.ee[k - 2] = c * ek2;
+      double c, sn, r;
+      givens(x, z, c, sn, r);
+      const double a11 = D_(k), a22 = D_(k - 1), a12 = E_(k - 1);
+      const double ek2 = (k - 1 > lo) ? E_(k - 2) : 0.0;
+      const double cc = c * c, ss = sn * sn, cs = c * sn;
+      const double n11 = cc * a11 - 2.0 * cs * a12 + ss * a22;
+      const double n22 = ss * a11 + 2.0 * cs * a12 + cc * a22;
+      const double n12 = cs * (a11 - a22) + (cc - ss) * a12;
+      __syncwarp(gm);
+      if (gl == 0) {
+        if (k < hi) E_(k) = r;
+        D_(k) = n11;
+        D_(k - 1) = n22;
+        E_(k - 1) = n12;
+        if (k - 1 > lo) E_(k - 2) = c * ek2;
       }
-      for (int i = lane; i < p; i += 32) {
-        const double vk = s.S[k][i], vk1 = s.S[k - 1][i];
-        s.S[k][i] = c * vk - sn * vk1;
-        s.S[k - 1][i] = sn * vk + c * vk1;
+      for (int i = gl; i < p; i += G) {
+        const double vk = S_(k, i), vk1 = S_(k - 1, i);
+        S_(k, i) = c * vk - sn * vk1;
+        S_(k - 1, i) = sn * vk + c * vk1;
       }
-      __syncwarp();
+      __syncwarp(gm);
       if (k - 1 > lo) {
-        x = s.ee[k - 1];
+        x = n12;
         z = -sn * ek2;
       }
     }
   }
-  __syncwarp();
-  double lmin = s.dd[0];
-  for (int k = 1; k < p; ++k) lmin = fmin(lmin, s.dd[k]);
-  for (int k = lane; k < p; k += 32) s.ex[k] = exp(-dt * (s.dd[k] - lmin)) * s.S[k][0];
-  __syncwarp();
-  for (int i = lane; i < p; i += 32) {
+  __syncwarp(gm);
+  double lmin = D_(0);
+  for (int k = 1; k < p; ++k) lmin = fmin(lmin, D_(k));
+  for (int k = gl; k < p; k += G) X_(k) = exp(-dt * (D_(k) - lmin)) * S_(k, 0);
+  __syncwarp(gm);
+  for (int i = gl; i < p; i += G) {
     double acc = 0.0;
-    for (int k = 0; k < p; ++k) acc += s.S[k][i] * s.ex[k];
-    s.y[i] = acc;
+    for (int k = 0; k < p; ++k) acc = fma(S_(k, i), X_(k), acc);
+    Y_(i) = acc;
   }
   logfac = -dt * lmin;
-  __syncwarp();
+  __syncwarp(gm);
   return ok;
+#undef A_
+#undef B_
+#undef D_
+#undef E_
+#undef X_
+#undef Y_
+#undef S_
 }
 
 struct ItemAcc {
   unsigned long long ops, intervals, iters, pmax, noconv, flops_vec, flops_tri, bytes_apply;
 };
 
-template <typename VT, int DMAX, int PMAX>
+template <typename VT, int G, int DMAX, int PMAX>
 __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, Workspace ws,
-                                                    kt_stats *stats, int warps_per_block) {
+                                                    kt_stats *stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int R = (DMAX + 31) / 32;  // rows per lane
+  constexpr int IPW = 32 / G;
+  constexpr int R = (DMAX + G - 1) / G;  // rows per lane
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  WarpSmem<VT, DMAX, PMAX> &s = reinterpret_cast<WarpSmem<VT, DMAX, PMAX> *>(smem_raw)[wib];
+  const int grp = lane / G, gl = lane % G;
+  const unsigned gm = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
+  WarpTile<VT, G, DMAX, PMAX> &s = reinterpret_cast<WarpTile<VT, G, DMAX, PMAX> *>(smem_raw)[wib];
+#define Q_(j, r) s.q[((j) * DMAX + (r)) * IPW + grp]
+#define A_(k) s.a[(k) * IPW + grp]
+#define B_(k) s.b[(k) * IPW + grp]
+#define Y_(k) s.y[(k) * IPW + grp]
   const VT *__restrict__ tdiag = Tab<VT>::diag(M);
   const VT *__restrict__ tval = Tab<VT>::val(M);
   const VT *__restrict__ tkept = Tab<VT>::kept(M);
@@ -349,8 +470,8 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
 
   for (;;) {
     int it = 0;
-    if (lane == 0) it = atomicAdd(&ws.counters[1], 1);
-    it = __shfl_sync(FULL, it, 0);
+    if (gl == 0) it = atomicAdd(&ws.counters[1], 1);
+    it = __shfl_sync(gm, it, grp * G);
     if (it >= n_alive) break;
     const int item = ws.worklist[it];
     const int w = item / nk, q = item - w * nk;
@@ -364,20 +485,21 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
     ItemAcc acc{};
     int status = KT_OK;
     bool vanished = false;
-    double L = 0.0;
+    double Ladd = 0.0;  // additive part of log|contribution|
+    LogScale Linv;      // product of the normalisation factors applied (their inverse was taken out)
     int sgn = 1;
 
     if (Kn == 0) {
-      L = -M.beta * Ek;
+      Ladd = -M.beta * Ek;
     } else {
 #pragma unroll
       for (int j = 0; j < R; ++j) {
-        const int r = lane + 32 * j;
-        if (r < dim) s.q[0][r] = __ldg(tkept + koff + r);
+        const int r = gl + G * j;
+        if (r < dim) Q_(0, r) = __ldg(tkept + koff + r);
       }
-      __syncwarp();
+      __syncwarp(gm);
       Op op = cur.get(0);
-      L = -op.t * Ek;
+      Ladd = -op.t * Ek;
       for (int i = 0; i < Kn; ++i) {
         // ---- step 4: apply c_f / c_f^+ (gather with Jordan-Wigner sign) ----
         const int b2 = __ldg(M.blk_target + ((size_t)b * nf + op.f) * 2 + op.dag);
@@ -386,42 +508,38 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
           break;
         }
         const int off2 = __ldg(M.blk_off + b2), dim2 = __ldg(M.blk_dim + b2);
-        double nrm2 = 0.0;
         VT tv[R];
+        VT n2 = VT(0);
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          const int r = lane + 32 * j;
+          const int r = gl + G * j;
           VT v = VT(0);
           if (r < dim2) {
             const int g = off2 + r;
             const int x = __ldg(M.st_bits + g);
             if (((x >> op.f) & 1) == op.dag) {
               const unsigned pe = __ldg(M.partner + (size_t)g * nf + op.f);
-              v = s.q[0][pe & 0x7fffu];
+              v = Q_(0, pe & 0x7fffu);
               if (pe & 0x8000u) v = -v;
             }
-            nrm2 += (double)v * (double)v;
           }
           tv[j] = v;
         }
-        nrm2 = warp_sum(nrm2);
+        (void)n2;
         acc.ops += 1;
         acc.flops_vec += 3ull * dim2;
         acc.bytes_apply += (unsigned long long)dim2 * (2 * sizeof(VT) + 4);
-        if (!(nrm2 > 0.0)) {
+        if (!normalize_rows<VT, G, R>(tv, gl, dim2, gm, Linv)) {
           vanished = true;
           break;
         }
-        const double nrm = sqrt(nrm2);
-        L += log(nrm);
-        const VT inv = VT(1.0 / nrm);
-        __syncwarp();
+        __syncwarp(gm);
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          const int r = lane + 32 * j;
-          if (r < dim2) s.q[0][r] = tv[j] * inv;
+          const int r = gl + G * j;
+          if (r < dim2) Q_(0, r) = tv[j];
         }
-        __syncwarp();
+        __syncwarp(gm);
         b = b2;
         dim = dim2;
         if (i + 1 >= Kn) break;
@@ -429,7 +547,7 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
         const double dt = nx.t - op.t;
         op = nx;
         if (!(dt > 0.0)) continue;
-        // ---- step 5: Lanczos approximation of exp(-dt (H_b - E0)) q0 ----
+        // ---- step 5: Lanczos approximation of exp(-dt (H_b - E0)) q_0 ----
         const int off = __ldg(M.blk_off + b), wid = __ldg(M.blk_nnz + b), ell = __ldg(M.blk_ell + b);
         const double shift = __ldg(M.blk_shift + b);
         const double brk = M.brk_rel * fmax(__ldg(M.blk_norm + b), 1e-300);
@@ -437,152 +555,142 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
         VT qc[R], qp[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          const int r = lane + 32 * j;
-          qc[j] = (r < dim) ? s.q[0][r] : VT(0);
+          const int r = gl + G * j;
+          qc[j] = (r < dim) ? Q_(0, r) : VT(0);
           qp[j] = VT(0);
         }
         double bprev = 0.0, logfac = 0.0;
         int p = 0;
         bool conv = false;
-        unsigned long long nnz_row_sum = 0;
         for (int jj = 0; jj < pcap; ++jj) {
-          // w = (H_b - s_b) q_jj
           VT wv[R];
-          double al = 0.0;
+          Dot<VT> da;
 #pragma unroll
           for (int j = 0; j < R; ++j) {
-            const int r = lane + 32 * j;
+            const int r = gl + G * j;
             VT a = VT(0);
             if (r < dim) {
               a = __ldg(tdiag + off + r) * qc[j];
               for (int k = 0; k < wid; ++k) {
                 const int col = __ldg(M.ell_col + ell + k * dim + r);
-                if (col >= 0) a += __ldg(tval + ell + k * dim + r) * s.q[jj][col];
+                if (col >= 0) a += __ldg(tval + ell + k * dim + r) * Q_(jj, col);
               }
-              al += (double)a * (double)qc[j];
+              da.add(a, qc[j]);
             }
             wv[j] = a;
           }
-          al = warp_sum(al);
-          double bb = 0.0;
+          const double al = gsum<G>(da.value(), gm);
           const VT alv = VT(al), bpv = VT(bprev);
+          Dot<VT> db;
 #pragma unroll
           for (int j = 0; j < R; ++j) {
-            const int r = lane + 32 * j;
+            const int r = gl + G * j;
             if (r < dim) {
               wv[j] = wv[j] - alv * qc[j] - bpv * qp[j];
-              bb += (double)wv[j] * (double)wv[j];
+              db.add(wv[j], wv[j]);
             }
           }
-          bb = sqrt(warp_sum(bb));
+          const double bb = sqrt(gsum<G>(db.value(), gm));
           p = jj + 1;
-          if (lane == 0) {
-            s.alpha[jj] = al;
-            s.beta[jj] = bb;
+          if (gl == 0) {
+            A_(jj) = al;
+            B_(jj) = bb;
           }
-          __syncwarp();
+          __syncwarp(gm);
           const bool exact = (p == dim) || !(bb > brk);
-          const bool okq = tri_exp(s, p, dt, lane, logfac);
-          acc.flops_tri += (p <= 2) ? 30ull : (unsigned long long)(12 * p * p * p + 40 * p);
+          const bool okq = tri_exp(s, grp, gl, gm, p, dt, logfac);
+          if (stats) acc.flops_tri += (p <= 2) ? 30ull : (unsigned long long)(12 * p * p * p + 40 * p);
           if (!okq) status = KT_ENUMERIC;
           if (exact) {
             conv = true;
             break;
           }
           double yn = 0.0;
-          for (int k = lane; k < p; k += 32) yn += s.y[k] * s.y[k];
-          yn = sqrt(warp_sum(yn));
-          const double err = bb * fabs(s.y[p - 1]);
+          for (int k = gl; k < p; k += G) yn = fma(Y_(k), Y_(k), yn);
+          yn = sqrt(gsum<G>(yn, gm));
+          const double err = bb * fabs(Y_(p - 1));
           if (err <= M.tol * yn) {
             conv = true;
             break;
           }
           if (p == pcap) break;
-          // q_{jj+1} = w / beta
-          const VT ib = VT(1.0 / bb);
+          const VT ib = VT(1) / VT(bb);
 #pragma unroll
           for (int j = 0; j < R; ++j) {
-            const int r = lane + 32 * j;
+            const int r = gl + G * j;
             qp[j] = qc[j];
             qc[j] = wv[j] * ib;
-            if (r < dim) s.q[jj + 1][r] = qc[j];
+            if (r < dim) Q_(jj + 1, r) = qc[j];
           }
           bprev = bb;
-          __syncwarp();
+          __syncwarp(gm);
         }
-        (void)nnz_row_sum;
         if (!conv) {
           acc.noconv += 1;
           if (status == KT_OK) status = KT_ENOCONV;
         }
-        // v = sum_j y_j q_j, renormalised; log of everything taken out goes to L
-        double vn = 0.0;
+        // v = sum_j y_j q_j, renormalised; what is taken out goes to the log-weight
         VT vv[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          const int r = lane + 32 * j;
+          const int r = gl + G * j;
           VT a = VT(0);
           if (r < dim)
-            for (int k = 0; k < p; ++k) a += VT(s.y[k]) * s.q[k][r];
+            for (int k = 0; k < p; ++k) a += VT(Y_(k)) * Q_(k, r);
           vv[j] = a;
-          vn += (double)a * (double)a;
         }
-        vn = warp_sum(vn);
-        if (!(vn > 0.0)) {
+        if (!normalize_rows<VT, G, R>(vv, gl, dim, gm, Linv)) {
           vanished = true;
           break;
         }
-        vn = sqrt(vn);
-        L += logfac + log(vn) - dt * (shift - M.E0);
-        const VT ivn = VT(1.0 / vn);
-        __syncwarp();
+        Ladd += logfac - dt * (shift - M.E0);
+        __syncwarp(gm);
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          const int r = lane + 32 * j;
-          if (r < dim) s.q[0][r] = vv[j] * ivn;
+          const int r = gl + G * j;
+          if (r < dim) Q_(0, r) = vv[j];
         }
-        __syncwarp();
-        // algorithmic flops of this propagation
-        int nnz_blk = 0;
-        {
-          // nnz of the block (diagonal + stored off-diagonals), counted from the ELL columns
+        __syncwarp(gm);
+        acc.intervals += 1;
+        acc.iters += p;
+        acc.pmax = acc.pmax > (unsigned long long)p ? acc.pmax : (unsigned long long)p;
+        if (stats) {
           int cnt = 0;
+#pragma unroll
           for (int j = 0; j < R; ++j) {
-            const int r = lane + 32 * j;
+            const int r = gl + G * j;
             if (r < dim) {
               cnt += 1;
               for (int k = 0; k < wid; ++k) cnt += (__ldg(M.ell_col + ell + k * dim + r) >= 0);
             }
           }
-          nnz_blk = (int)warp_sum((double)cnt);
+          const int nnz_blk = gsum_int<G>(cnt, gm);
+          acc.flops_vec += (unsigned long long)p * (2ull * nnz_blk + 9ull * dim) + 2ull * p * dim + 3ull * dim;
         }
-        acc.intervals += 1;
-        acc.iters += p;
-        acc.pmax = acc.pmax > (unsigned long long)p ? acc.pmax : (unsigned long long)p;
-        acc.flops_vec += (unsigned long long)p * (2ull * nnz_blk + 9ull * dim) + 2ull * p * dim + 3ull * dim;
       }
     }
+    double L = Ladd;
     if (!vanished && Kn > 0) {
       if (b != b_kept) {
         vanished = true;
       } else {
-        double ov = 0.0;
+        Dot<VT> dov;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-          const int r = lane + 32 * j;
-          if (r < dim) ov += (double)__ldg(tkept + koff + r) * (double)s.q[0][r];
+          const int r = gl + G * j;
+          if (r < dim) dov.add(__ldg(tkept + koff + r), Q_(0, r));
         }
-        ov = warp_sum(ov);
+        const double ov = gsum<G>(dov.value(), gm);
         if (ov == 0.0) {
           vanished = true;
         } else {
           sgn = ov > 0.0 ? 1 : -1;
-          L += log(fabs(ov)) - (M.beta - cur.get(Kn - 1).t) * Ek;
+          L += -Linv.log_value() + log(fabs(ov)) - (M.beta - cur.get(Kn - 1).t) * Ek;
         }
       }
     }
     if (!vanished && !isfinite(L)) status = KT_ENUMERIC;
-    if (lane == 0) {
+    if (gl == 0) {
       ws.item_sign[item] = vanished ? 0 : (int8_t)sgn;
       ws.item_log[item] = vanished ? -INFINITY : L;
       ws.item_status[item] = status;
@@ -598,8 +706,12 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
         stat_add(&stats->bytes_apply, acc.bytes_apply);
       }
     }
-    __syncwarp();
+    __syncwarp(gm);
   }
+#undef Q_
+#undef A_
+#undef B_
+#undef Y_
 }
 
 // ---------------------------------------------------------------------------
@@ -651,51 +763,83 @@ __global__ void reduce_kernel(DevModel M, int n, int has_moves, const int8_t *cu
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-template <typename VT, int DMAX, int PMAX>
+template <typename VT, int G, int DMAX, int PMAX>
 int launch_items(const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves, const Workspace &ws,
                  kt_stats *stats, cudaStream_t st) {
-  using Sm = WarpSmem<VT, DMAX, PMAX>;
+  using Tile = WarpTile<VT, G, DMAX, PMAX>;
   static int cached_grid = 0, cached_wpb = 0;
   if (cached_grid == 0) {
-    int wpb = (int)((48 * 1024) / sizeof(Sm));
+    int wpb = (int)((200 * 1024) / sizeof(Tile));
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
-    const size_t smem = (size_t)wpb * sizeof(Sm);
+    const size_t smem = (size_t)wpb * sizeof(Tile);
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(items_kernel<VT, DMAX, PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(items_kernel<VT, G, DMAX, PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, items_kernel<VT, DMAX, PMAX>, wpb * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, items_kernel<VT, G, DMAX, PMAX>, wpb * 32, smem);
     if (per_sm < 1) per_sm = 1;
     cached_wpb = wpb;
     cached_grid = sms * per_sm;
   }
-  const size_t smem = (size_t)cached_wpb * sizeof(Sm);
-  items_kernel<VT, DMAX, PMAX><<<cached_grid, cached_wpb * 32, smem, st>>>(M, S, mv, has_moves, ws, stats, cached_wpb);
+  const size_t smem = (size_t)cached_wpb * sizeof(Tile);
+  items_kernel<VT, G, DMAX, PMAX><<<cached_grid, cached_wpb * 32, smem, st>>>(M, S, mv, has_moves, ws, stats);
   return (int)cudaGetLastError();
+}
+
+// Variant table: row capacity DMAX, Krylov cap PMAX and the lane-group sizes G
+// compiled for it.
+#define KT_FOR_VARIANTS(X)                                                                                 \
+  X(10, 10, 1) X(10, 10, 2) X(10, 10, 4) X(10, 10, 8) X(10, 10, 16) X(10, 10, 32) X(36, 24, 4) X(36, 24, 8) \
+      X(36, 24, 16) X(36, 24, 32) X(128, 40, 32)
+
+template <typename VT>
+int dispatch_items(int kd, int G, const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves,
+                   const Workspace &ws, kt_stats *stats, cudaStream_t st) {
+#define KT_CASE(D, P, GG) \
+  if (kd == D && G == GG) return launch_items<VT, GG, D, P>(M, S, mv, has_moves, ws, stats, st);
+  KT_FOR_VARIANTS(KT_CASE)
+#undef KT_CASE
+  return (int)cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 int kernel_dmax_for(int d_max) {
-  if (d_max <= 16) return 16;
-  if (d_max <= 32) return 32;
-  if (d_max <= 64) return 64;
+  if (d_max <= 10) return 10;
+  if (d_max <= 36) return 36;
   if (d_max <= 128) return 128;
   return 0;
 }
 
 int kernel_pmax_for(int kd) {
   switch (kd) {
-    case 16: return 16;
-    case 32: return 32;
-    case 64: return 32;
+    case 10: return 10;
+    case 36: return 24;
     case 128: return 40;
   }
   return 0;
 }
 
-int launch_pipeline(const DevModel &M, int precision, int kd, const SeqView &S, const MoveView *moves,
+int kernel_groups_for(int kd, int *out, int cap) {
+  int n = 0;
+#define KT_LIST(D, P, GG) \
+  if (kd == D && n < cap) out[n++] = GG;
+  KT_FOR_VARIANTS(KT_LIST)
+#undef KT_LIST
+  return n;
+}
+
+int default_group_for(int kd) {
+  switch (kd) {
+    case 10: return 4;
+    case 36: return 8;
+    case 128: return 32;
+  }
+  return 32;
+}
+
+int launch_pipeline(const DevModel &M, int precision, int kd, int G, const SeqView &S, const MoveView *moves,
                     const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv, int32_t *status,
                     kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing) {
   cudaStream_t st = (cudaStream_t)stream;
@@ -715,23 +859,8 @@ int launch_pipeline(const DevModel &M, int precision, int kd, const SeqView &S, 
   int rc = (int)cudaGetLastError();
   if (rc) return rc;
   if (items > 0) {
-    if (precision == KT_FP64) {
-      switch (kd) {
-        case 16: rc = launch_items<double, 16, 16>(M, S, mv, has_moves, ws, stats, st); break;
-        case 32: rc = launch_items<double, 32, 32>(M, S, mv, has_moves, ws, stats, st); break;
-        case 64: rc = launch_items<double, 64, 32>(M, S, mv, has_moves, ws, stats, st); break;
-        case 128: rc = launch_items<double, 128, 40>(M, S, mv, has_moves, ws, stats, st); break;
-        default: return (int)cudaErrorInvalidValue;
-      }
-    } else {
-      switch (kd) {
-        case 16: rc = launch_items<float, 16, 16>(M, S, mv, has_moves, ws, stats, st); break;
-        case 32: rc = launch_items<float, 32, 32>(M, S, mv, has_moves, ws, stats, st); break;
-        case 64: rc = launch_items<float, 64, 32>(M, S, mv, has_moves, ws, stats, st); break;
-        case 128: rc = launch_items<float, 128, 40>(M, S, mv, has_moves, ws, stats, st); break;
-        default: return (int)cudaErrorInvalidValue;
-      }
-    }
+    rc = (precision == KT_FP64) ? dispatch_items<double>(kd, G, M, S, mv, has_moves, ws, stats, st)
+                                : dispatch_items<float>(kd, G, M, S, mv, has_moves, ws, stats, st);
     if (rc) return rc;
   }
   mark(3);

@@ -96,6 +96,7 @@ struct kt_model {
   void *dev_mem = nullptr;
   size_t dev_bytes = 0;
   int kernel_dmax = 0;
+  int group_lanes = 32;
   int nnz_max = 0;
   // host copies for kt_model_kept
   std::vector<double> kept_e;
@@ -271,6 +272,7 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
 
   M->kernel_dmax = kt::kernel_dmax_for(d_max);
   if (M->kernel_dmax == 0) { delete M; return KT_EUNSUPPORTED; }
+  M->group_lanes = kt::default_group_for(M->kernel_dmax);
 
   // ---- per block: dense H, Jacobi spectrum, shift, ELL rows ----
   std::vector<std::vector<double>> evals(B), evecs(B);
@@ -461,7 +463,7 @@ kt_status kt_model_query(const kt_model *m, kt_model_info *o) {
   o->n_orb = m->dev.n_orb; o->n_flavors = m->dev.nf; o->n_states = m->dev.n_states;
   o->n_blocks = m->dev.n_blocks; o->d_max = m->dev.d_max; o->nnz_max = m->nnz_max;
   o->n_kept = m->dev.n_kept; o->precision = m->params.precision; o->krylov_pmax = m->dev.pmax;
-  o->kernel_dmax = m->kernel_dmax; o->E0 = m->dev.E0; o->e_kept_max = m->e_kept_max;
+  o->kernel_dmax = m->kernel_dmax; o->group_lanes = m->group_lanes; o->E0 = m->dev.E0; o->e_kept_max = m->e_kept_max;
   o->device_bytes = m->dev_bytes;
   return KT_OK;
 }
@@ -511,9 +513,59 @@ static kt_status run(kt_model *m, const kt_seq_batch *b, const kt_move_batch *mv
   kt::Workspace w = kt::carve_workspace(ws, b->n, m->dev.n_kept);
   const kt::StageEvents *tev = nullptr;
   if (m->timing_on && m->timing_used < (int)m->timing.size()) tev = &m->timing[m->timing_used++];
-  const int rc = kt::launch_pipeline(m->dev, m->params.precision, m->kernel_dmax, sv, mv ? &mvv : nullptr, cur_sign,
-                                     cur_logabs, sign, logv, status, stats, w, stream, tev);
+  const int rc = kt::launch_pipeline(m->dev, m->params.precision, m->kernel_dmax, m->group_lanes, sv,
+                                     mv ? &mvv : nullptr, cur_sign, cur_logabs, sign, logv, status, stats, w, stream, tev);
   return rc == 0 ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_model_set_tiling(kt_model *m, int32_t g) {
+  if (!m) return KT_EINVAL;
+  int gs[8];
+  const int n = kt::kernel_groups_for(m->kernel_dmax, gs, 8);
+  for (int i = 0; i < n; ++i)
+    if (gs[i] == g) {
+      m->group_lanes = g;
+      return KT_OK;
+    }
+  return KT_EINVAL;
+}
+
+kt_status kt_autotune(kt_model *m, const kt_seq_batch *b, int8_t *sign, double *logabs, int32_t *status, void *ws,
+                      size_t ws_bytes, void *stream, int32_t *chosen) {
+  if (!m || !b || m->host_only || !chosen) return KT_EINVAL;
+  int gs[8];
+  const int n = kt::kernel_groups_for(m->kernel_dmax, gs, 8);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return KT_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return KT_ECUDA; }
+  const int keep = m->group_lanes;
+  const bool timing = m->timing_on;
+  m->timing_on = false;
+  float best = 1e30f;
+  int best_g = keep;
+  kt_status rc = KT_OK;
+  for (int i = 0; i < n && rc == KT_OK; ++i) {
+    m->group_lanes = gs[i];
+    rc = kt_trace(m, b, sign, logabs, status, nullptr, ws, ws_bytes, stream);  // warm-up (also caches launch shape)
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3 && rc == KT_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = kt_trace(m, b, sign, logabs, status, nullptr, ws, ws_bytes, stream);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = KT_ECUDA; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin = ms < tmin ? ms : tmin;
+    }
+    if (rc == KT_OK && tmin < best) { best = tmin; best_g = gs[i]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->timing_on = timing;
+  m->group_lanes = (rc == KT_OK) ? best_g : keep;
+  *chosen = m->group_lanes;
+  return rc;
 }
 
 kt_status kt_timing_begin(kt_model *m, int32_t max_launches) {

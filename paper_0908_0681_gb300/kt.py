@@ -32,7 +32,8 @@ class kt_model_info(ctypes.Structure):
     _fields_ = [("n_orb", ctypes.c_int32), ("n_flavors", ctypes.c_int32), ("n_states", ctypes.c_int32),
                 ("n_blocks", ctypes.c_int32), ("d_max", ctypes.c_int32), ("nnz_max", ctypes.c_int32),
                 ("n_kept", ctypes.c_int32), ("precision", ctypes.c_int32), ("krylov_pmax", ctypes.c_int32),
-                ("kernel_dmax", ctypes.c_int32), ("E0", ctypes.c_double), ("e_kept_max", ctypes.c_double),
+                ("kernel_dmax", ctypes.c_int32), ("group_lanes", ctypes.c_int32), ("E0", ctypes.c_double),
+                ("e_kept_max", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t)]
 
 
@@ -57,7 +58,7 @@ class kt_move_batch(ctypes.Structure):
 # Every function the header declares (checked by the CPU test suite).
 ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_model_kept", "kt_model_spectrum",
                  "kt_model_destroy", "kt_workspace_size", "kt_trace", "kt_trace_ratio", "kt_timing_begin",
-                 "kt_timing_end"]
+                 "kt_timing_end", "kt_model_set_tiling", "kt_autotune"]
 
 _lib = None
 
@@ -89,6 +90,9 @@ def load():
     lib.kt_trace_ratio.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
                                    vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.kt_timing_begin.argtypes = [vp, i32]
+    lib.kt_model_set_tiling.argtypes = [vp, i32]
+    lib.kt_autotune.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, vp, vp, ctypes.c_size_t, vp,
+                                ctypes.POINTER(ctypes.c_int32)]
     lib.kt_timing_end.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
     for f in ABI_FUNCTIONS:
         if f not in ("kt_status_string", "kt_model_destroy"):
@@ -206,6 +210,18 @@ def kt_trace_ratio(m: KtModel, cur: kt_seq_batch, cur_sign, cur_logabs, moves: k
     _check(load().kt_trace_ratio(m.handle, ctypes.byref(cur), _ptr(cur_sign), _ptr(cur_logabs), ctypes.byref(moves),
                                  _ptr(sign), _ptr(logratio), _ptr(status), _ptr(stats), _ptr(workspace), ws_bytes,
                                  _stream_handle(stream)), "kt_trace_ratio")
+
+
+def kt_model_set_tiling(m: KtModel, group_lanes: int) -> None:
+    _check(load().kt_model_set_tiling(m.handle, int(group_lanes)), "kt_model_set_tiling")
+
+
+def kt_autotune(m: KtModel, batch: kt_seq_batch, sign, logabs, status, workspace, stream=None) -> int:
+    g = ctypes.c_int32()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(load().kt_autotune(m.handle, ctypes.byref(batch), _ptr(sign), _ptr(logabs), _ptr(status), _ptr(workspace),
+                              ws_bytes, _stream_handle(stream), ctypes.byref(g)), "kt_autotune")
+    return int(g.value)
 
 
 def kt_timing_begin(m: KtModel, max_launches: int) -> None:
