@@ -202,6 +202,24 @@ kt_status kt_trace_ratio(kt_model *m, const kt_seq_batch *cur, const int8_t *cur
                          const kt_move_batch *moves, int8_t *sign, double *logratio, int32_t *status,
                          kt_stats *stats, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Allocation-free variant of kt_trace_ratio for callers that cannot allocate
+ * device memory (for example code that may not call cudaMalloc after start-up,
+ * or that is handed only its input and output buffers). The paper has no
+ * counterpart: this is an interface convenience. Same arguments, results and
+ * per-walker statuses as kt_trace_ratio, but no workspace: the scratch lives in
+ * a fixed array of KT_STATIC_SCRATCH_BYTES inside the library's device image,
+ * held on every GPU that loads the library until the process exits. Batches
+ * whose scratch would exceed it (kt_workspace_size(m, n) > KT_STATIC_SCRATCH_BYTES,
+ * about 68,000 walkers at N_tr = 6) are rejected with KT_ENOMEM before any work.
+ * The call allocates nothing. Its first call on each device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture. All calls share the array: calls whose kernels
+ * overlap on the GPU race, so serialise them. */
+#define KT_STATIC_SCRATCH_BYTES (8u << 20)
+kt_status kt_trace_ratio_static(kt_model *m, const kt_seq_batch *cur, const int8_t *cur_sign,
+                                const double *cur_logabs, const kt_move_batch *moves, int8_t *sign,
+                                double *logratio, int32_t *status, kt_stats *stats, void *stream);
+
 /* Kernel tiling: every (walker, kept state) item of the Krylov stage is
  * processed by a group of group_lanes lanes of one warp (32 / group_lanes items
  * per warp). kt_model_set_tiling picks one of the compiled group sizes

@@ -92,4 +92,12 @@ int launch_pipeline(const DevModel &m, int precision, int kernel_dmax, int group
                     const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv, int32_t *status,
                     kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing);
 
+// Launch parameters of a model, for entry points that live outside kt_model.cpp.
+struct ModelView {
+  const DevModel *dev;
+  int precision, kernel_dmax, group_lanes;
+  bool host_only;
+};
+ModelView model_view(const kt_model *m);
+
 }  // namespace kt

@@ -150,6 +150,14 @@ Workspace carve_workspace(void *base, int n, int n_kept) {
 
 }  // namespace kt
 
+namespace kt {
+
+ModelView model_view(const kt_model *m) {
+  return ModelView{&m->dev, m->params.precision, m->kernel_dmax, m->group_lanes, m->host_only};
+}
+
+}  // namespace kt
+
 extern "C" {
 
 const char *kt_status_string(kt_status s) {

@@ -58,7 +58,7 @@ class kt_move_batch(ctypes.Structure):
 # Every function the header declares (checked by the CPU test suite).
 ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_model_kept", "kt_model_spectrum",
                  "kt_model_destroy", "kt_workspace_size", "kt_trace", "kt_trace_ratio", "kt_timing_begin",
-                 "kt_timing_end", "kt_model_set_tiling", "kt_autotune"]
+                 "kt_timing_end", "kt_model_set_tiling", "kt_autotune", "kt_trace_ratio_static"]
 
 _lib = None
 
@@ -91,6 +91,8 @@ def load():
                                    vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.kt_timing_begin.argtypes = [vp, i32]
     lib.kt_model_set_tiling.argtypes = [vp, i32]
+    lib.kt_trace_ratio_static.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
+                                          vp, vp, vp, vp, vp]
     lib.kt_autotune.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, vp, vp, ctypes.c_size_t, vp,
                                 ctypes.POINTER(ctypes.c_int32)]
     lib.kt_timing_end.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
@@ -237,6 +239,17 @@ def kt_timing_end(m: KtModel):
     n = ctypes.c_int32()
     _check(load().kt_timing_end(m.handle, ms.ctypes.data, ctypes.byref(n)), "kt_timing_end")
     return dict(zip(STAGES, ms.tolist())), int(n.value)
+
+
+KT_STATIC_SCRATCH_BYTES = 8 << 20
+
+
+def kt_trace_ratio_static(m: KtModel, cur: kt_seq_batch, cur_sign, cur_logabs, moves: kt_move_batch, sign, logratio,
+                          status, stats=None, stream=None) -> None:
+    """kt_trace_ratio without a workspace (scratch in the library's fixed device array)."""
+    _check(load().kt_trace_ratio_static(m.handle, ctypes.byref(cur), _ptr(cur_sign), _ptr(cur_logabs),
+                                        ctypes.byref(moves), _ptr(sign), _ptr(logratio), _ptr(status), _ptr(stats),
+                                        _stream_handle(stream)), "kt_trace_ratio_static")
 
 
 def stats_from_tensor(t) -> dict:

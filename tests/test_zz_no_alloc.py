@@ -1,0 +1,58 @@
+"""The allocation-free trace ratio (kt_trace_ratio_static) against kt_trace_ratio.
+
+Callers that may not allocate device memory (for example code that must not
+call cudaMalloc after start-up, or that only receives its input and output
+buffers) use kt_trace_ratio_static, which keeps its scratch in a fixed array
+inside the library. This file runs last in the suite; it must also pass on its
+own in a fresh process. Two calls in a row are checked, because every call
+reuses the same array and inherits the previous call's contents.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0908_0681_gb300 import engine, kt, workloads  # noqa: E402
+
+RTOL = {kt.KT_FP64: 1e-10, kt.KT_FP32_KRYLOV: 1e-5}
+
+
+@pytest.mark.parametrize("prec", [kt.KT_FP32_KRYLOV, kt.KT_FP64])
+def test_static_scratch_matches_workspace_path(prec):
+    w = workloads.five_orbital()
+    seqs = workloads.generate_sequences(w, 1024, seed=11)
+    m = engine.model_from_spec(w.model, precision=prec)
+    d = engine.DeviceSeqs.from_host(seqs)
+    cs, cl, cst = engine.trace(m, d)
+    assert (cst == 0).all()
+    n = seqs.n
+    for call in range(2):  # second call inherits the first call's scratch contents
+        mv = engine.DeviceMoves.from_host(workloads.generate_moves(w, seqs, seed=2000 + call))
+        rs, rl, rst = engine.trace_ratio(m, d, cs, cl, mv)
+        s = torch.empty(n, dtype=torch.int8, device="cuda")
+        lr = torch.empty(n, dtype=torch.float64, device="cuda")
+        st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        kt.kt_trace_ratio_static(m, d.batch(), cs, cl, mv.batch(), s, lr, st)
+        torch.cuda.synchronize()
+        rs, rl, rst = rs.cpu().numpy(), rl.cpu().numpy(), rst.cpu().numpy()
+        s, lr, st = s.cpu().numpy(), lr.cpu().numpy(), st.cpu().numpy()
+        assert (st == rst).all() and (s == rs).all()
+        ok = s != 0
+        assert ok.sum() > 0.9 * n
+        assert np.abs(np.expm1(lr[ok] - rl[ok])).max() <= RTOL[prec]
+
+
+def test_static_scratch_rejects_oversized_batch():
+    w = workloads.five_orbital()
+    m = engine.model_from_spec(w.model, precision=kt.KT_FP32_KRYLOV)
+    n = 200_000
+    assert kt.kt_workspace_size(m, n) > kt.KT_STATIC_SCRATCH_BYTES
+    dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
+    b = kt.kt_seq_batch(n, dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr())
+    mv = kt.kt_move_batch(*(dummy.data_ptr(),) * 5)
+    with pytest.raises(kt.KtError) as e:
+        kt.kt_trace_ratio_static(m, b, dummy, dummy, mv, dummy, dummy, dummy)
+    assert e.value.code == kt.KT_ENOMEM
