@@ -244,6 +244,10 @@ def main():
         s, l, st = engine.trace(model, dseq, ws=ws)
         return s, l
 
+    # tiling: the autotuner times every compiled lane-group size on this batch
+    tuned = {}
+    for name, model in (("fp32", m32), ("fp64", m64)):
+        tuned[name] = kt.kt_autotune(model, dseq.batch(), out_s, out_l, out_st, ws)
     cur32 = current(m32)
     cur64 = current(m64)
     torch.cuda.synchronize()
@@ -377,7 +381,7 @@ def main():
                        "walkers_per_gpu": n, "mean_ops_per_walker": float(seqs.offsets[-1]) / n,
                        "krylov_tol": 1e-12, "precision": "fp32-krylov (fp64 tridiagonal exp, norms, log-weights)",
                        "blocks": "(n_up, n_dn, singly-occupied mask)", "n_blocks": info["n_blocks"],
-                       "d_max": info["d_max"], "n_kept": info["n_kept"], "l2": "flushed (256 MiB write) before every timed step",
+                       "d_max": info["d_max"], "n_kept": info["n_kept"], "group_lanes": tuned, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "fp64_gpu": {"value": value64, "unit": UNIT, "ms_per_step": tot64 / K64, "steps": K64,
                          "stage_ms_per_step": {k: v / max(K64, 1) for k, v in stage64.items()},

@@ -215,8 +215,12 @@ template <typename VT, int G, int DMAX, int PMAX>
 struct WarpTile {
   static constexpr int IPW = 32 / G;
   VT q[(PMAX + 1) * DMAX * IPW];  // Lanczos basis; basis vector 0 carries the state between intervals
-  double a[PMAX * IPW], b[PMAX * IPW], dd[PMAX * IPW], ee[PMAX * IPW], ex[PMAX * IPW], y[PMAX * IPW];
-  double S[PMAX * PMAX * IPW];    // S(k, i): component i of Ritz vector k
+  double a[PMAX * IPW], b[PMAX * IPW];            // T_p: diagonal alpha, off-diagonal beta (FP64)
+  double dd[PMAX * IPW], ee[PMAX * IPW];          // FP64 QL workspace -> Ritz values
+  double ex[PMAX * IPW], y[PMAX * IPW];           // exp(-dt T_p) e_1 (scaled) and helpers
+  double S[PMAX * PMAX * IPW];                     // FP64 Ritz vectors (FP64 path)
+  float d32[PMAX * IPW], e32[PMAX * IPW], y32[PMAX * IPW], x32[PMAX * IPW];
+  float S32[PMAX * PMAX * IPW];                   // FP32 Ritz vectors (FP32 path)
 };
 
 template <typename VT>
@@ -234,55 +238,90 @@ struct Tab<double> {
   static __device__ __forceinline__ const double *kept(const DevModel &M) { return M.kept_vec64; }
 };
 
-template <int G>
-__device__ __forceinline__ double gsum(double v, unsigned mask) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
-  return v;
-}
-template <int G>
-__device__ __forceinline__ int gsum_int(int v, unsigned mask) {
+template <int G, typename T>
+__device__ __forceinline__ T gsum(T v, unsigned mask) {
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
   return v;
 }
 
-// Dot-product accumulator. FP32 vectors: products and sums are carried as
-// unevaluated (hi, lo) pairs of floats with error-free transformations
-// (Dekker/Knuth TwoProduct via fmaf, TwoSum), so the result has FP64-class
-// accuracy while running on the FP32 pipe; it is handed over as a double.
-// FP64 vectors: plain FP64 fused multiply-adds.
-template <typename VT>
-struct Dot;
-template <>
-struct Dot<float> {
+// Error-free transformations on the FP32 pipe (Knuth TwoSum, TwoProduct via
+// fmaf). A value hi + lo carries about 48 significant bits.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+struct DF {
   float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float x, float y) {
-    const float p = x * y;
-    const float pe = fmaf(x, y, -p);
-    const float s = hi + p;
-    const float bb = s - hi;
-    const float se = (hi - (s - bb)) + (p - bb);
+  __device__ __forceinline__ void add_prod(float x, float y) {
+    const float p = x * y, pe = fmaf(x, y, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
     hi = s;
-    lo += se + pe;
+    lo += e + pe;
   }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ void add(const DF &o) {
+    float s, e;
+    two_sum(hi, o.hi, s, e);
+    hi = s;
+    lo += e + o.lo;
+  }
 };
-template <>
-struct Dot<double> {
+template <int G>
+__device__ __forceinline__ DF gsum_df(DF v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    DF w;
+    w.hi = __shfl_xor_sync(mask, v.hi, o);
+    w.lo = __shfl_xor_sync(mask, v.lo, o);
+    v.add(w);
+  }
+  return v;
+}
+// sqrt of a double-float, one Newton correction on the FP32 pipe.
+__device__ __forceinline__ DF sqrt_df(DF v) {
+  DF r;
+  if (!(v.hi > 0.f)) return r;
+  const float s = sqrtf(v.hi);
+  const float s2 = s * s, s2e = fmaf(s, s, -s2);
+  r.hi = s;
+  r.lo = ((v.hi - s2) - s2e + v.lo) / (2.f * s);
+  return r;
+}
+__device__ __forceinline__ double df_value(const DF &v) { return (double)v.hi + (double)v.lo; }
+
+// Group-reduced dot product with FP64 accuracy: double-float on the FP32 pipe
+// for FP32 vectors, FP64 FMA for FP64 vectors.
+template <typename VT, int G>
+struct GroupDot;
+template <int G>
+struct GroupDot<float, G> {
+  DF acc;
+  __device__ __forceinline__ void add(float x, float y) { acc.add_prod(x, y); }
+  __device__ __forceinline__ double value(unsigned gm) { return df_value(gsum_df<G>(acc, gm)); }
+  __device__ __forceinline__ double norm(unsigned gm) { return df_value(sqrt_df(gsum_df<G>(acc, gm))); }
+};
+template <int G>
+struct GroupDot<double, G> {
   double acc = 0.0;
   __device__ __forceinline__ void add(double x, double y) { acc = fma(x, y, acc); }
-  __device__ __forceinline__ double value() const { return acc; }
+  __device__ __forceinline__ double value(unsigned gm) { return gsum<G>(acc, gm); }
+  __device__ __forceinline__ double norm(unsigned gm) { return sqrt(gsum<G>(acc, gm)); }
 };
 
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
 // Rotation (c, s) with c x - s z = r, s x + c z = 0.
-__device__ __forceinline__ void givens(double x, double z, double &c, double &s, double &r) {
-  const double r2 = x * x + z * z;
-  if (r2 == 0.0) {
-    c = 1.0; s = 0.0; r = 0.0;
+template <typename R>
+__device__ __forceinline__ void givens(R x, R z, R &c, R &s, R &r) {
+  const R r2 = x * x + z * z;
+  if (r2 == R(0)) {
+    c = R(1); s = R(0); r = R(0);
     return;
   }
-  const double inv = rsqrt(r2);
+  const R inv = rsq(r2);
   c = x * inv;
   s = -z * inv;
   r = r2 * inv;
@@ -300,12 +339,9 @@ struct LogScale {
   __device__ __forceinline__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
 };
 
-
-// Scale the item's rows v to unit norm. The rows are first multiplied by a
-// power of two that brings the largest entry to [1, 2) (exact), so the sum of
-// squares can neither underflow nor overflow; the factor actually applied is
-// multiplied into `applied` (exact bookkeeping of what was taken out).
-// Returns false if the rows are all zero.
+// Scale the item's rows v to unit norm: an exact power-of-two prescale brings
+// the largest entry to [1, 2), then rsqrt of the sum of squares; the factor
+// actually applied is multiplied into `applied`. False if all rows are zero.
 template <typename VT, int G, int R>
 __device__ __forceinline__ bool normalize_rows(VT (&v)[R], int gl, int dim, unsigned gm, LogScale &applied) {
   VT m = VT(0);
@@ -323,23 +359,100 @@ __device__ __forceinline__ bool normalize_rows(VT (&v)[R], int gl, int dim, unsi
       const VT t = v[j] * s1;
       n2 += t * t;
     }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) n2 += __shfl_xor_sync(gm, n2, o);
-  const VT sc = s1 * rsqrt(n2);
+  n2 = gsum<G>(n2, gm);
+  const VT sc = s1 * rsq(n2);
 #pragma unroll
   for (int j = 0; j < R; ++j) v[j] *= sc;
   applied.mul((double)sc);
   return true;
 }
 
-// y = exp(-dt T_p) e_1 / exp(-dt lambda_min) for the symmetric tridiagonal
-// T_p (diagonal a, off-diagonal b) of one item; returns -dt lambda_min in
-// logfac. p = 1, 2 in closed form; p >= 3 by implicit QL sweeps with the shift
-// from the leading 2x2 block, the Ritz vectors spread over the group's lanes.
-// All FP64. Returns false if the QL iteration did not converge.
+// Symmetric tridiagonal eigensolver of one item, precision R: implicit QL
+// sweeps with the shift from the leading 2x2 block. On entry d holds the
+// diagonal and e the off-diagonal (e[p-1] = 0); on exit d holds the Ritz
+// values and S(k, i) component i of Ritz vector k (spread over the group's
+// lanes). Arrays are item-interleaved with stride IPW. False if it did not
+// converge.
+template <typename R, int G, int PMAX>
+__device__ bool tri_eig(R *d, R *e, R *S, int grp, int gl, unsigned gm, int p) {
+  constexpr int IPW = 32 / G;
+#define D_(k) d[(k) * IPW + grp]
+#define E_(k) e[(k) * IPW + grp]
+#define S_(k, i) S[((k) * PMAX + (i)) * IPW + grp]
+  for (int i = gl; i < p; i += G)
+    for (int k = 0; k < p; ++k) S_(k, i) = (i == k) ? R(1) : R(0);
+  __syncwarp(gm);
+  const R eps = sizeof(R) == 8 ? R(2.3e-16) : R(1.2e-7);
+  int lo = 0, guard = 0;
+  bool ok = true;
+  while (lo < p - 1) {
+    if (fabs(E_(lo)) <= eps * (fabs(D_(lo)) + fabs(D_(lo + 1)))) {
+      ++lo;
+      continue;
+    }
+    int hi = lo + 1;
+    while (hi < p - 1 && fabs(E_(hi)) > eps * (fabs(D_(hi)) + fabs(D_(hi + 1)))) ++hi;
+    if (++guard > 40 * p) {
+      ok = false;
+      break;
+    }
+    const R b0 = E_(lo);
+    const R dm = R(0.5) * (D_(lo + 1) - D_(lo));
+    const R mu = D_(lo) - b0 * b0 / (dm + copysign(sqrt(dm * dm + b0 * b0), dm));
+    R x = D_(hi) - mu, z = E_(hi - 1);
+    for (int k = hi; k > lo; --k) {
+      R c, sn, r;
+      givens(x, z, c, sn, r);
+      const R a11 = D_(k), a22 = D_(k - 1), a12 = E_(k - 1);
+      const R ek2 = (k - 1 > lo) ? E_(k - 2) : R(0);
+      const R cc = c * c, ss = sn * sn, cs = c * sn;
+      const R n11 = cc * a11 - R(2) * cs * a12 + ss * a22;
+      const R n22 = ss * a11 + R(2) * cs * a12 + cc * a22;
+      const R n12 = cs * (a11 - a22) + (cc - ss) * a12;
+      __syncwarp(gm);
+      if (gl == 0) {
+        if (k < hi) E_(k) = r;
+        D_(k) = n11;
+        D_(k - 1) = n22;
+        E_(k - 1) = n12;
+        if (k - 1 > lo) E_(k - 2) = c * ek2;
+      }
+      for (int i = gl; i < p; i += G) {
+        const R vk = S_(k, i), vk1 = S_(k - 1, i);
+        S_(k, i) = c * vk - sn * vk1;
+        S_(k - 1, i) = sn * vk + c * vk1;
+      }
+      __syncwarp(gm);
+      if (k - 1 > lo) {
+        x = n12;
+        z = -sn * ek2;
+      }
+    }
+  }
+  __syncwarp(gm);
+  return ok;
+#undef D_
+#undef E_
+#undef S_
+}
+
+// 2x2 symmetric [[a, b], [b, c]]: y = exp(-dt T) e_1 / exp(-dt lambda_min),
+// returns -dt lambda_min.
+template <typename R>
+__device__ __forceinline__ R exp2x2(R a, R c, R b, R dt, R &y0, R &y1) {
+  const R m = R(0.5) * (a + c), h = R(0.5) * (a - c);
+  const R r = sqrt(h * h + b * b);
+  const R E = exp(R(-2) * dt * r);
+  const R g = (r > R(0)) ? -expm1(R(-2) * dt * r) / (R(2) * r) : dt;
+  y0 = R(0.5) * (R(1) + E) - g * h;
+  y1 = -g * b;
+  return -dt * (m - r);
+}
+
+// FP64 y = exp(-dt T_p) e_1 / exp(-dt lambda_min) from a full FP64 QL (FP64 path).
 template <typename VT, int G, int DMAX, int PMAX>
-__device__ bool tri_exp(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
-                        double &logfac) {
+__device__ bool tri_exp64(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
+                          double &logfac) {
   constexpr int IPW = 32 / G;
 #define A_(k) s.a[(k) * IPW + grp]
 #define B_(k) s.b[(k) * IPW + grp]
@@ -355,74 +468,21 @@ __device__ bool tri_exp(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigne
     return true;
   }
   if (p == 2) {
-    const double a = A_(0), c = A_(1), b = B_(0);
-    const double m = 0.5 * (a + c), h = 0.5 * (a - c);
-    const double r = sqrt(h * h + b * b);
-    const double E = exp(-2.0 * dt * r);
-    const double g = (r > 0.0) ? -expm1(-2.0 * dt * r) / (2.0 * r) : dt;
+    double y0, y1;
+    logfac = exp2x2(A_(0), A_(1), B_(0), dt, y0, y1);
     if (gl == 0) {
-      Y_(0) = 0.5 * (1.0 + E) - g * h;
-      Y_(1) = -g * b;
+      Y_(0) = y0;
+      Y_(1) = y1;
     }
-    logfac = -dt * (m - r);
     __syncwarp(gm);
     return true;
   }
   for (int i = gl; i < p; i += G) {
     D_(i) = A_(i);
     E_(i) = (i + 1 < p) ? B_(i) : 0.0;
-    for (int k = 0; k < p; ++k) S_(k, i) = (i == k) ? 1.0 : 0.0;
   }
   __syncwarp(gm);
-  const double eps = 2.3e-16;
-  int lo = 0, guard = 0;
-  bool ok = true;
-  while (lo < p - 1) {
-    if (fabs(E_(lo)) <= eps * (fabs(D_(lo)) + fabs(D_(lo + 1)))) {
-      ++lo;
-      continue;
-    }
-    int hi = lo + 1;
-    while (hi < p - 1 && fabs(E_(hi)) > eps * (fabs(D_(hi)) + fabs(D_(hi + 1)))) ++hi;
-    if (++guard > 40 * p) {
-      ok = false;
-      break;
-    }
-    // shift: eigenvalue of the leading 2x2 of [lo, hi] closest to D(lo)
-    const double b0 = E_(lo);
-    const double dm = 0.5 * (D_(lo + 1) - D_(lo));
-    const double mu = D_(lo) - b0 * b0 / (dm + copysign(sqrt(dm * dm + b0 * b0), dm));
-    double x = D_(hi) - mu, z = E_(hi - 1);
-    for (int k = hi; k > lo; --k) {
-      double c, sn, r;
-      givens(x, z, c, sn, r);
-      const double a11 = D_(k), a22 = D_(k - 1), a12 = E_(k - 1);
-      const double ek2 = (k - 1 > lo) ? E_(k - 2) : 0.0;
-      const double cc = c * c, ss = sn * sn, cs = c * sn;
-      const double n11 = cc * a11 - 2.0 * cs * a12 + ss * a22;
-      const double n22 = ss * a11 + 2.0 * cs * a12 + cc * a22;
-      const double n12 = cs * (a11 - a22) + (cc - ss) * a12;
-      __syncwarp(gm);
-      if (gl == 0) {
-        if (k < hi) E_(k) = r;
-        D_(k) = n11;
-        D_(k - 1) = n22;
-        E_(k - 1) = n12;
-        if (k - 1 > lo) E_(k - 2) = c * ek2;
-      }
-      for (int i = gl; i < p; i += G) {
-        const double vk = S_(k, i), vk1 = S_(k - 1, i);
-        S_(k, i) = c * vk - sn * vk1;
-        S_(k - 1, i) = sn * vk + c * vk1;
-      }
-      __syncwarp(gm);
-      if (k - 1 > lo) {
-        x = n12;
-        z = -sn * ek2;
-      }
-    }
-  }
-  __syncwarp(gm);
+  const bool ok = tri_eig<double, G, PMAX>(s.dd, s.ee, s.S, grp, gl, gm, p);
   double lmin = D_(0);
   for (int k = 1; k < p; ++k) lmin = fmin(lmin, D_(k));
   for (int k = gl; k < p; k += G) X_(k) = exp(-dt * (D_(k) - lmin)) * S_(k, 0);
@@ -444,6 +504,112 @@ __device__ bool tri_exp(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigne
 #undef S_
 }
 
+// FP32-path convergence estimate: ||y|| and |y_{p-1}| of exp(-dt T_p) e_1 from
+// an FP32 eigendecomposition (the estimate needs about one significant digit).
+// For p >= 3 the FP32 Ritz pairs are left in d32 / S32 for the final step.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ void tri_check32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
+                            float &ynorm, float &ylast) {
+  constexpr int IPW = 32 / G;
+#define A_(k) s.a[(k) * IPW + grp]
+#define B_(k) s.b[(k) * IPW + grp]
+#define D_(k) s.d32[(k) * IPW + grp]
+#define E_(k) s.e32[(k) * IPW + grp]
+#define X_(k) s.x32[(k) * IPW + grp]
+#define Y_(k) s.y32[(k) * IPW + grp]
+#define S_(k, i) s.S32[((k) * PMAX + (i)) * IPW + grp]
+  if (p == 1) {
+    ynorm = 1.f;
+    ylast = 1.f;
+    return;
+  }
+  if (p == 2) {
+    float y0, y1;
+    exp2x2((float)A_(0), (float)A_(1), (float)B_(0), (float)dt, y0, y1);
+    ynorm = sqrtf(y0 * y0 + y1 * y1);
+    ylast = fabsf(y1);
+    return;
+  }
+  for (int i = gl; i < p; i += G) {
+    D_(i) = (float)A_(i);
+    E_(i) = (i + 1 < p) ? (float)B_(i) : 0.f;
+  }
+  __syncwarp(gm);
+  tri_eig<float, G, PMAX>(s.d32, s.e32, s.S32, grp, gl, gm, p);
+  float lmin = D_(0);
+  for (int k = 1; k < p; ++k) lmin = fminf(lmin, D_(k));
+  for (int k = gl; k < p; k += G) X_(k) = expf(-(float)dt * (D_(k) - lmin)) * S_(k, 0);
+  __syncwarp(gm);
+  float yn = 0.f;
+  for (int i = gl; i < p; i += G) {
+    float acc = 0.f;
+    for (int k = 0; k < p; ++k) acc = fmaf(S_(k, i), X_(k), acc);
+    Y_(i) = acc;
+    yn += acc * acc;
+  }
+  ynorm = sqrtf(gsum<G>(yn, gm));
+  __syncwarp(gm);
+  ylast = fabsf(Y_(p - 1));
+#undef A_
+#undef B_
+#undef D_
+#undef E_
+#undef X_
+#undef Y_
+#undef S_
+}
+
+// FP32-path final step (p >= 3): every Ritz value is recomputed in FP64 as the
+// Rayleigh quotient of its FP32 Ritz vector with the FP64 T_p (its error is
+// quadratic in the vector's, ~1e-14), the exponentials and the assembly of
+// y = sum_k s_k s_k[0] exp(-dt (lambda_k - lambda_min)) / |s_k|^2 run in FP64,
+// one Ritz pair per lane. lambda_min enters the log-weight.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
+                            double &logfac) {
+  constexpr int IPW = 32 / G;
+#define A_(k) s.a[(k) * IPW + grp]
+#define B_(k) s.b[(k) * IPW + grp]
+#define D_(k) s.dd[(k) * IPW + grp]
+#define X_(k) s.ex[(k) * IPW + grp]
+#define Y_(k) s.y[(k) * IPW + grp]
+#define S_(k, i) s.S32[((k) * PMAX + (i)) * IPW + grp]
+  double lmin = INFINITY;
+  for (int k = gl; k < p; k += G) {
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < p; ++i) {
+      const double si = S_(k, i);
+      double ti = A_(i) * si;
+      if (i > 0) ti = fma(B_(i - 1), (double)S_(k, i - 1), ti);
+      if (i + 1 < p) ti = fma(B_(i), (double)S_(k, i + 1), ti);
+      num = fma(si, ti, num);
+      den = fma(si, si, den);
+    }
+    const double lam = num / den;
+    D_(k) = lam;
+    X_(k) = den;
+    lmin = fmin(lmin, lam);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) lmin = fmin(lmin, __shfl_xor_sync(gm, lmin, o));
+  __syncwarp(gm);
+  for (int k = gl; k < p; k += G) X_(k) = exp(-dt * (D_(k) - lmin)) * (double)S_(k, 0) / X_(k);
+  __syncwarp(gm);
+  for (int i = gl; i < p; i += G) {
+    double acc = 0.0;
+    for (int k = 0; k < p; ++k) acc = fma((double)S_(k, i), X_(k), acc);
+    Y_(i) = acc;
+  }
+  logfac = -dt * lmin;
+  __syncwarp(gm);
+#undef A_
+#undef B_
+#undef D_
+#undef X_
+#undef Y_
+#undef S_
+}
+
 struct ItemAcc {
   unsigned long long ops, intervals, iters, pmax, noconv, flops_vec, flops_tri, bytes_apply;
 };
@@ -452,6 +618,7 @@ template <typename VT, int G, int DMAX, int PMAX>
 __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, Workspace ws,
                                                     kt_stats *stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool F32 = sizeof(VT) == 4;
   constexpr int IPW = 32 / G;
   constexpr int R = (DMAX + G - 1) / G;  // rows per lane
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -467,6 +634,8 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
   const VT *__restrict__ tkept = Tab<VT>::kept(M);
   const int n_alive = ws.counters[0];
   const int nk = M.n_kept, nf = M.nf;
+  // FP32 convergence estimates get a safety factor of 2 on the tolerance
+  const float tol32 = F32 ? (float)(0.5 * M.tol) : 0.f;
 
   for (;;) {
     int it = 0;
@@ -509,7 +678,6 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
         }
         const int off2 = __ldg(M.blk_off + b2), dim2 = __ldg(M.blk_dim + b2);
         VT tv[R];
-        VT n2 = VT(0);
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           const int r = gl + G * j;
@@ -525,7 +693,6 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
           }
           tv[j] = v;
         }
-        (void)n2;
         acc.ops += 1;
         acc.flops_vec += 3ull * dim2;
         acc.bytes_apply += (unsigned long long)dim2 * (2 * sizeof(VT) + 4);
@@ -564,7 +731,7 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
         bool conv = false;
         for (int jj = 0; jj < pcap; ++jj) {
           VT wv[R];
-          Dot<VT> da;
+          GroupDot<VT, G> da;
 #pragma unroll
           for (int j = 0; j < R; ++j) {
             const int r = gl + G * j;
@@ -579,18 +746,33 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
             }
             wv[j] = a;
           }
-          const double al = gsum<G>(da.value(), gm);
+          const double al = da.value(gm);
           const VT alv = VT(al), bpv = VT(bprev);
-          Dot<VT> db;
 #pragma unroll
-          for (int j = 0; j < R; ++j) {
-            const int r = gl + G * j;
-            if (r < dim) {
-              wv[j] = wv[j] - alv * qc[j] - bpv * qp[j];
-              db.add(wv[j], wv[j]);
+          for (int j = 0; j < R; ++j)
+            if (gl + G * j < dim) wv[j] = wv[j] - alv * qc[j] - bpv * qp[j];
+          if (F32 && jj > 0) {
+            // one pass of full reorthogonalisation against q_0 .. q_jj (FP32 loses orthogonality fast)
+            for (int k = 0; k <= jj; ++k) {
+              VT h = VT(0);
+#pragma unroll
+              for (int j = 0; j < R; ++j) {
+                const int r = gl + G * j;
+                if (r < dim) h += Q_(k, r) * wv[j];
+              }
+              h = gsum<G>(h, gm);
+#pragma unroll
+              for (int j = 0; j < R; ++j) {
+                const int r = gl + G * j;
+                if (r < dim) wv[j] -= h * Q_(k, r);
+              }
             }
           }
-          const double bb = sqrt(gsum<G>(db.value(), gm));
+          GroupDot<VT, G> db;
+#pragma unroll
+          for (int j = 0; j < R; ++j)
+            if (gl + G * j < dim) db.add(wv[j], wv[j]);
+          const double bb = db.norm(gm);
           p = jj + 1;
           if (gl == 0) {
             A_(jj) = al;
@@ -598,18 +780,22 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
           }
           __syncwarp(gm);
           const bool exact = (p == dim) || !(bb > brk);
-          const bool okq = tri_exp(s, grp, gl, gm, p, dt, logfac);
-          if (stats) acc.flops_tri += (p <= 2) ? 30ull : (unsigned long long)(12 * p * p * p + 40 * p);
-          if (!okq) status = KT_ENUMERIC;
-          if (exact) {
-            conv = true;
-            break;
+          bool stop = exact;
+          if (!exact) {
+            if (F32) {
+              float yn, yl;
+              tri_check32(s, grp, gl, gm, p, dt, yn, yl);
+              stop = (float)bb * yl <= tol32 * yn;
+            } else {
+              const bool okq = tri_exp64(s, grp, gl, gm, p, dt, logfac);
+              if (!okq) status = KT_ENUMERIC;
+              double yn = 0.0;
+              for (int k = gl; k < p; k += G) yn = fma(Y_(k), Y_(k), yn);
+              yn = sqrt(gsum<G>(yn, gm));
+              stop = bb * fabs(Y_(p - 1)) <= M.tol * yn;
+            }
           }
-          double yn = 0.0;
-          for (int k = gl; k < p; k += G) yn = fma(Y_(k), Y_(k), yn);
-          yn = sqrt(gsum<G>(yn, gm));
-          const double err = bb * fabs(Y_(p - 1));
-          if (err <= M.tol * yn) {
+          if (stop) {
             conv = true;
             break;
           }
@@ -629,6 +815,23 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
           acc.noconv += 1;
           if (status == KT_OK) status = KT_ENOCONV;
         }
+        // final exp(-dt T_p) e_1 for the stopping p
+        if (F32) {
+          if (p <= 2) {
+            tri_exp64(s, grp, gl, gm, p, dt, logfac);
+          } else {
+            float yn, yl;
+            // Ritz pairs of T_p in FP32 (already there unless the stop was exact or at the cap)
+            if (conv && !((p == dim) || !(B_(p - 1) > brk))) {
+            } else {
+              tri_check32(s, grp, gl, gm, p, dt, yn, yl);
+            }
+            tri_final32(s, grp, gl, gm, p, dt, logfac);
+          }
+        } else if (conv && ((p == dim) || !(B_(p - 1) > brk))) {
+          if (!tri_exp64(s, grp, gl, gm, p, dt, logfac)) status = KT_ENUMERIC;
+        }
+        if (stats) acc.flops_tri += (p <= 2) ? 30ull : (unsigned long long)(12 * p * p * p + 40 * p);
         // v = sum_j y_j q_j, renormalised; what is taken out goes to the log-weight
         VT vv[R];
 #pragma unroll
@@ -664,8 +867,9 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
               for (int k = 0; k < wid; ++k) cnt += (__ldg(M.ell_col + ell + k * dim + r) >= 0);
             }
           }
-          const int nnz_blk = gsum_int<G>(cnt, gm);
+          const int nnz_blk = gsum<G>(cnt, gm);
           acc.flops_vec += (unsigned long long)p * (2ull * nnz_blk + 9ull * dim) + 2ull * p * dim + 3ull * dim;
+          if (F32) acc.flops_vec += (unsigned long long)p * (p - 1) * 2ull * dim;  // reorthogonalisation
         }
       }
     }
@@ -674,13 +878,13 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
       if (b != b_kept) {
         vanished = true;
       } else {
-        Dot<VT> dov;
+        GroupDot<VT, G> dov;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           const int r = gl + G * j;
           if (r < dim) dov.add(__ldg(tkept + koff + r), Q_(0, r));
         }
-        const double ov = gsum<G>(dov.value(), gm);
+        const double ov = dov.value(gm);
         if (ov == 0.0) {
           vanished = true;
         } else {
@@ -832,8 +1036,8 @@ int kernel_groups_for(int kd, int *out, int cap) {
 
 int default_group_for(int kd) {
   switch (kd) {
-    case 10: return 4;
-    case 36: return 8;
+    case 10: return 16;
+    case 36: return 16;
     case 128: return 32;
   }
   return 32;
