@@ -210,7 +210,8 @@ kt_status kt_trace_ratio(kt_model *m, const kt_seq_batch *cur, const int8_t *cur
  * a fixed array of KT_STATIC_SCRATCH_BYTES inside the library's device image,
  * held on every GPU that loads the library until the process exits. Batches
  * whose scratch would exceed it (kt_workspace_size(m, n) > KT_STATIC_SCRATCH_BYTES,
- * about 68,000 walkers at N_tr = 6) are rejected with KT_ENOMEM before any work.
+ * about 6,700 walkers of the five-orbital model) are rejected with KT_ENOMEM
+ * before any work.
  * The call allocates nothing. Its first call on each device looks up the
  * array's device address with that device current; make that first call
  * before any stream capture. All calls share the array: calls whose kernels

@@ -69,10 +69,19 @@ struct Workspace {
   int8_t *item_sign;   // [n * n_kept]
   double *item_log;    // [n * n_kept] log|contribution| (relative to exp(-beta E0))
   int32_t *item_status;// [n * n_kept]
+  int32_t *pair_flag;  // [n * n_kept] halves of the item published so far
+  double *half_log;    // [2 * n * n_kept] log-weight of each half
+  int32_t *half_info;  // [2 * n * n_kept] block | status << 24, or -1 if the half vanished
+  void *half_vec;      // [2 * n * n_kept][d_max] final vector of each half (FP32 or FP64)
 };
 
-size_t workspace_bytes(int n_walkers, int n_kept);
-Workspace carve_workspace(void *base, int n_walkers, int n_kept);
+size_t workspace_bytes(int n_walkers, int n_kept, int d_max);
+Workspace carve_workspace(void *base, int n_walkers, int n_kept, int d_max);
+
+// Compiled variants of the Krylov items kernel: (row capacity DMAX, Krylov cap
+// PMAX, lanes per item G).
+#define KT_FOR_VARIANTS(X) \
+  X(10, 10, 4) X(10, 10, 8) X(10, 10, 16) X(10, 10, 32) X(36, 24, 8) X(36, 24, 16) X(36, 24, 32) X(128, 40, 32)
 
 // Kernel variants compiled for sm_103a: rows per block (DMAX) and Krylov cap (PMAX).
 int kernel_dmax_for(int d_max);    // 0 if no variant fits

@@ -1,0 +1,846 @@
+// Krylov items kernel templates (internal; instantiated per precision in
+// kt_items_f32.cu and kt_items_f64.cu so the two compile in parallel).
+#pragma once
+
+#include "kt_device.cuh"
+
+namespace kt {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// 3. Krylov items
+//
+// G lanes cooperate on one (walker, kept state) item; a warp holds 32/G items.
+// Vector rows are spread over the G lanes of the item (row r on lane r % G).
+// With small G every FP64 instruction of the scalar part (tridiagonal
+// exponential, norms, log-weights) serves several items at once, which
+// matters on GB300 where an FP64 warp instruction occupies the SM's FP64 pipe
+// for 16 cycles however many lanes are active.
+// Shared memory is interleaved item-minor: element e of item g of a warp lives
+// at e * IPW + g, so lanes of different items touch consecutive words.
+// ---------------------------------------------------------------------------
+template <typename VT, int G, int DMAX, int PMAX>
+struct WarpTile {
+  static constexpr int IPW = 32 / G;
+  VT q[(PMAX + 1) * DMAX * IPW];  // Lanczos basis; basis vector 0 carries the state between intervals
+  double a[PMAX * IPW], b[PMAX * IPW];            // T_p: diagonal alpha, off-diagonal beta (FP64)
+  double dd[PMAX * IPW], ee[PMAX * IPW];          // FP64 QL workspace -> Ritz values
+  double ex[PMAX * IPW], y[PMAX * IPW];           // exp(-dt T_p) e_1 (scaled) and helpers
+  double S[PMAX * PMAX * IPW];                     // FP64 Ritz vectors (FP64 path)
+  float d32[PMAX * IPW], e32[PMAX * IPW], y32[PMAX * IPW], x32[PMAX * IPW];
+  float S32[PMAX * PMAX * IPW];                   // FP32 Ritz vectors (FP32 path)
+};
+
+template <typename VT>
+struct Tab;
+template <>
+struct Tab<float> {
+  static __device__ __forceinline__ const float *diag(const DevModel &M) { return M.st_diag32; }
+  static __device__ __forceinline__ const float *val(const DevModel &M) { return M.ell_val32; }
+  static __device__ __forceinline__ const float *kept(const DevModel &M) { return M.kept_vec32; }
+};
+template <>
+struct Tab<double> {
+  static __device__ __forceinline__ const double *diag(const DevModel &M) { return M.st_diag64; }
+  static __device__ __forceinline__ const double *val(const DevModel &M) { return M.ell_val64; }
+  static __device__ __forceinline__ const double *kept(const DevModel &M) { return M.kept_vec64; }
+};
+
+template <int G, typename T>
+__device__ __forceinline__ T gsum(T v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+// Error-free transformations on the FP32 pipe (Knuth TwoSum, TwoProduct via
+// fmaf). A value hi + lo carries about 48 significant bits.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+struct DF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float x, float y) {
+    const float p = x * y, pe = fmaf(x, y, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo += e + pe;
+  }
+  __device__ __forceinline__ void add(const DF &o) {
+    float s, e;
+    two_sum(hi, o.hi, s, e);
+    hi = s;
+    lo += e + o.lo;
+  }
+};
+template <int G>
+__device__ __forceinline__ DF gsum_df(DF v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    DF w;
+    w.hi = __shfl_xor_sync(mask, v.hi, o);
+    w.lo = __shfl_xor_sync(mask, v.lo, o);
+    v.add(w);
+  }
+  return v;
+}
+// sqrt of a double-float, one Newton correction on the FP32 pipe.
+__device__ __forceinline__ DF sqrt_df(DF v) {
+  DF r;
+  if (!(v.hi > 0.f)) return r;
+  const float s = sqrtf(v.hi);
+  const float s2 = s * s, s2e = fmaf(s, s, -s2);
+  r.hi = s;
+  r.lo = ((v.hi - s2) - s2e + v.lo) / (2.f * s);
+  return r;
+}
+__device__ __forceinline__ double df_value(const DF &v) { return (double)v.hi + (double)v.lo; }
+
+// Group-reduced dot product with FP64 accuracy: double-float on the FP32 pipe
+// for FP32 vectors, FP64 FMA for FP64 vectors.
+template <typename VT, int G>
+struct GroupDot;
+template <int G>
+struct GroupDot<float, G> {
+  DF acc;
+  __device__ __forceinline__ void add(float x, float y) { acc.add_prod(x, y); }
+  __device__ __forceinline__ double value(unsigned gm) { return df_value(gsum_df<G>(acc, gm)); }
+  __device__ __forceinline__ double norm(unsigned gm) { return df_value(sqrt_df(gsum_df<G>(acc, gm))); }
+};
+template <int G>
+struct GroupDot<double, G> {
+  double acc = 0.0;
+  __device__ __forceinline__ void add(double x, double y) { acc = fma(x, y, acc); }
+  __device__ __forceinline__ double value(unsigned gm) { return gsum<G>(acc, gm); }
+  __device__ __forceinline__ double norm(unsigned gm) { return sqrt(gsum<G>(acc, gm)); }
+};
+
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+// Rotation (c, s) with c x - s z = r, s x + c z = 0.
+template <typename R>
+__device__ __forceinline__ void givens(R x, R z, R &c, R &s, R &r) {
+  const R r2 = x * x + z * z;
+  if (r2 == R(0)) {
+    c = R(1); s = R(0); r = R(0);
+    return;
+  }
+  const R inv = rsq(r2);
+  c = x * inv;
+  s = -z * inv;
+  r = r2 * inv;
+}
+
+// Product of positive factors kept as mantissa * 2^exponent (no log per step).
+struct LogScale {
+  double m = 1.0;
+  int e = 0;
+  __device__ __forceinline__ void mul(double f) {
+    int k;
+    m = frexp(m * f, &k);
+    e += k;
+  }
+  __device__ __forceinline__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
+};
+
+// Scale the item's rows v to unit norm: an exact power-of-two prescale brings
+// the largest entry to [1, 2), then rsqrt of the sum of squares; the factor
+// actually applied is multiplied into `applied`. False if all rows are zero.
+template <typename VT, int G, int R>
+__device__ __forceinline__ bool normalize_rows(VT (&v)[R], int gl, int dim, unsigned gm, LogScale &applied) {
+  VT m = VT(0);
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (gl + G * j < dim) m = fmax(m, fabs(v[j]));
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(gm, m, o));
+  if (!(m > VT(0))) return false;
+  const VT s1 = scalbn(VT(1), -ilogb(m));
+  VT n2 = VT(0);
+#pragma unroll
+  for (int j = 0; j < R; ++j)
+    if (gl + G * j < dim) {
+      const VT t = v[j] * s1;
+      n2 += t * t;
+    }
+  n2 = gsum<G>(n2, gm);
+  const VT sc = s1 * rsq(n2);
+#pragma unroll
+  for (int j = 0; j < R; ++j) v[j] *= sc;
+  applied.mul((double)sc);
+  return true;
+}
+
+// Symmetric tridiagonal eigensolver of one item, precision R: implicit QL
+// sweeps with the shift from the leading 2x2 block. On entry d holds the
+// diagonal and e the off-diagonal (e[p-1] = 0); on exit d holds the Ritz
+// values and S(k, i) component i of Ritz vector k (spread over the group's
+// lanes). Arrays are item-interleaved with stride IPW. False if it did not
+// converge.
+template <typename R, int G, int PMAX>
+__device__ bool tri_eig(R *d, R *e, R *S, int grp, int gl, unsigned gm, int p) {
+  constexpr int IPW = 32 / G;
+#define D_(k) d[(k) * IPW + grp]
+#define E_(k) e[(k) * IPW + grp]
+#define S_(k, i) S[((k) * PMAX + (i)) * IPW + grp]
+  for (int i = gl; i < p; i += G)
+    for (int k = 0; k < p; ++k) S_(k, i) = (i == k) ? R(1) : R(0);
+  __syncwarp(gm);
+  const R eps = sizeof(R) == 8 ? R(2.3e-16) : R(1.2e-7);
+  int lo = 0, guard = 0;
+  bool ok = true;
+  while (lo < p - 1) {
+    if (fabs(E_(lo)) <= eps * (fabs(D_(lo)) + fabs(D_(lo + 1)))) {
+      ++lo;
+      continue;
+    }
+    int hi = lo + 1;
+    while (hi < p - 1 && fabs(E_(hi)) > eps * (fabs(D_(hi)) + fabs(D_(hi + 1)))) ++hi;
+    if (++guard > 40 * p) {
+      ok = false;
+      break;
+    }
+    const R b0 = E_(lo);
+    const R dm = R(0.5) * (D_(lo + 1) - D_(lo));
+    const R mu = D_(lo) - b0 * b0 / (dm + copysign(sqrt(dm * dm + b0 * b0), dm));
+    R x = D_(hi) - mu, z = E_(hi - 1);
+    for (int k = hi; k > lo; --k) {
+      R c, sn, r;
+      givens(x, z, c, sn, r);
+      const R a11 = D_(k), a22 = D_(k - 1), a12 = E_(k - 1);
+      const R ek2 = (k - 1 > lo) ? E_(k - 2) : R(0);
+      const R cc = c * c, ss = sn * sn, cs = c * sn;
+      const R n11 = cc * a11 - R(2) * cs * a12 + ss * a22;
+      const R n22 = ss * a11 + R(2) * cs * a12 + cc * a22;
+      const R n12 = cs * (a11 - a22) + (cc - ss) * a12;
+      __syncwarp(gm);
+      if (gl == 0) {
+        if (k < hi) E_(k) = r;
+        D_(k) = n11;
+        D_(k - 1) = n22;
+        E_(k - 1) = n12;
+        if (k - 1 > lo) E_(k - 2) = c * ek2;
+      }
+      for (int i = gl; i < p; i += G) {
+        const R vk = S_(k, i), vk1 = S_(k - 1, i);
+        S_(k, i) = c * vk - sn * vk1;
+        S_(k - 1, i) = sn * vk + c * vk1;
+      }
+      __syncwarp(gm);
+      if (k - 1 > lo) {
+        x = n12;
+        z = -sn * ek2;
+      }
+    }
+  }
+  __syncwarp(gm);
+  return ok;
+#undef D_
+#undef E_
+#undef S_
+}
+
+// 2x2 symmetric [[a, b], [b, c]]: y = exp(-dt T) e_1 / exp(-dt lambda_min),
+// returns -dt lambda_min.
+template <typename R>
+__device__ __forceinline__ R exp2x2(R a, R c, R b, R dt, R &y0, R &y1) {
+  const R m = R(0.5) * (a + c), h = R(0.5) * (a - c);
+  const R r = sqrt(h * h + b * b);
+  const R E = exp(R(-2) * dt * r);
+  const R g = (r > R(0)) ? -expm1(R(-2) * dt * r) / (R(2) * r) : dt;
+  y0 = R(0.5) * (R(1) + E) - g * h;
+  y1 = -g * b;
+  return -dt * (m - r);
+}
+
+// FP64 y for p <= 2 (closed forms), used by the FP32 path.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ __forceinline__ void tri_small64(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p,
+                                            double dt, double &logfac) {
+  constexpr int IPW = 32 / G;
+  double y0 = 1.0, y1 = 0.0;
+  if (p == 1) {
+    logfac = -dt * s.a[grp];
+  } else {
+    logfac = exp2x2(s.a[grp], s.a[IPW + grp], s.b[grp], dt, y0, y1);
+  }
+  if (gl == 0) {
+    s.y[grp] = y0;
+    s.y[IPW + grp] = y1;
+  }
+  __syncwarp(gm);
+}
+
+// FP64 y = exp(-dt T_p) e_1 / exp(-dt lambda_min) from a full FP64 QL (FP64 path).
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ bool tri_exp64(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
+                          double &logfac) {
+  constexpr int IPW = 32 / G;
+#define A_(k) s.a[(k) * IPW + grp]
+#define B_(k) s.b[(k) * IPW + grp]
+#define D_(k) s.dd[(k) * IPW + grp]
+#define E_(k) s.ee[(k) * IPW + grp]
+#define X_(k) s.ex[(k) * IPW + grp]
+#define Y_(k) s.y[(k) * IPW + grp]
+#define S_(k, i) s.S[((k) * PMAX + (i)) * IPW + grp]
+  if (p == 1) {
+    if (gl == 0) Y_(0) = 1.0;
+    logfac = -dt * A_(0);
+    __syncwarp(gm);
+    return true;
+  }
+  if (p == 2) {
+    double y0, y1;
+    logfac = exp2x2(A_(0), A_(1), B_(0), dt, y0, y1);
+    if (gl == 0) {
+      Y_(0) = y0;
+      Y_(1) = y1;
+    }
+    __syncwarp(gm);
+    return true;
+  }
+  for (int i = gl; i < p; i += G) {
+    D_(i) = A_(i);
+    E_(i) = (i + 1 < p) ? B_(i) : 0.0;
+  }
+  __syncwarp(gm);
+  const bool ok = tri_eig<double, G, PMAX>(s.dd, s.ee, s.S, grp, gl, gm, p);
+  double lmin = D_(0);
+  for (int k = 1; k < p; ++k) lmin = fmin(lmin, D_(k));
+  for (int k = gl; k < p; k += G) X_(k) = exp(-dt * (D_(k) - lmin)) * S_(k, 0);
+  __syncwarp(gm);
+  for (int i = gl; i < p; i += G) {
+    double acc = 0.0;
+    for (int k = 0; k < p; ++k) acc = fma(S_(k, i), X_(k), acc);
+    Y_(i) = acc;
+  }
+  logfac = -dt * lmin;
+  __syncwarp(gm);
+  return ok;
+#undef A_
+#undef B_
+#undef D_
+#undef E_
+#undef X_
+#undef Y_
+#undef S_
+}
+
+// FP32-path convergence estimate: ||y|| and |y_{p-1}| of exp(-dt T_p) e_1 from
+// an FP32 eigendecomposition (the estimate needs about one significant digit).
+// For p >= 3 the FP32 Ritz pairs are left in d32 / S32 for the final step.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ void tri_check32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
+                            float &ynorm, float &ylast) {
+  constexpr int IPW = 32 / G;
+#define A_(k) s.a[(k) * IPW + grp]
+#define B_(k) s.b[(k) * IPW + grp]
+#define D_(k) s.d32[(k) * IPW + grp]
+#define E_(k) s.e32[(k) * IPW + grp]
+#define X_(k) s.x32[(k) * IPW + grp]
+#define Y_(k) s.y32[(k) * IPW + grp]
+#define S_(k, i) s.S32[((k) * PMAX + (i)) * IPW + grp]
+  if (p == 1) {
+    ynorm = 1.f;
+    ylast = 1.f;
+    return;
+  }
+  if (p == 2) {
+    float y0, y1;
+    exp2x2((float)A_(0), (float)A_(1), (float)B_(0), (float)dt, y0, y1);
+    ynorm = sqrtf(y0 * y0 + y1 * y1);
+    ylast = fabsf(y1);
+    return;
+  }
+  for (int i = gl; i < p; i += G) {
+    D_(i) = (float)A_(i);
+    E_(i) = (i + 1 < p) ? (float)B_(i) : 0.f;
+  }
+  __syncwarp(gm);
+  tri_eig<float, G, PMAX>(s.d32, s.e32, s.S32, grp, gl, gm, p);
+  float lmin = D_(0);
+  for (int k = 1; k < p; ++k) lmin = fminf(lmin, D_(k));
+  for (int k = gl; k < p; k += G) X_(k) = expf(-(float)dt * (D_(k) - lmin)) * S_(k, 0);
+  __syncwarp(gm);
+  float yn = 0.f;
+  for (int i = gl; i < p; i += G) {
+    float acc = 0.f;
+    for (int k = 0; k < p; ++k) acc = fmaf(S_(k, i), X_(k), acc);
+    Y_(i) = acc;
+    yn += acc * acc;
+  }
+  ynorm = sqrtf(gsum<G>(yn, gm));
+  __syncwarp(gm);
+  ylast = fabsf(Y_(p - 1));
+#undef A_
+#undef B_
+#undef D_
+#undef E_
+#undef X_
+#undef Y_
+#undef S_
+}
+
+// FP32-path final step (p >= 3): every Ritz value is recomputed in FP64 as the
+// Rayleigh quotient of its FP32 Ritz vector with the FP64 T_p (its error is
+// quadratic in the vector's, ~1e-14), the exponentials and the assembly of
+// y = sum_k s_k s_k[0] exp(-dt (lambda_k - lambda_min)) / |s_k|^2 run in FP64,
+// one Ritz pair per lane. lambda_min enters the log-weight.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
+                            double &logfac) {
+  constexpr int IPW = 32 / G;
+#define A_(k) s.a[(k) * IPW + grp]
+#define B_(k) s.b[(k) * IPW + grp]
+#define D_(k) s.dd[(k) * IPW + grp]
+#define X_(k) s.ex[(k) * IPW + grp]
+#define Y_(k) s.y[(k) * IPW + grp]
+#define S_(k, i) s.S32[((k) * PMAX + (i)) * IPW + grp]
+  double lmin = INFINITY;
+  for (int k = gl; k < p; k += G) {
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < p; ++i) {
+      const double si = S_(k, i);
+      double ti = A_(i) * si;
+      if (i > 0) ti = fma(B_(i - 1), (double)S_(k, i - 1), ti);
+      if (i + 1 < p) ti = fma(B_(i), (double)S_(k, i + 1), ti);
+      num = fma(si, ti, num);
+      den = fma(si, si, den);
+    }
+    const double lam = num / den;
+    D_(k) = lam;
+    X_(k) = den;
+    lmin = fmin(lmin, lam);
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) lmin = fmin(lmin, __shfl_xor_sync(gm, lmin, o));
+  __syncwarp(gm);
+  for (int k = gl; k < p; k += G) X_(k) = exp(-dt * (D_(k) - lmin)) * (double)S_(k, 0) / X_(k);
+  __syncwarp(gm);
+  for (int i = gl; i < p; i += G) {
+    double acc = 0.0;
+    for (int k = 0; k < p; ++k) acc = fma((double)S_(k, i), X_(k), acc);
+    Y_(i) = acc;
+  }
+  logfac = -dt * lmin;
+  __syncwarp(gm);
+#undef A_
+#undef B_
+#undef D_
+#undef X_
+#undef Y_
+#undef S_
+}
+
+struct ItemAcc {
+  unsigned long long ops, intervals, iters, pmax, noconv, flops_vec, flops_tri, bytes_apply;
+};
+
+// Per-group context of one work unit (half of a (walker, kept state) item).
+template <typename VT, int G, int DMAX, int PMAX>
+struct Unit {
+  static constexpr int IPW = 32 / G;
+  static constexpr int R = (DMAX + G - 1) / G;  // rows per lane
+  WarpTile<VT, G, DMAX, PMAX> &s;
+  int grp, gl;
+  unsigned gm;
+  int b, dim;
+  double Ladd;    // additive part of the log-weight
+  LogScale Linv;  // product of the normalisation factors applied
+  int status;
+  ItemAcc acc;
+  __device__ __forceinline__ VT &Q(int j, int r) { return s.q[((j) * DMAX + (r)) * IPW + grp]; }
+};
+
+// Step 4: apply c_f (dag = 0) or c_f^+ (dag = 1) to the unit's vector q_0:
+// a gather with the Jordan-Wigner sign into the target block, then
+// normalisation. False if the result is exactly zero.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ bool apply_op(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, int f, int dag) {
+  constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
+  const int nf = M.nf;
+  const int b2 = __ldg(M.blk_target + ((size_t)u.b * nf + f) * 2 + dag);
+  if (b2 < 0) return false;
+  const int off2 = __ldg(M.blk_off + b2), dim2 = __ldg(M.blk_dim + b2);
+  VT tv[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = u.gl + G * j;
+    VT v = VT(0);
+    if (r < dim2) {
+      const int g = off2 + r;
+      const int x = __ldg(M.st_bits + g);
+      if (((x >> f) & 1) == dag) {
+        const unsigned pe = __ldg(M.partner + (size_t)g * nf + f);
+        v = u.Q(0, pe & 0x7fffu);
+        if (pe & 0x8000u) v = -v;
+      }
+    }
+    tv[j] = v;
+  }
+  u.acc.ops += 1;
+  u.acc.flops_vec += 3ull * dim2;
+  u.acc.bytes_apply += (unsigned long long)dim2 * (2 * sizeof(VT) + 4);
+  if (!normalize_rows<VT, G, R>(tv, u.gl, dim2, u.gm, u.Linv)) return false;
+  __syncwarp(u.gm);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = u.gl + G * j;
+    if (r < dim2) u.Q(0, r) = tv[j];
+  }
+  __syncwarp(u.gm);
+  u.b = b2;
+  u.dim = dim2;
+  return true;
+}
+
+// Step 5: q_0 <- exp(-dt (H_b - E0)) q_0 by Lanczos on H_b - s_b with the
+// a-posteriori stop; the scalars taken out go to the log-weight.
+// False if the propagated vector is exactly zero.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double dt, bool with_stats) {
+  constexpr bool F32 = sizeof(VT) == 4;
+  constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
+  constexpr int IPW = 32 / G;
+  auto &s = u.s;
+  const int grp = u.grp, gl = u.gl;
+  const unsigned gm = u.gm;
+#define A_(k) s.a[(k) * IPW + grp]
+#define B_(k) s.b[(k) * IPW + grp]
+#define Y_(k) s.y[(k) * IPW + grp]
+  const VT *__restrict__ tdiag = Tab<VT>::diag(M);
+  const VT *__restrict__ tval = Tab<VT>::val(M);
+  const int b = u.b, dim = u.dim;
+  const int off = __ldg(M.blk_off + b), wid = __ldg(M.blk_nnz + b), ell = __ldg(M.blk_ell + b);
+  const double shift = __ldg(M.blk_shift + b);
+  const double brk = M.brk_rel * fmax(__ldg(M.blk_norm + b), 1e-300);
+  const int pcap = min(dim, M.pmax);
+  const float tol32 = F32 ? (float)(0.5 * M.tol) : 0.f;  // safety factor 2 on FP32 estimates
+  VT qc[R], qp[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = gl + G * j;
+    qc[j] = (r < dim) ? u.Q(0, r) : VT(0);
+    qp[j] = VT(0);
+  }
+  double bprev = 0.0, logfac = 0.0;
+  int p = 0;
+  bool conv = false, exact = false;
+  for (int jj = 0; jj < pcap; ++jj) {
+    VT wv[R];
+    GroupDot<VT, G> da;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = gl + G * j;
+      VT a = VT(0);
+      if (r < dim) {
+        a = __ldg(tdiag + off + r) * qc[j];
+        for (int k = 0; k < wid; ++k) {
+          const int col = __ldg(M.ell_col + ell + k * dim + r);
+          if (col >= 0) a += __ldg(tval + ell + k * dim + r) * u.Q(jj, col);
+        }
+        da.add(a, qc[j]);
+      }
+      wv[j] = a;
+    }
+    const double al = da.value(gm);
+    const VT alv = VT(al), bpv = VT(bprev);
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (gl + G * j < dim) wv[j] = wv[j] - alv * qc[j] - bpv * qp[j];
+    if constexpr (F32) {
+      // one pass of full reorthogonalisation against q_0 .. q_jj
+      for (int k = 0; k <= jj && jj > 0; ++k) {
+        VT h = VT(0);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int r = gl + G * j;
+          if (r < dim) h += u.Q(k, r) * wv[j];
+        }
+        h = gsum<G>(h, gm);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int r = gl + G * j;
+          if (r < dim) wv[j] -= h * u.Q(k, r);
+        }
+      }
+    }
+    GroupDot<VT, G> db;
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (gl + G * j < dim) db.add(wv[j], wv[j]);
+    const double bb = db.norm(gm);
+    p = jj + 1;
+    if (gl == 0) {
+      A_(jj) = al;
+      B_(jj) = bb;
+    }
+    __syncwarp(gm);
+    exact = (p == dim) || !(bb > brk);
+    bool stop = exact;
+    if (!exact) {
+      if constexpr (F32) {
+        float yn, yl;
+        tri_check32(s, grp, gl, gm, p, dt, yn, yl);
+        stop = (float)bb * yl <= tol32 * yn;
+      } else {
+        if (!tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
+        double yn = 0.0;
+        for (int k = gl; k < p; k += G) yn = fma(Y_(k), Y_(k), yn);
+        yn = sqrt(gsum<G>(yn, gm));
+        stop = bb * fabs(Y_(p - 1)) <= M.tol * yn;
+      }
+    }
+    if (stop) {
+      conv = true;
+      break;
+    }
+    if (p == pcap) break;
+    const VT ib = VT(1) / VT(bb);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = gl + G * j;
+      qp[j] = qc[j];
+      qc[j] = wv[j] * ib;
+      if (r < dim) u.Q(jj + 1, r) = qc[j];
+    }
+    bprev = bb;
+    __syncwarp(gm);
+  }
+  if (!conv) {
+    u.acc.noconv += 1;
+    if (u.status == KT_OK) u.status = KT_ENOCONV;
+  }
+  // final exp(-dt T_p) e_1 at the stopping p
+  if constexpr (F32) {
+    if (p <= 2) {
+      tri_small64(s, grp, gl, gm, p, dt, logfac);
+    } else {
+      if (exact || !conv) {
+        float yn, yl;
+        tri_check32(s, grp, gl, gm, p, dt, yn, yl);  // Ritz pairs of T_p (unless the last check made them)
+      }
+      tri_final32(s, grp, gl, gm, p, dt, logfac);
+    }
+  } else {
+    if (exact && !tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
+  }
+  // v = sum_j y_j q_j, renormalised; what is taken out goes to the log-weight
+  VT vv[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = gl + G * j;
+    VT a = VT(0);
+    if (r < dim)
+      for (int k = 0; k < p; ++k) a += VT(Y_(k)) * u.Q(k, r);
+    vv[j] = a;
+  }
+  if (!normalize_rows<VT, G, R>(vv, gl, dim, gm, u.Linv)) return false;
+  u.Ladd += logfac - dt * (shift - M.E0);
+  __syncwarp(gm);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = gl + G * j;
+    if (r < dim) u.Q(0, r) = vv[j];
+  }
+  __syncwarp(gm);
+  u.acc.intervals += 1;
+  u.acc.iters += p;
+  u.acc.pmax = u.acc.pmax > (unsigned long long)p ? u.acc.pmax : (unsigned long long)p;
+  if (with_stats) {
+    u.acc.flops_tri += (p <= 2) ? 30ull : (unsigned long long)(12 * p * p * p + 40 * p);
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = gl + G * j;
+      if (r < dim) {
+        cnt += 1;
+        for (int k = 0; k < wid; ++k) cnt += (__ldg(M.ell_col + ell + k * dim + r) >= 0);
+      }
+    }
+    const int nnz_blk = gsum<G>(cnt, gm);
+    u.acc.flops_vec += (unsigned long long)p * (2ull * nnz_blk + 9ull * dim) + 2ull * p * dim + 3ull * dim;
+    if (F32) u.acc.flops_vec += (unsigned long long)p * (p - 1) * 2ull * dim;  // reorthogonalisation
+  }
+  return true;
+#undef A_
+#undef B_
+#undef Y_
+}
+
+// Work units: every alive (walker, kept state) item is split at the middle of
+// its sequence into a forward unit (ops 0 .. m-1 acting on |n>, Sec. III step 3
+// "forward") and a backward unit (the adjoints of ops K-1 .. m acting on <n|,
+// "backward", including the interval between ops m-1 and m). Each unit
+// publishes its normalised vector and log-weight to the workspace; whichever
+// finishes second forms the overlap <backward|forward>. No unit ever waits.
+template <typename VT, int G, int DMAX, int PMAX>
+__global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, Workspace ws,
+                                                    kt_stats *stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int R = (DMAX + G - 1) / G;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane % G;
+  const unsigned gm = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
+  WarpTile<VT, G, DMAX, PMAX> &tile = reinterpret_cast<WarpTile<VT, G, DMAX, PMAX> *>(smem_raw)[wib];
+  const VT *__restrict__ tkept = Tab<VT>::kept(M);
+  const int n_units = 2 * ws.counters[0];
+  const int nk = M.n_kept;
+  const int vstride = M.d_max;
+  VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
+
+  for (;;) {
+    int uix = 0;
+    if (gl == 0) uix = atomicAdd(&ws.counters[1], 1);
+    uix = __shfl_sync(gm, uix, grp * G);
+    if (uix >= n_units) break;
+    const int it = uix >> 1, half = uix & 1;
+    const int item = ws.worklist[it];
+    const int w = item / nk, q = item - w * nk;
+    const Cursor cur = make_cursor(S, mv, has_moves != 0, ws.desc, w);
+    const int Kn = cur.d.w;
+    const int b_kept = __ldg(M.kept_blk + q);
+    const double Ek = __ldg(M.kept_e + q);
+    const int koff = __ldg(M.kept_off + q);
+    if (Kn == 0) {  // empty sequence: the kept state alone, no split
+      if (half == 0 && gl == 0) {
+        ws.item_sign[item] = 1;
+        ws.item_log[item] = -M.beta * Ek;
+        ws.item_status[item] = KT_OK;
+      }
+      continue;
+    }
+    Unit<VT, G, DMAX, PMAX> u{tile, grp, gl, gm, b_kept, __ldg(M.blk_dim + b_kept), 0.0, LogScale(), KT_OK, ItemAcc{}};
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = gl + G * j;
+      if (r < u.dim) u.Q(0, r) = __ldg(tkept + koff + r);
+    }
+    __syncwarp(gm);
+    const int m = Kn / 2 > 1 ? Kn / 2 : 1;
+    bool vanished = false;
+    // forward: ops 0 .. m-1 in order; backward: adjoints of ops K-1 .. m, each
+    // followed by the interval down to the previous operator (the last one
+    // bridges to op m-1)
+    const int nsteps = half == 0 ? m : Kn - m;
+    Op op = cur.get(half == 0 ? 0 : Kn - 1);
+    u.Ladd = half == 0 ? -op.t * Ek : -(M.beta - op.t) * Ek;  // |n> is an eigenstate at both ends
+    for (int s = 0; s < nsteps; ++s) {
+      const int idx = half == 0 ? s : Kn - 1 - s;
+      if (!apply_op(M, u, op.f, half == 0 ? op.dag : 1 - op.dag)) {
+        vanished = true;
+        break;
+      }
+      if (half == 0 && s + 1 >= m) break;
+      const Op nx = cur.get(half == 0 ? idx + 1 : idx - 1);
+      const double dt = half == 0 ? nx.t - op.t : op.t - nx.t;
+      op = nx;
+      if (dt > 0.0 && !propagate(M, u, dt, stats != nullptr)) {
+        vanished = true;
+        break;
+      }
+    }
+    // publish this half
+    const int hslot = 2 * item + half;
+    if (!vanished) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int r = gl + G * j;
+        if (r < u.dim) hvec[(size_t)hslot * vstride + r] = u.Q(0, r);
+      }
+    }
+    const double Lh = vanished ? 0.0 : u.Ladd - u.Linv.log_value();
+    if (gl == 0) {
+      ws.half_log[hslot] = Lh;
+      ws.half_info[hslot] = vanished ? -1 : (u.b | (u.status << 24));
+    }
+    __threadfence();
+    __syncwarp(gm);
+    int old = 0;
+    if (gl == 0) old = atomicAdd(&ws.pair_flag[item], 1);
+    old = __shfl_sync(gm, old, grp * G);
+    if (old == 1) {
+      // the other half is published: form the overlap
+      __threadfence();
+      const int oslot = 2 * item + (1 - half);
+      const int oinfo = __ldcg(ws.half_info + oslot);
+      const double Lo = __ldcg(ws.half_log + oslot);
+      bool zero = vanished || oinfo < 0 || (oinfo & 0xffffff) != u.b;
+      double ov = 0.0;
+      if (!zero) {
+        GroupDot<VT, G> d;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int r = gl + G * j;
+          if (r < u.dim) d.add(u.Q(0, r), __ldcg(hvec + (size_t)oslot * vstride + r));
+        }
+        ov = d.value(gm);
+        zero = (ov == 0.0);
+      }
+      int st = u.status;
+      if (oinfo >= 0 && (oinfo >> 24) > st) st = oinfo >> 24;
+      const double L = Lh + Lo + (zero ? 0.0 : log(fabs(ov)));
+      if (!zero && !isfinite(L)) st = KT_ENUMERIC;
+      if (gl == 0) {
+        ws.item_sign[item] = zero ? 0 : (ov > 0.0 ? 1 : -1);
+        ws.item_log[item] = zero ? -INFINITY : L;
+        ws.item_status[item] = st;
+      }
+    }
+    if (gl == 0 && stats) {
+      if (old == 1 && ws.item_sign[item] == 0) atomicAdd(&stats->items_vanished, 1ull);
+      stat_add(&stats->ops_applied, u.acc.ops);
+      stat_add(&stats->intervals, u.acc.intervals);
+      stat_add(&stats->krylov_iters, u.acc.iters);
+      if (u.acc.pmax) atomicMax(&stats->p_max, u.acc.pmax);
+      stat_add(&stats->noconv, u.acc.noconv);
+      stat_add(&stats->flops_vec, u.acc.flops_vec);
+      stat_add(&stats->flops_tri, u.acc.flops_tri);
+      stat_add(&stats->bytes_apply, u.acc.bytes_apply);
+    }
+    __syncwarp(gm);
+  }
+}
+
+// launch helpers
+template <typename VT, int G, int DMAX, int PMAX>
+int launch_items(const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves, const Workspace &ws,
+                 kt_stats *stats, cudaStream_t st) {
+  using Tile = WarpTile<VT, G, DMAX, PMAX>;
+  static int cached_grid = 0, cached_wpb = 0;
+  if (cached_grid == 0) {
+    int wpb = (int)((200 * 1024) / sizeof(Tile));
+    wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
+    const size_t smem = (size_t)wpb * sizeof(Tile);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(items_kernel<VT, G, DMAX, PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, items_kernel<VT, G, DMAX, PMAX>, wpb * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    cached_wpb = wpb;
+    cached_grid = sms * per_sm;
+  }
+  const size_t smem = (size_t)cached_wpb * sizeof(Tile);
+  items_kernel<VT, G, DMAX, PMAX><<<cached_grid, cached_wpb * 32, smem, st>>>(M, S, mv, has_moves, ws, stats);
+  return (int)cudaGetLastError();
+}
+
+
+template <typename VT>
+int dispatch_items(int kd, int G, const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves,
+                   const Workspace &ws, kt_stats *stats, cudaStream_t st) {
+#define KT_CASE(D, P, GG) \
+  if (kd == D && G == GG) return launch_items<VT, GG, D, P>(M, S, mv, has_moves, ws, stats, st);
+  KT_FOR_VARIANTS(KT_CASE)
+#undef KT_CASE
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace dev
+}  // namespace kt

@@ -121,7 +121,7 @@ static void timing_release(kt_model *m) {
 
 namespace kt {
 
-size_t workspace_bytes(int n, int n_kept) {
+size_t workspace_bytes(int n, int n_kept, int d_max) {
   const size_t items = (size_t)n * (size_t)n_kept;
   size_t b = 0;
   b += align_up(4 * sizeof(int32_t), 256);
@@ -131,10 +131,14 @@ size_t workspace_bytes(int n, int n_kept) {
   b += align_up(items * sizeof(int8_t), 256);
   b += align_up(items * sizeof(double), 256);
   b += align_up(items * sizeof(int32_t), 256);
+  b += align_up(items * sizeof(int32_t), 256);
+  b += align_up(2 * items * sizeof(double), 256);
+  b += align_up(2 * items * sizeof(int32_t), 256);
+  b += align_up(2 * items * (size_t)d_max * sizeof(double), 256);
   return b;
 }
 
-Workspace carve_workspace(void *base, int n, int n_kept) {
+Workspace carve_workspace(void *base, int n, int n_kept, int d_max) {
   const size_t items = (size_t)n * (size_t)n_kept;
   char *p = (char *)base;
   Workspace w;
@@ -144,7 +148,11 @@ Workspace carve_workspace(void *base, int n, int n_kept) {
   w.worklist = (int32_t *)p; p += align_up(items * sizeof(int32_t), 256);
   w.item_sign = (int8_t *)p; p += align_up(items * sizeof(int8_t), 256);
   w.item_log = (double *)p; p += align_up(items * sizeof(double), 256);
-  w.item_status = (int32_t *)p;
+  w.item_status = (int32_t *)p; p += align_up(items * sizeof(int32_t), 256);
+  w.pair_flag = (int32_t *)p; p += align_up(items * sizeof(int32_t), 256);
+  w.half_log = (double *)p; p += align_up(2 * items * sizeof(double), 256);
+  w.half_info = (int32_t *)p; p += align_up(2 * items * sizeof(int32_t), 256);
+  w.half_vec = (void *)p;
   return w;
 }
 
@@ -502,7 +510,7 @@ void kt_model_destroy(kt_model *m) {
 
 kt_status kt_workspace_size(const kt_model *m, int32_t n, size_t *bytes) {
   if (!m || !bytes || n < 0) return KT_EINVAL;
-  *bytes = kt::workspace_bytes(n, m->dev.n_kept);
+  *bytes = kt::workspace_bytes(n, m->dev.n_kept, m->dev.d_max);
   return KT_OK;
 }
 
@@ -514,11 +522,11 @@ static kt_status run(kt_model *m, const kt_seq_batch *b, const kt_move_batch *mv
   if (!sign || !logv || !status || !b->offsets || !ws) return KT_EINVAL;
   if (mv && (!mv->kind || !mv->flavor || !mv->t_dag || !mv->t_ann || !mv->rem_idx || !cur_sign || !cur_logabs))
     return KT_EINVAL;
-  if (ws_bytes < kt::workspace_bytes(b->n, m->dev.n_kept)) return KT_ENOMEM;
+  if (ws_bytes < kt::workspace_bytes(b->n, m->dev.n_kept, m->dev.d_max)) return KT_ENOMEM;
   kt::SeqView sv{b->n, b->offsets, b->tau, b->flavor, b->dagger};
   kt::MoveView mvv{};
   if (mv) mvv = kt::MoveView{mv->kind, mv->flavor, mv->t_dag, mv->t_ann, mv->rem_idx};
-  kt::Workspace w = kt::carve_workspace(ws, b->n, m->dev.n_kept);
+  kt::Workspace w = kt::carve_workspace(ws, b->n, m->dev.n_kept, m->dev.d_max);
   const kt::StageEvents *tev = nullptr;
   if (m->timing_on && m->timing_used < (int)m->timing.size()) tev = &m->timing[m->timing_used++];
   const int rc = kt::launch_pipeline(m->dev, m->params.precision, m->kernel_dmax, m->group_lanes, sv,

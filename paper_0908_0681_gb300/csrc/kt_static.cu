@@ -63,13 +63,13 @@ extern "C" kt_status kt_trace_ratio_static(kt_model *m, const kt_seq_batch *cur,
   if (!sign || !logratio || !status || !cur->offsets || !cur_sign || !cur_logabs || !moves->kind || !moves->flavor ||
       !moves->t_dag || !moves->t_ann || !moves->rem_idx)
     return KT_EINVAL;
-  if (kt::workspace_bytes(cur->n, v.dev->n_kept) > (size_t)KT_STATIC_SCRATCH_BYTES) return KT_ENOMEM;
+  if (kt::workspace_bytes(cur->n, v.dev->n_kept, v.dev->d_max) > (size_t)KT_STATIC_SCRATCH_BYTES) return KT_ENOMEM;
   void *scratch = nullptr;
   const kt_status rc = scratch_address(&scratch);
   if (rc != KT_OK) return rc;
   kt::SeqView sv{cur->n, cur->offsets, cur->tau, cur->flavor, cur->dagger};
   kt::MoveView mv{moves->kind, moves->flavor, moves->t_dag, moves->t_ann, moves->rem_idx};
-  const kt::Workspace w = kt::carve_workspace(scratch, cur->n, v.dev->n_kept);
+  const kt::Workspace w = kt::carve_workspace(scratch, cur->n, v.dev->n_kept, v.dev->d_max);
   const int e = kt::launch_pipeline(*v.dev, v.precision, v.kernel_dmax, v.group_lanes, sv, &mv, cur_sign, cur_logabs,
                                     sign, logratio, status, stats, w, stream, nullptr);
   return e == 0 ? KT_OK : KT_ECUDA;

@@ -242,20 +242,20 @@ def test_full_batch_sampled(prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_every_tiling_matches_oracle(five, prec):
-    """Each compiled lane-group size G gives oracle-parity results (and G = 32 and G = 1
-    agree to rounding)."""
+    """Each compiled lane-group size G gives oracle-parity results (and G = 4 and G = 32
+    agree in sign)."""
     w, seqs, o64, ox, cls, sx, lx = five
     sub = seqs.subset(range(160))
     m = engine.model_from_spec(w.model, precision=prec)
     outs = {}
-    for g in (1, 2, 4, 8, 16, 32):
+    for g in (4, 8, 16, 32):
         kt.kt_model_set_tiling(m, g)
         assert kt.kt_model_query(m)["group_lanes"] == g
         s, l, st = gpu_trace(m, sub)
         assert (st == kt.KT_OK).all()
         parity.compare(cls[:160], sx[:160], lx[:160], s, l, prec, ox.nkept, w.model.beta * ox.E0, f"G={g}")
         outs[g] = (s, l)
-    assert (outs[1][0] == outs[32][0]).all()
+    assert (outs[4][0] == outs[32][0]).all()
     with pytest.raises(kt.KtError):
         kt.kt_model_set_tiling(m, 3)
 
@@ -269,6 +269,6 @@ def test_autotune_picks_a_compiled_tiling(five):
     l = torch.empty(n, dtype=torch.float64, device="cuda")
     st = torch.empty(n, dtype=torch.int32, device="cuda")
     g = kt.kt_autotune(m, d.batch(), s, l, st, engine.workspace(m, n))
-    assert g in (1, 2, 4, 8, 16, 32) and kt.kt_model_query(m)["group_lanes"] == g
+    assert g in (4, 8, 16, 32) and kt.kt_model_query(m)["group_lanes"] == g
     s2, l2, st2 = gpu_trace(m, seqs)
     parity.compare(cls, sx, lx, s2, l2, kt.KT_FP32_KRYLOV, ox.nkept, w.model.beta * ox.E0, "autotuned")
