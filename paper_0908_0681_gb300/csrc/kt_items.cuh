@@ -136,16 +136,24 @@ __device__ __forceinline__ void givens(R x, R z, R &c, R &s, R &r) {
 }
 
 // Product of positive factors kept as mantissa * 2^exponent (no log per step).
+// The mantissa is renormalised into [1, 2) by editing its exponent bits.
 struct LogScale {
   double m = 1.0;
   int e = 0;
   __device__ __forceinline__ void mul(double f) {
-    int k;
-    m = frexp(m * f, &k);
-    e += k;
+    const long long bits = __double_as_longlong(m * f);
+    e += (int)((bits >> 52) & 0x7ff) - 1023;
+    m = __longlong_as_double((bits & 0x800fffffffffffffLL) | 0x3ff0000000000000LL);
   }
   __device__ __forceinline__ double log_value() const { return log(m) + (double)e * 0.69314718055994530942; }
 };
+
+// Exact power of two 2^-floor(log2 m) for a positive finite m (normal or not).
+__device__ __forceinline__ float pow2_inv(float m) {
+  if (m >= 1.17549435e-38f) return __int_as_float((254 - ((__float_as_int(m) >> 23) & 0xff)) << 23);
+  return scalbnf(1.f, -ilogbf(m));
+}
+__device__ __forceinline__ double pow2_inv(double m) { return scalbn(1.0, -ilogb(m)); }
 
 // Scale the item's rows v to unit norm: an exact power-of-two prescale brings
 // the largest entry to [1, 2), then rsqrt of the sum of squares; the factor
@@ -159,7 +167,7 @@ __device__ __forceinline__ bool normalize_rows(VT (&v)[R], int gl, int dim, unsi
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(gm, m, o));
   if (!(m > VT(0))) return false;
-  const VT s1 = scalbn(VT(1), -ilogb(m));
+  const VT s1 = pow2_inv(m);
   VT n2 = VT(0);
 #pragma unroll
   for (int j = 0; j < R; ++j)
@@ -257,20 +265,31 @@ __device__ __forceinline__ R exp2x2(R a, R c, R b, R dt, R &y0, R &y1) {
   return -dt * (m - r);
 }
 
-// FP64 y for p <= 2 (closed forms), used by the FP32 path.
+// FP32 path, p <= 2. The Ritz values and the scale exp(-dt lambda_min) (kept
+// in log space) are FP64; the relative weights exp(-dt (lambda - lambda_min))
+// in (0, 1] and y are formed in FP32, the precision of the Krylov vectors they
+// multiply. y lands in y32.
 template <typename VT, int G, int DMAX, int PMAX>
-__device__ __forceinline__ void tri_small64(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p,
-                                            double dt, double &logfac) {
+__device__ __forceinline__ void tri_small_f32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p,
+                                              double dt, double &logfac) {
   constexpr int IPW = 32 / G;
-  double y0 = 1.0, y1 = 0.0;
+  float y0 = 1.f, y1 = 0.f;
   if (p == 1) {
     logfac = -dt * s.a[grp];
   } else {
-    logfac = exp2x2(s.a[grp], s.a[IPW + grp], s.b[grp], dt, y0, y1);
+    const double a = s.a[grp], c = s.a[IPW + grp], b = s.b[grp];
+    const double m = 0.5 * (a + c), h = 0.5 * (a - c);
+    const double r = sqrt(h * h + b * b);
+    logfac = -dt * (m - r);
+    const float x = (float)(2.0 * dt * r);  // dt (lambda_+ - lambda_-)
+    const float E = expf(-x);
+    const float g = (x > 1e-3f) ? (1.f - E) / (float)(2.0 * r) : (float)dt * (1.f - 0.5f * x);
+    y0 = 0.5f * (1.f + E) - g * (float)h;
+    y1 = -g * (float)b;
   }
   if (gl == 0) {
-    s.y[grp] = y0;
-    s.y[IPW + grp] = y1;
+    s.y32[grp] = y0;
+    s.y32[IPW + grp] = y1;
   }
   __syncwarp(gm);
 }
@@ -386,10 +405,11 @@ __device__ void tri_check32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
 }
 
 // FP32-path final step (p >= 3): every Ritz value is recomputed in FP64 as the
-// Rayleigh quotient of its FP32 Ritz vector with the FP64 T_p (its error is
-// quadratic in the vector's, ~1e-14), the exponentials and the assembly of
-// y = sum_k s_k s_k[0] exp(-dt (lambda_k - lambda_min)) / |s_k|^2 run in FP64,
-// one Ritz pair per lane. lambda_min enters the log-weight.
+// Rayleigh quotient of its FP32 Ritz vector with the FP64 T_p (the error is
+// quadratic in the vector's, ~1e-14); lambda_min enters the log-weight in
+// FP64. The relative weights exp(-dt (lambda_k - lambda_min)) in (0, 1] and
+// y = sum_k s_k s_k[0] w_k / |s_k|^2 are formed in FP32 (one Ritz pair per
+// lane), the precision of the Krylov vectors they multiply. y lands in y32.
 template <typename VT, int G, int DMAX, int PMAX>
 __device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
                             double &logfac) {
@@ -397,33 +417,51 @@ __device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
 #define A_(k) s.a[(k) * IPW + grp]
 #define B_(k) s.b[(k) * IPW + grp]
 #define D_(k) s.dd[(k) * IPW + grp]
-#define X_(k) s.ex[(k) * IPW + grp]
-#define Y_(k) s.y[(k) * IPW + grp]
+#define X_(k) s.x32[(k) * IPW + grp]
+#define Y_(k) s.y32[(k) * IPW + grp]
 #define S_(k, i) s.S32[((k) * PMAX + (i)) * IPW + grp]
-  double lmin = INFINITY;
+  // lane-local Ritz pair k: FP64 Rayleigh quotient
+  float lmin32 = INFINITY;
+  int kmin = 0;
   for (int k = gl; k < p; k += G) {
-    double num = 0.0, den = 0.0;
+    double num = 0.0, den = 0.0, sprev = 0.0, scur = (double)S_(k, 0);
     for (int i = 0; i < p; ++i) {
-      const double si = S_(k, i);
-      double ti = A_(i) * si;
-      if (i > 0) ti = fma(B_(i - 1), (double)S_(k, i - 1), ti);
-      if (i + 1 < p) ti = fma(B_(i), (double)S_(k, i + 1), ti);
-      num = fma(si, ti, num);
-      den = fma(si, si, den);
+      const double snext = (i + 1 < p) ? (double)S_(k, i + 1) : 0.0;
+      double ti = A_(i) * scur;
+      if (i > 0) ti = fma(B_(i - 1), sprev, ti);
+      if (i + 1 < p) ti = fma(B_(i), snext, ti);
+      num = fma(scur, ti, num);
+      den = fma(scur, scur, den);
+      sprev = scur;
+      scur = snext;
     }
-    const double lam = num / den;
+    const double r0 = (double)(1.f / (float)den);
+    const double inv = r0 * fma(-den, r0, 2.0);  // one Newton step: 1/den to ~1e-14
+    const double lam = num * inv;
     D_(k) = lam;
-    X_(k) = den;
-    lmin = fmin(lmin, lam);
+    X_(k) = (float)inv;
+    if ((float)lam < lmin32) {
+      lmin32 = (float)lam;
+      kmin = k;
+    }
   }
+  // smallest Ritz value: argmin in FP32, its FP64 value from the owning lane
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) lmin = fmin(lmin, __shfl_xor_sync(gm, lmin, o));
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const float ol = __shfl_xor_sync(gm, lmin32, o);
+    const int ok = __shfl_xor_sync(gm, kmin, o);
+    if (ol < lmin32 || (ol == lmin32 && ok < kmin)) {
+      lmin32 = ol;
+      kmin = ok;
+    }
+  }
   __syncwarp(gm);
-  for (int k = gl; k < p; k += G) X_(k) = exp(-dt * (D_(k) - lmin)) * (double)S_(k, 0) / X_(k);
+  const double lmin = D_(kmin);
+  for (int k = gl; k < p; k += G) X_(k) = expf(-(float)(dt * (D_(k) - lmin))) * S_(k, 0) * X_(k);
   __syncwarp(gm);
   for (int i = gl; i < p; i += G) {
-    double acc = 0.0;
-    for (int k = 0; k < p; ++k) acc = fma((double)S_(k, i), X_(k), acc);
+    float acc = 0.f;
+    for (int k = 0; k < p; ++k) acc = fmaf(S_(k, i), X_(k), acc);
     Y_(i) = acc;
   }
   logfac = -dt * lmin;
@@ -618,7 +656,7 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
   // final exp(-dt T_p) e_1 at the stopping p
   if constexpr (F32) {
     if (p <= 2) {
-      tri_small64(s, grp, gl, gm, p, dt, logfac);
+      tri_small_f32(s, grp, gl, gm, p, dt, logfac);
     } else {
       if (exact || !conv) {
         float yn, yl;
@@ -635,8 +673,13 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
   for (int j = 0; j < R; ++j) {
     const int r = gl + G * j;
     VT a = VT(0);
-    if (r < dim)
-      for (int k = 0; k < p; ++k) a += VT(Y_(k)) * u.Q(k, r);
+    if (r < dim) {
+      if constexpr (F32) {
+        for (int k = 0; k < p; ++k) a += s.y32[k * IPW + grp] * u.Q(k, r);
+      } else {
+        for (int k = 0; k < p; ++k) a += Y_(k) * u.Q(k, r);
+      }
+    }
     vv[j] = a;
   }
   if (!normalize_rows<VT, G, R>(vv, gl, dim, gm, u.Linv)) return false;

@@ -25,6 +25,7 @@ def main():
     p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--flags", type=int, default=0)
+    p.add_argument("--group-lanes", type=int, default=0, help="lanes per item (0: the model default)")
     a = p.parse_args()
     import torch
 
@@ -35,6 +36,8 @@ def main():
     moves = [engine.DeviceMoves.from_host(workloads.generate_moves(w, seqs, seed=1000 + r)) for r in range(a.launches)]
     prec = kt.KT_FP32_KRYLOV if a.precision == "fp32" else kt.KT_FP64
     m = engine.model_from_spec(w.model, precision=prec, flags=a.flags)
+    if a.group_lanes:
+        kt.kt_model_set_tiling(m, a.group_lanes)
     d = engine.DeviceSeqs.from_host(seqs)
     ws = engine.workspace(m, seqs.n)
     cs, cl, st = engine.trace(m, d, ws=ws)
