@@ -74,6 +74,11 @@ typedef struct {
   real **H;      /* [nsec] dense d x d, row-major */
   real **V;      /* [nsec] eigenvectors, column j = eigenvector j, row-major */
   real **w;      /* [nsec] eigenvalues ascending */
+  /* per sector: connected components of H's nonzero pattern; V is block
+   * diagonal in them. Component c owns rows comp_rows[s][crow_off[s][c] ..]
+   * and eigenvector columns comp_cols[s][crow_off[s][c] ..]. */
+  int *ncomp;
+  int **crow_off, **comp_rows, **comp_cols;
   real E0, beta;
   int nkept;
   int *kept_sec, *kept_col; /* kept eigenstates: sector and eigenvector column */
@@ -258,7 +263,8 @@ static int sym_eig(int d, real *A, real *w, real *Q) {
  * components. (A joint FP64 decomposition would couple the decoupled
  * components at rounding level, and exp(dtau dE) growth over an imaginary-time
  * path can amplify that coupling beyond the true trace.) */
-static int sector_eig(int d, const real *H, real *w, real *V) {
+static int sector_eig(int d, const real *H, real *w, real *V, int *ncomp_out, int **off_out, int **rows_out,
+                      int **cols_out) {
   int *comp = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
   int *stack = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
   int *idx = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
@@ -267,8 +273,12 @@ static int sector_eig(int d, const real *H, real *w, real *V) {
   real *Q = (real *)malloc(sizeof(real) * (size_t)(d * d > 0 ? d * d : 1));
   int *perm = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
   real *Vt = (real *)malloc(sizeof(real) * (size_t)(d * d > 0 ? d * d : 1));
+  int *col_comp = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
+  int *off = (int *)calloc((size_t)d + 2, sizeof(int));
+  int *rows = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
+  int *cols = (int *)malloc(sizeof(int) * (size_t)(d > 0 ? d : 1));
   int rc = OR_OK;
-  if (!comp || !stack || !idx || !wv || !A || !Q || !perm || !Vt) rc = OR_ENOMEM;
+  if (!comp || !stack || !idx || !wv || !A || !Q || !perm || !Vt || !col_comp || !off || !rows || !cols) rc = OR_ENOMEM;
   int ncomp = 0, col = 0;
   if (rc == OR_OK) {
     for (int i = 0; i < d; ++i) comp[i] = -1;
@@ -295,6 +305,7 @@ static int sector_eig(int d, const real *H, real *w, real *V) {
       rc = sym_eig(n, A, wv, Q);
       for (int k = 0; k < n && rc == OR_OK; ++k, ++col) {
         w[col] = wv[k];
+        col_comp[col] = ncomp;
         for (int a = 0; a < n; ++a) Vt[idx[a] * d + col] = Q[a * n + k];
       }
       ++ncomp;
@@ -312,8 +323,21 @@ static int sector_eig(int d, const real *H, real *w, real *V) {
       w[j] = wv[j];
       for (int i = 0; i < d; ++i) V[i * d + j] = Vt[i * d + perm[j]];
     }
+    /* component CSR: rows in ascending order, columns in eigenvalue order */
+    for (int i = 0; i < d; ++i) off[comp[i] + 1]++;
+    for (int c = 0; c < ncomp; ++c) off[c + 1] += off[c];
+    int *fill = stack; /* reuse as a cursor array */
+    for (int c = 0; c < ncomp; ++c) fill[c] = off[c];
+    for (int i = 0; i < d; ++i) rows[fill[comp[i]]++] = i;
+    for (int c = 0; c < ncomp; ++c) fill[c] = off[c];
+    for (int j = 0; j < d; ++j) cols[fill[col_comp[perm[j]]]++] = j;
   }
-  free(comp); free(stack); free(idx); free(wv); free(A); free(Q); free(perm); free(Vt);
+  free(comp); free(stack); free(idx); free(wv); free(A); free(Q); free(perm); free(Vt); free(col_comp);
+  if (rc == OR_OK) {
+    *ncomp_out = ncomp; *off_out = off; *rows_out = rows; *cols_out = cols;
+  } else {
+    free(off); free(rows); free(cols);
+  }
   return rc;
 }
 
@@ -324,6 +348,9 @@ void FN(model_free)(void *hm) {
   if (!m) return;
   if (m->H) for (int s = 0; s < m->nsec; ++s) { free(m->H[s]); free(m->V[s]); free(m->w[s]); }
   free(m->H); free(m->V); free(m->w);
+  if (m->crow_off)
+    for (int s = 0; s < m->nsec; ++s) { free(m->crow_off[s]); free(m->comp_rows[s]); free(m->comp_cols[s]); }
+  free(m->ncomp); free(m->crow_off); free(m->comp_rows); free(m->comp_cols);
   free(m->sec_of); free(m->rank); free(m->sec_dim); free(m->sec_off); free(m->states);
   free(m->kept_sec); free(m->kept_col); free(m->kept_E);
   free(m);
@@ -349,7 +376,12 @@ int FN(model_create)(int n, double U_, double J_, double Up_, double mu_, const 
   m->H = (real **)calloc((size_t)m->nsec, sizeof(real *));
   m->V = (real **)calloc((size_t)m->nsec, sizeof(real *));
   m->w = (real **)calloc((size_t)m->nsec, sizeof(real *));
-  if (!m->sec_of || !m->rank || !m->states || !m->sec_dim || !m->sec_off || !m->H || !m->V || !m->w) {
+  m->ncomp = (int *)calloc((size_t)m->nsec, sizeof(int));
+  m->crow_off = (int **)calloc((size_t)m->nsec, sizeof(int *));
+  m->comp_rows = (int **)calloc((size_t)m->nsec, sizeof(int *));
+  m->comp_cols = (int **)calloc((size_t)m->nsec, sizeof(int *));
+  if (!m->sec_of || !m->rank || !m->states || !m->sec_dim || !m->sec_off || !m->H || !m->V || !m->w || !m->ncomp ||
+      !m->crow_off || !m->comp_rows || !m->comp_cols) {
     FN(model_free)(m);
     return OR_ENOMEM;
   }
@@ -390,7 +422,7 @@ int FN(model_create)(int n, double U_, double J_, double Up_, double mu_, const 
           if (apply_string(x, f2, g2, 4, &y, &sg)) H[m->rank[y] * d + i] += -J * (real)sg;
         }
     }
-    int rc = sector_eig(d, H, m->w[s], m->V[s]);
+    int rc = sector_eig(d, H, m->w[s], m->V[s], &m->ncomp[s], &m->crow_off[s], &m->comp_rows[s], &m->comp_cols[s]);
     if (rc) { FN(model_free)(m); return rc; }
   }
   /* global ground energy */
@@ -502,20 +534,26 @@ static int apply_vec(const or_model *m, int s, const real *v, int f, int dag, re
 static real propagate(const or_model *m, int s, real dtau, real *v, real *tmp) {
   int d = m->sec_dim[s];
   const real *V = m->V[s], *w = m->w[s];
+  const int *off = m->crow_off[s], *rows = m->comp_rows[s], *cols = m->comp_cols[s];
+  /* V is block diagonal in the components: u = V^T v one component at a time */
   real wref = INFINITY;
-  for (int j = 0; j < d; ++j) {
-    real u = 0;
-    for (int i = 0; i < d; ++i) u += V[i * d + j] * v[i];
-    tmp[j] = u;
-    if (u != 0 && w[j] < wref) wref = w[j];
-  }
+  for (int c = 0; c < m->ncomp[s]; ++c)
+    for (int b = off[c]; b < off[c + 1]; ++b) {
+      int j = cols[b];
+      real u = 0;
+      for (int a = off[c]; a < off[c + 1]; ++a) u += V[rows[a] * d + j] * v[rows[a]];
+      tmp[j] = u;
+      if (u != 0 && w[j] < wref) wref = w[j];
+    }
   if (!(wref < INFINITY)) return 0;
   for (int j = 0; j < d; ++j) tmp[j] = (tmp[j] != 0) ? tmp[j] * exp(-dtau * (w[j] - wref)) : 0;
-  for (int i = 0; i < d; ++i) {
-    real u = 0;
-    for (int j = 0; j < d; ++j) u += V[i * d + j] * tmp[j];
-    v[i] = u;
-  }
+  for (int c = 0; c < m->ncomp[s]; ++c)
+    for (int a = off[c]; a < off[c + 1]; ++a) {
+      int i = rows[a];
+      real u = 0;
+      for (int b = off[c]; b < off[c + 1]; ++b) u += V[i * d + cols[b]] * tmp[cols[b]];
+      v[i] = u;
+    }
   return -dtau * (wref - m->E0);
 }
 
