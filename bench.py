@@ -35,6 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "5-orbital trace-ratio evals/s (batched FP32) vs plain FP64 GPU; rel err ≤1e-5"
+METRIC_7 = "7-orbital trace-ratio evals/s (batched FP32) vs plain FP64 GPU; rel err ≤1e-5"
 UNIT = "evals/s"
 N_WALKERS = 4096
 N_ROUNDS = 200
@@ -52,6 +53,8 @@ def args_():
     p.add_argument("--fp64-steps", type=int, default=0, help="steps for the FP64 comparator (default min(K, 100))")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    p.add_argument("--workload", choices=["five_orbital", "seven_orbital"], default="five_orbital",
+                   help="five_orbital (4,096 walkers, the headline) or seven_orbital (256 walkers)")
     return p.parse_args()
 
 
@@ -123,10 +126,13 @@ def measured_traffic(sha: str):
     return d.get("dram_bytes_per_launch") if d.get("source_sha") == sha else None
 
 
-def make_workload(rank: int, rounds: int):
+WALKERS = {"five_orbital": 4096, "seven_orbital": 256}
+
+
+def make_workload(rank: int, rounds: int, name: str = "five_orbital"):
     from paper_0908_0681_gb300 import workloads
-    w = workloads.five_orbital()
-    seqs = workloads.generate_sequences(w, N_WALKERS, seed=1 + 7919 * rank)
+    w = workloads.WORKLOADS[name]()
+    seqs = workloads.generate_sequences(w, WALKERS[name], seed=1 + 7919 * rank)
     moves = [workloads.generate_moves(w, seqs, seed=1000 + r + 100000 * rank) for r in range(rounds)]
     return w, seqs, moves
 
@@ -173,12 +179,12 @@ def reference_arm(a):
     import numpy as np
     from oracle.oracle import Model, Params, SeqBatch, ratio
 
-    w, seqs, moves = make_workload(0, min(N_ROUNDS, a.warmup + a.steps))
+    w, seqs, moves = make_workload(0, min(N_ROUNDS, a.warmup + a.steps), a.workload)
     spec = w.model
     P = Params(spec.n_orb, spec.U, spec.J, Up=spec.up, mu=spec.mu, delta=spec.delta, beta=spec.beta,
                trunc_eps=spec.trunc_eps, deg_tol=spec.deg_tol)
     o = Model(P)
-    sample = 256
+    sample = min(256, seqs.n)
     sub = seqs.subset(range(sample))
     sb = SeqBatch(sub.offsets, sub.tau, sub.flavor, sub.dagger)
     cs, cl, _ = o.trace(sb)
@@ -193,13 +199,13 @@ def reference_arm(a):
         ratio(o, sb, cs, cl, mv_sub(moves[(a.warmup + i) % len(moves)]))
     dt = time.perf_counter() - t0
     v = sample * a.steps / dt
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+    line = {"impl": "reference", "metric": METRIC if a.workload == "five_orbital" else METRIC_7, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1000 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "five_orbital_4096_walkers", "n_orb": 5, "walkers": N_WALKERS, "beta": 50.0,
-                       "sample_walkers_per_step": sample},
+            "config": {"workload": f"{a.workload}_{seqs.n}_walkers", "n_orb": spec.n_orb, "walkers": seqs.n,
+                       "beta": spec.beta, "sample_walkers_per_step": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(o.threads_used), "kind": "oracle",
-                             "sample": f"{sample} of {N_WALKERS} walkers per step, FP64 dense-block oracle, OpenMP"},
+                             "sample": f"{sample} of {seqs.n} walkers per step, FP64 dense-block oracle, OpenMP"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -226,7 +232,7 @@ def main():
             torch.distributed.barrier()
 
     n_rounds = min(N_ROUNDS, a.warmup + a.steps)
-    w, seqs, moves = make_workload(rank, n_rounds)
+    w, seqs, moves = make_workload(rank, n_rounds, a.workload)
     dseq = engine.DeviceSeqs.from_host(seqs, dev)
     dmoves = [engine.DeviceMoves.from_host(m, dev) for m in moves]
     m32 = engine.model_from_spec(w.model, precision=kt.KT_FP32_KRYLOV)
@@ -370,12 +376,13 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "metric": METRIC if a.workload == "five_orbital" else METRIC_7, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": tot32 / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "five_orbital_4096_walkers", "n_orb": 5, "U": 4.0, "J": 1.0, "beta": 50.0,
+            "config": {"workload": f"{a.workload}_{n}_walkers", "n_orb": w.model.n_orb, "U": w.model.U,
+                       "J": w.model.J, "beta": w.model.beta,
                        "walkers_per_gpu": n, "mean_ops_per_walker": float(seqs.offsets[-1]) / n,
-                       "krylov_tol": 1e-12, "precision": "fp32-krylov (fp64 tridiagonal exp, norms, log-weights)",
+                       "krylov_tol": w.model.krylov_tol, "trunc_eps": w.model.trunc_eps, "precision": "fp32-krylov (fp64 tridiagonal exp, norms, log-weights)",
                        "blocks": "(n_up, n_dn, singly-occupied mask)", "n_blocks": info["n_blocks"],
                        "d_max": info["d_max"], "n_kept": info["n_kept"], "group_lanes": tuned, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}"},

@@ -620,7 +620,10 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
     __syncwarp(gm);
     exact = (p == dim) || !(bb > brk);
     bool stop = exact;
-    if (!exact) {
+    // a-posteriori checks at every p up to 4, then on a geometric schedule
+    // (6, 8, 11, 15, 20, 27): each check costs an eigendecomposition of T_p
+    const bool check = p <= 4 || p == 6 || p == 8 || p == 11 || p == 15 || p == 20 || p == 27 || p == pcap;
+    if (!exact && check) {
       if constexpr (F32) {
         float yn, yl;
         tri_check32(s, grp, gl, gm, p, dt, yn, yl);
@@ -658,11 +661,19 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
     if (p <= 2) {
       tri_small_f32(s, grp, gl, gm, p, dt, logfac);
     } else {
-      if (exact || !conv) {
-        float yn, yl;
-        tri_check32(s, grp, gl, gm, p, dt, yn, yl);  // Ritz pairs of T_p (unless the last check made them)
+      if constexpr (DMAX > 16) {
+        // blocks beyond 16 rows (seven orbitals) hold close Ritz pairs whose FP32
+        // vectors would leak rotation errors into y: full FP64 eigensolve at the final p
+        if (!tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
+        for (int k = gl; k < p; k += G) s.y32[k * IPW + grp] = (float)Y_(k);
+        __syncwarp(gm);
+      } else {
+        if (exact) {
+          float yn, yl;
+          tri_check32(s, grp, gl, gm, p, dt, yn, yl);  // Ritz pairs of T_p (a check at p made them otherwise)
+        }
+        tri_final32(s, grp, gl, gm, p, dt, logfac);
       }
-      tri_final32(s, grp, gl, gm, p, dt, logfac);
     }
   } else {
     if (exact && !tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;

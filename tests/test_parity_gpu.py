@@ -272,3 +272,34 @@ def test_autotune_picks_a_compiled_tiling(five):
     assert g in (4, 8, 16, 32) and kt.kt_model_query(m)["group_lanes"] == g
     s2, l2, st2 = gpu_trace(m, seqs)
     parity.compare(cls, sx, lx, s2, l2, kt.KT_FP32_KRYLOV, ox.nkept, w.model.beta * ox.E0, "autotuned")
+
+
+@pytest.fixture(scope="module")
+def seven():
+    w = workloads.seven_orbital()
+    seqs = workloads.generate_sequences(w, 48, seed=1)
+    o64, ox = parity.oracle_pair(w.model)
+    cls, sx, lx = parity.oracle_traces(o64, ox, seqs)
+    return w, seqs, o64, ox, cls, sx, lx
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_seven_orbital_traces_and_ratios(seven, prec):
+    """7-orbital f-shell model (16,384 states, blocks up to 35 rows, N_tr = 63)."""
+    w, seqs, o64, ox, cls, sx, lx = seven
+    m = engine.model_from_spec(w.model, precision=prec)
+    info = kt.kt_model_query(m)
+    assert info["n_kept"] == ox.nkept == 63 and info["d_max"] == 35
+    s, l, st = gpu_trace(m, seqs)
+    assert (st == kt.KT_OK).all(), np.unique(st, return_counts=True)
+    r = parity.compare(cls, sx, lx, s, l, prec, ox.nkept, w.model.beta * ox.E0, "7-orbital traces")
+    assert r["regular"] >= 0.9 * len(cls)
+    moves = workloads.generate_moves(w, seqs, seed=1000)
+    cur_s = np.where(cls == 2, sx, 0).astype(np.int8)
+    ncls, nsx, nlx = parity.oracle_ratios(o64, ox, seqs, cur_s, lx, moves)
+    rs, rl, rst = gpu_ratio(m, seqs, cur_s, lx, moves)
+    reg = cls == 2
+    assert (rst[reg] == kt.KT_OK).all()
+    idx = np.nonzero(reg)[0]
+    parity.compare(ncls[idx], nsx[idx] * cur_s[idx], nlx[idx] - lx[idx], rs[idx], rl[idx], prec, ox.nkept,
+                   w.model.beta * ox.E0 + lx[idx], "7-orbital ratios")
