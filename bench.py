@@ -109,9 +109,13 @@ class ClockSampler:
 
 
 def source_sha() -> str:
+    """Hash of every kernel and host source file (ties a committed ncu summary to the code)."""
     h = hashlib.sha256()
-    for f in ("kt_kernels.cu", "kt_model.cpp", "kt_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_0908_0681_gb300", "csrc", f), "rb").read())
+    d = os.path.join(ROOT, "paper_0908_0681_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
