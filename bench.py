@@ -133,11 +133,28 @@ def measured_traffic(sha: str):
 WALKERS = {"five_orbital": 4096, "seven_orbital": 256}
 
 
+def rank_seeds(rank: int, rounds: int):
+    """Per-rank seeds: each rank (replica) draws its own walkers and moves."""
+    return 1 + 7919 * rank, [1000 + r + 100000 * rank for r in range(rounds)]
+
+
+def aggregate(times_ms, n_per_rank: int, steps: int, world: int, reduce_max=None):
+    """Whole-job throughput of weak-scaled replicas: units of all ranks / max time over ranks.
+
+    times_ms: this rank's [timed total, ...] in ms; reduce_max: callable doing an element-wise
+    max over ranks (None for one rank). Returns (value, max_times)."""
+    t = list(times_ms)
+    if world > 1 and reduce_max is not None:
+        t = reduce_max(t)
+    return world * n_per_rank * steps / (t[0] / 1000.0), t
+
+
 def make_workload(rank: int, rounds: int, name: str = "five_orbital"):
     from paper_0908_0681_gb300 import workloads
     w = workloads.WORKLOADS[name]()
-    seqs = workloads.generate_sequences(w, WALKERS[name], seed=1 + 7919 * rank)
-    moves = [workloads.generate_moves(w, seqs, seed=1000 + r + 100000 * rank) for r in range(rounds)]
+    seq_seed, move_seeds = rank_seeds(rank, rounds)
+    seqs = workloads.generate_sequences(w, WALKERS[name], seed=seq_seed)
+    moves = [workloads.generate_moves(w, seqs, seed=sd) for sd in move_seeds]
     return w, seqs, moves
 
 
@@ -343,13 +360,12 @@ def main():
     barrier()
 
     # aggregate over ranks: max time
-    tot32 = sum(ms32)
-    tot64 = sum(ms64)
-    if world > 1:
-        t = torch.tensor([tot32, tot64, e2e_ms], dtype=torch.float64, device=dev)
+    def reduce_max(vals):
+        t = torch.tensor(vals, dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot32, tot64, e2e_ms = t.tolist()
-    value = world * n * a.steps / (tot32 / 1000.0)
+        return t.tolist()
+
+    value, (tot32, tot64, e2e_ms) = aggregate([sum(ms32), sum(ms64), e2e_ms], n, a.steps, world, reduce_max)
     value64 = world * n * K64 / (tot64 / 1000.0)
     e2e_value = world * n / (e2e_ms / 1000.0)
 
