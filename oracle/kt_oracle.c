@@ -32,6 +32,9 @@
  *    first and last intervals as scalars (|n> is an eigenstate) and every
  *    inner interval as an exact block exponential. Results are reported as
  *    (sign, log|T|) with log|T| = log|T~| - beta E0.
+ *  - The same trace with a diagonal operator of the occupation basis inserted
+ *    at one time (Sec. III: local observables measured at tau = beta/2 in the
+ *    truncated trace), evaluated right to left as written.
  *
  * Conventions (the paper is silent on these): flavor f = 2a + s with orbital
  * a and spin s (0 = up, 1 = down); bit f of the state is n_f; c_f and c_f^+
@@ -654,6 +657,130 @@ int FN(trace_batch)(void *hm, int nseq, const int *offsets, const double *tau, c
                                              : OR_ENOMEM;
       sign[i] = sgn; logabs[i] = la; if (logtt) logtt[i] = lt; status[i] = rc;
     }
+    free(va); free(vb); free(tmp); free(lg); free(sg);
+#ifdef _OPENMP
+  }
+#endif
+  return used;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Diagonal observables inserted at tau = t_obs (Sec. III: measurements at  */
+/* beta/2 in the truncated trace)                                          */
+/* ---------------------------------------------------------------------- */
+
+/* T_O = sum over kept |n> of <n| e^{-(beta-tau_K)(H-E0)} O_K ... O(t_obs) ...
+ * O_1 e^{-tau_1 (H-E0)} |n>, with the diagonal operator O (values obs[x] on
+ * bitstring x) placed after every operator with tau < t_obs. The product is
+ * evaluated right to left as written: every interval that starts from a
+ * vector other than the kept eigenstate is an exact block exponential. */
+static int trace_obs_one(const or_model *m, int K, const double *tau, const uint8_t *flv, const uint8_t *dag,
+                         real t_obs, const double *obs, real *va, real *vb, real *tmp, real *lg, int *sg,
+                         int *sign, double *logabs) {
+  const real beta = m->beta;
+  for (int k = 0; k < K; ++k) {
+    if (flv[k] >= m->nf || !(tau[k] >= 0) || !(tau[k] < (double)beta)) return OR_EINVAL;
+    if (k > 0 && tau[k] < tau[k - 1]) return OR_EINVAL;
+  }
+  if (!(t_obs >= 0) || !(t_obs <= beta)) return OR_EINVAL;
+  int mcut = 0;
+  while (mcut < K && (real)tau[mcut] < t_obs) ++mcut;
+  int nalive = 0;
+  for (int q = 0; q < m->nkept; ++q) {
+    int s0 = m->kept_sec[q], col = m->kept_col[q];
+    real En = m->kept_E[q];
+    int d0 = m->sec_dim[s0];
+    for (int i = 0; i < d0; ++i) va[i] = m->V[s0][i * d0 + col];
+    real L = 0, t = 0;
+    int s = s0, alive = 1, eig = 1;
+    /* events: ops 0 .. mcut-1, the observable, ops mcut .. K-1 */
+    for (int e = 0; e <= K && alive; ++e) {
+      const int is_obs = (e == mcut);
+      const int k = e < mcut ? e : e - 1;
+      const real te = is_obs ? t_obs : (real)tau[k];
+      if (te > t) {
+        if (eig) {
+          L += -(te - t) * (En - m->E0);
+        } else {
+          L += propagate(m, s, te - t, va, tmp);
+        }
+      }
+      t = te;
+      int d = m->sec_dim[s];
+      if (is_obs) {
+        for (int i = 0; i < d; ++i) vb[i] = va[i] * (real)obs[m->states[m->sec_off[s] + i]];
+      } else {
+        int tg = apply_vec(m, s, va, flv[k], dag[k], vb);
+        if (tg < 0) { alive = 0; break; }
+        s = tg;
+        d = m->sec_dim[s];
+      }
+      eig = 0;
+      real nrm = 0;
+      for (int i = 0; i < d; ++i) nrm += vb[i] * vb[i];
+      nrm = sqrt(nrm);
+      if (nrm == 0) { alive = 0; break; }
+      L += log(nrm);
+      for (int i = 0; i < d; ++i) va[i] = vb[i] / nrm;
+    }
+    if (!alive || s != s0) { sg[q] = 0; continue; }
+    /* last interval: <n| e^{-(beta - t)(H - E0)} = e^{-(beta - t)(E_n - E0)} <n| */
+    real ov = 0;
+    for (int i = 0; i < d0; ++i) ov += m->V[s0][i * d0 + col] * va[i];
+    if (ov == 0) { sg[q] = 0; continue; }
+    L += log(fabs(ov)) - (beta - t) * (En - m->E0);
+    lg[q] = L; sg[q] = (ov > 0) ? 1 : -1;
+    ++nalive;
+  }
+  if (nalive == 0) { *sign = 0; *logabs = -INFINITY; return OR_OK; }
+  real mx = -INFINITY;
+  for (int q = 0; q < m->nkept; ++q) if (sg[q] && lg[q] > mx) mx = lg[q];
+  real acc = 0;
+  for (int q = 0; q < m->nkept; ++q) if (sg[q]) acc += (real)sg[q] * exp(lg[q] - mx);
+  if (acc == 0) { *sign = 0; *logabs = -INFINITY; return OR_OK; }
+  *sign = (acc > 0) ? 1 : -1;
+  *logabs = (double)(mx + log(fabs(acc)) - beta * m->E0);
+  return OR_OK;
+}
+
+/* Batch: for every sequence i and observable j (obs[j * nstates + x]),
+ * sign[i * nobs + j] and logabs[i * nobs + j] of T_O. status[i] as
+ * trace_batch. Returns the number of threads used. */
+int FN(trace_obs_batch)(void *hm, int nseq, const int *offsets, const double *tau, const uint8_t *flavor,
+                        const uint8_t *dagger, double t_obs, int nobs, const double *obs, int *sign, double *logabs,
+                        int *status, int nthreads) {
+  or_model *m = (or_model *)hm;
+  int dmax = 1;
+  for (int s = 0; s < m->nsec; ++s) if (m->sec_dim[s] > dmax) dmax = m->sec_dim[s];
+  int used = 1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+  {
+#pragma omp single
+    used = omp_get_num_threads();
+#endif
+    real *va = (real *)malloc(sizeof(real) * (size_t)dmax);
+    real *vb = (real *)malloc(sizeof(real) * (size_t)dmax);
+    real *tmp = (real *)malloc(sizeof(real) * (size_t)dmax);
+    real *lg = (real *)malloc(sizeof(real) * (size_t)(m->nkept + 1));
+    int *sg = (int *)malloc(sizeof(int) * (size_t)(m->nkept + 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1) collapse(2)
+#endif
+    for (int i = 0; i < nseq; ++i)
+      for (int j = 0; j < nobs; ++j) {
+        int o = offsets[i], K = offsets[i + 1] - offsets[i];
+        double la = 0;
+        int sgn = 0;
+        int rc = (va && vb && tmp && lg && sg)
+                     ? trace_obs_one(m, K, tau + o, flavor + o, dagger + o, (real)t_obs, obs + (size_t)j * m->nstates,
+                                     va, vb, tmp, lg, sg, &sgn, &la)
+                     : OR_ENOMEM;
+        sign[(size_t)i * nobs + j] = sgn;
+        logabs[(size_t)i * nobs + j] = la;
+        if (j == 0) status[i] = rc;
+      }
     free(va); free(vb); free(tmp); free(lg); free(sg);
 #ifdef _OPENMP
   }

@@ -64,6 +64,9 @@ def _load():
             getattr(_lib, p + "model_block").argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3
             getattr(_lib, p + "model_kept").argtypes = [ctypes.c_void_p] * 4
             getattr(_lib, p + "trace_batch").argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 8 + [ctypes.c_int]
+            getattr(_lib, p + "trace_obs_batch").argtypes = (
+                [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_double, ctypes.c_int]
+                + [ctypes.c_void_p] * 4 + [ctypes.c_int])
     return _lib
 
 
@@ -160,6 +163,55 @@ class Model:
         if st.any():
             raise ValueError(f"oracle rejected {int((st != 0).sum())} sequences (first at {int(np.argmax(st != 0))})")
         return sign.astype(np.int8), la, lt
+
+
+    def trace_obs(self, seqs: "SeqBatch", t_obs: float, obs: np.ndarray, nthreads: int = 0):
+        """Traces with a diagonal operator inserted at t_obs (after every operator with tau < t_obs).
+
+        obs: [nobs, 4^n_orb] values of each operator on every bitstring. Returns
+        (sign int8 [n, nobs], log|T_O| float64 [n, nobs]).
+        """
+        obs = np.ascontiguousarray(obs, dtype=np.float64).reshape(-1, self.nstates)
+        n, k = seqs.n, obs.shape[0]
+        if k < 1:
+            raise ValueError("at least one observable")
+        sign = np.zeros((n, k), dtype=np.int32)
+        la = np.zeros((n, k), dtype=np.float64)
+        st = np.zeros(n, dtype=np.int32)
+        self.threads_used = getattr(_lib, self.prefix + "trace_obs_batch")(
+            self._h, n, _ptr(seqs.offsets), _ptr(seqs.tau), _ptr(seqs.flavor), _ptr(seqs.dagger), float(t_obs), k,
+            _ptr(obs), _ptr(sign), _ptr(la), _ptr(st), int(nthreads))
+        if st.any():
+            raise ValueError(f"oracle rejected {int((st != 0).sum())} sequences (first at {int(np.argmax(st != 0))})")
+        return sign.astype(np.int8), la
+
+
+def observable_table(n_orb: int) -> np.ndarray:
+    """Diagonal observables of the occupation basis, one row per operator, one column per
+    bitstring x (bit f = n_f): n_f for f = 2a + s, then n_{a up} n_{a dn} per orbital a,
+    then the projector on each (n_up, n_dn) sector, index n_up (n_orb + 1) + n_dn."""
+    nf, ns = 2 * n_orb, 4 ** n_orb
+    x = np.arange(ns)
+    rows = [((x >> f) & 1).astype(np.float64) for f in range(nf)]
+    rows += [(((x >> (2 * a)) & 1) * ((x >> (2 * a + 1)) & 1)).astype(np.float64) for a in range(n_orb)]
+    nup = sum((x >> (2 * a)) & 1 for a in range(n_orb))
+    ndn = sum((x >> (2 * a + 1)) & 1 for a in range(n_orb))
+    for u in range(n_orb + 1):
+        for d in range(n_orb + 1):
+            rows.append(((nup == u) & (ndn == d)).astype(np.float64))
+    return np.array(rows)
+
+
+def measure(model: Model, seqs: "SeqBatch", nthreads: int = 0):
+    """<O(beta/2)> = T_O / T for the observables of observable_table, per sequence.
+
+    Returns (obs [n, nobs] with NaN where T = 0, sign_T, log|T|)."""
+    s, la, _ = model.trace(seqs, nthreads)
+    so, lo = model.trace_obs(seqs, 0.5 * model.p.beta, observable_table(model.p.n_orb), nthreads)
+    with np.errstate(invalid="ignore", over="ignore"):
+        val = so.astype(np.float64) * s[:, None].astype(np.float64) * np.exp(lo - la[:, None])
+    val[s == 0, :] = np.nan
+    return val, s, la
 
 
 @dataclass
