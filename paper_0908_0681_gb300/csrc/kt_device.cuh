@@ -77,6 +77,16 @@ __device__ __forceinline__ int upper_bound(const double *t, int K, double x) {
   return lo;
 }
 
+// Number of entries of the sorted t[0 .. K) that are < x.
+__device__ __forceinline__ int lower_bound(const double *t, int K, double x) {
+  int lo = 0, hi = K;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (t[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ void stat_add(unsigned long long *p, unsigned long long v) {
   if (v) atomicAdd(p, v);
 }

@@ -73,10 +73,14 @@ struct Workspace {
   double *half_log;    // [2 * n * n_kept] log-weight of each half
   int32_t *half_info;  // [2 * n * n_kept] block | status << 24, or -1 if the half vanished
   void *half_vec;      // [2 * n * n_kept][d_max] final vector of each half (FP32 or FP64)
+  // measurement at tau = beta/2 only (nullptr otherwise)
+  double *item_obs;    // [n * n_kept][nf + n_orb] <O> of each item: n_f, then n_{a up} n_{a dn}
+  int32_t *item_blk;   // [n * n_kept] block of the item at tau = beta/2
 };
 
-size_t workspace_bytes(int n_walkers, int n_kept, int d_max);
-Workspace carve_workspace(void *base, int n_walkers, int n_kept, int d_max);
+// n_obs_item = 0: trace and ratio calls; nf + n_orb: measurement calls.
+size_t workspace_bytes(int n_walkers, int n_kept, int d_max, int n_obs_item = 0);
+Workspace carve_workspace(void *base, int n_walkers, int n_kept, int d_max, int n_obs_item = 0);
 
 // Compiled variants of the Krylov items kernel: (row capacity DMAX, Krylov cap
 // PMAX, lanes per item G).
@@ -95,11 +99,14 @@ struct StageEvents {
 };
 
 // Launch the full pipeline (validation/edit, pruning, Krylov items, reduction).
-// moves == nullptr: plain traces. Returns a CUDA error code (0 = success).
+// moves == nullptr: plain traces. obs != nullptr (plain traces only, with the
+// measurement regions of the workspace carved): also the local observables at
+// tau = beta/2, [n][KT_MEASURE_NOBS(n_orb)]. Returns a CUDA error code (0 = success).
 int launch_pipeline(const DevModel &m, int precision, int kernel_dmax, int group_lanes, const SeqView &seq,
                     const MoveView *moves,
                     const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv, int32_t *status,
-                    kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing);
+                    kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing,
+                    double *obs = nullptr);
 
 // Launch parameters of a model, for entry points that live outside kt_model.cpp.
 struct ModelView {

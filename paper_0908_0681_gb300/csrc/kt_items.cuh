@@ -746,6 +746,7 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
   const int nk = M.n_kept;
   const int vstride = M.d_max;
   VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
+  const bool meas = ws.item_obs != nullptr;
 
   for (;;) {
     int uix = 0;
@@ -760,7 +761,7 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
     const int b_kept = __ldg(M.kept_blk + q);
     const double Ek = __ldg(M.kept_e + q);
     const int koff = __ldg(M.kept_off + q);
-    if (Kn == 0) {  // empty sequence: the kept state alone, no split
+    if (Kn == 0 && !meas) {  // empty sequence: the kept state alone, no split
       if (half == 0 && gl == 0) {
         ws.item_sign[item] = 1;
         ws.item_log[item] = -M.beta * Ek;
@@ -775,27 +776,45 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
       if (r < u.dim) u.Q(0, r) = __ldg(tkept + koff + r);
     }
     __syncwarp(gm);
-    const int m = Kn / 2 > 1 ? Kn / 2 : 1;
+    // Split: ops 0 .. m-1 go forward from tau = 0, ops m .. K-1 backward from
+    // beta; the halves meet at t_s. Traces and ratios split at the middle
+    // operator (t_s = tau_{m-1}); measurements at t_s = beta/2, with m the
+    // number of operators before beta/2 (possibly 0 or K).
+    int m;
+    double t_s;
+    if (meas) {
+      t_s = 0.5 * M.beta;
+      m = lower_bound(S.tau + cur.o, Kn, t_s);
+    } else {
+      m = Kn / 2 > 1 ? Kn / 2 : 1;
+      t_s = cur.get(m - 1).t;
+    }
     bool vanished = false;
-    // forward: ops 0 .. m-1 in order; backward: adjoints of ops K-1 .. m, each
-    // followed by the interval down to the previous operator (the last one
-    // bridges to op m-1)
+    // forward: ops 0 .. m-1 in order; backward: adjoints of ops K-1 .. m; each
+    // op is followed by the interval to the next op of its half, the last one
+    // by the interval to t_s
     const int nsteps = half == 0 ? m : Kn - m;
-    Op op = cur.get(half == 0 ? 0 : Kn - 1);
-    u.Ladd = half == 0 ? -op.t * Ek : -(M.beta - op.t) * Ek;  // |n> is an eigenstate at both ends
-    for (int s = 0; s < nsteps; ++s) {
-      const int idx = half == 0 ? s : Kn - 1 - s;
-      if (!apply_op(M, u, op.f, half == 0 ? op.dag : 1 - op.dag)) {
-        vanished = true;
-        break;
-      }
-      if (half == 0 && s + 1 >= m) break;
-      const Op nx = cur.get(half == 0 ? idx + 1 : idx - 1);
-      const double dt = half == 0 ? nx.t - op.t : op.t - nx.t;
-      op = nx;
-      if (dt > 0.0 && !propagate(M, u, dt, stats != nullptr)) {
-        vanished = true;
-        break;
+    if (nsteps == 0) {
+      u.Ladd = half == 0 ? -t_s * Ek : -(M.beta - t_s) * Ek;  // |n> is an eigenstate
+    } else {
+      Op op = cur.get(half == 0 ? 0 : Kn - 1);
+      u.Ladd = half == 0 ? -op.t * Ek : -(M.beta - op.t) * Ek;  // |n> is an eigenstate at both ends
+      for (int s = 0; s < nsteps; ++s) {
+        const int idx = half == 0 ? s : Kn - 1 - s;
+        if (!apply_op(M, u, op.f, half == 0 ? op.dag : 1 - op.dag)) {
+          vanished = true;
+          break;
+        }
+        const bool last = s + 1 == nsteps;
+        Op nx;
+        if (!last) nx = cur.get(half == 0 ? idx + 1 : idx - 1);
+        const double tn = last ? t_s : nx.t;
+        const double dt = half == 0 ? tn - op.t : op.t - tn;
+        if (!last) op = nx;
+        if (dt > 0.0 && !propagate(M, u, dt, stats != nullptr)) {
+          vanished = true;
+          break;
+        }
       }
     }
     // publish this half
@@ -839,6 +858,36 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
       if (oinfo >= 0 && (oinfo >> 24) > st) st = oinfo >> 24;
       const double L = Lh + Lo + (zero ? 0.0 : log(fabs(ov)));
       if (!zero && !isfinite(L)) st = KT_ENUMERIC;
+      if (meas && !zero) {
+        // <O> of this item for the diagonal observables at beta/2:
+        // sum_r o(x_r) bwd_r fwd_r / sum_r bwd_r fwd_r
+        const int nf = M.nf, nl = nf + M.n_orb;
+        const int off = __ldg(M.blk_off + u.b);
+        VT pr[R];
+        int xr[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int r = gl + G * j;
+          pr[j] = VT(0);
+          xr[j] = 0;
+          if (r < u.dim) {
+            pr[j] = u.Q(0, r) * __ldcg(hvec + (size_t)oslot * vstride + r);
+            xr[j] = __ldg(M.st_bits + off + r);
+          }
+        }
+        const double iov = 1.0 / ov;
+        for (int k = 0; k < nl; ++k) {
+          const int sh = k < nf ? k : 2 * (k - nf);
+          const int msk = k < nf ? 1 : 3;
+          GroupDot<VT, G> d;
+#pragma unroll
+          for (int j = 0; j < R; ++j)
+            if (((xr[j] >> sh) & msk) == msk) d.add(pr[j], VT(1));
+          const double v = d.value(gm) * iov;
+          if (gl == 0) ws.item_obs[(size_t)item * nl + k] = v;
+        }
+        if (gl == 0) ws.item_blk[item] = u.b;
+      }
       if (gl == 0) {
         ws.item_sign[item] = zero ? 0 : (ov > 0.0 ? 1 : -1);
         ws.item_log[item] = zero ? -INFINITY : L;

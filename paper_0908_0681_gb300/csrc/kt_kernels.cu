@@ -185,6 +185,37 @@ __global__ void reduce_kernel(DevModel M, int n, int has_moves, const int8_t *cu
   status[w] = st;
 }
 
+// Observables at tau = beta/2: per walker, the kept-state items weighted by
+// their share of the trace (same signed log-sum-exp as reduce_kernel).
+__global__ void measure_reduce_kernel(DevModel M, int n, Workspace ws, double *obs) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n) return;
+  const int nk = M.n_kept, nf = M.nf, no = M.n_orb, nl = nf + no;
+  const int nsec = (no + 1) * (no + 1), ntot = nl + nsec;
+  double *out = obs + (size_t)w * ntot;
+  double mx = -INFINITY;
+  if (ws.wstatus[w] == KT_OK)
+    for (int q = 0; q < nk; ++q) {
+      const int it = w * nk + q;
+      if (ws.item_sign[it] != 0) mx = fmax(mx, ws.item_log[it]);
+    }
+  for (int k = 0; k < ntot; ++k) out[k] = 0.0;
+  double den = 0.0;
+  if (mx > -INFINITY)
+    for (int q = 0; q < nk; ++q) {
+      const int it = w * nk + q;
+      if (ws.item_sign[it] == 0) continue;
+      const double c = (double)ws.item_sign[it] * exp(ws.item_log[it] - mx);
+      den += c;
+      for (int k = 0; k < nl; ++k) out[k] += c * ws.item_obs[(size_t)it * nl + k];
+      const int x = __ldg(M.st_bits + __ldg(M.blk_off + ws.item_blk[it]));
+      const int nup = __popc(x & 0x5555), ndn = __popc(x & 0xaaaa);
+      out[nl + nup * (no + 1) + ndn] += c;
+    }
+  const double inv = (den != 0.0 && isfinite(mx)) ? 1.0 / den : NAN;
+  for (int k = 0; k < ntot; ++k) out[k] *= inv;
+}
+
 }  // namespace
 
 
@@ -224,7 +255,7 @@ int default_group_for(int kd) {
 
 int launch_pipeline(const DevModel &M, int precision, int kd, int G, const SeqView &S, const MoveView *moves,
                     const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv, int32_t *status,
-                    kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing) {
+                    kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing, double *obs) {
   cudaStream_t st = (cudaStream_t)stream;
   auto mark = [&](int i) {
     if (timing) cudaEventRecord((cudaEvent_t)timing->ev[i], st);
@@ -248,6 +279,7 @@ int launch_pipeline(const DevModel &M, int precision, int kd, int G, const SeqVi
   }
   mark(3);
   reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, has_moves, cur_sign, cur_logabs, ws, sign, logv, status);
+  if (obs) measure_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, ws, obs);
   mark(4);
   return (int)cudaGetLastError();
 }

@@ -121,7 +121,7 @@ static void timing_release(kt_model *m) {
 
 namespace kt {
 
-size_t workspace_bytes(int n, int n_kept, int d_max) {
+size_t workspace_bytes(int n, int n_kept, int d_max, int n_obs_item) {
   const size_t items = (size_t)n * (size_t)n_kept;
   size_t b = 0;
   b += align_up(4 * sizeof(int32_t), 256);
@@ -135,10 +135,14 @@ size_t workspace_bytes(int n, int n_kept, int d_max) {
   b += align_up(2 * items * sizeof(double), 256);
   b += align_up(2 * items * sizeof(int32_t), 256);
   b += align_up(2 * items * (size_t)d_max * sizeof(double), 256);
+  if (n_obs_item > 0) {
+    b += align_up(items * (size_t)n_obs_item * sizeof(double), 256);
+    b += align_up(items * sizeof(int32_t), 256);
+  }
   return b;
 }
 
-Workspace carve_workspace(void *base, int n, int n_kept, int d_max) {
+Workspace carve_workspace(void *base, int n, int n_kept, int d_max, int n_obs_item) {
   const size_t items = (size_t)n * (size_t)n_kept;
   char *p = (char *)base;
   Workspace w;
@@ -152,7 +156,13 @@ Workspace carve_workspace(void *base, int n, int n_kept, int d_max) {
   w.pair_flag = (int32_t *)p; p += align_up(items * sizeof(int32_t), 256);
   w.half_log = (double *)p; p += align_up(2 * items * sizeof(double), 256);
   w.half_info = (int32_t *)p; p += align_up(2 * items * sizeof(int32_t), 256);
-  w.half_vec = (void *)p;
+  w.half_vec = (void *)p; p += align_up(2 * items * (size_t)d_max * sizeof(double), 256);
+  w.item_obs = nullptr;
+  w.item_blk = nullptr;
+  if (n_obs_item > 0) {
+    w.item_obs = (double *)p; p += align_up(items * (size_t)n_obs_item * sizeof(double), 256);
+    w.item_blk = (int32_t *)p;
+  }
   return w;
 }
 
@@ -516,21 +526,23 @@ kt_status kt_workspace_size(const kt_model *m, int32_t n, size_t *bytes) {
 
 static kt_status run(kt_model *m, const kt_seq_batch *b, const kt_move_batch *mv, const int8_t *cur_sign,
                      const double *cur_logabs, int8_t *sign, double *logv, int32_t *status, kt_stats *stats,
-                     void *ws, size_t ws_bytes, void *stream) {
+                     void *ws, size_t ws_bytes, void *stream, double *obs = nullptr) {
   if (!m || !b || b->n < 0 || m->host_only) return KT_EINVAL;
   if (b->n == 0) return KT_OK;
   if (!sign || !logv || !status || !b->offsets || !ws) return KT_EINVAL;
   if (mv && (!mv->kind || !mv->flavor || !mv->t_dag || !mv->t_ann || !mv->rem_idx || !cur_sign || !cur_logabs))
     return KT_EINVAL;
-  if (ws_bytes < kt::workspace_bytes(b->n, m->dev.n_kept, m->dev.d_max)) return KT_ENOMEM;
+  const int nobs_item = obs ? m->dev.nf + m->dev.n_orb : 0;
+  if (ws_bytes < kt::workspace_bytes(b->n, m->dev.n_kept, m->dev.d_max, nobs_item)) return KT_ENOMEM;
   kt::SeqView sv{b->n, b->offsets, b->tau, b->flavor, b->dagger};
   kt::MoveView mvv{};
   if (mv) mvv = kt::MoveView{mv->kind, mv->flavor, mv->t_dag, mv->t_ann, mv->rem_idx};
-  kt::Workspace w = kt::carve_workspace(ws, b->n, m->dev.n_kept, m->dev.d_max);
+  kt::Workspace w = kt::carve_workspace(ws, b->n, m->dev.n_kept, m->dev.d_max, nobs_item);
   const kt::StageEvents *tev = nullptr;
   if (m->timing_on && m->timing_used < (int)m->timing.size()) tev = &m->timing[m->timing_used++];
   const int rc = kt::launch_pipeline(m->dev, m->params.precision, m->kernel_dmax, m->group_lanes, sv,
-                                     mv ? &mvv : nullptr, cur_sign, cur_logabs, sign, logv, status, stats, w, stream, tev);
+                                     mv ? &mvv : nullptr, cur_sign, cur_logabs, sign, logv, status, stats, w, stream, tev,
+                                     obs);
   return rc == 0 ? KT_OK : KT_ECUDA;
 }
 
@@ -624,6 +636,18 @@ kt_status kt_timing_end(kt_model *m, double *ms, int32_t *launches) {
 kt_status kt_trace(kt_model *m, const kt_seq_batch *b, int8_t *sign, double *logabs, int32_t *status, kt_stats *stats,
                    void *ws, size_t ws_bytes, void *stream) {
   return run(m, b, nullptr, nullptr, nullptr, sign, logabs, status, stats, ws, ws_bytes, stream);
+}
+
+kt_status kt_measure_workspace_size(const kt_model *m, int32_t n, size_t *bytes) {
+  if (!m || !bytes || n < 0) return KT_EINVAL;
+  *bytes = kt::workspace_bytes(n, m->dev.n_kept, m->dev.d_max, m->dev.nf + m->dev.n_orb);
+  return KT_OK;
+}
+
+kt_status kt_measure(kt_model *m, const kt_seq_batch *b, int8_t *sign, double *logabs, double *obs, int32_t *status,
+                     kt_stats *stats, void *ws, size_t ws_bytes, void *stream) {
+  if (!obs && b && b->n > 0) return KT_EINVAL;
+  return run(m, b, nullptr, nullptr, nullptr, sign, logabs, status, stats, ws, ws_bytes, stream, obs);
 }
 
 kt_status kt_trace_ratio(kt_model *m, const kt_seq_batch *cur, const int8_t *cur_sign, const double *cur_logabs,

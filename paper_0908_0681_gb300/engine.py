@@ -88,6 +88,27 @@ def trace(model: kt.KtModel, seqs: DeviceSeqs, stats: torch.Tensor | None = None
     return sign, la, st
 
 
+def measure(model: kt.KtModel, seqs: DeviceSeqs, stats: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+    """Observables at tau = beta/2 (kt_measure): (sign, log|T|, obs [n, KT_MEASURE_NOBS], status)."""
+    n = seqs.n
+    dev = seqs.offsets.device
+    n_orb = kt.kt_model_query(model)["n_orb"]
+    sign = torch.empty(n, dtype=torch.int8, device=dev)
+    la = torch.empty(n, dtype=torch.float64, device=dev)
+    obs = torch.empty((n, kt.measure_nobs(n_orb)), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = torch.empty(max(kt.kt_measure_workspace_size(model, n), 1), dtype=torch.uint8, device=dev)
+    kt.kt_measure(model, seqs.batch(), sign, la, obs, st, stats, ws)
+    return sign, la, obs, st
+
+
+def measure_layout(n_orb: int) -> dict:
+    """Column slices of kt_measure's output: n_f, double occupancy, (n_up, n_dn) histogram."""
+    nf = 2 * n_orb
+    return {"n": slice(0, nf), "docc": slice(nf, nf + n_orb), "sector": slice(nf + n_orb, nf + n_orb + (n_orb + 1) ** 2)}
+
+
 def trace_ratio(model: kt.KtModel, seqs: DeviceSeqs, cur_sign: torch.Tensor, cur_logabs: torch.Tensor,
                 moves: DeviceMoves, stats: torch.Tensor | None = None, ws: torch.Tensor | None = None):
     """(sign int8, log|ratio| float64, status int32) device tensors for every walker."""

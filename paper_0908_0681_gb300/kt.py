@@ -58,7 +58,8 @@ class kt_move_batch(ctypes.Structure):
 # Every function the header declares (checked by the CPU test suite).
 ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_model_kept", "kt_model_spectrum",
                  "kt_model_destroy", "kt_workspace_size", "kt_trace", "kt_trace_ratio", "kt_timing_begin",
-                 "kt_timing_end", "kt_model_set_tiling", "kt_autotune", "kt_trace_ratio_static"]
+                 "kt_timing_end", "kt_model_set_tiling", "kt_autotune", "kt_trace_ratio_static",
+                 "kt_measure_workspace_size", "kt_measure"]
 
 _lib = None
 
@@ -89,6 +90,8 @@ def load():
     lib.kt_trace.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.kt_trace_ratio.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
                                    vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    lib.kt_measure_workspace_size.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t)]
+    lib.kt_measure.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.kt_timing_begin.argtypes = [vp, i32]
     lib.kt_model_set_tiling.argtypes = [vp, i32]
     lib.kt_trace_ratio_static.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
@@ -212,6 +215,24 @@ def kt_trace_ratio(m: KtModel, cur: kt_seq_batch, cur_sign, cur_logabs, moves: k
     _check(load().kt_trace_ratio(m.handle, ctypes.byref(cur), _ptr(cur_sign), _ptr(cur_logabs), ctypes.byref(moves),
                                  _ptr(sign), _ptr(logratio), _ptr(status), _ptr(stats), _ptr(workspace), ws_bytes,
                                  _stream_handle(stream)), "kt_trace_ratio")
+
+
+def kt_measure_workspace_size(m: KtModel, n: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().kt_measure_workspace_size(m.handle, int(n), ctypes.byref(b)), "kt_measure_workspace_size")
+    return int(b.value)
+
+
+def measure_nobs(n_orb: int) -> int:
+    """KT_MEASURE_NOBS: observables per walker returned by kt_measure."""
+    return 3 * n_orb + (n_orb + 1) ** 2
+
+
+def kt_measure(m: KtModel, batch: kt_seq_batch, sign, logabs, obs, status, stats=None, workspace=None,
+               stream=None) -> None:
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load().kt_measure(m.handle, ctypes.byref(batch), _ptr(sign), _ptr(logabs), _ptr(obs), _ptr(status),
+                             _ptr(stats), _ptr(workspace), ws_bytes, _stream_handle(stream)), "kt_measure")
 
 
 def kt_model_set_tiling(m: KtModel, group_lanes: int) -> None:
