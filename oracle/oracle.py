@@ -252,8 +252,10 @@ def edit(ops, kind: int, flavor: int, t_dag: float, t_ann: float, rem_idx: int):
 
     kind 0 (insert): c^+_flavor at t_dag and c_flavor at t_ann, each placed after
     every existing operator at an equal time; if t_dag == t_ann the c goes first.
-    kind 1 (remove): drop the c^+ at index rem_idx and the next operator of the
-    same flavor after it in cyclic order, which must be a c.
+    kind 1 (remove): drop the operator at index rem_idx and the next operator of
+    the same flavor after it in cyclic order, which must be of the other type (a
+    c^+ with the c that closes its segment, or a c with the c^+ that closes its
+    anti-segment).
     Returns the new list, or None if the move is malformed.
     """
     ops = list(ops)
@@ -269,7 +271,7 @@ def edit(ops, kind: int, flavor: int, t_dag: float, t_ann: float, rem_idx: int):
         return ops
     if kind == 1:
         K = len(ops)
-        if not (0 <= rem_idx < K) or ops[rem_idx][1] != flavor or ops[rem_idx][2] != 1:
+        if not (0 <= rem_idx < K) or ops[rem_idx][1] != flavor:
             return None
         j = None
         for step in range(1, K):
@@ -277,7 +279,7 @@ def edit(ops, kind: int, flavor: int, t_dag: float, t_ann: float, rem_idx: int):
             if ops[c][1] == flavor:
                 j = c
                 break
-        if j is None or ops[j][2] != 0:
+        if j is None or ops[j][2] == ops[rem_idx][2]:
             return None
         return [op for i, op in enumerate(ops) if i not in (rem_idx, j)]
     return None

@@ -89,6 +89,42 @@ def seven_orbital(trunc_eps: float = 1e-10) -> Workload:
 WORKLOADS = {"three_orbital": three_orbital, "five_orbital": five_orbital, "seven_orbital": seven_orbital}
 
 
+def five_orbital_sweep(beta: float = 50.0) -> Workload:
+    """The five-orbital model at inverse temperature beta, for full CT-HYB sweeps."""
+    w = five_orbital()
+    m = w.model
+    return Workload(f"five_orbital_sweep_beta{beta:g}", ModelSpec(m.n_orb, m.U, m.J, mu=m.mu, delta=m.delta, beta=beta),
+                    start="empty", order="none")
+
+
+def semicircular_hybridization(beta: float, n_flavors: int, n_tau: int = 2000, half_bandwidth: float = 2.0,
+                               n_quad: int = 4096) -> np.ndarray:
+    """Bath correlator of a semicircular density of states (the synthetic stand-in for a
+    DMFT hybridization function), tabulated for every flavor on tau_i = i beta / n_tau:
+
+        F(tau) = -Delta(tau) = t^2 int rho(e) e^{-tau e} / (1 + e^{-beta e}) de,
+        rho(e) = 2 sqrt(D^2 - e^2) / (pi D^2),  t = D / 2,
+
+    i.e. Delta = t^2 G of the half-filled Bethe lattice with bandwidth 2D. The integral
+    is taken over e = D cos(theta) with Gauss-Legendre nodes in theta. Shape
+    [n_flavors, n_tau + 1]."""
+    D = float(half_bandwidth)
+    t2 = (0.5 * D) ** 2
+    x, wq = np.polynomial.legendre.leggauss(n_quad)
+    th = 0.5 * np.pi * (x + 1.0)
+    wth = 0.5 * np.pi * wq * (2.0 / np.pi) * np.sin(th) ** 2   # rho(e) de = (2/pi) sin^2(theta) dtheta
+    e = D * np.cos(th)
+    tau = np.linspace(0.0, beta, n_tau + 1)
+    expo = -np.outer(tau, e) - np.logaddexp(0.0, -beta * e)[None, :]
+    F = t2 * (np.exp(expo) * wth[None, :]).sum(axis=1)
+    return np.ascontiguousarray(np.broadcast_to(F, (n_flavors, n_tau + 1)))
+
+
+def sweep_uniforms(n_steps: int, n_walkers: int, seed: int) -> np.ndarray:
+    """The random numbers of a run of Metropolis steps: [n_steps, n_walkers, 6] uniforms in [0, 1)."""
+    return np.random.default_rng(seed).random((n_steps, n_walkers, 6))
+
+
 @dataclass
 class Sequences:
     """CSR operator sequences: ops of walker i are offsets[i] .. offsets[i+1]-1."""

@@ -375,7 +375,7 @@ def test_density_only_segment_picture():
 
 def test_edit_insert_and_remove():
     """Local updates: insertion places each new operator after equal times; removal takes
-    the c^+ and its cyclic successor c of the same flavor."""
+    an operator and its cyclic successor of the same flavor, which has the other type."""
     ops = [(0.5, 0, 1), (1.0, 1, 0), (2.0, 0, 0), (3.0, 1, 1)]
     new = edit(ops, 0, 2, 1.5, 2.5, 0)
     assert new == [(0.5, 0, 1), (1.0, 1, 0), (1.5, 2, 1), (2.0, 0, 0), (2.5, 2, 0), (3.0, 1, 1)]
@@ -383,4 +383,7 @@ def test_edit_insert_and_remove():
     assert new == [(0.5, 0, 1), (1.0, 1, 0), (1.5, 2, 0), (2.0, 0, 0), (2.5, 2, 1), (3.0, 1, 1)]
     assert edit(ops, 1, 0, 0, 0, 0) == [(1.0, 1, 0), (3.0, 1, 1)]
     assert edit(ops, 1, 1, 0, 0, 3) == [(0.5, 0, 1), (2.0, 0, 0)]  # wraps: successor is at index 1
-    assert edit(ops, 1, 1, 0, 0, 1) is None   # index 1 is a c, not a c^+
+    assert edit(ops, 1, 1, 0, 0, 1) == [(0.5, 0, 1), (2.0, 0, 0)]   # a c and the c^+ after it
+    assert edit(ops, 1, 0, 0, 0, 2) == [(1.0, 1, 0), (3.0, 1, 1)]   # wraps: the c at 2, then the c^+ at 0
+    assert edit(ops, 1, 0, 0, 0, 1) is None   # index 1 is not of flavor 0
+    assert edit([(0.5, 0, 1), (1.0, 0, 1)], 1, 0, 0, 0, 0) is None   # successor of the same type
