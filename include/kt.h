@@ -144,9 +144,11 @@ typedef struct {
   const double *t_ann;     /* insert: time of the new c; each new operator goes after all
                               existing operators at an equal time; if t_dag == t_ann the c
                               is placed first */
-  const int32_t *rem_idx;  /* remove: index (inside the walker's sequence) of the c^+ to drop;
-                              the next operator of the same flavor after it, cyclically,
-                              must be a c and is dropped with it */
+  const int32_t *rem_idx;  /* remove: index (inside the walker's sequence) of an operator of
+                              this flavor to drop; the next operator of the same flavor after
+                              it, cyclically, must be of the other type (the c closing a
+                              segment, or the c^+ closing an anti-segment) and is dropped
+                              with it */
 } kt_move_batch;
 
 /* Human-readable name of a status code (static storage). */
@@ -237,6 +239,99 @@ kt_status kt_measure(kt_model *m, const kt_seq_batch *batch, int8_t *sign, doubl
 kt_status kt_trace_ratio_static(kt_model *m, const kt_seq_batch *cur, const int8_t *cur_sign,
                                 const double *cur_logabs, const kt_move_batch *moves, int8_t *sign,
                                 double *logratio, int32_t *status, kt_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched CT-HYB Markov chains (Sec. II): Metropolis insertion and removal  */
+/* of c^+/c pairs with the weight of Eq. (weight_strong) for a hybridization */
+/* that is diagonal in the flavors.                                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * Weight of a configuration: w = s_P * T * prod_f det G_f, with T the truncated
+ * local trace of this library, G_f[i][j] = Fh_f(tau'_i - tau_j) over the creator
+ * times tau'_i and annihilator times tau_j of flavor f, Fh_f(x) = F_f(x) for
+ * x >= 0 and -F_f(x + beta) for x < 0, F_f(tau) = -Delta_f(tau) >= 0 the bath
+ * correlator (linear interpolation of the caller's table), and s_P the sign of
+ * the permutation taking the bath operators, written flavor by flavor as
+ * a(tau'_1) a^+(tau_1) a(tau'_2) a^+(tau_2) ..., into descending time order.
+ *
+ * Each step proposes one move per walker from six caller-supplied uniforms
+ * u[0..5] in [0, 1) (DEVICE, [n_steps][n_walkers][6]):
+ *   u0 < 1/2 insert, else remove; flavor f = floor(u1 * n_flavors);
+ *   insert: t1 = u2 beta; with no f operators a coin u4 < 1/2 picks a segment
+ *     (c^+ at t1, c at t2) or an anti-segment (c at t1, c^+ at t2) and l = beta;
+ *     otherwise the next f operator after t1 (cyclically) decides (a c^+ next: a
+ *     segment; a c next: an anti-segment) and l is the distance to it;
+ *     t2 = t1 + u3 l (mod beta); proposal factor beta^2 (k_f = 0) or
+ *     beta l / (2 (k_f + 1));
+ *   remove: the floor(u2 * 2 k_f)-th f operator in time order and the next f
+ *     operator after it (cyclically); proposal factor 1 / beta^2 (k_f = 1) or
+ *     2 k_f / (beta l'), l' the distance from the first removed operator to the
+ *     f operator that follows the pair;
+ *   accept when log(u5) < log|w_new / w_old| + log(proposal factor).
+ * Null moves (nothing changes): removal from an empty flavor, insertion past
+ * k_cap pairs, t1 >= beta after rounding, t2 == t1.
+ * The trace ratio is this library's pipeline (the model's precision); the
+ * determinant ratio and the inverse matrices use O(k^2) updates in FP64 (the
+ * bordered-matrix inverse for an insertion, the Schur complement for a removal).
+ * Measurements, every meas_every steps, weighted by the sign of w:
+ *   G_f(tau): sum over pairs of M_ji dh(tau, tau_j - tau'_i), M = G_f^{-1},
+ *     dh = +1 in the bin of x > 0, -1 in the bin of x + beta for x < 0, binned on
+ *     n_bins bins of [0, beta); G_f(tau_b) = n_bins / beta^2 * g_tau[b] / sign_sum;
+ *   the expansion order of every flavor;
+ *   optionally the observables of kt_measure at beta/2.
+ * Every chain starts from the empty configuration.
+ */
+typedef struct kt_sweep kt_sweep;
+
+typedef struct {
+  int32_t n_walkers;    /* independent chains */
+  int32_t k_cap;        /* pairs per flavor and walker, 1..128 */
+  int32_t n_tau;        /* intervals of the bath table (>= 1) */
+  const double *hyb;    /* HOST [n_flavors][n_tau + 1]: F_f(i beta / n_tau) */
+  int32_t n_bins;       /* G(tau) bins (>= 1) */
+  int32_t measure_obs;  /* nonzero: accumulate the kt_measure observables at each measurement */
+} kt_sweep_params;
+
+/* Caller-owned DEVICE destinations for kt_sweep_get_state; NULL entries are skipped. */
+typedef struct {
+  int32_t *lens;          /* [n_walkers] operators per walker */
+  double *tau;            /* [n_walkers][capacity] capacity = 2 * n_flavors * k_cap */
+  uint8_t *flavor;        /* [n_walkers][capacity] */
+  uint8_t *dagger;        /* [n_walkers][capacity] */
+  int8_t *sign;           /* [n_walkers] sign of w */
+  int8_t *trace_sign;     /* [n_walkers] */
+  double *trace_logabs;   /* [n_walkers] log|T| */
+  double *det_logabs;     /* [n_walkers] sum over flavors of log|det G_f| (updated incrementally) */
+  int32_t *order;         /* [n_walkers][n_flavors] pairs per flavor */
+} kt_sweep_state;
+
+/* Caller-owned DEVICE destinations for kt_sweep_get_accumulators; NULL entries are skipped. */
+typedef struct {
+  double *g_tau;          /* [n_walkers][n_flavors][n_bins] */
+  double *sign_sum;       /* [n_walkers] */
+  double *order_sum;      /* [n_walkers][n_flavors] sign-weighted */
+  double *obs_sum;        /* [n_walkers][KT_MEASURE_NOBS(n_orb)] sign-weighted */
+} kt_sweep_accum;
+
+/* Counters of kt_sweep_counters (HOST [8]): 0 insertions proposed, 1 accepted,
+ * 2 removals proposed, 3 accepted, 4 null moves, 5 insertions refused at k_cap,
+ * 6 proposals rejected because the trace pipeline reported an error, 7 measurements. */
+#define KT_SWEEP_NCOUNTERS 8
+
+/* Allocate the chains of a model (device state on the current device; the model
+ * must outlive the sweep) and set every walker to the empty configuration.
+ * Synchronises. Errors: KT_EINVAL, KT_ENOMEM, KT_ECUDA. */
+kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out);
+/* n_steps Metropolis steps of every walker, measuring after every meas_every-th
+ * step (0: never). Enqueued on the stream; returns launch errors only. */
+kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream);
+kt_status kt_sweep_get_state(kt_sweep *s, const kt_sweep_state *dst, void *stream);
+kt_status kt_sweep_get_accumulators(kt_sweep *s, const kt_sweep_accum *dst, void *stream);
+/* Synchronises the device and copies the counters to out[KT_SWEEP_NCOUNTERS]. */
+kt_status kt_sweep_counters(kt_sweep *s, unsigned long long *out);
+/* Zero the accumulators and counters (the configurations are kept). */
+kt_status kt_sweep_reset_accumulators(kt_sweep *s, void *stream);
+void kt_sweep_destroy(kt_sweep *s);
 
 /* Kernel tiling: every (walker, kept state) item of the Krylov stage is
  * processed by a group of group_lanes lanes of one warp (32 / group_lanes items

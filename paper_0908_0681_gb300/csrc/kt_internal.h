@@ -44,12 +44,16 @@ struct DevModel {
   const float *kept_vec32;
 };
 
+// Operator sequences: walker i owns entries offsets[i] .. offsets[i] + K_i - 1 with
+// K_i = lens[i] when lens is set (fixed-capacity slots of the sweep state) and
+// offsets[i+1] - offsets[i] otherwise (the CSR batches of the ABI).
 struct SeqView {
   int n;
   const int32_t *offsets;
   const double *tau;
   const uint8_t *flavor;
   const uint8_t *dagger;
+  const int32_t *lens = nullptr;
 };
 
 struct MoveView {

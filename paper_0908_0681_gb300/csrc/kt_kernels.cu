@@ -50,7 +50,7 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
     ws.counters[1] = 0;
   }
   if (w >= S.n) return;
-  const int o = S.offsets[w], K = S.offsets[w + 1] - o;
+  const int o = S.offsets[w], K = S.lens ? S.lens[w] : S.offsets[w + 1] - o;
   int st = KT_OK;
   int4 d = make_int4(-1, 0, 0, K);
   if (K < 0) {
@@ -81,7 +81,7 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
       }
     } else if (kind == 1) {
       const int r = mv.rem_idx[w];
-      if (r < 0 || r >= K || S.flavor[o + r] != f || S.dagger[o + r] != 1) {
+      if (r < 0 || r >= K || S.flavor[o + r] != f) {
         st = KT_EINVAL;
       } else {
         int j = -1;
@@ -92,7 +92,7 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
             break;
           }
         }
-        if (j < 0 || S.dagger[o + j] != 0) {
+        if (j < 0 || S.dagger[o + j] == S.dagger[o + r]) {
           st = KT_EINVAL;
         } else {
           d = make_int4(1, r < j ? r : j, r < j ? j : r, K - 2);

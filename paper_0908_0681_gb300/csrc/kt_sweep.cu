@@ -1,0 +1,732 @@
+// Batched CT-HYB Markov chains (Sec. II): one Metropolis step per walker and
+// launch group, with the weight of Eq. (weight_strong) for a flavor-diagonal
+// hybridization, w = s_P * T * prod_f det G_f.
+//
+// Per step (all on the caller's stream, no host synchronisation):
+//   propose  - one warp per walker: the move from its six uniforms, the
+//              proposal factor, and the FP64 determinant ratio with the
+//              permutation sign. Insertion borders G_f with a new creator row
+//              and annihilator column: ratio lambda = d - R M C (M = G_f^{-1}),
+//              and the vectors M C and R M are kept for the update. Removal of
+//              the pair in storage row i / column j: ratio M_ji.
+//   trace    - the trace-ratio pipeline of the library on the proposed edits.
+//   accept   - one warp per walker: Metropolis test on the product of the
+//              ratios; an accepted move edits the walker's sequence in place and
+//              updates M in O(k^2) (bordered inverse, or Schur complement after
+//              moving the removed row and column to the end).
+//   measure  - every meas_every steps: G_f(tau) from M, the expansion orders,
+//              and optionally the observables at beta/2 (kt_measure pipeline).
+//
+// Storage of flavor f of walker w: creator times row_t[0..k), annihilator times
+// col_t[0..k) in insertion order (not sorted), and M = G_f^{-1} row-major with
+// rows indexed by annihilators and columns by creators, M[j * k_cap + i].
+// The weight's sign is s_P * sign(T) * prod sign(det G_f); it is independent of
+// how rows and columns are ordered (a row or column swap flips det G_f and the
+// permutation sign together), so an insertion appends its pair at the end of the
+// flavor's block of the bath-operator sequence and
+//   s_P(new) / s_P(old) = (-1)^X,  X = sum over the two new times t of
+//     #{old ops x : flavor(x) <= f, tau_x < t} + #{old ops x : flavor(x) > f, tau_x > t}
+//   plus 1 if tau'_new < tau_new,
+// and a removal is the inverse of inserting its pair into the reduced configuration.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cmath>
+#include <new>
+
+#include "kt_internal.h"
+
+#include "kt_device.cuh"
+
+namespace kt {
+namespace {
+using namespace dev;
+
+enum { C_INS_PROP, C_INS_ACC, C_REM_PROP, C_REM_ACC, C_NULL, C_CAP, C_TRACE_ERR, C_MEAS };
+
+struct SweepView {
+  int nw, nf, kcap, cap, n_tau, n_bins, nobs;
+  double beta;
+  const int32_t *offsets;
+  int32_t *lens;
+  double *tau;
+  uint8_t *flv, *dag;
+  int32_t *kf;        // [nw][nf]
+  double *row_t;      // [nw][nf][kcap]
+  double *col_t;      // [nw][nf][kcap]
+  double *M;          // [nw][nf][kcap][kcap]
+  const double *hyb;  // [nf][n_tau + 1]
+  int8_t *tr_sign;
+  double *tr_log;
+  int8_t *w_sign;
+  double *det_log;
+  // proposal
+  uint8_t *mv_kind, *mv_flv;
+  double *mv_tdag, *mv_tann;
+  int32_t *mv_rem;
+  int8_t *p_valid;    // 1 move to test, 0 null
+  int8_t *p_sign;     // sign of the determinant ratio times (-1)^X
+  double *p_lprop;    // log proposal factor
+  double *p_ldet;     // log |determinant ratio|
+  double *p_lambda;   // insertion: lambda
+  int32_t *p_ij;      // removal: [2] storage row i (creator), column j (annihilator)
+  double *p_vec;      // insertion: [nw][2 kcap]: M C (by annihilator), R M (by creator)
+  // trace ratio outputs
+  int8_t *r_sign;
+  double *r_log;
+  int32_t *r_status;
+  // measurement
+  double *g_acc, *sign_sum, *order_sum, *obs_sum, *obs_tmp;
+  int8_t *m_sign;
+  double *m_log;
+  int32_t *m_status;
+  unsigned long long *counters;
+};
+
+// Fh_f(x): linear interpolation of F_f on tau_i = i beta / n_tau, antiperiodic for x < 0.
+__device__ __forceinline__ double hyb_F(const SweepView &S, int f, double t) {
+  const double pos = t / S.beta * S.n_tau;
+  int i = (int)floor(pos);
+  i = i < 0 ? 0 : (i > S.n_tau - 1 ? S.n_tau - 1 : i);
+  const double fr = pos - i;
+  const double *tab = S.hyb + (size_t)f * (S.n_tau + 1);
+  const double a = __ldg(tab + i), b = __ldg(tab + i + 1);
+  return a + fr * (b - a);
+}
+__device__ __forceinline__ double hyb_Fh(const SweepView &S, int f, double x) {
+  return x >= 0.0 ? hyb_F(S, f, x) : -hyb_F(S, f, x + S.beta);
+}
+
+__device__ __forceinline__ int warp_sum(int v) { return __reduce_add_sync(FULL, (unsigned)v); }
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Index of the m-th (0-based) operator of flavor f among ops[0 .. K), or -1.
+__device__ int nth_of_flavor(const uint8_t *fl, int K, int f, int m, int lane) {
+  int cnt = 0;
+  for (int base = 0; base < K; base += 32) {
+    const int idx = base + lane;
+    unsigned msk = __ballot_sync(FULL, idx < K && fl[idx] == f);
+    const int c = __popc(msk);
+    if (cnt + c > m) {
+      for (int r = m - cnt; r > 0; --r) msk &= msk - 1;
+      return base + __ffs(msk) - 1;
+    }
+    cnt += c;
+  }
+  return -1;
+}
+
+// Parity count X of the permutation sign change for a pair (tdag, tann) of flavor f
+// appended at the end of its flavor block, over the ops of [0, K) except skip1, skip2.
+__device__ int perm_count(const double *tau, const uint8_t *fl, int K, int f, double tdag, double tann, int skip1,
+                          int skip2, int lane) {
+  int c = 0;
+  for (int idx = lane; idx < K; idx += 32) {
+    if (idx == skip1 || idx == skip2) continue;
+    const double t = tau[idx];
+    const int g = fl[idx];
+    if (g <= f) c += (t < tdag) + (t < tann);
+    else c += (t > tdag) + (t > tann);
+  }
+  c = warp_sum(c);
+  return c + (tdag < tann ? 1 : 0);
+}
+
+__global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni) {
+  extern __shared__ double sh[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (w >= S.nw) return;
+  double *Cv = sh + (size_t)wib * 2 * S.kcap;  // new column C (by creator) / row R (by annihilator)
+  double *Rv = Cv + S.kcap;
+  const double *u = uni + (size_t)w * 6;
+  const int nf = S.nf;
+  const double beta = S.beta;
+  const int o = S.offsets[w], K = S.lens[w];
+  const double *tau = S.tau + o;
+  const uint8_t *fl = S.flv + o, *dg = S.dag + o;
+  int f = (int)(u[1] * nf);
+  f = f > nf - 1 ? nf - 1 : (f < 0 ? 0 : f);
+  const int kf = S.kf[w * nf + f];
+  const size_t fb = (size_t)w * nf + f;
+  const double *Mf = S.M + fb * S.kcap * S.kcap;
+  const double *rt = S.row_t + fb * S.kcap, *ct = S.col_t + fb * S.kcap;
+  int valid = 0;
+  if (u[0] < 0.5) {
+    // ---- insertion ----
+    if (lane == 0) atomicAdd(&S.counters[C_INS_PROP], 1ull);
+    const double t1 = u[2] * beta;
+    bool null_move = false;
+    if (kf >= S.kcap) {
+      null_move = true;
+      if (lane == 0) atomicAdd(&S.counters[C_CAP], 1ull);
+    }
+    if (!(t1 < beta)) null_move = true;
+    bool seg = true;
+    double lmax = beta;
+    if (!null_move && kf > 0) {
+      int first_any = -1, found = -1;
+      for (int base = 0; base < K && found < 0; base += 32) {
+        const int idx = base + lane;
+        const bool isf = idx < K && fl[idx] == f;
+        const unsigned m_any = __ballot_sync(FULL, isf);
+        const unsigned m_after = __ballot_sync(FULL, isf && tau[idx] > t1);
+        if (first_any < 0 && m_any) first_any = base + __ffs(m_any) - 1;
+        if (m_after) found = base + __ffs(m_after) - 1;
+      }
+      const int j = found >= 0 ? found : first_any;
+      if (j < 0) {  // the operator counts always match k_f; the guard only keeps reads in bounds
+        null_move = true;
+      } else {
+        seg = dg[j] == 1;
+        const double tn = tau[j];
+        lmax = tn > t1 ? tn - t1 : tn + beta - t1;
+      }
+    } else if (!null_move) {
+      seg = u[4] < 0.5;
+    }
+    // separate multiply and add (no contraction): the proposal times are rounded as
+    // written, so chains driven by the same uniforms visit bit-identical times
+    double t2 = __dadd_rn(t1, __dmul_rn(u[3], lmax));
+    if (t2 >= beta) t2 -= beta;
+    if (t2 == t1) null_move = true;
+    if (!null_move) {
+      const double td = seg ? t1 : t2, ta = seg ? t2 : t1;
+      const double lp = kf == 0 ? 2.0 * log(beta) : log(beta * lmax / (2.0 * (kf + 1)));
+      // bordered matrix: C_i = Fh(tau'_i - ta), R_j = Fh(td - tau_j), d = Fh(td - ta)
+      for (int i = lane; i < kf; i += 32) {
+        Cv[i] = hyb_Fh(S, f, rt[i] - ta);
+        Rv[i] = hyb_Fh(S, f, td - ct[i]);
+      }
+      __syncwarp();
+      double *mc = S.p_vec + (size_t)w * 2 * S.kcap, *rm = mc + S.kcap;
+      double part = 0.0;
+      for (int j = lane; j < kf; j += 32) {  // (M C)_j
+        double a = 0.0;
+        for (int i = 0; i < kf; ++i) a = fma(Mf[(size_t)j * S.kcap + i], Cv[i], a);
+        mc[j] = a;
+        part = fma(Rv[j], a, part);
+      }
+      for (int i = lane; i < kf; i += 32) {  // (R M)_i
+        double a = 0.0;
+        for (int j = 0; j < kf; ++j) a = fma(Rv[j], Mf[(size_t)j * S.kcap + i], a);
+        rm[i] = a;
+      }
+      const double lambda = hyb_Fh(S, f, td - ta) - warp_sum(part);
+      const int X = perm_count(tau, fl, K, f, td, ta, -1, -1, lane);
+      if (lane == 0) {
+        S.mv_kind[w] = 0;
+        S.mv_tdag[w] = td;
+        S.mv_tann[w] = ta;
+        S.p_lprop[w] = lp;
+        S.p_ldet[w] = log(fabs(lambda));
+        S.p_sign[w] = (int8_t)((lambda > 0.0 ? 1 : (lambda < 0.0 ? -1 : 0)) * ((X & 1) ? -1 : 1));
+        S.p_lambda[w] = lambda;
+      }
+      valid = lambda != 0.0 ? 1 : 0;
+    }
+  } else {
+    // ---- removal ----
+    if (lane == 0) atomicAdd(&S.counters[C_REM_PROP], 1ull);
+    if (kf > 0) {
+      int jsel = (int)(u[2] * 2 * kf);
+      jsel = jsel > 2 * kf - 1 ? 2 * kf - 1 : jsel;
+      const int a = nth_of_flavor(fl, K, f, jsel, lane);
+      const int b = nth_of_flavor(fl, K, f, (jsel + 1) % (2 * kf), lane);
+      const int c = kf > 1 ? nth_of_flavor(fl, K, f, (jsel + 2) % (2 * kf), lane) : a;
+      // the operator counts always match k_f; the guard only keeps every read in bounds
+      const bool found = a >= 0 && b >= 0 && c >= 0;
+      const double t1 = found ? tau[a] : 0.0, t2 = found ? tau[b] : 0.0;
+      double lp;
+      if (kf == 1) {
+        lp = -2.0 * log(beta);
+      } else {
+        const double tc = found ? tau[c] : 0.0;
+        const double lmax = tc > t1 ? tc - t1 : tc + beta - t1;
+        lp = log(2.0 * kf / (beta * lmax));
+      }
+      const int da = found ? dg[a] : 0, db = found ? dg[b] : 0;
+      const double td = da == 1 ? t1 : t2, ta = da == 1 ? t2 : t1;
+      int ri = -1, cj = -1;
+      for (int base = 0; base < kf; base += 32) {
+        const int idx = base + lane;
+        const unsigned mr = __ballot_sync(FULL, idx < kf && rt[idx] == td);
+        const unsigned mcn = __ballot_sync(FULL, idx < kf && ct[idx] == ta);
+        if (ri < 0 && mr) ri = base + __ffs(mr) - 1;
+        if (cj < 0 && mcn) cj = base + __ffs(mcn) - 1;
+      }
+      if (found && ri >= 0 && cj >= 0 && da != db) {
+        const double ratio = Mf[(size_t)cj * S.kcap + ri];
+        const int X = perm_count(tau, fl, K, f, td, ta, a, b, lane);
+        if (lane == 0) {
+          S.mv_kind[w] = 1;
+          S.mv_rem[w] = a;
+          S.p_lprop[w] = lp;
+          S.p_ldet[w] = log(fabs(ratio));
+          S.p_sign[w] = (int8_t)((ratio > 0.0 ? 1 : (ratio < 0.0 ? -1 : 0)) * ((X & 1) ? -1 : 1));
+          S.p_ij[2 * w] = ri;
+          S.p_ij[2 * w + 1] = cj;
+        }
+        valid = ratio != 0.0 ? 1 : 0;
+      }
+    }
+  }
+  if (lane == 0) {
+    S.mv_flv[w] = (uint8_t)f;
+    S.p_valid[w] = (int8_t)valid;
+    if (!valid) {
+      // a move the trace stage skips (structural zero of the pipeline is avoided:
+      // kind 2 is rejected by its validation without any work)
+      S.mv_kind[w] = 2;
+      atomicAdd(&S.counters[C_NULL], 1ull);
+    }
+  }
+}
+
+__global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni, const int4 *__restrict__ desc) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= S.nw) return;
+  if (!S.p_valid[w]) return;
+  const int st = S.r_status[w];
+  if (st != KT_OK) {
+    if (lane == 0) atomicAdd(&S.counters[C_TRACE_ERR], 1ull);
+    return;
+  }
+  const int tsg = S.r_sign[w];
+  if (tsg == 0) return;  // the new trace is zero
+  const double logR = S.r_log[w] + S.p_ldet[w] + S.p_lprop[w];
+  const double u5 = uni[(size_t)w * 6 + 5];
+  const bool accept = (u5 > 0.0 ? log(u5) : -INFINITY) < logR;
+  if (!accept) return;
+  const int nf = S.nf, f = S.mv_flv[w], kind = S.mv_kind[w];
+  const int o = S.offsets[w];
+  double *tau = S.tau + o;
+  uint8_t *fl = S.flv + o, *dg = S.dag + o;
+  const int4 d = desc[w];
+  // 1. the walker's sequence, edited in place (same index map as the trace pipeline)
+  if (kind == 0) {
+    const double td = S.mv_tdag[w], ta = S.mv_tann[w];
+    const double tA = td < ta ? td : ta, tB = td < ta ? ta : td;
+    const int dA = td < ta ? 1 : 0, dB = 1 - dA;
+    // new index i: i < p1 old i; i == p1 A; p1 < i <= p2 old i-1; i == p2+1 B; else old i-2.
+    // Chunks from the top: every source index is <= i, read before any write of the chunk.
+    const int Kn = d.w;
+    for (int top = Kn - 1; top >= 0; top -= 32) {
+      const int i = top - lane;
+      double t = 0.0;
+      int g = 0, h = 0;
+      if (i >= 0) {
+        int src = -1;
+        if (i < d.y) src = i;
+        else if (i == d.y) { t = tA; g = f; h = dA; }
+        else if (i <= d.z) src = i - 1;
+        else if (i == d.z + 1) { t = tB; g = f; h = dB; }
+        else src = i - 2;
+        if (src >= 0) { t = tau[src]; g = fl[src]; h = dg[src]; }
+      }
+      __syncwarp();
+      if (i >= 0) { tau[i] = t; fl[i] = (uint8_t)g; dg[i] = (uint8_t)h; }
+      __syncwarp();
+    }
+  } else {
+    // new index i: i < p1 old i; p1 <= i < p2 - 1 old i+1; else old i+2. Chunks from the bottom.
+    const int Kn = d.w;
+    for (int base = 0; base < Kn; base += 32) {
+      const int i = base + lane;
+      double t = 0.0;
+      int g = 0, h = 0;
+      if (i < Kn) {
+        const int src = i < d.y ? i : (i < d.z - 1 ? i + 1 : i + 2);
+        t = tau[src]; g = fl[src]; h = dg[src];
+      }
+      __syncwarp();
+      if (i < Kn) { tau[i] = t; fl[i] = (uint8_t)g; dg[i] = (uint8_t)h; }
+      __syncwarp();
+    }
+  }
+  // 2. the inverse bath matrix of flavor f
+  const size_t fb = (size_t)w * nf + f;
+  const int kc = S.kcap;
+  double *Mf = S.M + fb * kc * kc;
+  double *rt = S.row_t + fb * kc, *ct = S.col_t + fb * kc;
+  const int k = S.kf[fb];
+  if (kind == 0) {
+    const double lam = S.p_lambda[w], il = 1.0 / lam;
+    const double *mc = S.p_vec + (size_t)w * 2 * kc, *rm = mc + kc;
+    for (int e = lane; e < k * k; e += 32) {
+      const int j = e / k, i = e - j * k;
+      Mf[(size_t)j * kc + i] = fma(mc[j] * il, rm[i], Mf[(size_t)j * kc + i]);
+    }
+    for (int e = lane; e < k; e += 32) {
+      Mf[(size_t)e * kc + k] = -mc[e] * il;   // new creator column
+      Mf[(size_t)k * kc + e] = -rm[e] * il;   // new annihilator row
+    }
+    if (lane == 0) {
+      Mf[(size_t)k * kc + k] = il;
+      rt[k] = S.mv_tdag[w];
+      ct[k] = S.mv_tann[w];
+      S.kf[fb] = k + 1;
+    }
+  } else {
+    const int i = S.p_ij[2 * w], j = S.p_ij[2 * w + 1], L = k - 1;
+    // creator i <-> L: columns of M; annihilator j <-> L: rows of M
+    if (i != L)
+      for (int r = lane; r < k; r += 32) {
+        const double x = Mf[(size_t)r * kc + i];
+        Mf[(size_t)r * kc + i] = Mf[(size_t)r * kc + L];
+        Mf[(size_t)r * kc + L] = x;
+      }
+    __syncwarp();
+    if (j != L)
+      for (int c = lane; c < k; c += 32) {
+        const double x = Mf[(size_t)j * kc + c];
+        Mf[(size_t)j * kc + c] = Mf[(size_t)L * kc + c];
+        Mf[(size_t)L * kc + c] = x;
+      }
+    __syncwarp();
+    const double is = 1.0 / Mf[(size_t)L * kc + L];
+    for (int e = lane; e < L * L; e += 32) {
+      const int r = e / L, c = e - r * L;
+      Mf[(size_t)r * kc + c] -= Mf[(size_t)r * kc + L] * Mf[(size_t)L * kc + c] * is;
+    }
+    if (lane == 0) {
+      rt[i] = rt[L];
+      ct[j] = ct[L];
+      S.kf[fb] = L;
+    }
+  }
+  if (lane == 0) {
+    S.lens[w] = d.w;
+    S.tr_sign[w] = (int8_t)(tsg * S.tr_sign[w]);
+    S.tr_log[w] += S.r_log[w];
+    S.w_sign[w] = (int8_t)(S.w_sign[w] * tsg * S.p_sign[w]);
+    S.det_log[w] += S.p_ldet[w];
+    atomicAdd(&S.counters[kind == 0 ? C_INS_ACC : C_REM_ACC], 1ull);
+  }
+}
+
+__global__ void sweep_measure_kernel(SweepView S) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= S.nw) return;
+  const double s = (double)S.w_sign[w];
+  const int nf = S.nf, kc = S.kcap, nb = S.n_bins;
+  const double beta = S.beta;
+  if (lane == 0) {
+    S.sign_sum[w] += s;
+    if (w == 0) atomicAdd(&S.counters[C_MEAS], 1ull);
+  }
+  for (int f = 0; f < nf; ++f) {
+    const size_t fb = (size_t)w * nf + f;
+    const int k = S.kf[fb];
+    if (lane == 0) S.order_sum[fb] += s * k;
+    const double *Mf = S.M + fb * kc * kc;
+    const double *rt = S.row_t + fb * kc, *ct = S.col_t + fb * kc;
+    double *g = S.g_acc + fb * nb;
+    for (int e = lane; e < k * k; e += 32) {
+      const int j = e / k, i = e - j * k;
+      double x = ct[j] - rt[i], v = Mf[(size_t)j * kc + i];
+      if (x < 0.0) {
+        x += beta;
+        v = -v;
+      }
+      int b = (int)(x / beta * nb);
+      b = b > nb - 1 ? nb - 1 : (b < 0 ? 0 : b);
+      atomicAdd(g + b, s * v);
+    }
+  }
+}
+
+__global__ void sweep_obs_accumulate_kernel(SweepView S) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= S.nw * S.nobs) return;
+  const int w = t / S.nobs;
+  const double v = S.obs_tmp[t];
+  if (isfinite(v)) S.obs_sum[t] += (double)S.w_sign[w] * v;
+}
+
+__global__ void sweep_init_kernel(SweepView S, const int8_t *sg, const double *lg) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= S.nw) return;
+  S.tr_sign[w] = sg[w];
+  S.tr_log[w] = lg[w];
+  S.w_sign[w] = sg[w];
+  S.det_log[w] = 0.0;
+}
+
+template <typename T>
+__global__ void gather_padded_kernel(const T *src, T *dst, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = src[t];
+}
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace kt
+
+struct kt_sweep {
+  kt_model *model = nullptr;
+  kt::ModelView mv{};
+  kt::SweepView v{};
+  void *mem = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool measure_obs = false;
+};
+
+namespace {
+
+kt_status carve_and_alloc(kt_sweep *s) {
+  kt::SweepView &v = s->v;
+  const size_t nw = v.nw, nf = v.nf, kc = v.kcap, cap = v.cap;
+  size_t b = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = b;
+    b += kt::up256(bytes);
+    return at;
+  };
+  const size_t o_off = take((nw + 1) * 4), o_len = take(nw * 4), o_tau = take(nw * cap * 8), o_flv = take(nw * cap),
+               o_dag = take(nw * cap), o_kf = take(nw * nf * 4), o_rt = take(nw * nf * kc * 8),
+               o_ct = take(nw * nf * kc * 8), o_M = take(nw * nf * kc * kc * 8), o_hyb = take(nf * (v.n_tau + 1) * 8),
+               o_trs = take(nw), o_trl = take(nw * 8), o_ws = take(nw), o_dl = take(nw * 8), o_mk = take(nw),
+               o_mf = take(nw), o_md = take(nw * 8), o_ma = take(nw * 8), o_mr = take(nw * 4), o_pv = take(nw),
+               o_ps = take(nw), o_plp = take(nw * 8), o_pld = take(nw * 8), o_plam = take(nw * 8),
+               o_pij = take(nw * 2 * 4), o_pvec = take(nw * 2 * kc * 8), o_rs = take(nw), o_rl = take(nw * 8),
+               o_rst = take(nw * 4), o_g = take(nw * nf * v.n_bins * 8), o_ss = take(nw * 8), o_os = take(nw * nf * 8),
+               o_obs = take(nw * v.nobs * 8), o_obt = take(nw * v.nobs * 8), o_msg = take(nw), o_mlg = take(nw * 8),
+               o_mst = take(nw * 4), o_cnt = take(KT_SWEEP_NCOUNTERS * 8);
+  if (cudaMalloc(&s->mem, b) != cudaSuccess) {
+    cudaGetLastError();
+    s->mem = nullptr;
+    return KT_ENOMEM;
+  }
+  if (cudaMemset(s->mem, 0, b) != cudaSuccess) return KT_ECUDA;
+  char *p = (char *)s->mem;
+  v.offsets = (int32_t *)(p + o_off);
+  v.lens = (int32_t *)(p + o_len);
+  v.tau = (double *)(p + o_tau);
+  v.flv = (uint8_t *)(p + o_flv);
+  v.dag = (uint8_t *)(p + o_dag);
+  v.kf = (int32_t *)(p + o_kf);
+  v.row_t = (double *)(p + o_rt);
+  v.col_t = (double *)(p + o_ct);
+  v.M = (double *)(p + o_M);
+  v.hyb = (const double *)(p + o_hyb);
+  v.tr_sign = (int8_t *)(p + o_trs);
+  v.tr_log = (double *)(p + o_trl);
+  v.w_sign = (int8_t *)(p + o_ws);
+  v.det_log = (double *)(p + o_dl);
+  v.mv_kind = (uint8_t *)(p + o_mk);
+  v.mv_flv = (uint8_t *)(p + o_mf);
+  v.mv_tdag = (double *)(p + o_md);
+  v.mv_tann = (double *)(p + o_ma);
+  v.mv_rem = (int32_t *)(p + o_mr);
+  v.p_valid = (int8_t *)(p + o_pv);
+  v.p_sign = (int8_t *)(p + o_ps);
+  v.p_lprop = (double *)(p + o_plp);
+  v.p_ldet = (double *)(p + o_pld);
+  v.p_lambda = (double *)(p + o_plam);
+  v.p_ij = (int32_t *)(p + o_pij);
+  v.p_vec = (double *)(p + o_pvec);
+  v.r_sign = (int8_t *)(p + o_rs);
+  v.r_log = (double *)(p + o_rl);
+  v.r_status = (int32_t *)(p + o_rst);
+  v.g_acc = (double *)(p + o_g);
+  v.sign_sum = (double *)(p + o_ss);
+  v.order_sum = (double *)(p + o_os);
+  v.obs_sum = (double *)(p + o_obs);
+  v.obs_tmp = (double *)(p + o_obt);
+  v.m_sign = (int8_t *)(p + o_msg);
+  v.m_log = (double *)(p + o_mlg);
+  v.m_status = (int32_t *)(p + o_mst);
+  v.counters = (unsigned long long *)(p + o_cnt);
+  return KT_OK;
+}
+
+kt::SeqView seq_view(const kt_sweep *s) {
+  kt::SeqView sv{s->v.nw, s->v.offsets, s->v.tau, s->v.flv, s->v.dag};
+  sv.lens = s->v.lens;
+  return sv;
+}
+
+// the trace pipeline on the current configurations, with the observables at beta/2 when obs != nullptr
+int current_traces(kt_sweep *s, int8_t *sg, double *lg, int32_t *st, double *obs, cudaStream_t stream) {
+  const kt::DevModel &M = *s->mv.dev;
+  const kt::Workspace w = kt::carve_workspace(s->ws, s->v.nw, M.n_kept, M.d_max, obs ? M.nf + M.n_orb : 0);
+  return kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, seq_view(s), nullptr, nullptr,
+                             nullptr, sg, lg, st, nullptr, w, stream, nullptr, obs);
+}
+
+}  // namespace
+
+extern "C" {
+
+kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out) {
+  if (!m || !p || !out || !p->hyb) return KT_EINVAL;
+  *out = nullptr;
+  const kt::ModelView mv = kt::model_view(m);
+  if (mv.host_only) return KT_EINVAL;
+  if (p->n_walkers < 1 || p->k_cap < 1 || p->k_cap > 128 || p->n_tau < 1 || p->n_bins < 1) return KT_EINVAL;
+  const int nf = mv.dev->nf;
+  for (long long i = 0; i < (long long)nf * (p->n_tau + 1); ++i)
+    if (!std::isfinite(p->hyb[i])) return KT_EINVAL;
+  kt_sweep *s = new (std::nothrow) kt_sweep();
+  if (!s) return KT_ENOMEM;
+  s->model = m;
+  s->mv = mv;
+  s->measure_obs = p->measure_obs != 0;
+  kt::SweepView &v = s->v;
+  v.nw = p->n_walkers;
+  v.nf = nf;
+  v.kcap = p->k_cap;
+  v.cap = 2 * nf * p->k_cap;
+  v.n_tau = p->n_tau;
+  v.n_bins = p->n_bins;
+  v.nobs = KT_MEASURE_NOBS(mv.dev->n_orb);
+  v.beta = mv.dev->beta;
+  kt_status rc = carve_and_alloc(s);
+  if (rc == KT_OK) {
+    s->ws_bytes = kt::workspace_bytes(v.nw, mv.dev->n_kept, mv.dev->d_max, nf + mv.dev->n_orb);
+    if (cudaMalloc(&s->ws, s->ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s->ws = nullptr;
+      rc = KT_ENOMEM;
+    }
+  }
+  if (rc == KT_OK) {
+    int32_t *offs = (int32_t *)malloc(sizeof(int32_t) * (v.nw + 1));
+    if (!offs) rc = KT_ENOMEM;
+    if (rc == KT_OK) {
+      for (int w = 0; w <= v.nw; ++w) offs[w] = w * v.cap;
+      if (cudaMemcpy((void *)v.offsets, offs, sizeof(int32_t) * (v.nw + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy((void *)v.hyb, p->hyb, sizeof(double) * nf * (p->n_tau + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = KT_ECUDA;
+      free(offs);
+    }
+  }
+  if (rc == KT_OK) {
+    // empty configurations: weight = trace (no determinants)
+    if (current_traces(s, v.m_sign, v.m_log, v.m_status, nullptr, 0) != 0) rc = KT_ECUDA;
+    if (rc == KT_OK) {
+      kt::sweep_init_kernel<<<(v.nw + 255) / 256, 256>>>(v, v.m_sign, v.m_log);
+      if (cudaDeviceSynchronize() != cudaSuccess) rc = KT_ECUDA;
+    }
+  }
+  if (rc != KT_OK) {
+    cudaGetLastError();
+    kt_sweep_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return KT_OK;
+}
+
+kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream) {
+  if (!s || n_steps < 0 || meas_every < 0) return KT_EINVAL;
+  if (n_steps == 0) return KT_OK;
+  if (!uniforms) return KT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  kt::SweepView &v = s->v;
+  const kt::DevModel &M = *s->mv.dev;
+  // ratios: the plain layout (no measurement regions, so the items split at the middle operator)
+  const kt::Workspace w = kt::carve_workspace(s->ws, v.nw, M.n_kept, M.d_max, 0);
+  const kt::MoveView mvv{v.mv_kind, v.mv_flv, v.mv_tdag, v.mv_tann, v.mv_rem};
+  const kt::SeqView sv = seq_view(s);
+  const int wpb = 8;
+  const unsigned grid = (unsigned)((v.nw + wpb - 1) / wpb);
+  const size_t shm = (size_t)wpb * 2 * v.kcap * sizeof(double);
+  cudaGetLastError();
+  for (int step = 0; step < n_steps; ++step) {
+    const double *u = uniforms + (size_t)step * v.nw * 6;
+    kt::sweep_propose_kernel<<<grid, wpb * 32, shm, st>>>(v, u);
+    if (kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, sv, &mvv, v.tr_sign, v.tr_log,
+                            v.r_sign, v.r_log, v.r_status, nullptr, w, st, nullptr) != 0)
+      return KT_ECUDA;
+    kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, u, w.desc);
+    if (meas_every > 0 && (step + 1) % meas_every == 0) {
+      kt::sweep_measure_kernel<<<grid, wpb * 32, 0, st>>>(v);
+      if (s->measure_obs) {
+        if (current_traces(s, v.m_sign, v.m_log, v.m_status, v.obs_tmp, st) != 0) return KT_ECUDA;
+        const int n = v.nw * v.nobs;
+        kt::sweep_obs_accumulate_kernel<<<(n + 255) / 256, 256, 0, st>>>(v);
+      }
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_sweep_get_state(kt_sweep *s, const kt_sweep_state *d, void *stream) {
+  if (!s || !d) return KT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const kt::SweepView &v = s->v;
+  const size_t nw = v.nw, cap = v.cap, nf = v.nf;
+  auto cp = [&](void *dst, const void *src, size_t bytes) {
+    return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) : cudaSuccess;
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cp(d->lens, v.lens, nw * 4);
+  if (e == cudaSuccess) e = cp(d->tau, v.tau, nw * cap * 8);
+  if (e == cudaSuccess) e = cp(d->flavor, v.flv, nw * cap);
+  if (e == cudaSuccess) e = cp(d->dagger, v.dag, nw * cap);
+  if (e == cudaSuccess) e = cp(d->sign, v.w_sign, nw);
+  if (e == cudaSuccess) e = cp(d->trace_sign, v.tr_sign, nw);
+  if (e == cudaSuccess) e = cp(d->trace_logabs, v.tr_log, nw * 8);
+  if (e == cudaSuccess) e = cp(d->det_logabs, v.det_log, nw * 8);
+  if (e == cudaSuccess) e = cp(d->order, v.kf, nw * nf * 4);
+  return e == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_sweep_get_accumulators(kt_sweep *s, const kt_sweep_accum *d, void *stream) {
+  if (!s || !d) return KT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const kt::SweepView &v = s->v;
+  const size_t nw = v.nw, nf = v.nf;
+  auto cp = [&](void *dst, const void *src, size_t bytes) {
+    return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) : cudaSuccess;
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cp(d->g_tau, v.g_acc, nw * nf * v.n_bins * 8);
+  if (e == cudaSuccess) e = cp(d->sign_sum, v.sign_sum, nw * 8);
+  if (e == cudaSuccess) e = cp(d->order_sum, v.order_sum, nw * nf * 8);
+  if (e == cudaSuccess) e = cp(d->obs_sum, v.obs_sum, nw * v.nobs * 8);
+  return e == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_sweep_counters(kt_sweep *s, unsigned long long *out) {
+  if (!s || !out) return KT_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return KT_ECUDA;
+  if (cudaMemcpy(out, s->v.counters, KT_SWEEP_NCOUNTERS * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return KT_ECUDA;
+  return KT_OK;
+}
+
+kt_status kt_sweep_reset_accumulators(kt_sweep *s, void *stream) {
+  if (!s) return KT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const kt::SweepView &v = s->v;
+  const size_t nw = v.nw, nf = v.nf;
+  cudaError_t e = cudaMemsetAsync(v.g_acc, 0, nw * nf * v.n_bins * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.sign_sum, 0, nw * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.order_sum, 0, nw * nf * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.obs_sum, 0, nw * v.nobs * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v.counters, 0, KT_SWEEP_NCOUNTERS * 8, st);
+  return e == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+void kt_sweep_destroy(kt_sweep *s) {
+  if (!s) return;
+  if (s->ws) cudaFree(s->ws);
+  if (s->mem) cudaFree(s->mem);
+  delete s;
+}
+
+}  // extern "C"

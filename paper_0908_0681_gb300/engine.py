@@ -120,3 +120,66 @@ def trace_ratio(model: kt.KtModel, seqs: DeviceSeqs, cur_sign: torch.Tensor, cur
     ws = workspace(model, n, dev) if ws is None else ws
     kt.kt_trace_ratio(model, seqs.batch(), cur_sign, cur_logabs, moves.batch(), sign, lr, st, stats, ws)
     return sign, lr, st
+
+
+class Sweep:
+    """Batched CT-HYB Markov chains on the device (kt_sweep_*): Metropolis insertion and
+    removal of c^+/c pairs with FP64 determinant updates and the library's trace ratios."""
+
+    def __init__(self, model: kt.KtModel, hyb: np.ndarray, beta: float, n_walkers: int, k_cap: int = 64,
+                 n_bins: int = 100, measure_obs: bool = False):
+        self.h = kt.KtSweep(model, hyb, n_walkers, k_cap=k_cap, n_bins=n_bins, measure_obs=measure_obs)
+        info = kt.kt_model_query(model)
+        self.nf, self.n_orb = info["n_flavors"], info["n_orb"]
+        self.beta = float(beta)
+        self.n_walkers, self.k_cap, self.n_bins = int(n_walkers), int(k_cap), int(n_bins)
+        self.capacity = 2 * self.nf * self.k_cap
+
+    def run(self, uniforms: torch.Tensor, meas_every: int = 0) -> None:
+        """uniforms: float64 device tensor [n_steps, n_walkers, 6]."""
+        assert uniforms.dtype == torch.float64 and uniforms.is_cuda and uniforms.is_contiguous()
+        assert uniforms.shape[1:] == (self.n_walkers, 6)
+        kt.kt_sweep_run(self.h, uniforms.shape[0], uniforms, meas_every)
+
+    def state(self) -> dict:
+        nw, cap, dev = self.n_walkers, self.capacity, "cuda"
+        out = {"lens": torch.empty(nw, dtype=torch.int32, device=dev),
+               "tau": torch.empty((nw, cap), dtype=torch.float64, device=dev),
+               "flavor": torch.empty((nw, cap), dtype=torch.uint8, device=dev),
+               "dagger": torch.empty((nw, cap), dtype=torch.uint8, device=dev),
+               "sign": torch.empty(nw, dtype=torch.int8, device=dev),
+               "trace_sign": torch.empty(nw, dtype=torch.int8, device=dev),
+               "trace_logabs": torch.empty(nw, dtype=torch.float64, device=dev),
+               "det_logabs": torch.empty(nw, dtype=torch.float64, device=dev),
+               "order": torch.empty((nw, self.nf), dtype=torch.int32, device=dev)}
+        kt.kt_sweep_get_state(self.h, **out)
+        return out
+
+    def configs(self) -> list:
+        """Current configurations as host lists of (tau, flavor, dagger)."""
+        st = {k: v.cpu().numpy() for k, v in self.state().items()}
+        res = []
+        for w in range(self.n_walkers):
+            k = int(st["lens"][w])
+            res.append(list(zip(st["tau"][w, :k].tolist(), st["flavor"][w, :k].tolist(), st["dagger"][w, :k].tolist())))
+        return res
+
+    def accumulators(self) -> dict:
+        nw, dev = self.n_walkers, "cuda"
+        out = {"g_tau": torch.zeros((nw, self.nf, self.n_bins), dtype=torch.float64, device=dev),
+               "sign_sum": torch.zeros(nw, dtype=torch.float64, device=dev),
+               "order_sum": torch.zeros((nw, self.nf), dtype=torch.float64, device=dev),
+               "obs_sum": torch.zeros((nw, kt.measure_nobs(self.n_orb)), dtype=torch.float64, device=dev)}
+        kt.kt_sweep_get_accumulators(self.h, **out)
+        return out
+
+    def counters(self) -> dict:
+        return kt.kt_sweep_counters(self.h)
+
+    def reset_accumulators(self) -> None:
+        kt.kt_sweep_reset_accumulators(self.h)
+
+    def green_function(self, acc: dict | None = None) -> torch.Tensor:
+        """G_f(tau) at the bin centres, pooled over walkers: [n_flavors, n_bins]."""
+        acc = self.accumulators() if acc is None else acc
+        return acc["g_tau"].sum(0) * (self.n_bins / self.beta ** 2) / acc["sign_sum"].sum()

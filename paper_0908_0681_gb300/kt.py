@@ -45,6 +45,20 @@ class kt_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_ulonglong) for f in STATS_FIELDS]
 
 
+class kt_sweep_params(ctypes.Structure):
+    _fields_ = [("n_walkers", ctypes.c_int32), ("k_cap", ctypes.c_int32), ("n_tau", ctypes.c_int32),
+                ("hyb", ctypes.c_void_p), ("n_bins", ctypes.c_int32), ("measure_obs", ctypes.c_int32)]
+
+
+class kt_sweep_state(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in ("lens", "tau", "flavor", "dagger", "sign", "trace_sign",
+                                                "trace_logabs", "det_logabs", "order")]
+
+
+class kt_sweep_accum(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in ("g_tau", "sign_sum", "order_sum", "obs_sum")]
+
+
 class kt_seq_batch(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("offsets", ctypes.c_void_p), ("tau", ctypes.c_void_p),
                 ("flavor", ctypes.c_void_p), ("dagger", ctypes.c_void_p)]
@@ -59,7 +73,13 @@ class kt_move_batch(ctypes.Structure):
 ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_model_kept", "kt_model_spectrum",
                  "kt_model_destroy", "kt_workspace_size", "kt_trace", "kt_trace_ratio", "kt_timing_begin",
                  "kt_timing_end", "kt_model_set_tiling", "kt_autotune", "kt_trace_ratio_static",
-                 "kt_measure_workspace_size", "kt_measure"]
+                 "kt_measure_workspace_size", "kt_measure",
+                 "kt_sweep_create", "kt_sweep_run", "kt_sweep_get_state", "kt_sweep_get_accumulators",
+                 "kt_sweep_counters", "kt_sweep_reset_accumulators", "kt_sweep_destroy"]
+
+KT_SWEEP_NCOUNTERS = 8
+SWEEP_COUNTERS = ["insert_proposed", "insert_accepted", "remove_proposed", "remove_accepted", "null_moves",
+                  "refused_at_k_cap", "trace_errors", "measurements"]
 
 _lib = None
 
@@ -92,6 +112,14 @@ def load():
                                    vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.kt_measure_workspace_size.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t)]
     lib.kt_measure.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    lib.kt_sweep_create.argtypes = [vp, ctypes.POINTER(kt_sweep_params), ctypes.POINTER(vp)]
+    lib.kt_sweep_run.argtypes = [vp, i32, vp, i32, vp]
+    lib.kt_sweep_get_state.argtypes = [vp, ctypes.POINTER(kt_sweep_state), vp]
+    lib.kt_sweep_get_accumulators.argtypes = [vp, ctypes.POINTER(kt_sweep_accum), vp]
+    lib.kt_sweep_counters.argtypes = [vp, vp]
+    lib.kt_sweep_reset_accumulators.argtypes = [vp, vp]
+    lib.kt_sweep_destroy.argtypes = [vp]
+    lib.kt_sweep_destroy.restype = None
     lib.kt_timing_begin.argtypes = [vp, i32]
     lib.kt_model_set_tiling.argtypes = [vp, i32]
     lib.kt_trace_ratio_static.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
@@ -100,7 +128,7 @@ def load():
                                 ctypes.POINTER(ctypes.c_int32)]
     lib.kt_timing_end.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
     for f in ABI_FUNCTIONS:
-        if f not in ("kt_status_string", "kt_model_destroy"):
+        if f not in ("kt_status_string", "kt_model_destroy", "kt_sweep_destroy"):
             getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -233,6 +261,53 @@ def kt_measure(m: KtModel, batch: kt_seq_batch, sign, logabs, obs, status, stats
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load().kt_measure(m.handle, ctypes.byref(batch), _ptr(sign), _ptr(logabs), _ptr(obs), _ptr(status),
                              _ptr(stats), _ptr(workspace), ws_bytes, _stream_handle(stream)), "kt_measure")
+
+
+class KtSweep:
+    """Owning handle of a kt_sweep (destroyed with the object); keeps its model alive."""
+
+    def __init__(self, model: KtModel, hyb: np.ndarray, n_walkers: int, k_cap: int = 64, n_bins: int = 100,
+                 measure_obs: bool = False):
+        self.model = model
+        self._hyb = np.ascontiguousarray(hyb, dtype=np.float64)
+        p = kt_sweep_params(int(n_walkers), int(k_cap), int(self._hyb.shape[1] - 1),
+                            self._hyb.ctypes.data_as(ctypes.c_void_p), int(n_bins), 1 if measure_obs else 0)
+        h = ctypes.c_void_p()
+        _check(load().kt_sweep_create(model.handle, ctypes.byref(p), ctypes.byref(h)), "kt_sweep_create")
+        self.handle = h
+        self.n_walkers, self.k_cap, self.n_bins = int(n_walkers), int(k_cap), int(n_bins)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.kt_sweep_destroy(h)
+            self.handle = None
+
+
+def kt_sweep_run(s: KtSweep, n_steps: int, uniforms, meas_every: int = 0, stream=None) -> None:
+    _check(load().kt_sweep_run(s.handle, int(n_steps), _ptr(uniforms), int(meas_every), _stream_handle(stream)),
+           "kt_sweep_run")
+
+
+def kt_sweep_get_state(s: KtSweep, stream=None, **dst) -> None:
+    st = kt_sweep_state(**{k: _ptr(v) for k, v in dst.items()})
+    _check(load().kt_sweep_get_state(s.handle, ctypes.byref(st), _stream_handle(stream)), "kt_sweep_get_state")
+
+
+def kt_sweep_get_accumulators(s: KtSweep, stream=None, **dst) -> None:
+    ac = kt_sweep_accum(**{k: _ptr(v) for k, v in dst.items()})
+    _check(load().kt_sweep_get_accumulators(s.handle, ctypes.byref(ac), _stream_handle(stream)),
+           "kt_sweep_get_accumulators")
+
+
+def kt_sweep_counters(s: KtSweep) -> dict:
+    out = (ctypes.c_ulonglong * KT_SWEEP_NCOUNTERS)()
+    _check(load().kt_sweep_counters(s.handle, out), "kt_sweep_counters")
+    return dict(zip(SWEEP_COUNTERS, [int(x) for x in out]))
+
+
+def kt_sweep_reset_accumulators(s: KtSweep, stream=None) -> None:
+    _check(load().kt_sweep_reset_accumulators(s.handle, _stream_handle(stream)), "kt_sweep_reset_accumulators")
 
 
 def kt_model_set_tiling(m: KtModel, group_lanes: int) -> None:

@@ -205,7 +205,7 @@ def test_invalid_moves():
     tau, fl, dg = seqs.walker(0)
     c_idx = int(np.nonzero(dg == 0)[0][0])
     mv.kind[:] = [1, 0, 2, 1]
-    mv.flavor[:] = [fl[c_idx], 0, 0, 0]
+    mv.flavor[:] = [(int(fl[c_idx]) + 1) % (2 * w.model.n_orb), 0, 0, 0]   # removal of an op of another flavor
     mv.rem_idx[:] = [c_idx, 0, 0, 10 ** 6]
     mv.t_dag[1], mv.t_ann[1] = -1.0, 3.0
     s, lr, st = gpu_ratio(m, seqs, cs, cl, mv)
