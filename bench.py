@@ -15,7 +15,9 @@ is flushed (256 MiB write) before every timed step. Each rank runs its own
 4,096 walkers (weak scaling); there is no data-path collective.
 
 Prints one JSON line (rank 0). The FP32-Krylov path is the headline; the plain
-FP64 GPU path is timed on the same rounds (key "fp64_gpu").
+FP64 GPU path is timed on the same rounds (key "fp64_gpu"). Key "sweep": full
+CT-HYB sweeps of the same model (semicircular bath, 1,024 chains, beta 50 by
+default) through kt_sweep, FP32-Krylov and FP64 traces.
 """
 from __future__ import annotations
 
@@ -53,6 +55,9 @@ def args_():
     p.add_argument("--fp64-steps", type=int, default=0, help="steps for the FP64 comparator (default min(K, 100))")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    p.add_argument("--sweep-steps", type=int, default=1000,
+                   help="timed Metropolis steps of the CT-HYB sweep line (0 skips it)")
+    p.add_argument("--sweep-beta", type=float, default=50.0)
     p.add_argument("--workload", choices=["five_orbital", "seven_orbital"], default="five_orbital",
                    help="five_orbital (4,096 walkers, the headline) or seven_orbital (256 walkers)")
     return p.parse_args()
@@ -231,6 +236,68 @@ def reference_arm(a):
     print(json.dumps(line), flush=True)
 
 
+def sweep_bench(dev, steps: int, beta: float, seed: int):
+    """Full CT-HYB sweeps of the five-orbital model (semicircular bath, 2,000 tau points,
+    1,024 chains): chains start from Poisson(6) configurations, thermalise untimed, then
+    `steps` Metropolis steps per chain are timed with CUDA events, measuring G(tau), the
+    orders and the beta/2 observables every 50 steps. FP32-Krylov traces; an FP64 run of
+    the same chains times the plain path."""
+    import numpy as np
+    import torch
+
+    from paper_0908_0681_gb300 import engine, kt, workloads
+
+    nw, therm, meas = 1024, 2000, 50
+    w = workloads.five_orbital()
+    spec = workloads.five_orbital_sweep(beta).model
+    gen = workloads.Workload(w.name, spec, start=w.start, order=w.order, lam=w.lam, cap=w.cap,
+                             pattern_singles=w.pattern_singles)
+    cand = workloads.generate_sequences(gen, 2 * nw, seed=seed)
+    table = workloads.semicircular_hybridization(beta, 2 * spec.n_orb, n_tau=2000)
+    out = {}
+    for name, prec in (("fp32", kt.KT_FP32_KRYLOV), ("fp64", kt.KT_FP64)):
+        model = engine.model_from_spec(spec, precision=prec)
+        sg, _, _ = engine.trace(model, engine.DeviceSeqs.from_host(cand, dev))
+        ok = np.nonzero(sg.cpu().numpy() != 0)[0][:nw]
+        sw = engine.Sweep(model, table, beta, nw, k_cap=128, n_bins=200, measure_obs=True)
+        sw.set_configs(cand.subset(ok))
+        g = torch.Generator(device=dev).manual_seed(seed)
+        n_t = steps if name == "fp32" else max(steps // 4, 50)
+        for c in range(0, therm, 500):
+            sw.run(torch.rand((500, nw, 6), dtype=torch.float64, device=dev, generator=g))
+        sw.reset_accumulators()
+        u = torch.rand((n_t, nw, 6), dtype=torch.float64, device=dev, generator=g)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sw.run(u, meas_every=meas)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        cnt = sw.counters()
+        st = sw.state()
+        acc = sw.accumulators()
+        ssum = acc["sign_sum"].sum().item()
+        obs = (acc["obs_sum"].sum(0) / ssum).cpu().numpy()
+        K = st["lens"].double().mean().item()
+        props = nw * n_t / (ms / 1000.0)
+        out[name] = {"proposals_per_s": props, "ms_per_step": ms / n_t, "steps": n_t,
+                     "sweeps_per_s": props / K, "mean_ops_per_chain": K,
+                     "mean_order_per_flavor": st["order"].double().mean().item(),
+                     "acceptance": (cnt["insert_accepted"] + cnt["remove_accepted"]) / (nw * n_t),
+                     "mean_sign": ssum / (nw * cnt["measurements"]) if cnt["measurements"] else None,
+                     "trace_errors": cnt["trace_errors"], "refused_at_k_cap": cnt["refused_at_k_cap"]}
+        if name == "fp32":
+            G = sw.green_function(acc).cpu().numpy()
+            out[name].update({"n_f_mean": float(obs[:10].mean()), "docc_mean": float(obs[10:15].mean()),
+                              "G_first_bin": float(G[:, 0].mean()), "G_last_bin": float(G[:, -1].mean())})
+    return {"workload": f"five_orbital_sweep_beta{beta:g}_1024_chains", "metric": "Metropolis proposals/s (all chains)",
+            "sweep_definition": "one sweep = as many proposals per chain as the chain holds operators on average",
+            "bath": "semicircular DOS, bandwidth 4, 2000 tau points", "thermalisation_steps": therm,
+            "measure_every": meas, "fp32": out["fp32"], "fp64": out["fp64"],
+            "speedup_fp32_over_fp64": out["fp32"]["proposals_per_s"] / out["fp64"]["proposals_per_s"]}
+
+
 def main():
     a = args_()
     if a.impl == "reference":
@@ -386,6 +453,8 @@ def main():
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock (sampled)",
                 "fp64_peak_tflops": peak64}
 
+    sweep = sweep_bench(dev, a.sweep_steps, a.sweep_beta, seed=100 + rank) if a.sweep_steps > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         # GPU ratios of the first timed round, for the sampled error statement
@@ -415,6 +484,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "sweep": sweep,
             "clocks": clocks,
             "gpu_launches": 4 * a.steps,
             "kernel_source_sha": sha,

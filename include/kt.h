@@ -325,6 +325,15 @@ kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out)
 /* n_steps Metropolis steps of every walker, measuring after every meas_every-th
  * step (0: never). Enqueued on the stream; returns launch errors only. */
 kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream);
+/* Replace every walker's configuration (a restart from kt_sweep_get_state, or a
+ * chosen starting point). HOST batch with n == n_walkers, same layout rules as
+ * kt_trace. Each sequence must hold, for every flavor, as many c^+ as c (at most
+ * k_cap pairs) alternating in time, and have a nonzero weight. The inverse bath
+ * matrices and log-determinants are computed from scratch in FP64 on the host
+ * (Gauss-Jordan elimination with partial pivoting), the traces on the device.
+ * Synchronises. On KT_EINVAL (a malformed sequence, too many pairs, a singular
+ * bath matrix or a zero trace) every walker is back at the empty configuration. */
+kt_status kt_sweep_set_configs(kt_sweep *s, const kt_seq_batch *host_batch);
 kt_status kt_sweep_get_state(kt_sweep *s, const kt_sweep_state *dst, void *stream);
 kt_status kt_sweep_get_accumulators(kt_sweep *s, const kt_sweep_accum *dst, void *stream);
 /* Synchronises the device and copies the counters to out[KT_SWEEP_NCOUNTERS]. */

@@ -35,8 +35,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
+#include <vector>
 
 #include "kt_internal.h"
 
@@ -482,6 +484,7 @@ struct kt_sweep {
   void *ws = nullptr;
   size_t ws_bytes = 0;
   bool measure_obs = false;
+  std::vector<double> hyb_host;
 };
 
 namespace {
@@ -567,6 +570,68 @@ int current_traces(kt_sweep *s, int8_t *sg, double *lg, int32_t *st, double *obs
                              nullptr, sg, lg, st, nullptr, w, stream, nullptr, obs);
 }
 
+// Every walker to the empty configuration: weight = trace of the empty sequence.
+kt_status reset_empty(kt_sweep *s) {
+  kt::SweepView &v = s->v;
+  const size_t nw = v.nw, nf = v.nf;
+  if (cudaMemset(v.lens, 0, nw * 4) != cudaSuccess || cudaMemset(v.kf, 0, nw * nf * 4) != cudaSuccess) return KT_ECUDA;
+  if (current_traces(s, v.m_sign, v.m_log, v.m_status, nullptr, 0) != 0) return KT_ECUDA;
+  kt::sweep_init_kernel<<<(v.nw + 255) / 256, 256>>>(v, v.m_sign, v.m_log);
+  return cudaDeviceSynchronize() == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+// Host copy of the device interpolation of Fh_f.
+double host_Fh(const std::vector<double> &hyb, int n_tau, double beta, int f, double x) {
+  double t = x >= 0.0 ? x : x + beta;
+  const double pos = t / beta * n_tau;
+  int i = (int)std::floor(pos);
+  i = i < 0 ? 0 : (i > n_tau - 1 ? n_tau - 1 : i);
+  const double fr = pos - i;
+  const double a = hyb[(size_t)f * (n_tau + 1) + i], b = hyb[(size_t)f * (n_tau + 1) + i + 1];
+  const double v = a + fr * (b - a);
+  return x >= 0.0 ? v : -v;
+}
+
+// Inverse of the k x k matrix A (row-major) by Gauss-Jordan elimination with partial
+// pivoting; writes inv (row-major), log|det A| and its sign. False if singular.
+bool gauss_jordan(int k, std::vector<double> A, std::vector<double> &inv, double &logdet, int &sgn) {
+  inv.assign((size_t)k * k, 0.0);
+  for (int i = 0; i < k; ++i) inv[(size_t)i * k + i] = 1.0;
+  logdet = 0.0;
+  sgn = 1;
+  for (int c = 0; c < k; ++c) {
+    int p = c;
+    for (int r = c + 1; r < k; ++r)
+      if (std::fabs(A[(size_t)r * k + c]) > std::fabs(A[(size_t)p * k + c])) p = r;
+    const double piv = A[(size_t)p * k + c];
+    if (piv == 0.0 || !std::isfinite(piv)) return false;
+    if (p != c) {
+      for (int j = 0; j < k; ++j) {
+        std::swap(A[(size_t)p * k + j], A[(size_t)c * k + j]);
+        std::swap(inv[(size_t)p * k + j], inv[(size_t)c * k + j]);
+      }
+      sgn = -sgn;
+    }
+    logdet += std::log(std::fabs(piv));
+    if (piv < 0) sgn = -sgn;
+    const double ip = 1.0 / piv;
+    for (int j = 0; j < k; ++j) {
+      A[(size_t)c * k + j] *= ip;
+      inv[(size_t)c * k + j] *= ip;
+    }
+    for (int r = 0; r < k; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * k + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < k; ++j) {
+        A[(size_t)r * k + j] -= f * A[(size_t)c * k + j];
+        inv[(size_t)r * k + j] -= f * inv[(size_t)c * k + j];
+      }
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -615,12 +680,8 @@ kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out)
     }
   }
   if (rc == KT_OK) {
-    // empty configurations: weight = trace (no determinants)
-    if (current_traces(s, v.m_sign, v.m_log, v.m_status, nullptr, 0) != 0) rc = KT_ECUDA;
-    if (rc == KT_OK) {
-      kt::sweep_init_kernel<<<(v.nw + 255) / 256, 256>>>(v, v.m_sign, v.m_log);
-      if (cudaDeviceSynchronize() != cudaSuccess) rc = KT_ECUDA;
-    }
+    s->hyb_host.assign(p->hyb, p->hyb + (size_t)nf * (p->n_tau + 1));
+    rc = reset_empty(s);
   }
   if (rc != KT_OK) {
     cudaGetLastError();
@@ -663,6 +724,145 @@ kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int
     }
   }
   return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+static kt_status set_configs_impl(kt_sweep *s, const kt_seq_batch *b);
+
+kt_status kt_sweep_set_configs(kt_sweep *s, const kt_seq_batch *b) {
+  if (!s) return KT_EINVAL;
+  const kt_status rc = set_configs_impl(s, b);
+  if (rc != KT_OK) {
+    cudaGetLastError();
+    reset_empty(s);
+  }
+  return rc;
+}
+
+static kt_status set_configs_impl(kt_sweep *s, const kt_seq_batch *b) {
+  if (!b || b->n != s->v.nw || !b->offsets) return KT_EINVAL;
+  kt::SweepView &v = s->v;
+  const int nw = v.nw, nf = v.nf, kc = v.kcap, cap = v.cap;
+  const double beta = v.beta;
+  if (b->offsets[0] != 0) return KT_EINVAL;
+  for (int w = 0; w < nw; ++w) {
+    const int K = b->offsets[w + 1] - b->offsets[w];
+    if (K < 0 || K > cap) return KT_EINVAL;
+  }
+  const size_t total = (size_t)b->offsets[nw];
+  if (total > 0 && (!b->tau || !b->flavor || !b->dagger)) return KT_EINVAL;
+  std::vector<int32_t> lens(nw), kf((size_t)nw * nf, 0);
+  std::vector<double> tau((size_t)nw * cap, 0.0), rt((size_t)nw * nf * kc, 0.0), ct((size_t)nw * nf * kc, 0.0);
+  std::vector<uint8_t> flv((size_t)nw * cap, 0), dag((size_t)nw * cap, 0);
+  std::vector<double> detlog(nw, 0.0);
+  std::vector<int> detsign(nw, 1);
+  // pass 1: validation, times, determinants' signs and logs (M uploaded in pass 2)
+  for (int w = 0; w < nw; ++w) {
+    const int o = b->offsets[w], K = b->offsets[w + 1] - o;
+    lens[w] = K;
+    std::vector<int> last(nf, -1);
+    for (int k = 0; k < K; ++k) {
+      const double t = b->tau[o + k];
+      const int f = b->flavor[o + k], d = b->dagger[o + k];
+      if (!(t >= 0.0) || !(t < beta) || f >= nf || d > 1 || (k > 0 && t < b->tau[o + k - 1])) return KT_EINVAL;
+      if (last[f] >= 0 && last[f] == d) return KT_EINVAL;  // types of one flavor alternate
+      last[f] = d;
+      tau[(size_t)w * cap + k] = t;
+      flv[(size_t)w * cap + k] = (uint8_t)f;
+      dag[(size_t)w * cap + k] = (uint8_t)d;
+      if (d == 1) {
+        const int i = kf[(size_t)w * nf + f]++;
+        if (i >= kc) return KT_EINVAL;
+        rt[((size_t)w * nf + f) * kc + i] = t;
+      }
+    }
+    std::vector<int> na(nf, 0);
+    for (int k = 0; k < K; ++k)
+      if (b->dagger[o + k] == 0) {
+        const int f = b->flavor[o + k];
+        const int j = na[f]++;
+        if (j >= kc) return KT_EINVAL;
+        ct[((size_t)w * nf + f) * kc + j] = b->tau[o + k];
+      }
+    for (int f = 0; f < nf; ++f)
+      if (na[f] != kf[(size_t)w * nf + f]) return KT_EINVAL;
+  }
+  // pass 2: inverses (chunks of walkers staged on the host), signs of the bath permutation
+  const int chunk = 16;
+  std::vector<double> Mh((size_t)chunk * nf * kc * kc);
+  std::vector<int> sP(nw, 1);
+  kt_status rc = KT_OK;
+  for (int w0 = 0; w0 < nw && rc == KT_OK; w0 += chunk) {
+    const int w1 = std::min(nw, w0 + chunk);
+    std::fill(Mh.begin(), Mh.end(), 0.0);
+    for (int w = w0; w < w1 && rc == KT_OK; ++w) {
+      std::vector<double> seq;  // bath operators flavor by flavor: tau'_1 tau_1 tau'_2 tau_2 ...
+      for (int f = 0; f < nf && rc == KT_OK; ++f) {
+        const size_t fb = (size_t)w * nf + f;
+        const int k = kf[fb];
+        for (int i = 0; i < k; ++i) {
+          seq.push_back(rt[fb * kc + i]);
+          seq.push_back(ct[fb * kc + i]);
+        }
+        if (k == 0) continue;
+        std::vector<double> A((size_t)k * k), inv;
+        for (int i = 0; i < k; ++i)
+          for (int j = 0; j < k; ++j) A[(size_t)i * k + j] = host_Fh(s->hyb_host, v.n_tau, beta, f, rt[fb * kc + i] - ct[fb * kc + j]);
+        double ld;
+        int sg;
+        if (!gauss_jordan(k, A, inv, ld, sg)) {
+          rc = KT_EINVAL;
+          break;
+        }
+        detlog[w] += ld;
+        detsign[w] *= sg;
+        double *Mw = Mh.data() + ((size_t)(w - w0) * nf + f) * kc * kc;
+        for (int j = 0; j < k; ++j)
+          for (int i = 0; i < k; ++i) Mw[(size_t)j * kc + i] = inv[(size_t)j * k + i];
+      }
+      long long inv_count = 0;
+      for (size_t a = 0; a < seq.size(); ++a)
+        for (size_t c = a + 1; c < seq.size(); ++c) inv_count += seq[a] < seq[c];
+      sP[w] = (inv_count & 1) ? -1 : 1;
+    }
+    if (rc == KT_OK &&
+        cudaMemcpy(v.M + (size_t)w0 * nf * kc * kc, Mh.data(), sizeof(double) * (w1 - w0) * nf * kc * kc,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = KT_ECUDA;
+  }
+  if (rc != KT_OK) {
+    return rc;
+  }
+  cudaError_t e = cudaMemcpy(v.lens, lens.data(), nw * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(v.tau, tau.data(), tau.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(v.flv, flv.data(), flv.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(v.dag, dag.data(), dag.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(v.kf, kf.data(), kf.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(v.row_t, rt.data(), rt.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(v.col_t, ct.data(), ct.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(v.det_log, detlog.data(), nw * 8, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    return KT_ECUDA;
+  }
+  if (current_traces(s, v.tr_sign, v.tr_log, v.m_status, nullptr, 0) != 0 || cudaDeviceSynchronize() != cudaSuccess) {
+    return KT_ECUDA;
+  }
+  std::vector<int8_t> ts(nw);
+  std::vector<int32_t> tst(nw);
+  if (cudaMemcpy(ts.data(), v.tr_sign, nw, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(tst.data(), v.m_status, nw * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    return KT_ECUDA;
+  }
+  std::vector<int8_t> ws(nw);
+  for (int w = 0; w < nw; ++w) {
+    if (ts[w] == 0 || tst[w] != KT_OK) {
+      return KT_EINVAL;
+    }
+    ws[w] = (int8_t)(ts[w] * sP[w] * detsign[w]);
+  }
+  if (cudaMemcpy(v.w_sign, ws.data(), nw, cudaMemcpyHostToDevice) != cudaSuccess) {
+    return KT_ECUDA;
+  }
+  return KT_OK;
 }
 
 kt_status kt_sweep_get_state(kt_sweep *s, const kt_sweep_state *d, void *stream) {

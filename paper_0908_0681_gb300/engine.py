@@ -141,6 +141,10 @@ class Sweep:
         assert uniforms.shape[1:] == (self.n_walkers, 6)
         kt.kt_sweep_run(self.h, uniforms.shape[0], uniforms, meas_every)
 
+    def set_configs(self, seqs) -> None:
+        """Start every chain from the given configurations (a Sequences-like CSR batch on the host)."""
+        kt.kt_sweep_set_configs(self.h, seqs.offsets, seqs.tau, seqs.flavor, seqs.dagger)
+
     def state(self) -> dict:
         nw, cap, dev = self.n_walkers, self.capacity, "cuda"
         out = {"lens": torch.empty(nw, dtype=torch.int32, device=dev),

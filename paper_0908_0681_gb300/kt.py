@@ -75,7 +75,8 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_timing_end", "kt_model_set_tiling", "kt_autotune", "kt_trace_ratio_static",
                  "kt_measure_workspace_size", "kt_measure",
                  "kt_sweep_create", "kt_sweep_run", "kt_sweep_get_state", "kt_sweep_get_accumulators",
-                 "kt_sweep_counters", "kt_sweep_reset_accumulators", "kt_sweep_destroy"]
+                 "kt_sweep_counters", "kt_sweep_reset_accumulators", "kt_sweep_destroy",
+                 "kt_sweep_set_configs"]
 
 KT_SWEEP_NCOUNTERS = 8
 SWEEP_COUNTERS = ["insert_proposed", "insert_accepted", "remove_proposed", "remove_accepted", "null_moves",
@@ -114,6 +115,7 @@ def load():
     lib.kt_measure.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.kt_sweep_create.argtypes = [vp, ctypes.POINTER(kt_sweep_params), ctypes.POINTER(vp)]
     lib.kt_sweep_run.argtypes = [vp, i32, vp, i32, vp]
+    lib.kt_sweep_set_configs.argtypes = [vp, ctypes.POINTER(kt_seq_batch)]
     lib.kt_sweep_get_state.argtypes = [vp, ctypes.POINTER(kt_sweep_state), vp]
     lib.kt_sweep_get_accumulators.argtypes = [vp, ctypes.POINTER(kt_sweep_accum), vp]
     lib.kt_sweep_counters.argtypes = [vp, vp]
@@ -287,6 +289,15 @@ class KtSweep:
 def kt_sweep_run(s: KtSweep, n_steps: int, uniforms, meas_every: int = 0, stream=None) -> None:
     _check(load().kt_sweep_run(s.handle, int(n_steps), _ptr(uniforms), int(meas_every), _stream_handle(stream)),
            "kt_sweep_run")
+
+
+def kt_sweep_set_configs(s: KtSweep, offsets: np.ndarray, tau: np.ndarray, flavor: np.ndarray,
+                         dagger: np.ndarray) -> None:
+    """HOST CSR arrays (int32 offsets, float64 tau, uint8 flavor / dagger)."""
+    arrs = [np.ascontiguousarray(a, dtype=t) for a, t in ((offsets, np.int32), (tau, np.float64),
+                                                         (flavor, np.uint8), (dagger, np.uint8))]
+    b = kt_seq_batch(len(arrs[0]) - 1, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs])
+    _check(load().kt_sweep_set_configs(s.handle, ctypes.byref(b)), "kt_sweep_set_configs")
 
 
 def kt_sweep_get_state(s: KtSweep, stream=None, **dst) -> None:

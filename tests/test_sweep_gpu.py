@@ -115,3 +115,45 @@ def test_semicircular_green_function_without_interaction():
     exact = np.array([-np.mean(np.interp(np.linspace(b * beta / nb, (b + 1) * beta / nb, 201), grid, table[0]))
                       for b in range(nb)])
     assert np.all(np.abs(mean - exact) < 5 * err + 1e-3), (mean, exact, err)
+
+
+def test_set_configs_restart_matches_oracle():
+    """Chains started from given configurations: the from-scratch weights (host inverses,
+    device traces) equal the oracle's, and the continued chains match the oracle chain."""
+    w = workloads.three_orbital()
+    spec = w.model
+    om, gm = model_pair(spec, kt.KT_FP64)
+    table = workloads.semicircular_hybridization(spec.beta, 6, n_tau=2000)
+    hyb = Hyb(table, spec.beta)
+    cand = workloads.generate_sequences(w, 400, seed=9)
+    keep = []
+    for i in range(cand.n):
+        ops = list(zip(*[a.tolist() for a in cand.walker(i)]))
+        if max([sum(1 for t, f, d in ops if f == g and d == 1) for g in range(6)] + [0]) <= 8 and weight(om, hyb, ops)[0] != 0:
+            keep.append(i)
+        if len(keep) == 16:
+            break
+    assert len(keep) == 16
+    seqs = cand.subset(keep)
+    init = [list(zip(*[a.tolist() for a in seqs.walker(i)])) for i in range(seqs.n)]
+    sw = engine.Sweep(gm, table, spec.beta, 16, k_cap=16, n_bins=10)
+    sw.set_configs(seqs)
+    assert sw.configs() == init
+    st = {k: v.cpu().numpy() for k, v in sw.state().items()}
+    for i, ops in enumerate(init):
+        s, lw, sT, lT = weight(om, hyb, ops)
+        assert s == st["sign"][i] and sT == st["trace_sign"][i]
+        assert abs(st["trace_logabs"][i] - lT) < 1e-9 and abs(st["det_logabs"][i] - (lw - lT)) < 1e-9
+    u = workloads.sweep_uniforms(200, 16, seed=33)
+    sw.run(torch.as_tensor(u, device="cuda"), meas_every=0)
+    ref = chain(om, hyb, init, u, k_cap=16)
+    assert sw.configs() == ref["configs"]
+    st = {k: v.cpu().numpy() for k, v in sw.state().items()}
+    assert (st["sign"] == ref["sign"]).all()
+    assert np.abs(st["det_logabs"] - (ref["logw"] - ref["trace_log"])).max() < 1e-8
+    # a malformed batch (a flavor with two c^+ in a row) is refused and the chains restart empty
+    bad = workloads.Sequences(np.array([0, 2] + [2] * 15, np.int32), np.array([1.0, 2.0]), np.array([0, 0], np.uint8),
+                              np.array([1, 1], np.uint8))
+    with pytest.raises(kt.KtError):
+        sw.set_configs(bad)
+    assert all(len(c) == 0 for c in sw.configs())
