@@ -342,6 +342,19 @@ kt_status kt_sweep_counters(kt_sweep *s, unsigned long long *out);
 kt_status kt_sweep_reset_accumulators(kt_sweep *s, void *stream);
 void kt_sweep_destroy(kt_sweep *s);
 
+/* ------------------------------------------------------------------------ */
+/* Tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulator in TMEM), the  */
+/* building block of the learned delayed-acceptance filter.                  */
+/* ------------------------------------------------------------------------ */
+/* C[M][N] = A[M][K] . B[N][K]^T. A, B: DEVICE BF16, row-major with leading
+ * dimensions lda, ldb (elements, multiples of 8, >= K), 16-byte aligned; C:
+ * DEVICE FP32 row-major, ldc >= N. N and K multiples of 16 (N >= 16, K >= 16;
+ * pad with zeros), any M >= 1. *err (DEVICE int32) is set to 1 if a bounded
+ * wait of the kernel on the tensor core timed out (the tile is then not
+ * written); the caller zeroes it. Asynchronous on the stream. */
+kt_status kt_gemm_bf16(const void *A, int32_t lda, const void *B, int32_t ldb, float *C, int32_t ldc, int32_t M,
+                       int32_t N, int32_t K, int32_t *err, void *stream);
+
 /* Kernel tiling: every (walker, kept state) item of the Krylov stage is
  * processed by a group of group_lanes lanes of one warp (32 / group_lanes items
  * per warp). kt_model_set_tiling picks one of the compiled group sizes

@@ -76,7 +76,7 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_measure_workspace_size", "kt_measure",
                  "kt_sweep_create", "kt_sweep_run", "kt_sweep_get_state", "kt_sweep_get_accumulators",
                  "kt_sweep_counters", "kt_sweep_reset_accumulators", "kt_sweep_destroy",
-                 "kt_sweep_set_configs"]
+                 "kt_sweep_set_configs", "kt_gemm_bf16"]
 
 KT_SWEEP_NCOUNTERS = 8
 SWEEP_COUNTERS = ["insert_proposed", "insert_accepted", "remove_proposed", "remove_accepted", "null_moves",
@@ -116,6 +116,7 @@ def load():
     lib.kt_sweep_create.argtypes = [vp, ctypes.POINTER(kt_sweep_params), ctypes.POINTER(vp)]
     lib.kt_sweep_run.argtypes = [vp, i32, vp, i32, vp]
     lib.kt_sweep_set_configs.argtypes = [vp, ctypes.POINTER(kt_seq_batch)]
+    lib.kt_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp, vp]
     lib.kt_sweep_get_state.argtypes = [vp, ctypes.POINTER(kt_sweep_state), vp]
     lib.kt_sweep_get_accumulators.argtypes = [vp, ctypes.POINTER(kt_sweep_accum), vp]
     lib.kt_sweep_counters.argtypes = [vp, vp]
@@ -319,6 +320,14 @@ def kt_sweep_counters(s: KtSweep) -> dict:
 
 def kt_sweep_reset_accumulators(s: KtSweep, stream=None) -> None:
     _check(load().kt_sweep_reset_accumulators(s.handle, _stream_handle(stream)), "kt_sweep_reset_accumulators")
+
+
+def kt_gemm_bf16(A, B, C, err, stream=None) -> None:
+    """C = A . B^T on the tensor cores (A [M, K], B [N, K] bfloat16; C [M, N] float32; err int32[1])."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load().kt_gemm_bf16(_ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), C.stride(0), M, N, K, _ptr(err),
+                               _stream_handle(stream)), "kt_gemm_bf16")
 
 
 def kt_model_set_tiling(m: KtModel, group_lanes: int) -> None:

@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "kt
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(kt_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(kt_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol():
