@@ -46,6 +46,12 @@ uniforms u[0..5] in [0, 1):
   accept when log(u5) < log|w_new / w_old| + log(proposal factor).
   Null moves (no change, no acceptance test): removing from an empty flavor,
   inserting beyond k_cap pairs, t1 >= beta after rounding, or t2 == t1.
+Delayed acceptance (Christen & Fox 2005) with a surrogate r~ of log|T_new / T_old|: a
+seventh uniform u6 per step; stage 1 accepts when
+  log(u6) < r~ + log|bath factor ratio| + log(proposal factor),
+and only then is the trace evaluated; stage 2 accepts when log(u5) < log|T_new/T_old| - r~.
+The product of the two stages satisfies detailed balance with respect to w for any fixed
+surrogate.
 Measurements every meas_every steps, weighted by the sign of w:
   G_f(tau) = (1/beta) < sum_{ij} M_ji dh(tau, tau_j - tau'_i) >,  M = G_f^{-1},
   dh(tau, x) = delta(tau - x) for x > 0 and -delta(tau - x - beta) for x < 0,
@@ -107,6 +113,23 @@ def permutation_sign(ops, nf) -> int:
     return -1 if inv % 2 else 1
 
 
+def bath_weight(hyb: Hyb, ops, nf: int):
+    """(sign, log|.|) of s_P * prod_f det G_f alone (no trace); sign 0 when singular."""
+    sgn, lw = permutation_sign(ops, nf), 0.0
+    for f in range(nf):
+        cre, ann = flavor_times(ops, f)
+        if len(cre) != len(ann):
+            return 0, -math.inf
+        if not cre:
+            continue
+        s, ld = np.linalg.slogdet(bath_matrix(hyb, f, cre, ann))
+        if s == 0:
+            return 0, -math.inf
+        sgn *= int(s)
+        lw += float(ld)
+    return sgn, lw
+
+
 def weight(model: Model, hyb: Hyb, ops):
     """(sign, log|w|, sign_T, log|T|) of a configuration; sign 0 when w = 0."""
     nf = 2 * model.p.n_orb
@@ -139,7 +162,8 @@ def _insert(ops, t, f, d):
 
 
 def propose(ops, u, nf, beta, k_cap):
-    """The move of one step: (new ops, log proposal factor), or None for a null move."""
+    """The move of one step: (new ops, log proposal factor, (kind, flavor, t_first,
+    t_second, first operator is a c^+)), or None for a null move."""
     f = min(int(u[1] * nf), nf - 1)
     fidx = [i for i, (t, g, d) in enumerate(ops) if g == f]
     k = len(fidx) // 2
@@ -169,7 +193,7 @@ def propose(ops, u, nf, beta, k_cap):
         new = _insert(new, first[0], f, first[1])
         new = _insert(new, second[0], f, second[1])
         lp = 2.0 * math.log(beta) if k == 0 else math.log(beta * lmax / (2.0 * (k + 1)))
-        return new, lp
+        return new, lp, (0, f, t1, t2, bool(seg))
     if k == 0:
         return None
     j = min(int(u[2] * 2 * k), 2 * k - 1)
@@ -184,14 +208,17 @@ def propose(ops, u, nf, beta, k_cap):
         lmax = tc - t1 if tc > t1 else tc + beta - t1
         lp = math.log(2.0 * k / (beta * lmax))
     new = [op for i, op in enumerate(ops) if i not in (a, b)]
-    return new, lp
+    return new, lp, (1, f, t1, ops[b][0], ops[a][2] == 1)
 
 
 def chain(model: Model, hyb: Hyb, init, uniforms: np.ndarray, k_cap: int = 64, n_bins: int = 50,
-          meas_every: int = 0, observables: bool = False):
-    """Run every walker's chain with the given uniforms [n_steps, n_walkers, 6].
+          meas_every: int = 0, observables: bool = False, surrogate=None):
+    """Run every walker's chain with the given uniforms [n_steps, n_walkers, 6] (7 with a
+    surrogate: a callable (ops, kind, flavor, t_first, t_second, seg) -> predicted
+    log|T_new / T_old|, used for delayed acceptance).
 
-    Returns a dict: accepted [n_steps, n_walkers] (1 accepted, 0 rejected, -1 null),
+    Returns a dict: accepted [n_steps, n_walkers] (1 accepted, 0 rejected, -1 null,
+    -2 rejected at stage 1),
     configs (final op lists), sign / logw (final weights, recomputed), and when
     meas_every > 0: g_acc [n_walkers, nf, n_bins], sign_sum, order_sum [n_walkers, nf],
     n_meas, and obs_sum [n_walkers, nobs] if observables.
@@ -213,11 +240,24 @@ def chain(model: Model, hyb: Hyb, init, uniforms: np.ndarray, k_cap: int = 64, n
             if mv is None:
                 acc[step, w] = -1
                 continue
-            new, lp = mv
+            new, lp, info = mv
+            lstage1 = 0.0
+            if surrogate is not None:
+                bs_new, bl_new = bath_weight(hyb, new, nf)
+                if bs_new == 0:
+                    acc[step, w] = -1
+                    continue
+                bs_old, bl_old = bath_weight(hyb, configs[w], nf)
+                rt = float(surrogate(configs[w], *info))
+                u6 = uniforms[step, w, 6]
+                if not (math.log(u6) if u6 > 0 else -math.inf) < rt + bl_new - bl_old + lp:
+                    acc[step, w] = -2
+                    continue
+                lstage1 = rt + bl_new - bl_old + lp
             nw_ = weight(model, hyb, new)
             if nw_[0] == 0:
                 continue
-            lr = nw_[1] - cur[w][1] + lp
+            lr = nw_[1] - cur[w][1] + lp - lstage1
             u5 = uniforms[step, w, 5]
             if (math.log(u5) if u5 > 0 else -math.inf) < lr:
                 configs[w] = new

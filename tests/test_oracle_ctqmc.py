@@ -163,3 +163,29 @@ def test_chain_reproduces_semicircular_green_function():
     assert (mean < 0).all()
     pooled = green_function(out["g_acc"], out["sign_sum"], beta)
     assert pooled.shape == (2, nb)
+
+
+@pytest.mark.slow
+def test_delayed_acceptance_keeps_the_distribution():
+    """Delayed acceptance with a crude surrogate (a linear guess in the pair's length)
+    samples the same distribution: the U = 0 Green's function is still semicircular,
+    and stage 1 rejects a share of the proposals before any trace is evaluated."""
+    beta, nw, steps = 4.0, 12, 2500
+    m = Model(Params(1, 0.0, 0.0, mu=0.0, beta=beta, trunc_eps=0.0))
+    table = workloads.semicircular_hybridization(beta, 2, n_tau=400)
+    hyb = Hyb(table, beta)
+    u = np.random.default_rng(12).random((steps, nw, 7))
+    nb = 10
+
+    def guess(ops, kind, flavor, t1, t2, seg):
+        d = (t2 - t1) % beta
+        return -0.3 * d if kind == 0 else 0.3 * d
+
+    out = chain(m, hyb, [[] for _ in range(nw)], u, k_cap=64, n_bins=nb, meas_every=5, surrogate=guess)
+    g_w = (out["g_acc"] * (nb / beta ** 2) / out["sign_sum"][:, None, None]).mean(axis=1)
+    mean, err = g_w.mean(axis=0), g_w.std(axis=0, ddof=1) / math.sqrt(nw)
+    grid = np.linspace(0, beta, 401)
+    exact = np.array([-np.mean(np.interp(np.linspace(b * beta / nb, (b + 1) * beta / nb, 41), grid, table[0]))
+                      for b in range(nb)])
+    assert np.all(np.abs(mean - exact) < 5 * err + 2e-3), (mean, exact, err)
+    assert (out["accepted"] == -2).mean() > 0.05
