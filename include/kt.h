@@ -313,10 +313,11 @@ typedef struct {
   double *obs_sum;        /* [n_walkers][KT_MEASURE_NOBS(n_orb)] sign-weighted */
 } kt_sweep_accum;
 
-/* Counters of kt_sweep_counters (HOST [8]): 0 insertions proposed, 1 accepted,
+/* Counters of kt_sweep_counters (HOST [10]): 0 insertions proposed, 1 accepted,
  * 2 removals proposed, 3 accepted, 4 null moves, 5 insertions refused at k_cap,
- * 6 proposals rejected because the trace pipeline reported an error, 7 measurements. */
-#define KT_SWEEP_NCOUNTERS 8
+ * 6 proposals rejected because the trace pipeline reported an error, 7 measurements,
+ * 8 proposals rejected at stage 1 of delayed acceptance, 9 trace ratios evaluated. */
+#define KT_SWEEP_NCOUNTERS 10
 
 /* Allocate the chains of a model (device state on the current device; the model
  * must outlive the sweep) and set every walker to the empty configuration.
@@ -354,6 +355,74 @@ void kt_sweep_destroy(kt_sweep *s);
  * written); the caller zeroes it. Asynchronous on the stream. */
 kt_status kt_gemm_bf16(const void *A, int32_t lda, const void *B, int32_t ldb, float *C, int32_t ldc, int32_t M,
                        int32_t N, int32_t K, int32_t *err, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned delayed acceptance: a surrogate network predicts log|T_new/T_old| */
+/* of a proposed move; stage 1 of a two-stage Metropolis test (Christen &    */
+/* Fox) uses it, and only moves that pass stage 1 get their true trace.      */
+/* ------------------------------------------------------------------------ */
+/*
+ * Network: y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 with 256 hidden units,
+ * input size n_in (a multiple of 16). BF16 operands on the tensor cores
+ * (kt_gemm_bf16), FP32 accumulation; FP32 master weights, biases, output layer
+ * and Adam state. Parameters are packed FP32 in the order W1 [256][n_in],
+ * b1 [256], W2 [256][256], b2 [256], w3 [256], b3 [1].
+ * Training minimises the mean squared error (1/B) sum (y - t)^2 with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
+ */
+typedef struct kt_mlp kt_mlp;
+#define KT_MLP_HIDDEN 256
+/* max_batch: largest batch of kt_mlp_forward / kt_mlp_backward (multiple of 16). */
+kt_status kt_mlp_create(int32_t n_in, int32_t max_batch, kt_mlp **out);
+kt_status kt_mlp_num_params(const kt_mlp *n, int64_t *count);
+/* HOST packed FP32 parameters in and out (set also resets the Adam state); synchronous. */
+kt_status kt_mlp_set_params(kt_mlp *n, const float *host_params);
+kt_status kt_mlp_get_params(kt_mlp *n, float *host_params_out);
+/* y[B] (DEVICE FP32) for inputs X (DEVICE BF16 [B][n_in], 16-byte aligned), B <= max_batch. */
+kt_status kt_mlp_forward(kt_mlp *n, const void *X, int32_t B, float *y, void *stream);
+/* Forward and backward pass on a batch (B a multiple of 16) with targets t (DEVICE FP32 [B]);
+ * keeps the gradients in the object and writes the loss to *loss (DEVICE FP32, may be NULL). */
+kt_status kt_mlp_backward(kt_mlp *n, const void *X, const float *t, int32_t B, float *loss, void *stream);
+/* HOST copy of the packed gradients of the last kt_mlp_backward; synchronous. */
+kt_status kt_mlp_get_grads(kt_mlp *n, float *host_grads_out);
+/* One Adam step with the stored gradients. */
+kt_status kt_mlp_adam(kt_mlp *n, float lr, void *stream);
+/* Synchronises; *out = 1 if a tensor-core wait of any call timed out so far. */
+kt_status kt_mlp_error(kt_mlp *n, int32_t *out);
+void kt_mlp_destroy(kt_mlp *n);
+
+/* Feature vector of a proposal (the surrogate's input; n_in = 34 n_flavors + 3 rounded
+ * up to a multiple of 16). It describes the base (the configuration without the move's
+ * pair: the current one for an insertion, the current one minus the pair for a
+ * removal) and the pair, so that a move and its reverse share it:
+ *   x[f] = k_f / 8 (pairs of flavor f in the base);
+ *   x[nf + 32 f + b] += 1/4 for every segment of f in the base (a c^+ to the next c of
+ *     f, cyclically) of length l with b = min(floor(32 l / beta), 31);
+ *   x[33 nf] = 0; x[33 nf + 1 + f_move] = 1;
+ *   x[34 nf + 1] = ((t_second - t_first) mod beta) / beta (t_first: t1 of an insertion,
+ *     the chosen operator of a removal; t_second its partner);
+ *   x[34 nf + 2] = +1 if the first operator is a c^+, else -1; zero padding.
+ * The network's output y predicts the log trace ratio of inserting the pair into the
+ * base; the prediction for the move is y for an insertion and -y for a removal. */
+kt_status kt_sweep_feature_size(const kt_sweep *s, int32_t *n_in);
+/* n_steps plain Metropolis steps (uniforms as kt_sweep_run) that also record, for
+ * every proposal whose trace ratio was evaluated and is nonzero, its features
+ * (DEVICE BF16 [capacity][n_in]) and the insertion log trace ratio (log|T_new / T_old|
+ * for an insertion, its negative for a removal; DEVICE FP32 [capacity]) at
+ * slot atomicAdd(count, 1) while the slot is below capacity (*count, DEVICE int32,
+ * keeps counting past it). */
+kt_status kt_sweep_collect(kt_sweep *s, int32_t n_steps, const double *uniforms, void *features, float *targets,
+                           int32_t *count, int32_t capacity, void *stream);
+/* Attach a trained network (n_in must match, max_batch >= n_walkers) or detach (NULL). */
+kt_status kt_sweep_set_surrogate(kt_sweep *s, kt_mlp *net);
+/* Steps with delayed acceptance: uniforms DEVICE [n_steps][n_walkers][7]; u[0..5] as
+ * kt_sweep_run, u6 decides stage 1: accept when log(u6) < r + log|det ratio| +
+ * log(proposal factor) with r the signed prediction (+y insertion, -y removal); stage 2
+ * accepts when log(u5) < log|T_new / T_old| - r. Because r is antisymmetric, this is
+ * the exact two-stage rule of Christen and Fox. Only stage-1 survivors reach the trace
+ * pipeline.
+ * Counters 8 (stage-1 rejections) and 9 (trace ratios evaluated) count them. */
+kt_status kt_sweep_run_da(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream);
 
 /* Kernel tiling: every (walker, kept state) item of the Krylov stage is
  * processed by a group of group_lanes lanes of one warp (32 / group_lanes items

@@ -50,8 +50,9 @@ Delayed acceptance (Christen & Fox 2005) with a surrogate r~ of log|T_new / T_ol
 seventh uniform u6 per step; stage 1 accepts when
   log(u6) < r~ + log|bath factor ratio| + log(proposal factor),
 and only then is the trace evaluated; stage 2 accepts when log(u5) < log|T_new/T_old| - r~.
-The product of the two stages satisfies detailed balance with respect to w for any fixed
-surrogate.
+This second stage is the Christen-Fox one, min(1, R alpha1(y, x) / alpha1(x, y)), for a
+surrogate that is antisymmetric (the reverse move gets -r~): the chain then satisfies
+detailed balance with respect to w. The surrogate callable must have that property.
 Measurements every meas_every steps, weighted by the sign of w:
   G_f(tau) = (1/beta) < sum_{ij} M_ji dh(tau, tau_j - tau'_i) >,  M = G_f^{-1},
   dh(tau, x) = delta(tau - x) for x > 0 and -delta(tau - x - beta) for x < 0,

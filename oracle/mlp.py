@@ -3,7 +3,7 @@
 Only the tests import this module; the product library never calls it.
 
 The surrogate predicts the log of the trace ratio |T_new / T_old| of a proposed local
-update from a feature vector x of the current configuration and the move:
+update from a feature vector x of a configuration and the move's pair:
 
     y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3,     W1: [H, n_in], W2: [H, H], w3: [H]
 
@@ -12,17 +12,26 @@ trained on the mean squared error L = (1/B) sum_b (y_b - t_b)^2 with Adam (Kingm
 beta2 = 0.999, eps = 1e-8, bias-corrected moments). Everything here is written out in
 FP64 with numpy products; the backward pass is the chain rule of the three layers.
 
-Features (a reading of "per-flavor operator counts, a 32-bin histogram of segment
-lengths per flavor, and the move type"; the move is described by its kind, flavor,
-length and orientation, because the log ratio depends on which pair is proposed):
-    x[f]                      = k_f / 8                 pairs of flavor f
-    x[nf + 32 f + b]         += 1/4 for every segment of flavor f (a c^+ to the next
-                                c of f, cyclically) whose length l has
+The network predicts the log trace ratio of INSERTING a pair into the configuration
+that does not hold it (the base): for an insertion the base is the current
+configuration, for a removal it is the current configuration without the pair, and the
+removal's prediction is minus the network's output. The surrogate is then exactly
+antisymmetric (a move and its reverse share the features and get opposite
+predictions), which is what makes the second delayed-acceptance stage
+min(1, R / R~) exact (Christen & Fox: stage 2 carries alpha1(y, x) / alpha1(x, y),
+equal to 1 / R~ only for an antisymmetric surrogate).
+
+Features of the base and the pair (a reading of "per-flavor operator counts, a 32-bin
+histogram of segment lengths per flavor, and the move type"; the pair is described by
+its flavor, length and orientation, because the log ratio depends on it):
+    x[f]                      = k_f / 8                 pairs of flavor f in the base
+    x[nf + 32 f + b]         += 1/4 for every segment of flavor f in the base (a c^+ to
+                                the next c of f, cyclically) whose length l has
                                 b = min(floor(32 l / beta), 31)
-    x[33 nf]                  = +1 insertion, -1 removal
+    x[33 nf]                  = 0 (unused)
     x[33 nf + 1 + f_move]     = 1
     x[34 nf + 1]              = ((t_second - t_first) mod beta) / beta, the distance from
-                                the move's first operator (t1 of an insertion, the chosen
+                                the pair's first operator (t1 of an insertion, the chosen
                                 operator of a removal) to its partner
     x[34 nf + 2]              = +1 when the first operator is a c^+ (segment), else -1
     the rest (up to n_in, a multiple of 16) is 0.
@@ -105,10 +114,24 @@ def adam_step(p: dict, g: dict, m: dict, v: dict, step: int, lr: float, beta1=0.
     return np_, nm, nv
 
 
+def base_config(ops, kind: int, flavor: int, t_first: float, t_second: float):
+    """The configuration without the move's pair (the current one for an insertion)."""
+    if kind == 0:
+        return list(ops)
+    out, dropped = [], 0
+    for t, g, d in ops:
+        if g == flavor and (t == t_first or t == t_second) and dropped < 2:
+            dropped += 1
+            continue
+        out.append((t, g, d))
+    return out
+
+
 def features(ops, nf: int, beta: float, kind: int, flavor: int, t_first: float, t_second: float, seg: bool,
              n_in: int | None = None) -> np.ndarray:
     """The surrogate's input for the configuration `ops` and one proposed move."""
     n_in = n_inputs(nf) if n_in is None else n_in
+    ops = base_config(ops, kind, flavor, t_first, t_second)
     x = np.zeros(n_in)
     for f in range(nf):
         mine = [(t, d) for t, g, d in ops if g == f]
@@ -121,7 +144,6 @@ def features(ops, nf: int, beta: float, kind: int, flavor: int, t_first: float, 
             b = min(int(ln / beta * 32), 31)
             x[nf + 32 * f + b] += 0.25
     base = 33 * nf
-    x[base] = 1.0 if kind == 0 else -1.0
     x[base + 1 + flavor] = 1.0
     d = t_second - t_first
     if d < 0:

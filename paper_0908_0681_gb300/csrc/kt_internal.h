@@ -112,6 +112,14 @@ int launch_pipeline(const DevModel &m, int precision, int kernel_dmax, int group
                     kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing,
                     double *obs = nullptr);
 
+// Tensor-core GEMM C = A . B^T (BF16 in, FP32 out) and the surrogate network's
+// forward pass (kt_mlp.cu), for the delayed-acceptance sweep.
+int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc, int M, int N, int K, int *err,
+              void *st_);
+int mlp_forward(kt_mlp *n, const void *X, int B, float *y, bool train, void *st_);
+int mlp_inputs(const kt_mlp *n);
+int mlp_max_batch(const kt_mlp *n);
+
 // Launch parameters of a model, for entry points that live outside kt_model.cpp.
 struct ModelView {
   const DevModel *dev;

@@ -13,7 +13,10 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <math.h>
 #include <stdint.h>
+
+#include <new>
 
 #include "kt_internal.h"
 
@@ -186,7 +189,8 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__r
 
 // C = A . B^T; requirements checked by the caller-facing entry point.
 int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc, int M, int N, int K, int *err,
-              cudaStream_t st) {
+              void *st_) {
+  cudaStream_t st = (cudaStream_t)st_;
   const int BN = N <= mlp::MAX_BN ? N : 128;
   const size_t smem = (size_t)mlp::BM * mlp::BK * 2 + (size_t)BN * mlp::BK * 2;
   static bool attr = false;
@@ -202,10 +206,341 @@ int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc,
 
 }  // namespace kt
 
+// ---------------------------------------------------------------------------
+// The surrogate network y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 (hidden 256):
+// BF16 operands on the tensor cores (kt_gemm_bf16), FP32 accumulation, FP32
+// master weights, biases, output layer and Adam state.
+// ---------------------------------------------------------------------------
+namespace kt {
+namespace mlp {
+
+constexpr int H = 256;
+
+__global__ void to_bf16_kernel(const float *__restrict__ src, __nv_bfloat16 *dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// dst[c][r] = src[r][c] (FP32 -> BF16), src [R][C] row-major
+__global__ void transpose_bf16_kernel(const float *__restrict__ src, __nv_bfloat16 *dst, int R, int C) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)R * C) return;
+  const int r = (int)(i / C), c = (int)(i - (long long)r * C);
+  dst[(size_t)c * R + r] = __float2bfloat16_rn(src[i]);
+}
+
+// dst[c][r] = src[r][c] for BF16 matrices
+__global__ void transpose_b16_kernel(const __nv_bfloat16 *__restrict__ src, __nv_bfloat16 *dst, int R, int C) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)R * C) return;
+  const int r = (int)(i / C), c = (int)(i - (long long)r * C);
+  dst[(size_t)c * R + r] = src[i];
+}
+
+// H1 = relu(Z1 + b1) in BF16 (row-major; with HT also transposed)
+__global__ void act1_kernel(const float *__restrict__ Z1, const float *__restrict__ b1, __nv_bfloat16 *H1,
+                            __nv_bfloat16 *H1T, int B) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)B * H) return;
+  const int b = (int)(i / H), j = (int)(i - (long long)b * H);
+  const __nv_bfloat16 h = __float2bfloat16_rn(fmaxf(Z1[i] + b1[j], 0.f));
+  H1[i] = h;
+  if (H1T) H1T[(size_t)j * B + b] = h;
+}
+
+// y_b = w3 . relu(Z2_b + b2) + b3 (warp per row); H2 keeps relu(...) when given
+__global__ void out_kernel(const float *__restrict__ Z2, const float *__restrict__ b2, const float *__restrict__ w3,
+                           const float *__restrict__ b3, float *H2, float *y, int B) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= B) return;
+  float acc = 0.f;
+  for (int j = lane; j < H; j += 32) {
+    const float h = fmaxf(Z2[(size_t)row * H + j] + b2[j], 0.f);
+    if (H2) H2[(size_t)row * H + j] = h;
+    acc = fmaf(h, w3[j], acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = acc + b3[0];
+}
+
+// dy = 2 (y - t) / B; loss += (y - t)^2 / B
+__global__ void loss_kernel(const float *__restrict__ y, const float *__restrict__ t, float *dy, float *loss, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  float c = 0.f;
+  if (b < B) {
+    const float r = y[b] - t[b];
+    dy[b] = 2.f * r / (float)B;
+    c = r * r / (float)B;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c != 0.f) atomicAdd(loss, c);
+}
+
+// dZ2 = dy w3^T masked by relu'(Z2 + b2), BF16 in both layouts
+__global__ void dz2_kernel(const float *__restrict__ Z2, const float *__restrict__ b2, const float *__restrict__ w3,
+                           const float *__restrict__ dy, __nv_bfloat16 *dZ2, __nv_bfloat16 *dZ2T, int B) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)B * H) return;
+  const int b = (int)(i / H), j = (int)(i - (long long)b * H);
+  const float d = (Z2[i] + b2[j] > 0.f) ? dy[b] * w3[j] : 0.f;
+  const __nv_bfloat16 v = __float2bfloat16_rn(d);
+  dZ2[i] = v;
+  dZ2T[(size_t)j * B + b] = v;
+}
+
+// column sums over the batch: gw3_j = sum_b dy_b H2_bj, gb2_j = sum_b dZ2_bj (FP32), gb3 = sum_b dy_b
+__global__ void out_grads_kernel(const float *__restrict__ Z2, const float *__restrict__ b2,
+                                 const float *__restrict__ w3, const float *__restrict__ H2,
+                                 const float *__restrict__ dy, float *gw3, float *gb2, float *gb3, int B) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < H) {
+    float a = 0.f, c = 0.f;
+    for (int b = 0; b < B; ++b) {
+      const float d = dy[b];
+      a = fmaf(d, H2[(size_t)b * H + j], a);
+      if (Z2[(size_t)b * H + j] + b2[j] > 0.f) c = fmaf(d, w3[j], c);
+    }
+    gw3[j] = a;
+    gb2[j] = c;
+  }
+  if (j == 0) {
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += dy[b];
+    gb3[0] = s;
+  }
+}
+
+// dZ1 = dH1 masked by relu'(Z1 + b1): BF16 transposed [H][B]; gb1 column sums (FP32)
+__global__ void dz1_kernel(const float *__restrict__ dH1, const float *__restrict__ Z1, const float *__restrict__ b1,
+                           __nv_bfloat16 *dZ1T, int B) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)B * H) return;
+  const int b = (int)(i / H), j = (int)(i - (long long)b * H);
+  const float d = (Z1[i] + b1[j] > 0.f) ? dH1[i] : 0.f;
+  dZ1T[(size_t)j * B + b] = __float2bfloat16_rn(d);
+}
+__global__ void gb1_kernel(const float *__restrict__ dH1, const float *__restrict__ Z1, const float *__restrict__ b1,
+                           float *gb1, int B) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= H) return;
+  float c = 0.f;
+  for (int b = 0; b < B; ++b)
+    if (Z1[(size_t)b * H + j] + b1[j] > 0.f) c += dH1[(size_t)b * H + j];
+  gb1[j] = c;
+}
+
+// Adam (Kingma & Ba 2015, Algorithm 1) on the packed FP32 parameters
+__global__ void adam_kernel(float *p, const float *__restrict__ g, float *m, float *v, long long n, float lr, float bc1,
+                            float bc2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+}
+
+inline unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace mlp
+}  // namespace kt
+
+struct kt_mlp {
+  int n_in = 0, maxB = 0, step = 0;
+  long long P = 0;
+  void *mem = nullptr;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  float *W1, *b1, *W2, *b2, *w3, *b3;
+  float *gW1, *gb1, *gW2, *gb2, *gw3, *gb3;
+  __nv_bfloat16 *W1b, *W2b, *W2Tb;
+  float *Z1, *Z2, *H2, *dH1, *y, *dy, *loss;
+  __nv_bfloat16 *H1b, *H1Tb, *dZ2b, *dZ2Tb, *dZ1Tb, *XTb;
+  int *err;
+};
+
+namespace kt {
+
+int mlp_inputs(const kt_mlp *n) { return n->n_in; }
+int mlp_max_batch(const kt_mlp *n) { return n->maxB; }
+
+int mlp_refresh_bf16(kt_mlp *n, cudaStream_t st) {
+  using namespace mlp;
+  to_bf16_kernel<<<blocks((long long)H * n->n_in), 256, 0, st>>>(n->W1, n->W1b, (long long)H * n->n_in);
+  to_bf16_kernel<<<blocks((long long)H * H), 256, 0, st>>>(n->W2, n->W2b, (long long)H * H);
+  transpose_bf16_kernel<<<blocks((long long)H * H), 256, 0, st>>>(n->W2, n->W2Tb, H, H);
+  return (int)cudaGetLastError();
+}
+
+// y[B] = network(X [B][n_in] BF16); with train, keeps what the backward pass needs
+int mlp_forward(kt_mlp *n, const void *X, int B, float *y, bool train, void *st_) {
+  using namespace mlp;
+  cudaStream_t st = (cudaStream_t)st_;
+  int rc = gemm_bf16(X, n->n_in, n->W1b, n->n_in, n->Z1, H, B, H, n->n_in, n->err, st);
+  if (rc) return rc;
+  act1_kernel<<<blocks((long long)B * H), 256, 0, st>>>(n->Z1, n->b1, n->H1b, train ? n->H1Tb : nullptr, B);
+  rc = gemm_bf16(n->H1b, H, n->W2b, H, n->Z2, H, B, H, H, n->err, st);
+  if (rc) return rc;
+  out_kernel<<<blocks((long long)B * 32), 256, 0, st>>>(n->Z2, n->b2, n->w3, n->b3, train ? n->H2 : nullptr, y, B);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace kt
+
+extern "C" {
+
+kt_status kt_mlp_create(int32_t n_in, int32_t max_batch, kt_mlp **out) {
+  using namespace kt::mlp;
+  if (!out || n_in < 16 || (n_in % 16) || max_batch < 16 || (max_batch % 16)) return KT_EINVAL;
+  *out = nullptr;
+  kt_mlp *n = new (std::nothrow) kt_mlp();
+  if (!n) return KT_ENOMEM;
+  n->n_in = n_in;
+  n->maxB = max_batch;
+  n->P = (long long)H * n_in + H + (long long)H * H + H + H + 1;
+  const size_t B = max_batch, P = n->P;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  const size_t o_p = take(P * 4), o_g = take(P * 4), o_m = take(P * 4), o_v = take(P * 4),
+               o_w1b = take((size_t)H * n_in * 2), o_w2b = take((size_t)H * H * 2), o_w2t = take((size_t)H * H * 2),
+               o_z1 = take(B * H * 4), o_z2 = take(B * H * 4), o_h2 = take(B * H * 4), o_dh1 = take(B * H * 4),
+               o_y = take(B * 4), o_dy = take(B * 4), o_loss = take(4), o_h1 = take(B * H * 2), o_h1t = take(B * H * 2),
+               o_dz2 = take(B * H * 2), o_dz2t = take(B * H * 2), o_dz1t = take(B * H * 2),
+               o_xt = take(B * (size_t)n_in * 2), o_err = take(4);
+  if (cudaMalloc(&n->mem, off) != cudaSuccess) {
+    cudaGetLastError();
+    delete n;
+    return KT_ENOMEM;
+  }
+  cudaMemset(n->mem, 0, off);
+  char *b = (char *)n->mem;
+  n->p = (float *)(b + o_p);
+  n->g = (float *)(b + o_g);
+  n->m = (float *)(b + o_m);
+  n->v = (float *)(b + o_v);
+  float *q = n->p, *r = n->g;
+  n->W1 = q; n->gW1 = r; q += (size_t)H * n_in; r += (size_t)H * n_in;
+  n->b1 = q; n->gb1 = r; q += H; r += H;
+  n->W2 = q; n->gW2 = r; q += (size_t)H * H; r += (size_t)H * H;
+  n->b2 = q; n->gb2 = r; q += H; r += H;
+  n->w3 = q; n->gw3 = r; q += H; r += H;
+  n->b3 = q; n->gb3 = r;
+  n->W1b = (__nv_bfloat16 *)(b + o_w1b);
+  n->W2b = (__nv_bfloat16 *)(b + o_w2b);
+  n->W2Tb = (__nv_bfloat16 *)(b + o_w2t);
+  n->Z1 = (float *)(b + o_z1);
+  n->Z2 = (float *)(b + o_z2);
+  n->H2 = (float *)(b + o_h2);
+  n->dH1 = (float *)(b + o_dh1);
+  n->y = (float *)(b + o_y);
+  n->dy = (float *)(b + o_dy);
+  n->loss = (float *)(b + o_loss);
+  n->H1b = (__nv_bfloat16 *)(b + o_h1);
+  n->H1Tb = (__nv_bfloat16 *)(b + o_h1t);
+  n->dZ2b = (__nv_bfloat16 *)(b + o_dz2);
+  n->dZ2Tb = (__nv_bfloat16 *)(b + o_dz2t);
+  n->dZ1Tb = (__nv_bfloat16 *)(b + o_dz1t);
+  n->XTb = (__nv_bfloat16 *)(b + o_xt);
+  n->err = (int *)(b + o_err);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    kt_mlp_destroy(n);
+    return KT_ECUDA;
+  }
+  *out = n;
+  return KT_OK;
+}
+
+kt_status kt_mlp_num_params(const kt_mlp *n, int64_t *count) {
+  if (!n || !count) return KT_EINVAL;
+  *count = n->P;
+  return KT_OK;
+}
+
+kt_status kt_mlp_set_params(kt_mlp *n, const float *host) {
+  if (!n || !host) return KT_EINVAL;
+  if (cudaMemcpy(n->p, host, (size_t)n->P * 4, cudaMemcpyHostToDevice) != cudaSuccess) return KT_ECUDA;
+  cudaMemset(n->m, 0, (size_t)n->P * 4);
+  cudaMemset(n->v, 0, (size_t)n->P * 4);
+  n->step = 0;
+  if (kt::mlp_refresh_bf16(n, 0) != 0) return KT_ECUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_mlp_get_params(kt_mlp *n, float *host) {
+  if (!n || !host) return KT_EINVAL;
+  return cudaMemcpy(host, n->p, (size_t)n->P * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_mlp_get_grads(kt_mlp *n, float *host) {
+  if (!n || !host) return KT_EINVAL;
+  return cudaMemcpy(host, n->g, (size_t)n->P * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_mlp_forward(kt_mlp *n, const void *X, int32_t B, float *y, void *stream) {
+  if (!n || !X || !y || B < 1 || B > n->maxB || ((uintptr_t)X % 16)) return KT_EINVAL;
+  return kt::mlp_forward(n, X, B, y, false, stream) == 0 ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_mlp_backward(kt_mlp *n, const void *X, const float *t, int32_t B, float *loss, void *stream) {
+  using namespace kt::mlp;
+  if (!n || !X || !t || B < 16 || (B % 16) || B > n->maxB || ((uintptr_t)X % 16)) return KT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nin = n->n_in;
+  if (kt::mlp_forward(n, X, B, n->y, true, st) != 0) return KT_ECUDA;
+  cudaMemsetAsync(n->loss, 0, 4, st);
+  loss_kernel<<<blocks(B), 256, 0, st>>>(n->y, t, n->dy, n->loss, B);
+  dz2_kernel<<<blocks((long long)B * H), 256, 0, st>>>(n->Z2, n->b2, n->w3, n->dy, n->dZ2b, n->dZ2Tb, B);
+  out_grads_kernel<<<1, H, 0, st>>>(n->Z2, n->b2, n->w3, n->H2, n->dy, n->gw3, n->gb2, n->gb3, B);
+  // dW2 = dZ2^T H1: A = dZ2T [H][B], B-operand = H1T [H][B]
+  if (kt::gemm_bf16(n->dZ2Tb, B, n->H1Tb, B, n->gW2, H, H, H, B, n->err, st)) return KT_ECUDA;
+  // dH1 = dZ2 W2: A = dZ2 [B][H], B-operand = W2T [H(in)][H(out)]
+  if (kt::gemm_bf16(n->dZ2b, H, n->W2Tb, H, n->dH1, H, B, H, H, n->err, st)) return KT_ECUDA;
+  dz1_kernel<<<blocks((long long)B * H), 256, 0, st>>>(n->dH1, n->Z1, n->b1, n->dZ1Tb, B);
+  gb1_kernel<<<1, H, 0, st>>>(n->dH1, n->Z1, n->b1, n->gb1, B);
+  // dW1 = dZ1^T X: A = dZ1T [H][B], B-operand = XT [n_in][B]
+  transpose_b16_kernel<<<blocks((long long)B * nin), 256, 0, st>>>((const __nv_bfloat16 *)X, n->XTb, B, nin);
+  if (kt::gemm_bf16(n->dZ1Tb, B, n->XTb, B, n->gW1, nin, H, nin, B, n->err, st)) return KT_ECUDA;
+  if (loss) cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToDevice, st);
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_mlp_adam(kt_mlp *n, float lr, void *stream) {
+  using namespace kt::mlp;
+  if (!n || !(lr > 0.f)) return KT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  n->step += 1;
+  const float bc1 = 1.f - powf(0.9f, (float)n->step), bc2 = 1.f - powf(0.999f, (float)n->step);
+  adam_kernel<<<blocks(n->P), 256, 0, st>>>(n->p, n->g, n->m, n->v, n->P, lr, bc1, bc2);
+  if (kt::mlp_refresh_bf16(n, st) != 0) return KT_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_mlp_error(kt_mlp *n, int32_t *out) {
+  if (!n || !out) return KT_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return KT_ECUDA;
+  return cudaMemcpy(out, n->err, 4, cudaMemcpyDeviceToHost) == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+void kt_mlp_destroy(kt_mlp *n) {
+  if (!n) return;
+  if (n->mem) cudaFree(n->mem);
+  delete n;
+}
+
+}  // extern "C"
+
 extern "C" kt_status kt_gemm_bf16(const void *A, int32_t lda, const void *B, int32_t ldb, float *C, int32_t ldc,
                                   int32_t M, int32_t N, int32_t K, int32_t *err, void *stream) {
   if (!A || !B || !C || !err || M < 1 || N < 16 || K < 16 || (N % 16) || (K % 16) || lda < K || ldb < K || ldc < N ||
       (lda % 8) || (ldb % 8) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16))
     return KT_EINVAL;
-  return kt::gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, err, (cudaStream_t)stream) == 0 ? KT_OK : KT_ECUDA;
+  return kt::gemm_bf16(A, lda, B, ldb, C, ldc, M, N, K, err, stream) == 0 ? KT_OK : KT_ECUDA;
 }

@@ -28,6 +28,7 @@
 //     #{old ops x : flavor(x) <= f, tau_x < t} + #{old ops x : flavor(x) > f, tau_x > t}
 //   plus 1 if tau'_new < tau_new,
 // and a removal is the inverse of inserting its pair into the reduced configuration.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -48,7 +49,7 @@ namespace kt {
 namespace {
 using namespace dev;
 
-enum { C_INS_PROP, C_INS_ACC, C_REM_PROP, C_REM_ACC, C_NULL, C_CAP, C_TRACE_ERR, C_MEAS };
+enum { C_INS_PROP, C_INS_ACC, C_REM_PROP, C_REM_ACC, C_NULL, C_CAP, C_TRACE_ERR, C_MEAS, C_STAGE1, C_TRACE_EVAL };
 
 struct SweepView {
   int nw, nf, kcap, cap, n_tau, n_bins, nobs;
@@ -77,6 +78,14 @@ struct SweepView {
   double *p_lambda;   // insertion: lambda
   int32_t *p_ij;      // removal: [2] storage row i (creator), column j (annihilator)
   double *p_vec;      // insertion: [nw][2 kcap]: M C (by annihilator), R M (by creator)
+  int8_t *p_kind;     // 0 insertion, 1 removal (also for null moves)
+  double *p_t1, *p_t2;  // the move's first operator time and its partner's
+  int8_t *p_seg;      // 1 if the first operator is a c^+
+  int32_t *p_pair;    // [2 nw] sequence indices of a removal's pair (-1 for insertions)
+  // delayed acceptance
+  int n_in;           // feature length
+  __nv_bfloat16 *X;   // [nw][n_in] features of the proposals
+  float *ytil;        // [nw] predicted log|T_new / T_old|
   // trace ratio outputs
   int8_t *r_sign;
   double *r_log;
@@ -142,17 +151,25 @@ __device__ int perm_count(const double *tau, const uint8_t *fl, int K, int f, do
   return c + (tdag < tann ? 1 : 0);
 }
 
-__global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni) {
+__global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni, int ustride) {
   extern __shared__ double sh[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int w = blockIdx.x * (blockDim.x >> 5) + wib;
   if (w >= S.nw) return;
   double *Cv = sh + (size_t)wib * 2 * S.kcap;  // new column C (by creator) / row R (by annihilator)
   double *Rv = Cv + S.kcap;
-  const double *u = uni + (size_t)w * 6;
+  const double *u = uni + (size_t)w * ustride;
   const int nf = S.nf;
   const double beta = S.beta;
   const int o = S.offsets[w], K = S.lens[w];
+  if (lane == 0) {
+    S.p_kind[w] = u[0] < 0.5 ? 0 : 1;
+    S.p_t1[w] = 0.0;
+    S.p_t2[w] = 0.0;
+    S.p_seg[w] = 0;
+    S.p_pair[2 * w] = -1;
+    S.p_pair[2 * w + 1] = -1;
+  }
   const double *tau = S.tau + o;
   const uint8_t *fl = S.flv + o, *dg = S.dag + o;
   int f = (int)(u[1] * nf);
@@ -225,6 +242,9 @@ __global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni
       const double lambda = hyb_Fh(S, f, td - ta) - warp_sum(part);
       const int X = perm_count(tau, fl, K, f, td, ta, -1, -1, lane);
       if (lane == 0) {
+        S.p_t1[w] = t1;
+        S.p_t2[w] = t2;
+        S.p_seg[w] = seg ? 1 : 0;
         S.mv_kind[w] = 0;
         S.mv_tdag[w] = td;
         S.mv_tann[w] = ta;
@@ -269,6 +289,11 @@ __global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni
         const double ratio = Mf[(size_t)cj * S.kcap + ri];
         const int X = perm_count(tau, fl, K, f, td, ta, a, b, lane);
         if (lane == 0) {
+          S.p_t1[w] = t1;
+          S.p_t2[w] = t2;
+          S.p_seg[w] = da == 1 ? 1 : 0;
+          S.p_pair[2 * w] = a;
+          S.p_pair[2 * w + 1] = b;
           S.mv_kind[w] = 1;
           S.mv_rem[w] = a;
           S.p_lprop[w] = lp;
@@ -293,11 +318,13 @@ __global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni
   }
 }
 
-__global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni, const int4 *__restrict__ desc) {
+__global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni, int ustride,
+                                    const int4 *__restrict__ desc, bool delayed) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= S.nw) return;
   if (!S.p_valid[w]) return;
+  if (lane == 0) atomicAdd(&S.counters[C_TRACE_EVAL], 1ull);
   const int st = S.r_status[w];
   if (st != KT_OK) {
     if (lane == 0) atomicAdd(&S.counters[C_TRACE_ERR], 1ull);
@@ -305,8 +332,9 @@ __global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni,
   }
   const int tsg = S.r_sign[w];
   if (tsg == 0) return;  // the new trace is zero
-  const double logR = S.r_log[w] + S.p_ldet[w] + S.p_lprop[w];
-  const double u5 = uni[(size_t)w * 6 + 5];
+  // plain Metropolis: the whole ratio; delayed acceptance, stage 2: true over predicted trace ratio
+  const double logR = delayed ? S.r_log[w] - (double)S.ytil[w] : S.r_log[w] + S.p_ldet[w] + S.p_lprop[w];
+  const double u5 = uni[(size_t)w * ustride + 5];
   const bool accept = (u5 > 0.0 ? log(u5) : -INFINITY) < logR;
   if (!accept) return;
   const int nf = S.nf, f = S.mv_flv[w], kind = S.mv_kind[w];
@@ -416,6 +444,97 @@ __global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni,
   }
 }
 
+// Feature vector of each proposal (see kt_sweep_feature_size): the configuration without
+// the move's pair (the base) and the pair. A removal's base skips the pair's operators.
+__global__ void sweep_features_kernel(SweepView S) {
+  extern __shared__ float hsm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (w >= S.nw) return;
+  const int nf = S.nf;
+  const double beta = S.beta;
+  float *hist = hsm + (size_t)wib * nf * 32;
+  for (int i = lane; i < nf * 32; i += 32) hist[i] = 0.f;
+  __syncwarp();
+  const int o = S.offsets[w], K = S.lens[w];
+  const double *tau = S.tau + o;
+  const uint8_t *fl = S.flv + o, *dg = S.dag + o;
+  const int pa = S.p_pair[2 * w], pb = S.p_pair[2 * w + 1];
+  for (int i = lane; i < K; i += 32) {
+    if (dg[i] != 1 || i == pa || i == pb) continue;
+    const int f = fl[i];
+    int j = -1;
+    for (int s2 = 1; s2 < K; ++s2) {
+      const int c = i + s2 < K ? i + s2 : i + s2 - K;
+      if (fl[c] == f && c != pa && c != pb) {
+        j = c;
+        break;
+      }
+    }
+    if (j < 0) continue;
+    const double l = tau[j] > tau[i] ? tau[j] - tau[i] : tau[j] + beta - tau[i];
+    int b = (int)(l / beta * 32);
+    b = b > 31 ? 31 : b;
+    atomicAdd(&hist[f * 32 + b], 0.25f);
+  }
+  __syncwarp();
+  __nv_bfloat16 *row = S.X + (size_t)w * S.n_in;
+  const int fm = S.mv_flv[w];
+  for (int i = lane; i < S.n_in; i += 32) {
+    float x = 0.f;
+    if (i < nf) {
+      x = (float)(S.kf[(size_t)w * nf + i] - (pa >= 0 && i == fm ? 1 : 0)) / 8.f;
+    } else if (i < 33 * nf) {
+      x = hist[i - nf];
+    } else if (i == 33 * nf) {
+      x = 0.f;
+    } else if (i <= 34 * nf) {
+      x = (i - 33 * nf - 1 == fm) ? 1.f : 0.f;
+    } else if (i == 34 * nf + 1) {
+      double d = S.p_t2[w] - S.p_t1[w];
+      if (d < 0.0) d += beta;
+      x = (float)(d / beta);
+    } else if (i == 34 * nf + 2) {
+      x = S.p_seg[w] ? 1.f : -1.f;
+    }
+    row[i] = __float2bfloat16_rn(x);
+  }
+}
+
+// Stage 1 of delayed acceptance: the surrogate's ratio decides whether the trace is computed.
+// The network predicts the insertion of the pair into the base; a removal takes minus
+// that, so a move and its reverse get opposite predictions (antisymmetric surrogate).
+__global__ void sweep_stage1_kernel(SweepView S, const double *__restrict__ uni) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= S.nw) return;
+  if (S.p_kind[w] != 0) S.ytil[w] = -S.ytil[w];
+  if (!S.p_valid[w]) return;
+  const double lt = (double)S.ytil[w] + S.p_ldet[w] + S.p_lprop[w];
+  const double u6 = uni[(size_t)w * 7 + 6];
+  if (!((u6 > 0.0 ? log(u6) : -INFINITY) < lt)) {
+    S.p_valid[w] = 0;
+    S.mv_kind[w] = 2;  // skipped by the trace pipeline (rejected by its validation without work)
+    atomicAdd(&S.counters[C_STAGE1], 1ull);
+  }
+}
+
+// Training data: features and the insertion log trace ratio of every evaluated nonzero
+// ratio (log|T_new / T_old| for an insertion, its negative for a removal).
+__global__ void sweep_record_kernel(SweepView S, __nv_bfloat16 *feat, float *targ, int *count, int cap) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= S.nw) return;
+  if (!S.p_valid[w] || S.r_status[w] != KT_OK || S.r_sign[w] == 0) return;
+  int slot = 0;
+  if (lane == 0) slot = atomicAdd(count, 1);
+  slot = __shfl_sync(FULL, slot, 0);
+  if (slot >= cap) return;
+  const __nv_bfloat16 *src = S.X + (size_t)w * S.n_in;
+  __nv_bfloat16 *dst = feat + (size_t)slot * S.n_in;
+  for (int i = lane; i < S.n_in; i += 32) dst[i] = src[i];
+  if (lane == 0) targ[slot] = (float)(S.p_kind[w] == 0 ? S.r_log[w] : -S.r_log[w]);
+}
+
 __global__ void sweep_measure_kernel(SweepView S) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -485,6 +604,7 @@ struct kt_sweep {
   size_t ws_bytes = 0;
   bool measure_obs = false;
   std::vector<double> hyb_host;
+  kt_mlp *net = nullptr;
 };
 
 namespace {
@@ -507,7 +627,9 @@ kt_status carve_and_alloc(kt_sweep *s) {
                o_pij = take(nw * 2 * 4), o_pvec = take(nw * 2 * kc * 8), o_rs = take(nw), o_rl = take(nw * 8),
                o_rst = take(nw * 4), o_g = take(nw * nf * v.n_bins * 8), o_ss = take(nw * 8), o_os = take(nw * nf * 8),
                o_obs = take(nw * v.nobs * 8), o_obt = take(nw * v.nobs * 8), o_msg = take(nw), o_mlg = take(nw * 8),
-               o_mst = take(nw * 4), o_cnt = take(KT_SWEEP_NCOUNTERS * 8);
+               o_mst = take(nw * 4), o_cnt = take(KT_SWEEP_NCOUNTERS * 8), o_pk = take(nw), o_pt1 = take(nw * 8),
+               o_pt2 = take(nw * 8), o_pseg = take(nw), o_X = take(nw * (size_t)v.n_in * 2), o_yt = take(nw * 4),
+               o_ppair = take(nw * 2 * 4);
   if (cudaMalloc(&s->mem, b) != cudaSuccess) {
     cudaGetLastError();
     s->mem = nullptr;
@@ -553,6 +675,13 @@ kt_status carve_and_alloc(kt_sweep *s) {
   v.m_log = (double *)(p + o_mlg);
   v.m_status = (int32_t *)(p + o_mst);
   v.counters = (unsigned long long *)(p + o_cnt);
+  v.p_kind = (int8_t *)(p + o_pk);
+  v.p_t1 = (double *)(p + o_pt1);
+  v.p_t2 = (double *)(p + o_pt2);
+  v.p_seg = (int8_t *)(p + o_pseg);
+  v.X = (__nv_bfloat16 *)(p + o_X);
+  v.ytil = (float *)(p + o_yt);
+  v.p_pair = (int32_t *)(p + o_ppair);
   return KT_OK;
 }
 
@@ -658,6 +787,7 @@ kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out)
   v.n_tau = p->n_tau;
   v.n_bins = p->n_bins;
   v.nobs = KT_MEASURE_NOBS(mv.dev->n_orb);
+  v.n_in = (34 * nf + 3 + 15) / 16 * 16;
   v.beta = mv.dev->beta;
   kt_status rc = carve_and_alloc(s);
   if (rc == KT_OK) {
@@ -692,10 +822,13 @@ kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out)
   return KT_OK;
 }
 
-kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream) {
+// Shared step loop of kt_sweep_run (mode 0), kt_sweep_run_da (1) and kt_sweep_collect (2).
+static kt_status run_steps(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream,
+                           int mode, __nv_bfloat16 *feat, float *targ, int *count, int cap) {
   if (!s || n_steps < 0 || meas_every < 0) return KT_EINVAL;
   if (n_steps == 0) return KT_OK;
   if (!uniforms) return KT_EINVAL;
+  const int ustride = mode == 1 ? 7 : 6;
   cudaStream_t st = (cudaStream_t)stream;
   kt::SweepView &v = s->v;
   const kt::DevModel &M = *s->mv.dev;
@@ -707,13 +840,20 @@ kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int
   const unsigned grid = (unsigned)((v.nw + wpb - 1) / wpb);
   const size_t shm = (size_t)wpb * 2 * v.kcap * sizeof(double);
   cudaGetLastError();
+  const size_t shf = (size_t)wpb * v.nf * 32 * sizeof(float);
   for (int step = 0; step < n_steps; ++step) {
-    const double *u = uniforms + (size_t)step * v.nw * 6;
-    kt::sweep_propose_kernel<<<grid, wpb * 32, shm, st>>>(v, u);
+    const double *u = uniforms + (size_t)step * v.nw * ustride;
+    kt::sweep_propose_kernel<<<grid, wpb * 32, shm, st>>>(v, u, ustride);
+    if (mode != 0) kt::sweep_features_kernel<<<grid, wpb * 32, shf, st>>>(v);
+    if (mode == 1) {
+      if (kt::mlp_forward(s->net, v.X, v.nw, v.ytil, false, st) != 0) return KT_ECUDA;
+      kt::sweep_stage1_kernel<<<(v.nw + 255) / 256, 256, 0, st>>>(v, u);
+    }
     if (kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, sv, &mvv, v.tr_sign, v.tr_log,
                             v.r_sign, v.r_log, v.r_status, nullptr, w, st, nullptr) != 0)
       return KT_ECUDA;
-    kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, u, w.desc);
+    if (mode == 2) kt::sweep_record_kernel<<<grid, wpb * 32, 0, st>>>(v, feat, targ, count, cap);
+    kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, u, ustride, w.desc, mode == 1);
     if (meas_every > 0 && (step + 1) % meas_every == 0) {
       kt::sweep_measure_kernel<<<grid, wpb * 32, 0, st>>>(v);
       if (s->measure_obs) {
@@ -724,6 +864,35 @@ kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int
     }
   }
   return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream) {
+  return run_steps(s, n_steps, uniforms, meas_every, stream, 0, nullptr, nullptr, nullptr, 0);
+}
+
+kt_status kt_sweep_run_da(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream) {
+  if (!s || !s->net) return KT_EINVAL;
+  return run_steps(s, n_steps, uniforms, meas_every, stream, 1, nullptr, nullptr, nullptr, 0);
+}
+
+kt_status kt_sweep_collect(kt_sweep *s, int32_t n_steps, const double *uniforms, void *features, float *targets,
+                           int32_t *count, int32_t capacity, void *stream) {
+  if (!s || !features || !targets || !count || capacity < 0) return KT_EINVAL;
+  return run_steps(s, n_steps, uniforms, 0, stream, 2, (__nv_bfloat16 *)features, targets, count, capacity);
+}
+
+kt_status kt_sweep_feature_size(const kt_sweep *s, int32_t *n_in) {
+  if (!s || !n_in) return KT_EINVAL;
+  *n_in = s->v.n_in;
+  return KT_OK;
+}
+
+kt_status kt_sweep_set_surrogate(kt_sweep *s, kt_mlp *net) {
+  if (!s) return KT_EINVAL;
+  if (net && kt::mlp_inputs(net) != s->v.n_in) return KT_EINVAL;
+  if (net && kt::mlp_max_batch(net) < s->v.nw) return KT_EINVAL;
+  s->net = net;
+  return KT_OK;
 }
 
 static kt_status set_configs_impl(kt_sweep *s, const kt_seq_batch *b);

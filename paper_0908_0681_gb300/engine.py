@@ -180,6 +180,31 @@ class Sweep:
     def counters(self) -> dict:
         return kt.kt_sweep_counters(self.h)
 
+    @property
+    def n_features(self) -> int:
+        return kt.kt_sweep_feature_size(self.h)
+
+    def collect(self, uniforms: torch.Tensor, capacity: int):
+        """Plain steps that record (features, log|T_new/T_old|) of every evaluated nonzero ratio.
+        Returns (features bf16 [n, n_in], targets float32 [n]) with n = min(count, capacity)."""
+        assert uniforms.dtype == torch.float64 and uniforms.is_cuda and uniforms.is_contiguous()
+        assert uniforms.shape[1:] == (self.n_walkers, 6)
+        feats = torch.empty((capacity, self.n_features), dtype=torch.bfloat16, device="cuda")
+        targs = torch.empty(capacity, dtype=torch.float32, device="cuda")
+        count = torch.zeros(1, dtype=torch.int32, device="cuda")
+        kt.kt_sweep_collect(self.h, uniforms.shape[0], uniforms, feats, targs, count)
+        n = min(int(count.item()), capacity)
+        return feats[:n], targs[:n]
+
+    def set_surrogate(self, net) -> None:
+        kt.kt_sweep_set_surrogate(self.h, None if net is None else net.h)
+
+    def run_da(self, uniforms: torch.Tensor, meas_every: int = 0) -> None:
+        """Delayed-acceptance steps; uniforms float64 [n_steps, n_walkers, 7]."""
+        assert uniforms.dtype == torch.float64 and uniforms.is_cuda and uniforms.is_contiguous()
+        assert uniforms.shape[1:] == (self.n_walkers, 7)
+        kt.kt_sweep_run_da(self.h, uniforms.shape[0], uniforms, meas_every)
+
     def reset_accumulators(self) -> None:
         kt.kt_sweep_reset_accumulators(self.h)
 
@@ -187,3 +212,49 @@ class Sweep:
         """G_f(tau) at the bin centres, pooled over walkers: [n_flavors, n_bins]."""
         acc = self.accumulators() if acc is None else acc
         return acc["g_tau"].sum(0) * (self.n_bins / self.beta ** 2) / acc["sign_sum"].sum()
+
+
+class Surrogate:
+    """The delayed-acceptance network (kt_mlp_*): predicts log|T_new / T_old| of a proposal."""
+
+    def __init__(self, n_in: int, max_batch: int = 4096, params: np.ndarray | None = None, seed: int = 0):
+        self.h = kt.KtMlp(n_in, max_batch)
+        self.n_in = n_in
+        if params is None:
+            rng = np.random.default_rng(seed)
+            H = kt.KT_MLP_HIDDEN
+            params = np.concatenate([rng.normal(0, np.sqrt(2.0 / n_in), H * n_in), np.zeros(H),
+                                     rng.normal(0, np.sqrt(2.0 / H), H * H), np.zeros(H),
+                                     rng.normal(0, np.sqrt(2.0 / H), H), np.zeros(1)])
+        self.set_params(params)
+
+    def set_params(self, params: np.ndarray) -> None:
+        kt.kt_mlp_set_params(self.h, params)
+
+    def params(self) -> np.ndarray:
+        return kt.kt_mlp_get_params(self.h)
+
+    def predict(self, X: torch.Tensor) -> torch.Tensor:
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        kt.kt_mlp_forward(self.h, X.contiguous(), y)
+        return y
+
+    def train(self, X: torch.Tensor, t: torch.Tensor, epochs: int = 3, batch: int = 4096, lr: float = 1e-3,
+              seed: int = 0) -> list:
+        """Adam on the mean squared error; returns the mean loss of every epoch."""
+        n = (X.shape[0] // batch) * batch
+        g = torch.Generator(device=X.device).manual_seed(seed)
+        loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+        hist = []
+        for _ in range(epochs):
+            perm = torch.randperm(X.shape[0], device=X.device, generator=g)[:n]
+            tot = torch.zeros((), dtype=torch.float64, device=X.device)
+            for i in range(0, n, batch):
+                idx = perm[i:i + batch]
+                kt.kt_mlp_backward(self.h, X[idx].contiguous(), t[idx].contiguous(), loss)
+                kt.kt_mlp_adam(self.h, lr)
+                tot += loss[0].double()
+            hist.append(float(tot.item()) / max(n // batch, 1))
+        if kt.kt_mlp_error(self.h):
+            raise kt.KtError("a tensor-core wait timed out during training")
+        return hist

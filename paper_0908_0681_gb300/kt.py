@@ -76,11 +76,15 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_measure_workspace_size", "kt_measure",
                  "kt_sweep_create", "kt_sweep_run", "kt_sweep_get_state", "kt_sweep_get_accumulators",
                  "kt_sweep_counters", "kt_sweep_reset_accumulators", "kt_sweep_destroy",
-                 "kt_sweep_set_configs", "kt_gemm_bf16"]
+                 "kt_sweep_set_configs", "kt_gemm_bf16", "kt_mlp_create", "kt_mlp_num_params",
+                 "kt_mlp_set_params", "kt_mlp_get_params", "kt_mlp_forward", "kt_mlp_backward", "kt_mlp_get_grads",
+                 "kt_mlp_adam", "kt_mlp_error", "kt_mlp_destroy", "kt_sweep_feature_size", "kt_sweep_collect",
+                 "kt_sweep_set_surrogate", "kt_sweep_run_da"]
 
-KT_SWEEP_NCOUNTERS = 8
+KT_SWEEP_NCOUNTERS = 10
+KT_MLP_HIDDEN = 256
 SWEEP_COUNTERS = ["insert_proposed", "insert_accepted", "remove_proposed", "remove_accepted", "null_moves",
-                  "refused_at_k_cap", "trace_errors", "measurements"]
+                  "refused_at_k_cap", "trace_errors", "measurements", "stage1_rejected", "trace_evaluations"]
 
 _lib = None
 
@@ -117,6 +121,21 @@ def load():
     lib.kt_sweep_run.argtypes = [vp, i32, vp, i32, vp]
     lib.kt_sweep_set_configs.argtypes = [vp, ctypes.POINTER(kt_seq_batch)]
     lib.kt_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp, vp]
+    lib.kt_mlp_create.argtypes = [i32, i32, ctypes.POINTER(vp)]
+    lib.kt_mlp_num_params.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.kt_mlp_set_params.argtypes = [vp, vp]
+    lib.kt_mlp_get_params.argtypes = [vp, vp]
+    lib.kt_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+    lib.kt_mlp_backward.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.kt_mlp_get_grads.argtypes = [vp, vp]
+    lib.kt_mlp_adam.argtypes = [vp, ctypes.c_float, vp]
+    lib.kt_mlp_error.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.kt_mlp_destroy.argtypes = [vp]
+    lib.kt_mlp_destroy.restype = None
+    lib.kt_sweep_feature_size.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.kt_sweep_collect.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
+    lib.kt_sweep_set_surrogate.argtypes = [vp, vp]
+    lib.kt_sweep_run_da.argtypes = [vp, i32, vp, i32, vp]
     lib.kt_sweep_get_state.argtypes = [vp, ctypes.POINTER(kt_sweep_state), vp]
     lib.kt_sweep_get_accumulators.argtypes = [vp, ctypes.POINTER(kt_sweep_accum), vp]
     lib.kt_sweep_counters.argtypes = [vp, vp]
@@ -131,7 +150,7 @@ def load():
                                 ctypes.POINTER(ctypes.c_int32)]
     lib.kt_timing_end.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
     for f in ABI_FUNCTIONS:
-        if f not in ("kt_status_string", "kt_model_destroy", "kt_sweep_destroy"):
+        if f not in ("kt_status_string", "kt_model_destroy", "kt_sweep_destroy", "kt_mlp_destroy"):
             getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -328,6 +347,83 @@ def kt_gemm_bf16(A, B, C, err, stream=None) -> None:
     N = B.shape[0]
     _check(load().kt_gemm_bf16(_ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), C.stride(0), M, N, K, _ptr(err),
                                _stream_handle(stream)), "kt_gemm_bf16")
+
+
+class KtMlp:
+    """Owning handle of a kt_mlp (the delayed-acceptance surrogate network)."""
+
+    def __init__(self, n_in: int, max_batch: int):
+        h = ctypes.c_void_p()
+        _check(load().kt_mlp_create(int(n_in), int(max_batch), ctypes.byref(h)), "kt_mlp_create")
+        self.handle = h
+        self.n_in, self.max_batch = int(n_in), int(max_batch)
+        c = ctypes.c_int64()
+        _check(_lib.kt_mlp_num_params(h, ctypes.byref(c)), "kt_mlp_num_params")
+        self.n_params = int(c.value)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.kt_mlp_destroy(h)
+            self.handle = None
+
+
+def kt_mlp_set_params(n: KtMlp, params: np.ndarray) -> None:
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    assert a.size == n.n_params
+    _check(load().kt_mlp_set_params(n.handle, a.ctypes.data_as(ctypes.c_void_p)), "kt_mlp_set_params")
+
+
+def kt_mlp_get_params(n: KtMlp) -> np.ndarray:
+    a = np.zeros(n.n_params, dtype=np.float32)
+    _check(load().kt_mlp_get_params(n.handle, a.ctypes.data_as(ctypes.c_void_p)), "kt_mlp_get_params")
+    return a
+
+
+def kt_mlp_get_grads(n: KtMlp) -> np.ndarray:
+    a = np.zeros(n.n_params, dtype=np.float32)
+    _check(load().kt_mlp_get_grads(n.handle, a.ctypes.data_as(ctypes.c_void_p)), "kt_mlp_get_grads")
+    return a
+
+
+def kt_mlp_forward(n: KtMlp, X, y, stream=None) -> None:
+    _check(load().kt_mlp_forward(n.handle, _ptr(X), X.shape[0], _ptr(y), _stream_handle(stream)), "kt_mlp_forward")
+
+
+def kt_mlp_backward(n: KtMlp, X, t, loss=None, stream=None) -> None:
+    _check(load().kt_mlp_backward(n.handle, _ptr(X), _ptr(t), X.shape[0], _ptr(loss), _stream_handle(stream)),
+           "kt_mlp_backward")
+
+
+def kt_mlp_adam(n: KtMlp, lr: float, stream=None) -> None:
+    _check(load().kt_mlp_adam(n.handle, ctypes.c_float(lr), _stream_handle(stream)), "kt_mlp_adam")
+
+
+def kt_mlp_error(n: KtMlp) -> int:
+    e = ctypes.c_int32()
+    _check(load().kt_mlp_error(n.handle, ctypes.byref(e)), "kt_mlp_error")
+    return int(e.value)
+
+
+def kt_sweep_feature_size(s: KtSweep) -> int:
+    n = ctypes.c_int32()
+    _check(load().kt_sweep_feature_size(s.handle, ctypes.byref(n)), "kt_sweep_feature_size")
+    return int(n.value)
+
+
+def kt_sweep_collect(s: KtSweep, n_steps: int, uniforms, features, targets, count, stream=None) -> None:
+    _check(load().kt_sweep_collect(s.handle, int(n_steps), _ptr(uniforms), _ptr(features), _ptr(targets), _ptr(count),
+                                   features.shape[0], _stream_handle(stream)), "kt_sweep_collect")
+
+
+def kt_sweep_set_surrogate(s: KtSweep, net) -> None:
+    _check(load().kt_sweep_set_surrogate(s.handle, None if net is None else net.handle), "kt_sweep_set_surrogate")
+    s.surrogate = net   # keep the network alive while attached
+
+
+def kt_sweep_run_da(s: KtSweep, n_steps: int, uniforms, meas_every: int = 0, stream=None) -> None:
+    _check(load().kt_sweep_run_da(s.handle, int(n_steps), _ptr(uniforms), int(meas_every), _stream_handle(stream)),
+           "kt_sweep_run_da")
 
 
 def kt_model_set_tiling(m: KtModel, group_lanes: int) -> None:
