@@ -238,64 +238,119 @@ def reference_arm(a):
 
 def sweep_bench(dev, steps: int, beta: float, seed: int):
     """Full CT-HYB sweeps of the five-orbital model (semicircular bath, 2,000 tau points,
-    1,024 chains): chains start from Poisson(6) configurations, thermalise untimed, then
-    `steps` Metropolis steps per chain are timed with CUDA events, measuring G(tau), the
-    orders and the beta/2 observables every 50 steps. FP32-Krylov traces; an FP64 run of
-    the same chains times the plain path."""
+    1,024 chains). Chains start from Poisson(6) configurations and thermalise untimed
+    (FP32-Krylov traces). The surrogate is trained on the chains' own ratios
+    (kt_sweep_collect, then Adam on the tensor cores). From the same thermalised state,
+    `steps` Metropolis steps are then timed with CUDA events for plain FP32-Krylov
+    sweeps, delayed-acceptance FP32 sweeps and plain FP64 sweeps,
+    measuring G(tau), the orders and the beta/2 observables every 50 steps.
+
+    Statistical efficiency at equal error: for an observable O the per-chain estimates
+    have a variance s2 across the 1,024 independent chains after wall time t; the time
+    needed for a given error scales as s2 * t, so eff = 1 / (s2 t) and the ratios of eff
+    between paths are the speedups at equal statistical error."""
     import numpy as np
     import torch
 
     from paper_0908_0681_gb300 import engine, kt, workloads
 
-    nw, therm, meas = 1024, 2000, 50
+    nw, therm, meas, ncollect = 1024, 2000, 50, 1000
     w = workloads.five_orbital()
     spec = workloads.five_orbital_sweep(beta).model
     gen = workloads.Workload(w.name, spec, start=w.start, order=w.order, lam=w.lam, cap=w.cap,
                              pattern_singles=w.pattern_singles)
     cand = workloads.generate_sequences(gen, 2 * nw, seed=seed)
     table = workloads.semicircular_hybridization(beta, 2 * spec.n_orb, n_tau=2000)
+    g = torch.Generator(device=dev).manual_seed(seed)
+
+    def uni(n, k):
+        return torch.rand((n, nw, k), dtype=torch.float64, device=dev, generator=g)
+
+    models = {name: engine.model_from_spec(spec, precision=prec)
+              for name, prec in (("fp32", kt.KT_FP32_KRYLOV), ("fp64", kt.KT_FP64))}
+    sg, _, _ = engine.trace(models["fp32"], engine.DeviceSeqs.from_host(cand, dev))
+    ok = np.nonzero(sg.cpu().numpy() != 0)[0][:nw]
+    base = engine.Sweep(models["fp32"], table, beta, nw, k_cap=128, n_bins=200, measure_obs=True)
+    base.set_configs(cand.subset(ok))
+    for _ in range(0, therm, 500):
+        base.run(uni(500, 6))
+    st = {k: v.cpu().numpy() for k, v in base.state().items()}
+    lens = st["lens"]
+    thermal = workloads.Sequences(np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
+                                  np.concatenate([st["tau"][i, :lens[i]] for i in range(nw)]),
+                                  np.concatenate([st["flavor"][i, :lens[i]] for i in range(nw)]),
+                                  np.concatenate([st["dagger"][i, :lens[i]] for i in range(nw)]))
+    # the surrogate: training data from the chains themselves, then Adam on the tensor cores
+    torch.cuda.synchronize()
+    t0 = time.time()
+    X, t = base.collect(uni(ncollect, 6), capacity=nw * ncollect)
+    torch.cuda.synchronize()
+    t_collect = time.time() - t0
+    # targets clipped to where the acceptance test can go either way (the chain stays exact
+    # for any surrogate; accuracy only matters near log ratio 0)
+    t = t.clamp(-25.0, 10.0)
+    net = engine.Surrogate(base.n_features, max_batch=4096, seed=seed)
+    t0 = time.time()
+    hist = net.train(X, t, epochs=6, batch=4096, lr=3e-3, seed=seed)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    pred = net.predict(X[:65536]).double()
+    resid = float(torch.sqrt(torch.mean((pred - t[:65536].double()) ** 2)).item())
+    spread = float(torch.std(t[:65536].double()).item())
+    del base
+
     out = {}
-    for name, prec in (("fp32", kt.KT_FP32_KRYLOV), ("fp64", kt.KT_FP64)):
-        model = engine.model_from_spec(spec, precision=prec)
-        sg, _, _ = engine.trace(model, engine.DeviceSeqs.from_host(cand, dev))
-        ok = np.nonzero(sg.cpu().numpy() != 0)[0][:nw]
+    for name, model, mode, n_t in (("fp32", models["fp32"], "plain", steps), ("fp32_da", models["fp32"], "da", steps),
+                                   ("fp64", models["fp64"], "plain", steps)):
         sw = engine.Sweep(model, table, beta, nw, k_cap=128, n_bins=200, measure_obs=True)
-        sw.set_configs(cand.subset(ok))
-        g = torch.Generator(device=dev).manual_seed(seed)
-        n_t = steps if name == "fp32" else max(steps // 4, 50)
-        for c in range(0, therm, 500):
-            sw.run(torch.rand((500, nw, 6), dtype=torch.float64, device=dev, generator=g))
-        sw.reset_accumulators()
-        u = torch.rand((n_t, nw, 6), dtype=torch.float64, device=dev, generator=g)
+        sw.set_configs(thermal)
+        if mode == "da":
+            sw.set_surrogate(net)
+        u = uni(n_t, 7 if mode == "da" else 6)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        sw.run(u, meas_every=meas)
+        if mode == "da":
+            sw.run_da(u, meas_every=meas)
+        else:
+            sw.run(u, meas_every=meas)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         cnt = sw.counters()
-        st = sw.state()
-        acc = sw.accumulators()
-        ssum = acc["sign_sum"].sum().item()
-        obs = (acc["obs_sum"].sum(0) / ssum).cpu().numpy()
-        K = st["lens"].double().mean().item()
+        stt = sw.state()
+        acc = {k: v.cpu().numpy() for k, v in sw.accumulators().items()}
+        ssum = acc["sign_sum"]
+        obs = acc["obs_sum"] / ssum[:, None]
+        docc = obs[:, 2 * spec.n_orb: 3 * spec.n_orb].mean(1)
+        order = acc["order_sum"].sum(1) / ssum
+        gmid = (acc["g_tau"][:, :, 95:105].mean(2) * (200 / beta ** 2) / ssum[:, None]).mean(1)
+        K = stt["lens"].double().mean().item()
         props = nw * n_t / (ms / 1000.0)
+        secs = ms / 1000.0
         out[name] = {"proposals_per_s": props, "ms_per_step": ms / n_t, "steps": n_t,
                      "sweeps_per_s": props / K, "mean_ops_per_chain": K,
-                     "mean_order_per_flavor": st["order"].double().mean().item(),
+                     "mean_order_per_flavor": stt["order"].double().mean().item(),
                      "acceptance": (cnt["insert_accepted"] + cnt["remove_accepted"]) / (nw * n_t),
-                     "mean_sign": ssum / (nw * cnt["measurements"]) if cnt["measurements"] else None,
-                     "trace_errors": cnt["trace_errors"], "refused_at_k_cap": cnt["refused_at_k_cap"]}
-        if name == "fp32":
-            G = sw.green_function(acc).cpu().numpy()
-            out[name].update({"n_f_mean": float(obs[:10].mean()), "docc_mean": float(obs[10:15].mean()),
-                              "G_first_bin": float(G[:, 0].mean()), "G_last_bin": float(G[:, -1].mean())})
+                     "trace_evaluations_per_proposal": cnt["trace_evaluations"] / (nw * n_t),
+                     "stage1_rejected_per_proposal": cnt["stage1_rejected"] / (nw * n_t),
+                     "mean_sign": float(ssum.sum() / (nw * cnt["measurements"])) if cnt["measurements"] else None,
+                     "trace_errors": cnt["trace_errors"], "refused_at_k_cap": cnt["refused_at_k_cap"],
+                     "docc": float(docc.mean()), "G_beta_half": float(gmid.mean()),
+                     "n_f": float(obs[:, :2 * spec.n_orb].mean()),
+                     "eff": {"docc": 1.0 / (docc.var(ddof=1) * secs), "order": 1.0 / (order.var(ddof=1) * secs),
+                             "G_beta_half": 1.0 / (gmid.var(ddof=1) * secs)}}
+    speed = {f"{a}_over_{b}": {k: out[a]["eff"][k] / out[b]["eff"][k] for k in out[a]["eff"]}
+             for a, b in (("fp32", "fp64"), ("fp32_da", "fp64"), ("fp32_da", "fp32"))}
     return {"workload": f"five_orbital_sweep_beta{beta:g}_1024_chains", "metric": "Metropolis proposals/s (all chains)",
             "sweep_definition": "one sweep = as many proposals per chain as the chain holds operators on average",
             "bath": "semicircular DOS, bandwidth 4, 2000 tau points", "thermalisation_steps": therm,
-            "measure_every": meas, "fp32": out["fp32"], "fp64": out["fp64"],
-            "speedup_fp32_over_fp64": out["fp32"]["proposals_per_s"] / out["fp64"]["proposals_per_s"]}
+            "measure_every": meas, "fp32": out["fp32"], "fp32_da": out["fp32_da"], "fp64": out["fp64"],
+            "speedup_fp32_over_fp64": out["fp32"]["proposals_per_s"] / out["fp64"]["proposals_per_s"],
+            "speedup_at_equal_error": speed,
+            "surrogate": {"training_samples": int(X.shape[0]), "collect_s": t_collect, "train_s": t_train,
+                          "epochs": len(hist), "loss_per_epoch": hist, "rms_residual_log_ratio": resid,
+                          "target_std": spread, "network": "n_in-256-256-1 ReLU, BF16 tcgen05, FP32 accumulate"}}
 
 
 def main():

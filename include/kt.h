@@ -391,7 +391,7 @@ kt_status kt_mlp_adam(kt_mlp *n, float lr, void *stream);
 kt_status kt_mlp_error(kt_mlp *n, int32_t *out);
 void kt_mlp_destroy(kt_mlp *n);
 
-/* Feature vector of a proposal (the surrogate's input; n_in = 34 n_flavors + 3 rounded
+/* Feature vector of a proposal (the surrogate's input; n_in = 35 n_flavors + 3 rounded
  * up to a multiple of 16). It describes the base (the configuration without the move's
  * pair: the current one for an insertion, the current one minus the pair for a
  * removal) and the pair, so that a move and its reverse share it:
@@ -401,7 +401,9 @@ void kt_mlp_destroy(kt_mlp *n);
  *   x[33 nf] = 0; x[33 nf + 1 + f_move] = 1;
  *   x[34 nf + 1] = ((t_second - t_first) mod beta) / beta (t_first: t1 of an insertion,
  *     the chosen operator of a removal; t_second its partner);
- *   x[34 nf + 2] = +1 if the first operator is a c^+, else -1; zero padding.
+ *   x[34 nf + 2] = +1 if the first operator is a c^+, else -1;
+ *   x[34 nf + 3 + g] = fraction of the pair's interval (first operator to partner,
+ *     cyclically) during which flavor g is occupied in the base; zero padding.
  * The network's output y predicts the log trace ratio of inserting the pair into the
  * base; the prediction for the move is y for an insertion and -y for a removal. */
 kt_status kt_sweep_feature_size(const kt_sweep *s, int32_t *n_in);

@@ -34,7 +34,12 @@ its flavor, length and orientation, because the log ratio depends on it):
                                 the pair's first operator (t1 of an insertion, the chosen
                                 operator of a removal) to its partner
     x[34 nf + 2]              = +1 when the first operator is a c^+ (segment), else -1
+    x[34 nf + 3 + g]          = the fraction of the pair's interval (from its first
+                                operator to its partner, cyclically) during which flavor g
+                                is occupied in the base (segments of g as above)
     the rest (up to n_in, a multiple of 16) is 0.
+The occupied fractions carry what decides the insertion cost: which other flavors
+hold an electron while the pair's flavor changes its occupation.
 """
 from __future__ import annotations
 
@@ -46,8 +51,19 @@ PARAMS = ("W1", "b1", "W2", "b2", "w3", "b3")
 
 
 def n_inputs(nf: int) -> int:
-    n = 34 * nf + 3
+    n = 35 * nf + 3
     return (n + 15) // 16 * 16
+
+
+def _overlap(a0: float, a1: float, b0: float, b1: float, beta: float) -> float:
+    """Length of the intersection of the cyclic intervals [a0, a0 + a1) and [b0, b0 + b1)
+    (start in [0, beta), lengths at most beta)."""
+    tot = 0.0
+    for k in (-1.0, 0.0, 1.0):
+        lo = max(a0, b0 + k * beta)
+        hi = min(a0 + a1, b0 + b1 + k * beta)
+        tot += max(0.0, hi - lo)
+    return tot
 
 
 def shapes(n_in: int, hidden: int = 256):
@@ -133,21 +149,25 @@ def features(ops, nf: int, beta: float, kind: int, flavor: int, t_first: float, 
     n_in = n_inputs(nf) if n_in is None else n_in
     ops = base_config(ops, kind, flavor, t_first, t_second)
     x = np.zeros(n_in)
+    d = t_second - t_first
+    if d < 0:
+        d += beta
     for f in range(nf):
-        mine = [(t, d) for t, g, d in ops if g == f]
-        x[f] = sum(1 for t, d in mine if d == 1) / 8.0
-        for i, (t, d) in enumerate(mine):
-            if d != 1:
+        mine = [(t, dg) for t, g, dg in ops if g == f]
+        x[f] = sum(1 for t, dg in mine if dg == 1) / 8.0
+        occ = 0.0
+        for i, (t, dg) in enumerate(mine):
+            if dg != 1:
                 continue
             tn = mine[(i + 1) % len(mine)][0]
             ln = tn - t if tn > t else tn + beta - t
             b = min(int(ln / beta * 32), 31)
             x[nf + 32 * f + b] += 0.25
+            occ += _overlap(t, ln, t_first, d, beta)
+        if d > 0:
+            x[34 * nf + 3 + f] = occ / d
     base = 33 * nf
     x[base + 1 + flavor] = 1.0
-    d = t_second - t_first
-    if d < 0:
-        d += beta
     x[base + 1 + nf] = d / beta
     x[base + 2 + nf] = 1.0 if seg else -1.0
     return x

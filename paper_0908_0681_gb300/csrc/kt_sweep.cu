@@ -453,9 +453,15 @@ __global__ void sweep_features_kernel(SweepView S) {
   if (w >= S.nw) return;
   const int nf = S.nf;
   const double beta = S.beta;
-  float *hist = hsm + (size_t)wib * nf * 32;
+  // per warp: nf x 32 histogram bins (float), then nf occupied lengths (double)
+  float *hist = hsm + (size_t)wib * nf * 34;
+  double *occ = reinterpret_cast<double *>(hist + nf * 32);
   for (int i = lane; i < nf * 32; i += 32) hist[i] = 0.f;
+  for (int i = lane; i < nf; i += 32) occ[i] = 0.0;
   __syncwarp();
+  const double m0 = S.p_t1[w];
+  double md = S.p_t2[w] - m0;
+  if (md < 0.0) md += beta;
   const int o = S.offsets[w], K = S.lens[w];
   const double *tau = S.tau + o;
   const uint8_t *fl = S.flv + o, *dg = S.dag + o;
@@ -476,6 +482,13 @@ __global__ void sweep_features_kernel(SweepView S) {
     int b = (int)(l / beta * 32);
     b = b > 31 ? 31 : b;
     atomicAdd(&hist[f * 32 + b], 0.25f);
+    // overlap of the segment [tau_i, tau_i + l) with the pair's interval [m0, m0 + md), cyclically
+    double ov = 0.0;
+    for (int k = -1; k <= 1; ++k) {
+      const double lo = fmax(tau[i], m0 + k * beta), hi = fmin(tau[i] + l, m0 + md + k * beta);
+      ov += fmax(0.0, hi - lo);
+    }
+    if (ov > 0.0) atomicAdd(&occ[f], ov);
   }
   __syncwarp();
   __nv_bfloat16 *row = S.X + (size_t)w * S.n_in;
@@ -496,6 +509,8 @@ __global__ void sweep_features_kernel(SweepView S) {
       x = (float)(d / beta);
     } else if (i == 34 * nf + 2) {
       x = S.p_seg[w] ? 1.f : -1.f;
+    } else if (i < 35 * nf + 3) {
+      x = md > 0.0 ? (float)(occ[i - 34 * nf - 3] / md) : 0.f;
     }
     row[i] = __float2bfloat16_rn(x);
   }
@@ -787,7 +802,7 @@ kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out)
   v.n_tau = p->n_tau;
   v.n_bins = p->n_bins;
   v.nobs = KT_MEASURE_NOBS(mv.dev->n_orb);
-  v.n_in = (34 * nf + 3 + 15) / 16 * 16;
+  v.n_in = (35 * nf + 3 + 15) / 16 * 16;
   v.beta = mv.dev->beta;
   kt_status rc = carve_and_alloc(s);
   if (rc == KT_OK) {
@@ -840,7 +855,7 @@ static kt_status run_steps(kt_sweep *s, int32_t n_steps, const double *uniforms,
   const unsigned grid = (unsigned)((v.nw + wpb - 1) / wpb);
   const size_t shm = (size_t)wpb * 2 * v.kcap * sizeof(double);
   cudaGetLastError();
-  const size_t shf = (size_t)wpb * v.nf * 32 * sizeof(float);
+  const size_t shf = (size_t)wpb * v.nf * 34 * sizeof(float);
   for (int step = 0; step < n_steps; ++step) {
     const double *u = uniforms + (size_t)step * v.nw * ustride;
     kt::sweep_propose_kernel<<<grid, wpb * 32, shm, st>>>(v, u, ustride);

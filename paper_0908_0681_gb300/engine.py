@@ -235,8 +235,11 @@ class Surrogate:
         return kt.kt_mlp_get_params(self.h)
 
     def predict(self, X: torch.Tensor) -> torch.Tensor:
+        """Network outputs for the rows of X (in chunks of max_batch)."""
         y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
-        kt.kt_mlp_forward(self.h, X.contiguous(), y)
+        mb = self.h.max_batch
+        for i in range(0, X.shape[0], mb):
+            kt.kt_mlp_forward(self.h, X[i:i + mb].contiguous(), y[i:i + mb])
         return y
 
     def train(self, X: torch.Tensor, t: torch.Tensor, epochs: int = 3, batch: int = 4096, lr: float = 1e-3,

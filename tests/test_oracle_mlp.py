@@ -95,20 +95,29 @@ def test_feature_vector_by_hand():
     # insertion of an anti-segment of flavor 1 (c at 5, c^+ at 5.5): the base is the configuration itself
     x = mlp.features(ops, nf, beta, kind=0, flavor=1, t_first=5.0, t_second=5.5, seg=False)
     assert len(x) == mlp.n_inputs(nf) == 80
+    # occupied fractions of [5, 5.5): flavor 0 is empty there, flavor 1 occupied (its segment 6 -> 4 wraps)
+    assert x[34 * nf + 3] == 0.0 and x[34 * nf + 4] == 0.0
     assert x[0] == 2 / 8 and x[1] == 1 / 8
     hist = x[nf:nf + 32 * nf].reshape(nf, 32)
     assert hist[0, 6] == 0.25 and hist[0, 4] == 0.25 and hist[1, 25] == 0.25 and hist.sum() == 0.75
     base = 33 * nf
     assert x[base] == 0.0 and x[base + 1 + 1] == 1.0 and x[base + 1] == 0.0
     assert abs(x[base + 1 + nf] - 0.05) < 1e-15 and x[base + 2 + nf] == -1.0
-    assert not x[base + 3 + nf:].any()
+    assert not x[base + 3 + nf:34 * nf + 3].any() and not x[35 * nf + 3:].any()
     # removal of flavor 1's pair (the c^+ at 6 and the c at 4 after it): the base has no flavor-1 operator
     y = mlp.features(ops, nf, beta, kind=1, flavor=1, t_first=6.0, t_second=4.0, seg=True)
     hy = y[nf:nf + 32 * nf].reshape(nf, 32)
     assert y[1] == 0.0 and hy[1].sum() == 0.0 and hy[0, 6] == 0.25 and hy[0, 4] == 0.25
     assert abs(y[base + 1 + nf] - 0.8) < 1e-15 and y[base + 2 + nf] == 1.0
+    # occupied fractions of the removed pair's interval [6, 4) (length 8, wrapping), base without
+    # flavor 1: flavor 0 holds [9, 0.5) and [1, 3) inside it -> (1.5 + 2) / 8
+    assert abs(y[34 * nf + 3] - 3.5 / 8) < 1e-15 and y[34 * nf + 4] == 0.0
     # a move and its reverse share their features: inserting that pair into the base
     z = mlp.features([op for op in ops if op[1] != 1], nf, beta, kind=0, flavor=1, t_first=6.0, t_second=4.0,
                      seg=True)
     assert np.array_equal(y, z)
     assert math.isclose(mlp.features([], nf, beta, 0, 0, 2.0, 7.0, False)[base + 1 + nf], 0.5)
+    # cyclic overlaps by hand
+    assert mlp._overlap(9.0, 3.0, 1.0, 1.0, beta) == 1.0     # [9, 12) wraps to cover [1, 2)
+    assert mlp._overlap(2.0, 1.0, 5.0, 1.0, beta) == 0.0
+    assert mlp._overlap(0.0, 10.0, 4.0, 10.0, beta) == 10.0
