@@ -95,7 +95,7 @@ Workspace carve_workspace(void *base, int n_walkers, int n_kept, int d_max, int 
 int kernel_dmax_for(int d_max);    // 0 if no variant fits
 int kernel_pmax_for(int kernel_dmax);
 int kernel_groups_for(int kernel_dmax, int *out, int cap);  // lane-group sizes compiled for this row capacity
-int default_group_for(int kernel_dmax);
+int default_group_for(int kernel_dmax, int precision);
 
 // Optional CUDA events recorded at the 5 stage boundaries of one pipeline call.
 struct StageEvents {

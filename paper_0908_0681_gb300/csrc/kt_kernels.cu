@@ -244,9 +244,12 @@ int kernel_groups_for(int kd, int *out, int cap) {
   return n;
 }
 
-int default_group_for(int kd) {
+// Lane-group size before any autotuning: the sizes kt_autotune picked on GB300 for the
+// five-orbital batch (10-row blocks: 8 lanes FP32, 4 lanes FP64) and the seven-orbital
+// batch (36-row blocks: 16 lanes).
+int default_group_for(int kd, int precision) {
   switch (kd) {
-    case 10: return 16;
+    case 10: return precision == KT_FP64 ? 4 : 8;
     case 36: return 16;
     case 128: return 32;
   }

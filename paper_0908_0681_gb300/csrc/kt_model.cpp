@@ -298,7 +298,7 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
 
   M->kernel_dmax = kt::kernel_dmax_for(d_max);
   if (M->kernel_dmax == 0) { delete M; return KT_EUNSUPPORTED; }
-  M->group_lanes = kt::default_group_for(M->kernel_dmax);
+  M->group_lanes = kt::default_group_for(M->kernel_dmax, P.precision);
 
   // ---- per block: dense H, Jacobi spectrum, shift, ELL rows ----
   std::vector<std::vector<double>> evals(B), evecs(B);

@@ -1,0 +1,70 @@
+"""A fixed invocation of the CT-HYB sweep for profiler captures.
+
+    python -m paper_0908_0681_gb300.profile_sweep [--beta 50] [--chains 1024] [--steps 20]
+           [--therm 200] [--collect 100] [--mode plain|da|both]
+
+Five-orbital model with the semicircular bath (2,000 tau points); the chains start from
+Poisson(6) configurations (kt_sweep_set_configs) and thermalise `therm` steps. For
+`da`, a surrogate is trained for one epoch on `collect` steps of the chains' own ratios.
+Then `steps` plain and/or delayed-acceptance steps run, measuring every 10 steps.
+Exits 0 when no chain reported a trace error.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--beta", type=float, default=50.0)
+    p.add_argument("--chains", type=int, default=1024)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--therm", type=int, default=200)
+    p.add_argument("--mode", choices=["plain", "da", "both"], default="both")
+    p.add_argument("--collect", type=int, default=100, help="steps of training data for the surrogate")
+    a = p.parse_args()
+    import numpy as np
+    import torch
+
+    from paper_0908_0681_gb300 import engine, kt, workloads
+
+    nw = a.chains
+    w = workloads.five_orbital()
+    spec = workloads.five_orbital_sweep(a.beta).model
+    gen = workloads.Workload(w.name, spec, start=w.start, order=w.order, lam=w.lam, cap=w.cap,
+                             pattern_singles=w.pattern_singles)
+    cand = workloads.generate_sequences(gen, 2 * nw, seed=7)
+    model = engine.model_from_spec(spec, precision=kt.KT_FP32_KRYLOV)
+    sg, _, _ = engine.trace(model, engine.DeviceSeqs.from_host(cand))
+    ok = np.nonzero(sg.cpu().numpy() != 0)[0][:nw]
+    table = workloads.semicircular_hybridization(a.beta, 2 * spec.n_orb, n_tau=2000)
+    sw = engine.Sweep(model, table, a.beta, nw, k_cap=128, n_bins=200, measure_obs=True)
+    sw.set_configs(cand.subset(ok))
+    g = torch.Generator(device="cuda").manual_seed(3)
+
+    def uni(n, k):
+        return torch.rand((n, nw, k), dtype=torch.float64, device="cuda", generator=g)
+
+    sw.run(uni(a.therm, 6))
+    if a.mode in ("plain", "both"):
+        sw.run(uni(a.steps, 6), meas_every=10)
+    if a.mode in ("da", "both"):
+        X, t = sw.collect(uni(a.collect, 6), capacity=a.collect * nw)
+        net = engine.Surrogate(sw.n_features, max_batch=4096, seed=1)
+        net.train(X, t.clamp(-25.0, 10.0), epochs=1, batch=4096, lr=3e-3)
+        sw.set_surrogate(net)
+        sw.run_da(uni(a.steps, 7), meas_every=10)
+    torch.cuda.synchronize()
+    c = sw.counters()
+    print(f"profile_sweep beta={a.beta:g} chains={nw} steps={a.steps} mode={a.mode} counters={c}")
+    return 0 if c["trace_errors"] == 0 else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())
