@@ -289,7 +289,7 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     # targets clipped to where the acceptance test can go either way (the chain stays exact
     # for any surrogate; accuracy only matters near log ratio 0)
     t = t.clamp(-25.0, 10.0)
-    net = engine.Surrogate(base.n_features, max_batch=4096, seed=seed)
+    net = engine.Surrogate(base.n_features, max_batch=8192, seed=seed)
     t0 = time.time()
     hist = net.train(X, t, epochs=6, batch=4096, lr=3e-3, seed=seed)
     torch.cuda.synchronize()
@@ -342,12 +342,49 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
                              "G_beta_half": 1.0 / (gmid.var(ddof=1) * secs)}}
     speed = {f"{a}_over_{b}": {k: out[a]["eff"][k] / out[b]["eff"][k] for k in out[a]["eff"]}
              for a, b in (("fp32", "fp64"), ("fp32_da", "fp64"), ("fp32_da", "fp32"))}
+    # throughput-bound batch: 8,192 chains (the 1,024-chain batch is bound by its longest chains)
+    nbig, nsteps_big = 8192, max(steps // 4, 100)
+    cand_big = workloads.generate_sequences(gen, int(1.3 * nbig), seed=seed + 1)
+    sgb, _, _ = engine.trace(models["fp32"], engine.DeviceSeqs.from_host(cand_big, dev))
+    okb = np.nonzero(sgb.cpu().numpy() != 0)[0][:nbig]
+
+    def unib(n, k):
+        return torch.rand((n, nbig, k), dtype=torch.float64, device=dev, generator=g)
+
+    big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200)
+    big.set_configs(cand_big.subset(okb))
+    for _ in range(0, therm, 500):
+        big.run(unib(500, 6))
+    thr = {}
+    for mode in ("plain", "da"):
+        if mode == "da":
+            big.set_surrogate(net)
+        u = unib(nsteps_big, 7 if mode == "da" else 6)
+        c0 = big.counters()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if mode == "da":
+            big.run_da(u)
+        else:
+            big.run(u)
+        e1.record()
+        torch.cuda.synchronize()
+        c1 = big.counters()
+        ms = e0.elapsed_time(e1)
+        thr[mode] = {"proposals_per_s": nbig * nsteps_big / (ms / 1000.0), "ms_per_step": ms / nsteps_big,
+                     "trace_evaluations_per_proposal": (c1["trace_evaluations"] - c0["trace_evaluations"]) / (nbig * nsteps_big),
+                     "acceptance": (c1["insert_accepted"] + c1["remove_accepted"] - c0["insert_accepted"]
+                                    - c0["remove_accepted"]) / (nbig * nsteps_big)}
+    thr.update(chains=nbig, steps=nsteps_big,
+               speedup_da_over_plain=thr["da"]["proposals_per_s"] / thr["plain"]["proposals_per_s"])
+    del big
     return {"workload": f"five_orbital_sweep_beta{beta:g}_1024_chains", "metric": "Metropolis proposals/s (all chains)",
             "sweep_definition": "one sweep = as many proposals per chain as the chain holds operators on average",
             "bath": "semicircular DOS, bandwidth 4, 2000 tau points", "thermalisation_steps": therm,
             "measure_every": meas, "fp32": out["fp32"], "fp32_da": out["fp32_da"], "fp64": out["fp64"],
             "speedup_fp32_over_fp64": out["fp32"]["proposals_per_s"] / out["fp64"]["proposals_per_s"],
-            "speedup_at_equal_error": speed,
+            "speedup_at_equal_error": speed, "throughput_8192_chains": thr,
             "surrogate": {"training_samples": int(X.shape[0]), "collect_s": t_collect, "train_s": t_train,
                           "epochs": len(hist), "loss_per_epoch": hist, "rms_residual_log_ratio": resid,
                           "target_std": spread, "network": "n_in-256-256-1 ReLU, BF16 tcgen05, FP32 accumulate"}}
