@@ -787,3 +787,117 @@ int FN(trace_obs_batch)(void *hm, int nseq, const int *offsets, const double *ta
 #endif
   return used;
 }
+
+/* ---------------------------------------------------------------------- */
+/* A general operator that conserves (n_up, n_dn), inserted at tau = t_obs  */
+/* ---------------------------------------------------------------------- */
+
+/* As trace_obs_one, with the operator given as a dense matrix over all
+ * bitstrings (op[y * nstates + x] = <y|O|x>) that maps each (n_up, n_dn)
+ * sector into itself. */
+static int trace_op_one(const or_model *m, int K, const double *tau, const uint8_t *flv, const uint8_t *dag,
+                        real t_obs, const double *op, real *va, real *vb, real *tmp, real *lg, int *sg, int *sign,
+                        double *logabs) {
+  const real beta = m->beta;
+  for (int k = 0; k < K; ++k) {
+    if (flv[k] >= m->nf || !(tau[k] >= 0) || !(tau[k] < (double)beta)) return OR_EINVAL;
+    if (k > 0 && tau[k] < tau[k - 1]) return OR_EINVAL;
+  }
+  if (!(t_obs >= 0) || !(t_obs <= beta)) return OR_EINVAL;
+  int mcut = 0;
+  while (mcut < K && (real)tau[mcut] < t_obs) ++mcut;
+  int nalive = 0;
+  for (int q = 0; q < m->nkept; ++q) {
+    int s0 = m->kept_sec[q], col = m->kept_col[q];
+    real En = m->kept_E[q];
+    int d0 = m->sec_dim[s0];
+    for (int i = 0; i < d0; ++i) va[i] = m->V[s0][i * d0 + col];
+    real L = 0, t = 0;
+    int s = s0, alive = 1, eig = 1;
+    for (int e = 0; e <= K && alive; ++e) {
+      const int is_obs = (e == mcut);
+      const int k = e < mcut ? e : e - 1;
+      const real te = is_obs ? t_obs : (real)tau[k];
+      if (te > t) {
+        if (eig) L += -(te - t) * (En - m->E0);
+        else L += propagate(m, s, te - t, va, tmp);
+      }
+      t = te;
+      int d = m->sec_dim[s];
+      if (is_obs) {
+        const int *st = m->states + m->sec_off[s];
+        for (int i = 0; i < d; ++i) {
+          real acc = 0;
+          for (int j = 0; j < d; ++j) acc += (real)op[(size_t)st[i] * m->nstates + st[j]] * va[j];
+          vb[i] = acc;
+        }
+      } else {
+        int tg = apply_vec(m, s, va, flv[k], dag[k], vb);
+        if (tg < 0) { alive = 0; break; }
+        s = tg;
+        d = m->sec_dim[s];
+      }
+      eig = 0;
+      real nrm = 0;
+      for (int i = 0; i < d; ++i) nrm += vb[i] * vb[i];
+      nrm = sqrt(nrm);
+      if (nrm == 0) { alive = 0; break; }
+      L += log(nrm);
+      for (int i = 0; i < d; ++i) va[i] = vb[i] / nrm;
+    }
+    if (!alive || s != s0) { sg[q] = 0; continue; }
+    real ov = 0;
+    for (int i = 0; i < d0; ++i) ov += m->V[s0][i * d0 + col] * va[i];
+    if (ov == 0) { sg[q] = 0; continue; }
+    L += log(fabs(ov)) - (beta - t) * (En - m->E0);
+    lg[q] = L; sg[q] = (ov > 0) ? 1 : -1;
+    ++nalive;
+  }
+  if (nalive == 0) { *sign = 0; *logabs = -INFINITY; return OR_OK; }
+  real mx = -INFINITY;
+  for (int q = 0; q < m->nkept; ++q) if (sg[q] && lg[q] > mx) mx = lg[q];
+  real acc = 0;
+  for (int q = 0; q < m->nkept; ++q) if (sg[q]) acc += (real)sg[q] * exp(lg[q] - mx);
+  if (acc == 0) { *sign = 0; *logabs = -INFINITY; return OR_OK; }
+  *sign = (acc > 0) ? 1 : -1;
+  *logabs = (double)(mx + log(fabs(acc)) - beta * m->E0);
+  return OR_OK;
+}
+
+int FN(trace_op_batch)(void *hm, int nseq, const int *offsets, const double *tau, const uint8_t *flavor,
+                       const uint8_t *dagger, double t_obs, const double *op, int *sign, double *logabs, int *status,
+                       int nthreads) {
+  or_model *m = (or_model *)hm;
+  int dmax = 1;
+  for (int s = 0; s < m->nsec; ++s) if (m->sec_dim[s] > dmax) dmax = m->sec_dim[s];
+  int used = 1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+  {
+#pragma omp single
+    used = omp_get_num_threads();
+#endif
+    real *va = (real *)malloc(sizeof(real) * (size_t)dmax);
+    real *vb = (real *)malloc(sizeof(real) * (size_t)dmax);
+    real *tmp = (real *)malloc(sizeof(real) * (size_t)dmax);
+    real *lg = (real *)malloc(sizeof(real) * (size_t)(m->nkept + 1));
+    int *sg = (int *)malloc(sizeof(int) * (size_t)(m->nkept + 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < nseq; ++i) {
+      int o = offsets[i], K = offsets[i + 1] - offsets[i];
+      double la = 0;
+      int sgn = 0;
+      int rc = (va && vb && tmp && lg && sg)
+                   ? trace_op_one(m, K, tau + o, flavor + o, dagger + o, (real)t_obs, op, va, vb, tmp, lg, sg, &sgn, &la)
+                   : OR_ENOMEM;
+      sign[i] = sgn; logabs[i] = la; status[i] = rc;
+    }
+    free(va); free(vb); free(tmp); free(lg); free(sg);
+#ifdef _OPENMP
+  }
+#endif
+  return used;
+}

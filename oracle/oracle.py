@@ -64,6 +64,9 @@ def _load():
             getattr(_lib, p + "model_block").argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3
             getattr(_lib, p + "model_kept").argtypes = [ctypes.c_void_p] * 4
             getattr(_lib, p + "trace_batch").argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 8 + [ctypes.c_int]
+            getattr(_lib, p + "trace_op_batch").argtypes = (
+                [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_double]
+                + [ctypes.c_void_p] * 4 + [ctypes.c_int])
             getattr(_lib, p + "trace_obs_batch").argtypes = (
                 [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_double, ctypes.c_int]
                 + [ctypes.c_void_p] * 4 + [ctypes.c_int])
@@ -165,6 +168,22 @@ class Model:
         return sign.astype(np.int8), la, lt
 
 
+    def trace_op(self, seqs: "SeqBatch", t_obs: float, op: np.ndarray, nthreads: int = 0):
+        """Traces with a general operator (dense [4^n, 4^n], <y|O|x> at [y, x], conserving
+        (n_up, n_dn)) inserted at t_obs. Returns (sign int8 [n], log|T_O| [n])."""
+        op = np.ascontiguousarray(op, dtype=np.float64)
+        assert op.shape == (self.nstates, self.nstates)
+        n = seqs.n
+        sign = np.zeros(n, dtype=np.int32)
+        la = np.zeros(n, dtype=np.float64)
+        st = np.zeros(n, dtype=np.int32)
+        getattr(_lib, self.prefix + "trace_op_batch")(
+            self._h, n, _ptr(seqs.offsets), _ptr(seqs.tau), _ptr(seqs.flavor), _ptr(seqs.dagger), float(t_obs),
+            _ptr(op), _ptr(sign), _ptr(la), _ptr(st), int(nthreads))
+        if st.any():
+            raise ValueError(f"oracle rejected {int((st != 0).sum())} sequences")
+        return sign.astype(np.int8), la
+
     def trace_obs(self, seqs: "SeqBatch", t_obs: float, obs: np.ndarray, nthreads: int = 0):
         """Traces with a diagonal operator inserted at t_obs (after every operator with tau < t_obs).
 
@@ -186,6 +205,28 @@ class Model:
         return sign.astype(np.int8), la
 
 
+def spin_squared(n_orb: int) -> np.ndarray:
+    """Total spin S^2 = S_x^2 + S_y^2 + S_z^2 over all bitstrings (dense), from
+    S_+ = sum_a c^+_{a up} c_{a dn}, S_x = (S_+ + S_-)/2, S_y = (S_+ - S_-)/(2i),
+    S_z = (N_up - N_dn)/2, with c_f built as Kronecker products carrying the
+    Jordan-Wigner string of the lower flavors."""
+    nf = 2 * n_orb
+    a = np.array([[0.0, 1.0], [0.0, 0.0]])   # |1> -> |0> on one flavor
+    Z = np.diag([1.0, -1.0])
+    I2 = np.eye(2)
+    c = []
+    for f in range(nf):
+        m = np.array([[1.0]])
+        for g in reversed(range(nf)):        # most significant flavor first
+            m = np.kron(m, a if g == f else (Z if g < f else I2))
+        c.append(m)
+    Sp = sum(c[2 * q].T @ c[2 * q + 1] for q in range(n_orb))
+    Sm = Sp.T
+    Sz = 0.5 * sum(c[2 * q].T @ c[2 * q] - c[2 * q + 1].T @ c[2 * q + 1] for q in range(n_orb))
+    Sx, Sy2 = 0.5 * (Sp + Sm), -0.25 * (Sp - Sm) @ (Sp - Sm)
+    return Sx @ Sx + Sy2 + Sz @ Sz
+
+
 def observable_table(n_orb: int) -> np.ndarray:
     """Diagonal observables of the occupation basis, one row per operator, one column per
     bitstring x (bit f = n_f): n_f for f = 2a + s, then n_{a up} n_{a dn} per orbital a,
@@ -202,14 +243,25 @@ def observable_table(n_orb: int) -> np.ndarray:
     return np.array(rows)
 
 
-def measure(model: Model, seqs: "SeqBatch", nthreads: int = 0):
-    """<O(beta/2)> = T_O / T for the observables of observable_table, per sequence.
+def measure(model: Model, seqs: "SeqBatch", nthreads: int = 0, spin: bool | None = None):
+    """<O(beta/2)> = T_O / T per sequence for n_f, n_{a up} n_{a dn}, S^2 (when spin; by
+    default for up to five orbitals, where the dense S^2 is small) and the (n_up, n_dn)
+    projectors, in that order.
 
     Returns (obs [n, nobs] with NaN where T = 0, sign_T, log|T|)."""
+    n = model.p.n_orb
     s, la, _ = model.trace(seqs, nthreads)
-    so, lo = model.trace_obs(seqs, 0.5 * model.p.beta, observable_table(model.p.n_orb), nthreads)
+    tab = observable_table(n)
+    so, lo = model.trace_obs(seqs, 0.5 * model.p.beta, tab, nthreads)
     with np.errstate(invalid="ignore", over="ignore"):
         val = so.astype(np.float64) * s[:, None].astype(np.float64) * np.exp(lo - la[:, None])
+    spin = (n <= 5) if spin is None else spin
+    col = np.full(seqs.n, np.nan)
+    if spin:
+        ss, ls = model.trace_op(seqs, 0.5 * model.p.beta, spin_squared(n), nthreads)
+        with np.errstate(invalid="ignore", over="ignore"):
+            col = ss.astype(np.float64) * s.astype(np.float64) * np.exp(ls - la)
+    val = np.concatenate([val[:, :3 * n], col[:, None], val[:, 3 * n:]], axis=1)
     val[s == 0, :] = np.nan
     return val, s, la
 

@@ -6,7 +6,9 @@ Each test ties oracle.measure / Model.trace_obs to something outside it: the pla
 c^+ c operators, closed forms of the kept multiplet, and the occupation-string picture of
 a density-density H_loc.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -15,10 +17,12 @@ from oracle.oracle import Model, Params, SeqBatch, classify, measure, observable
 from tests import brute
 from tests.test_oracle_pins import _random_ops, mu_half
 
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_degeneracies.json")))
+
 
 def _layout(n):
     nf = 2 * n
-    return slice(0, nf), slice(nf, nf + n), slice(nf + n, nf + n + (n + 1) ** 2)
+    return slice(0, nf), slice(nf, nf + n), slice(nf + n + 1, nf + n + 1 + (n + 1) ** 2)
 
 
 def test_observable_table_counts():
@@ -26,7 +30,8 @@ def test_observable_table_counts():
     for n in (1, 2, 3):
         t = observable_table(n)
         assert t.shape == (3 * n + (n + 1) ** 2, 4 ** n)
-        sn, sd, ss = _layout(n)
+        sn, sd = slice(0, 2 * n), slice(2 * n, 3 * n)
+        ss = slice(3 * n, 3 * n + (n + 1) ** 2)
         assert (t[sn].sum(axis=1) == 4 ** n / 2).all()          # each bit set in half of the states
         assert (t[sd].sum(axis=1) == 4 ** n / 4).all()
         assert (t[ss].sum(axis=0) == 1).all()                   # every state in exactly one sector
@@ -153,7 +158,7 @@ def test_density_only_occupation_at_half_beta():
         if den == 0.0:
             assert s[0] == 0 and np.isnan(val[0]).all()
             continue
-        assert np.allclose(val[0], num / den, rtol=1e-10, atol=1e-12)
+        assert np.allclose(np.delete(val[0], 3 * n), num / den, rtol=1e-10, atol=1e-12)   # all but S^2
         done += 1
     assert done >= 10
 
@@ -171,3 +176,82 @@ def test_histogram_and_densities_are_consistent():
     N = np.add.outer(np.arange(n + 1), np.arange(n + 1))
     assert np.allclose(hist.sum(axis=(1, 2)), 1.0, atol=1e-9)
     assert np.allclose((hist * N).sum(axis=(1, 2)), val[ok][:, sn].sum(axis=1), atol=1e-9)
+
+
+def test_spin_squared_operator():
+    """S^2 has the eigenvalues S(S+1), S = 0, 1/2, ..., n/2, and commutes with the
+    Kanamori H_loc at U' = U - 2J (Sec. IV.A: rotationally invariant), built
+    independently by Kronecker products in tests/brute.py."""
+    from oracle.oracle import spin_squared
+    for n in (1, 2, 3):
+        S2 = spin_squared(n)
+        assert np.allclose(S2, S2.T)
+        ev = np.linalg.eigvalsh(S2)
+        allowed = np.array([s * (s + 1) for s in np.arange(0, n / 2 + 0.25, 0.5)])
+        assert np.all(np.min(np.abs(ev[:, None] - allowed[None, :]), axis=1) < 1e-10)
+        H = brute.hamiltonian(n, 4.0, 1.0, 2.0, 1.3, np.linspace(0, 0.1, n))
+        assert np.abs(H @ S2 - S2 @ H).max() < 1e-10
+    # one orbital: |0>, |up>, |dn>, |updn> -> 0, 3/4, 3/4, 0
+    assert np.allclose(np.diag(spin_squared(1)), [0, 0.75, 0.75, 0])
+
+
+def _ground_sector_n(val, n):
+    hist = val[3 * n + 1:].reshape(n + 1, n + 1)
+    return {u + d for u in range(n + 1) for d in range(n + 1) if hist[u, d] > 1e-9}
+
+
+def test_total_spin_of_atomic_ground_states_paper():
+    """Sec. V (total spin): S^2 of the six-electron atomic ground states (golden file),
+    measured at beta/2 on the empty sequence with the ground multiplet alone."""
+    g = GOLD["five_orbital_total_spin"]
+    n, U = g["n_orb"], g["U"]
+    for case in g["cases"]:
+        J = case["J_over_U"] * U
+        delta = (case["delta_two_orbitals"],) * 2 + (0.0,) * 3
+        found = False
+        for mu in np.linspace(4.5 * U - 10 * J, 4.5 * U - 10 * J + 2 * U + 6 * J, 41)[1:]:
+            m = Model(Params(n, U, J, mu=float(mu), delta=delta, beta=50.0, trunc_eps=1.0))
+            val, s, _ = measure(m, SeqBatch.from_lists([[]]))
+            if _ground_sector_n(val[0], n) == {g["electrons"]}:
+                assert abs(val[0, 3 * n] - case["S2"]) < 1e-9, (case, mu, val[0, 3 * n])
+                found = True
+                break
+        assert found, case
+
+
+def test_spin_squared_as_operator_string():
+    """<S^2(beta/2)> = <S_z^2 + S_z + sum_a S-_a S+_a + sum_{a != b} S-_a S+_b>: the
+    exchange terms written as c^+ c^+ c c strings at beta/2 in the pinned plain trace,
+    the diagonal ones measured with the diagonal observable insertion."""
+    n, U, J, beta = 2, 4.0, 1.0, 6.0
+    rng = np.random.default_rng(21)
+    m = Model(Params(n, U, J, mu=mu_half(n, U, J) + 0.4, beta=beta, trunc_eps=0.0))
+    mx = Model(Params(n, U, J, mu=mu_half(n, U, J) + 0.4, beta=beta, trunc_eps=0.0), "ext")
+    lists = [_random_ops(rng, n, beta, 2) for _ in range(30)]
+    seqs = SeqBatch.from_lists(lists)
+    val, s, la = measure(m, seqs)
+    sx, lx, _ = mx.trace(seqs)
+    cls = classify(s, la, sx, lx)
+    x = np.arange(4 ** n)
+    nup = sum((x >> (2 * a)) & 1 for a in range(n))
+    ndn = sum((x >> (2 * a + 1)) & 1 for a in range(n))
+    sz = 0.5 * (nup - ndn)
+    diag = sz * sz + sz + sum(((x >> (2 * a + 1)) & 1) * (1 - ((x >> (2 * a)) & 1)) for a in range(n))
+    sd, ld = m.trace_obs(seqs, 0.5 * beta, diag[None, :].astype(float))
+    checked = 0
+    for i, ops in enumerate(lists):
+        if cls[i] != 2:
+            continue
+        tot = sd[i, 0] * math.exp(ld[i, 0] - la[i]) * s[i]
+        for a in range(n):
+            for b in range(n):
+                if a == b:
+                    continue
+                # S-_a S+_b = c^+_{a dn} c^+_{b up} c_{b dn} c_{a up}: applied right to left
+                st = [(2 * a, 0), (2 * b + 1, 0), (2 * b, 1), (2 * a + 1, 1)]
+                s2, l2, _ = m.trace(SeqBatch.from_lists([_insert_at(ops, 0.5 * beta, st)]))
+                if s2[0] != 0:
+                    tot += s2[0] * s[i] * math.exp(l2[0] - la[i])
+        assert abs(val[i, 3 * n] - tot) < 1e-9 * max(1.0, abs(tot)), (i, val[i, 3 * n], tot)
+        checked += 1
+    assert checked >= 10
