@@ -209,14 +209,17 @@ kt_status kt_trace_ratio(kt_model *m, const kt_seq_batch *cur, const int8_t *cur
  * propagated forward from tau = 0 and backward from beta, Sec. III step 3, and
  * the two meet at beta/2). For each walker and each diagonal operator O of the
  * occupation basis, <O> = Tr[... O(beta/2) ...] / Tr[...] with O inserted after
- * every operator with tau < beta/2. Layout of obs (DEVICE, [n][KT_MEASURE_NOBS]):
+ * every operator with tau < beta/2 (S^2 is not diagonal: it is applied to one of the
+ * two half vectors). Layout of obs (DEVICE, [n][KT_MEASURE_NOBS]):
  *   [0, 2 n_orb)              n_f, flavor f = 2a + s
  *   [2 n_orb, 3 n_orb)        n_{a up} n_{a dn} (double occupancy of orbital a)
- *   [3 n_orb, +(n_orb+1)^2)   projector on the (n_up, n_dn) sector, index
+ *   3 n_orb                   total spin S^2 (Sec. V: = S_z^2 + S_z + S- S+, whose
+ *                             exchange terms stay inside each block)
+ *   [3 n_orb + 1, +(n_orb+1)^2) projector on the (n_up, n_dn) sector, index
  *                             n_up * (n_orb + 1) + n_dn (a histogram summing to 1)
  * Walkers whose trace is 0 (sign 0) get NaN. sign, logabs, status as kt_trace.
  * The workspace must hold kt_measure_workspace_size(m, n) bytes. */
-#define KT_MEASURE_NOBS(n_orb) (3 * (n_orb) + ((n_orb) + 1) * ((n_orb) + 1))
+#define KT_MEASURE_NOBS(n_orb) (3 * (n_orb) + 1 + ((n_orb) + 1) * ((n_orb) + 1))
 kt_status kt_measure_workspace_size(const kt_model *m, int32_t n_walkers, size_t *bytes);
 kt_status kt_measure(kt_model *m, const kt_seq_batch *batch, int8_t *sign, double *logabs, double *obs,
                      int32_t *status, kt_stats *stats, void *workspace, size_t workspace_bytes, void *stream);

@@ -37,6 +37,12 @@ struct DevModel {
   const uint16_t *partner;    // [n_states * nf] rank of (x ^ 1<<f) in its block | 0x8000 if the
                               //   Jordan-Wigner sign of c_f / c_f^+ on x is negative
 
+  // S^2 inside each block (measurement at beta/2): diagonal per global row, ELL slot-major
+  // entries rank | 0x8000 for -1 (0xFFFF padding), width and first slot per block
+  const float *s2_diag;
+  const uint16_t *s2_ell;
+  const int32_t *blk_s2w, *blk_s2ell;
+
   const int32_t *kept_blk;    // [n_kept]
   const double *kept_e;       // [n_kept] E - E0
   const int32_t *kept_off;    // [n_kept] offset into kept_vec (block dimension entries)
@@ -78,11 +84,11 @@ struct Workspace {
   int32_t *half_info;  // [2 * n * n_kept] block | status << 24, or -1 if the half vanished
   void *half_vec;      // [2 * n * n_kept][d_max] final vector of each half (FP32 or FP64)
   // measurement at tau = beta/2 only (nullptr otherwise)
-  double *item_obs;    // [n * n_kept][nf + n_orb] <O> of each item: n_f, then n_{a up} n_{a dn}
+  double *item_obs;    // [n * n_kept][nf + n_orb + 1] <O> of each item: n_f, n_{a up} n_{a dn}, S^2
   int32_t *item_blk;   // [n * n_kept] block of the item at tau = beta/2
 };
 
-// n_obs_item = 0: trace and ratio calls; nf + n_orb: measurement calls.
+// n_obs_item = 0: trace and ratio calls; nf + n_orb + 1: measurement calls.
 size_t workspace_bytes(int n_walkers, int n_kept, int d_max, int n_obs_item = 0);
 Workspace carve_workspace(void *base, int n_walkers, int n_kept, int d_max, int n_obs_item = 0);
 

@@ -861,7 +861,7 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
       if (meas && !zero) {
         // <O> of this item for the diagonal observables at beta/2:
         // sum_r o(x_r) bwd_r fwd_r / sum_r bwd_r fwd_r
-        const int nf = M.nf, nl = nf + M.n_orb;
+        const int nf = M.nf, nl = nf + M.n_orb + 1;
         const int off = __ldg(M.blk_off + u.b);
         VT pr[R];
         int xr[R];
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
           }
         }
         const double iov = 1.0 / ov;
-        for (int k = 0; k < nl; ++k) {
+        for (int k = 0; k < nl - 1; ++k) {
           const int sh = k < nf ? k : 2 * (k - nf);
           const int msk = k < nf ? 1 : 3;
           GroupDot<VT, G> d;
@@ -885,6 +885,25 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
             if (((xr[j] >> sh) & msk) == msk) d.add(pr[j], VT(1));
           const double v = d.value(gm) * iov;
           if (gl == 0) ws.item_obs[(size_t)item * nl + k] = v;
+        }
+        {
+          // S^2: sum_r other_r (S^2 own)_r, S^2 applied to this unit's vector in shared memory
+          const int s2w = __ldg(M.blk_s2w + u.b), s2o = __ldg(M.blk_s2ell + u.b);
+          GroupDot<VT, G> d;
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const int r = gl + G * j;
+            if (r < u.dim) {
+              VT a = VT(__ldg(M.s2_diag + off + r)) * u.Q(0, r);
+              for (int k = 0; k < s2w; ++k) {
+                const unsigned e = __ldg(M.s2_ell + s2o + k * u.dim + r);
+                if (e != 0xFFFFu) a += (e & 0x8000u) ? -u.Q(0, e & 0x7fffu) : u.Q(0, e & 0x7fffu);
+              }
+              d.add(a, __ldcg(hvec + (size_t)oslot * vstride + r));
+            }
+          }
+          const double v = d.value(gm) * iov;
+          if (gl == 0) ws.item_obs[(size_t)item * nl + nl - 1] = v;
         }
         if (gl == 0) ws.item_blk[item] = u.b;
       }

@@ -190,7 +190,7 @@ __global__ void reduce_kernel(DevModel M, int n, int has_moves, const int8_t *cu
 __global__ void measure_reduce_kernel(DevModel M, int n, Workspace ws, double *obs) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= n) return;
-  const int nk = M.n_kept, nf = M.nf, no = M.n_orb, nl = nf + no;
+  const int nk = M.n_kept, nf = M.nf, no = M.n_orb, nl = nf + no + 1;
   const int nsec = (no + 1) * (no + 1), ntot = nl + nsec;
   double *out = obs + (size_t)w * ntot;
   double mx = -INFINITY;

@@ -350,6 +350,63 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
       }
     }
   }
+  // ---- S^2 per block (measurement at beta/2): diagonal S_z^2 + S_z + sum_a n_{a dn}(1 - n_{a up});
+  //      off-diagonal S-_a S+_b = psi+_{a dn} psi+_{b up} psi_{b dn} psi_{a up} (a != b), the
+  //      spin-flip string of H_loc with coefficient +1; it keeps the block ----
+  std::vector<float> s2_diag(N);
+  std::vector<std::vector<std::pair<int, int>>> s2rows(N);  // global row y: (column rank, sign)
+  for (uint32_t x = 0; x < (uint32_t)N; ++x) {
+    int nu = 0, nd = 0, flip_diag = 0;
+    for (int a = 0; a < n; ++a) {
+      const int u = (x >> (2 * a)) & 1, dn = (x >> (2 * a + 1)) & 1;
+      nu += u;
+      nd += dn;
+      flip_diag += dn * (1 - u);
+    }
+    const double sz = 0.5 * (nu - nd);
+    s2_diag[x] = (float)(sz * sz + sz + flip_diag);
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        if (a == b) continue;
+        const int seq[4][2] = {{2 * a, 0}, {2 * b + 1, 0}, {2 * b, 1}, {2 * a + 1, 1}};
+        uint32_t y = x;
+        int sg = 1;
+        bool ok = true;
+        for (int k = 0; k < 4 && ok; ++k) {
+          int s1;
+          ok = flip(y, seq[k][0], seq[k][1] != 0, y, s1);
+          sg *= s1;
+        }
+        if (ok) {
+          if (blk_of[y] != blk_of[x]) { delete M; return KT_EUNSUPPORTED; }
+          s2rows[y].push_back({rank_of[x], sg});
+        }
+      }
+  }
+  std::vector<int32_t> blk_s2w(B), blk_s2ell(B);
+  int n_s2 = 0;
+  for (int b = 0; b < B; ++b) {
+    int w = 0;
+    for (int r = 0; r < blk_dim[b]; ++r) w = std::max(w, (int)s2rows[members[b][r]].size());
+    blk_s2w[b] = w;
+    blk_s2ell[b] = n_s2;
+    n_s2 += w * blk_dim[b];
+  }
+  std::vector<uint16_t> s2_ell(std::max(n_s2, 1), (uint16_t)0xFFFF);
+  std::vector<float> s2_diag_blk(N);
+  for (int b = 0; b < B; ++b) {
+    const int d = blk_dim[b];
+    for (int r = 0; r < d; ++r) {
+      const uint32_t x = members[b][r];
+      s2_diag_blk[blk_off[b] + r] = s2_diag[x];
+      int k = 0;
+      for (auto &e : s2rows[x]) {
+        s2_ell[blk_s2ell[b] + k * d + r] = (uint16_t)(e.first | (e.second < 0 ? 0x8000 : 0));
+        ++k;
+      }
+    }
+  }
+
   // ---- c / c^+ block maps and partner table ----
   std::vector<int32_t> blk_target((size_t)B * nf * 2, -1);
   std::vector<uint16_t> partner((size_t)N * nf);
@@ -448,7 +505,9 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
                i_ecol = add(ell_col.data(), ell_col.size() * 2), i_ev64 = add(ell_val64.data(), ell_val64.size() * 8),
                i_ev32 = add(ell_val32.data(), ell_val32.size() * 4), i_part = add(partner.data(), partner.size() * 2),
                i_kb = add(kept_blk.data(), NK * 4), i_ke = add(kept_e.data(), NK * 8), i_ko = add(kept_off.data(), NK * 4),
-               i_kv64 = add(kept_vec64.data(), kept_vec64.size() * 8), i_kv32 = add(kept_vec32.data(), kept_vec32.size() * 4);
+               i_kv64 = add(kept_vec64.data(), kept_vec64.size() * 8), i_kv32 = add(kept_vec32.data(), kept_vec32.size() * 4),
+               i_s2d = add(s2_diag_blk.data(), N * 4), i_s2e = add(s2_ell.data(), s2_ell.size() * 2),
+               i_s2w = add(blk_s2w.data(), B * 4), i_s2o = add(blk_s2ell.data(), B * 4);
   void *dmem = nullptr;
   if (cudaMalloc(&dmem, total) != cudaSuccess) { cudaGetLastError(); delete M; return KT_ENOMEM; }
   std::vector<char> host(total, 0);
@@ -480,6 +539,8 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   D.partner = (const uint16_t *)at(i_part);
   D.kept_blk = (const int32_t *)at(i_kb); D.kept_e = (const double *)at(i_ke); D.kept_off = (const int32_t *)at(i_ko);
   D.kept_vec64 = (const double *)at(i_kv64); D.kept_vec32 = (const float *)at(i_kv32);
+  D.s2_diag = (const float *)at(i_s2d); D.s2_ell = (const uint16_t *)at(i_s2e);
+  D.blk_s2w = (const int32_t *)at(i_s2w); D.blk_s2ell = (const int32_t *)at(i_s2o);
   *out = M;
   return KT_OK;
 }
@@ -532,7 +593,7 @@ static kt_status run(kt_model *m, const kt_seq_batch *b, const kt_move_batch *mv
   if (!sign || !logv || !status || !b->offsets || !ws) return KT_EINVAL;
   if (mv && (!mv->kind || !mv->flavor || !mv->t_dag || !mv->t_ann || !mv->rem_idx || !cur_sign || !cur_logabs))
     return KT_EINVAL;
-  const int nobs_item = obs ? m->dev.nf + m->dev.n_orb : 0;
+  const int nobs_item = obs ? m->dev.nf + m->dev.n_orb + 1 : 0;
   if (ws_bytes < kt::workspace_bytes(b->n, m->dev.n_kept, m->dev.d_max, nobs_item)) return KT_ENOMEM;
   kt::SeqView sv{b->n, b->offsets, b->tau, b->flavor, b->dagger};
   kt::MoveView mvv{};
@@ -640,7 +701,7 @@ kt_status kt_trace(kt_model *m, const kt_seq_batch *b, int8_t *sign, double *log
 
 kt_status kt_measure_workspace_size(const kt_model *m, int32_t n, size_t *bytes) {
   if (!m || !bytes || n < 0) return KT_EINVAL;
-  *bytes = kt::workspace_bytes(n, m->dev.n_kept, m->dev.d_max, m->dev.nf + m->dev.n_orb);
+  *bytes = kt::workspace_bytes(n, m->dev.n_kept, m->dev.d_max, m->dev.nf + m->dev.n_orb + 1);
   return KT_OK;
 }
 

@@ -709,7 +709,7 @@ kt::SeqView seq_view(const kt_sweep *s) {
 // the trace pipeline on the current configurations, with the observables at beta/2 when obs != nullptr
 int current_traces(kt_sweep *s, int8_t *sg, double *lg, int32_t *st, double *obs, cudaStream_t stream) {
   const kt::DevModel &M = *s->mv.dev;
-  const kt::Workspace w = kt::carve_workspace(s->ws, s->v.nw, M.n_kept, M.d_max, obs ? M.nf + M.n_orb : 0);
+  const kt::Workspace w = kt::carve_workspace(s->ws, s->v.nw, M.n_kept, M.d_max, obs ? M.nf + M.n_orb + 1 : 0);
   return kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, seq_view(s), nullptr, nullptr,
                              nullptr, sg, lg, st, nullptr, w, stream, nullptr, obs);
 }
@@ -806,7 +806,7 @@ kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out)
   v.beta = mv.dev->beta;
   kt_status rc = carve_and_alloc(s);
   if (rc == KT_OK) {
-    s->ws_bytes = kt::workspace_bytes(v.nw, mv.dev->n_kept, mv.dev->d_max, nf + mv.dev->n_orb);
+    s->ws_bytes = kt::workspace_bytes(v.nw, mv.dev->n_kept, mv.dev->d_max, nf + mv.dev->n_orb + 1);
     if (cudaMalloc(&s->ws, s->ws_bytes) != cudaSuccess) {
       cudaGetLastError();
       s->ws = nullptr;

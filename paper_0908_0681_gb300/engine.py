@@ -104,9 +104,10 @@ def measure(model: kt.KtModel, seqs: DeviceSeqs, stats: torch.Tensor | None = No
 
 
 def measure_layout(n_orb: int) -> dict:
-    """Column slices of kt_measure's output: n_f, double occupancy, (n_up, n_dn) histogram."""
+    """Column slices of kt_measure's output: n_f, double occupancy, S^2, (n_up, n_dn) histogram."""
     nf = 2 * n_orb
-    return {"n": slice(0, nf), "docc": slice(nf, nf + n_orb), "sector": slice(nf + n_orb, nf + n_orb + (n_orb + 1) ** 2)}
+    return {"n": slice(0, nf), "docc": slice(nf, nf + n_orb), "S2": slice(nf + n_orb, nf + n_orb + 1),
+            "sector": slice(nf + n_orb + 1, nf + n_orb + 1 + (n_orb + 1) ** 2)}
 
 
 def trace_ratio(model: kt.KtModel, seqs: DeviceSeqs, cur_sign: torch.Tensor, cur_logabs: torch.Tensor,

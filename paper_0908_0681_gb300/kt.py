@@ -275,7 +275,7 @@ def kt_measure_workspace_size(m: KtModel, n: int) -> int:
 
 def measure_nobs(n_orb: int) -> int:
     """KT_MEASURE_NOBS: observables per walker returned by kt_measure."""
-    return 3 * n_orb + (n_orb + 1) ** 2
+    return 3 * n_orb + 1 + (n_orb + 1) ** 2
 
 
 def kt_measure(m: KtModel, batch: kt_seq_batch, sign, logabs, obs, status, stats=None, workspace=None,
