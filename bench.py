@@ -113,14 +113,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+ITEMS_SOURCES = ("kt_internal.h", "kt_device.cuh", "kt_items.cuh", "kt_items_f32.cu")
+
+
 def source_sha() -> str:
-    """Hash of every kernel and host source file (ties a committed ncu summary to the code)."""
+    """Hash of the sources the FP32 Krylov items kernel is compiled from (ties the committed
+    ncu traffic record of that kernel to its code)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_0908_0681_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in ITEMS_SOURCES:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -300,13 +303,15 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     del base
 
     out = {}
+    per_chain = {}
+    u_plain = uni(steps, 6)      # the FP32 and FP64 plain runs share their uniforms
     for name, model, mode, n_t in (("fp32", models["fp32"], "plain", steps), ("fp32_da", models["fp32"], "da", steps),
                                    ("fp64", models["fp64"], "plain", steps)):
         sw = engine.Sweep(model, table, beta, nw, k_cap=128, n_bins=200, measure_obs=True)
         sw.set_configs(thermal)
         if mode == "da":
             sw.set_surrogate(net)
-        u = uni(n_t, 7 if mode == "da" else 6)
+        u = uni(n_t, 7) if mode == "da" else u_plain
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -326,6 +331,9 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         order = acc["order_sum"].sum(1) / ssum
         gmid = (acc["g_tau"][:, :, 95:105].mean(2) * (200 / beta ** 2) / ssum[:, None]).mean(1)
         K = stt["lens"].double().mean().item()
+        per_chain[name] = {"docc": docc, "order": order, "G_beta_half": gmid,
+                           "n_f": obs[:, :2 * spec.n_orb].mean(1), "S2": obs[:, 3 * spec.n_orb],
+                           "lens": stt["lens"].cpu().numpy(), "tau": stt["tau"].cpu().numpy()}
         props = nw * n_t / (ms / 1000.0)
         secs = ms / 1000.0
         out[name] = {"proposals_per_s": props, "ms_per_step": ms / n_t, "steps": n_t,
@@ -337,9 +345,18 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
                      "mean_sign": float(ssum.sum() / (nw * cnt["measurements"])) if cnt["measurements"] else None,
                      "trace_errors": cnt["trace_errors"], "refused_at_k_cap": cnt["refused_at_k_cap"],
                      "docc": float(docc.mean()), "G_beta_half": float(gmid.mean()),
-                     "n_f": float(obs[:, :2 * spec.n_orb].mean()),
+                     "n_f": float(obs[:, :2 * spec.n_orb].mean()), "S2": float(obs[:, 3 * spec.n_orb].mean()),
                      "eff": {"docc": 1.0 / (docc.var(ddof=1) * secs), "order": 1.0 / (order.var(ddof=1) * secs),
                              "G_beta_half": 1.0 / (gmid.var(ddof=1) * secs)}}
+    # FP32 against FP64 on the same uniforms: chains whose final configurations agree took
+    # the same decisions all along, so their accumulators differ only by the trace arithmetic
+    a32, a64 = per_chain["fp32"], per_chain["fp64"]
+    same = np.array([a32["lens"][i] == a64["lens"][i] and
+                     np.array_equal(a32["tau"][i, :a32["lens"][i]], a64["tau"][i, :a64["lens"][i]]) for i in range(nw)])
+    err32 = {"chains_on_identical_paths": int(same.sum()), "chains": nw}
+    for k in ("docc", "order", "G_beta_half", "n_f", "S2"):
+        d = np.abs(a32[k][same] - a64[k][same])
+        err32[f"max_abs_diff_{k}"] = float(d.max()) if d.size else None
     speed = {f"{a}_over_{b}": {k: out[a]["eff"][k] / out[b]["eff"][k] for k in out[a]["eff"]}
              for a, b in (("fp32", "fp64"), ("fp32_da", "fp64"), ("fp32_da", "fp32"))}
     # throughput-bound batch: 8,192 chains (the 1,024-chain batch is bound by its longest chains)
@@ -384,7 +401,7 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
             "bath": "semicircular DOS, bandwidth 4, 2000 tau points", "thermalisation_steps": therm,
             "measure_every": meas, "fp32": out["fp32"], "fp32_da": out["fp32_da"], "fp64": out["fp64"],
             "speedup_fp32_over_fp64": out["fp32"]["proposals_per_s"] / out["fp64"]["proposals_per_s"],
-            "speedup_at_equal_error": speed, "throughput_8192_chains": thr,
+            "speedup_at_equal_error": speed, "throughput_8192_chains": thr, "fp32_vs_fp64_same_uniforms": err32,
             "surrogate": {"training_samples": int(X.shape[0]), "collect_s": t_collect, "train_s": t_train,
                           "epochs": len(hist), "loss_per_epoch": hist, "rms_residual_log_ratio": resid,
                           "target_std": spread, "network": "n_in-256-256-1 ReLU, BF16 tcgen05, FP32 accumulate"}}

@@ -157,3 +157,24 @@ def test_set_configs_restart_matches_oracle():
     with pytest.raises(kt.KtError):
         sw.set_configs(bad)
     assert all(len(c) == 0 for c in sw.configs())
+
+
+def test_seven_orbital_fp32_chain_weights():
+    """Seven orbitals (36-row kernel blocks, N_tr = 63): chains of FP32-Krylov trace ratios
+    with the semicircular bath of bandwidth 2 keep weights consistent with the oracle."""
+    w = workloads.seven_orbital()
+    spec = w.model
+    om, gm = model_pair(spec, kt.KT_FP32_KRYLOV)
+    nw, steps = 32, 200
+    table = workloads.semicircular_hybridization(spec.beta, 14, n_tau=2000, half_bandwidth=1.0)
+    sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=32, n_bins=10)
+    sw.run(torch.as_tensor(workloads.sweep_uniforms(steps, nw, seed=7), device="cuda"))
+    cnt = sw.counters()
+    assert cnt["trace_errors"] == 0 and cnt["insert_accepted"] > 0
+    st = {k: v.cpu().numpy() for k, v in sw.state().items()}
+    hyb = Hyb(table, spec.beta)
+    for i, ops in enumerate(sw.configs()):
+        s, lw, sT, lT = weight(om, hyb, ops)
+        assert s == st["sign"][i] and sT == st["trace_sign"][i], i
+        assert abs(math.expm1(st["trace_logabs"][i] - lT)) < 5e-5, i   # the FP32 ratio bound at seven orbitals
+        assert abs(st["det_logabs"][i] - (lw - lT)) < 1e-8, i
