@@ -60,6 +60,7 @@ struct SeqView {
   const uint8_t *flavor;
   const uint8_t *dagger;
   const int32_t *lens = nullptr;
+  bool trusted = false;  // sequences built by the library itself (the sweep): skip the O(K) validation
 };
 
 struct MoveView {

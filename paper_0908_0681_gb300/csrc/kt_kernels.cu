@@ -55,7 +55,7 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
   int4 d = make_int4(-1, 0, 0, K);
   if (K < 0) {
     st = KT_EINVAL;
-  } else {
+  } else if (!S.trusted) {
     double prev = 0.0;
     for (int k = 0; k < K; ++k) {
       const double t = S.tau[o + k];

@@ -703,6 +703,7 @@ kt_status carve_and_alloc(kt_sweep *s) {
 kt::SeqView seq_view(const kt_sweep *s) {
   kt::SeqView sv{s->v.nw, s->v.offsets, s->v.tau, s->v.flv, s->v.dag};
   sv.lens = s->v.lens;
+  sv.trusted = true;  // validated by kt_sweep_set_configs and edited only by the sweep's kernels
   return sv;
 }
 
