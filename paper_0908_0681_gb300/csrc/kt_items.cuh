@@ -99,6 +99,39 @@ __device__ __forceinline__ DF sqrt_df(DF v) {
 }
 __device__ __forceinline__ double df_value(const DF &v) { return (double)v.hi + (double)v.lo; }
 
+// Double-float arithmetic (Dekker / Knuth; about 44 significant bits), used on the FP32
+// path for the tridiagonal scalars so that no FP64 instruction sits in the interval loop.
+__device__ __forceinline__ DF df_norm(float hi, float lo) {  // fast two-sum, |hi| >= |lo|
+  DF r;
+  r.hi = hi + lo;
+  r.lo = lo - (r.hi - hi);
+  return r;
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df_norm(s, e + a.lo + b.lo);
+}
+__device__ __forceinline__ DF df_neg(DF a) {
+  a.hi = -a.hi;
+  a.lo = -a.lo;
+  return a;
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  return df_norm(p, fmaf(a.hi, b.hi, -p) + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+__device__ __forceinline__ DF df_mulf(DF a, float b) {
+  const float p = a.hi * b;
+  return df_norm(p, fmaf(a.hi, b, -p) + a.lo * b);
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = a.hi / b.hi;
+  const DF r = df_add(a, df_neg(df_mulf(b, q1)));
+  return df_norm(q1, r.hi / b.hi);
+}
+__device__ __forceinline__ bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
 // Group-reduced dot product with FP64 accuracy: double-float on the FP32 pipe
 // for FP32 vectors, FP64 FMA for FP64 vectors.
 template <typename VT, int G>
@@ -109,6 +142,14 @@ struct GroupDot<float, G> {
   __device__ __forceinline__ void add(float x, float y) { acc.add_prod(x, y); }
   __device__ __forceinline__ double value(unsigned gm) { return df_value(gsum_df<G>(acc, gm)); }
   __device__ __forceinline__ double norm(unsigned gm) { return df_value(sqrt_df(gsum_df<G>(acc, gm))); }
+  __device__ __forceinline__ DF value_df(unsigned gm) {
+    const DF v = gsum_df<G>(acc, gm);
+    return df_norm(v.hi, v.lo);
+  }
+  __device__ __forceinline__ DF norm_df(unsigned gm) {
+    const DF v = sqrt_df(gsum_df<G>(acc, gm));
+    return df_norm(v.hi, v.lo);
+  }
 };
 template <int G>
 struct GroupDot<double, G> {
@@ -273,19 +314,24 @@ template <typename VT, int G, int DMAX, int PMAX>
 __device__ __forceinline__ void tri_small_f32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p,
                                               double dt, double &logfac) {
   constexpr int IPW = 32 / G;
+  const float2 *af = reinterpret_cast<const float2 *>(s.a), *bf = reinterpret_cast<const float2 *>(s.b);
   float y0 = 1.f, y1 = 0.f;
   if (p == 1) {
-    logfac = -dt * s.a[grp];
+    logfac = -dt * ((double)af[grp].x + (double)af[grp].y);
   } else {
-    const double a = s.a[grp], c = s.a[IPW + grp], b = s.b[grp];
-    const double m = 0.5 * (a + c), h = 0.5 * (a - c);
-    const double r = sqrt(h * h + b * b);
-    logfac = -dt * (m - r);
-    const float x = (float)(2.0 * dt * r);  // dt (lambda_+ - lambda_-)
+    DF a, c, b;
+    a.hi = af[grp].x; a.lo = af[grp].y;
+    c.hi = af[IPW + grp].x; c.lo = af[IPW + grp].y;
+    b.hi = bf[grp].x; b.lo = bf[grp].y;
+    const DF m = df_mulf(df_add(a, c), 0.5f), h = df_mulf(df_add(a, df_neg(c)), 0.5f);
+    const DF r = sqrt_df(df_add(df_mul(h, h), df_mul(b, b)));
+    const DF lmin = df_add(m, df_neg(r));
+    logfac = -dt * ((double)lmin.hi + (double)lmin.lo);
+    const float x = 2.f * (float)dt * r.hi;  // dt (lambda_+ - lambda_-)
     const float E = expf(-x);
-    const float g = (x > 1e-3f) ? (1.f - E) / (float)(2.0 * r) : (float)dt * (1.f - 0.5f * x);
-    y0 = 0.5f * (1.f + E) - g * (float)h;
-    y1 = -g * (float)b;
+    const float g = (x > 1e-3f) ? (1.f - E) / (2.f * r.hi) : (float)dt * (1.f - 0.5f * x);
+    y0 = 0.5f * (1.f + E) - g * h.hi;
+    y1 = -g * b.hi;
   }
   if (gl == 0) {
     s.y32[grp] = y0;
@@ -356,8 +402,8 @@ template <typename VT, int G, int DMAX, int PMAX>
 __device__ void tri_check32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
                             float &ynorm, float &ylast) {
   constexpr int IPW = 32 / G;
-#define A_(k) s.a[(k) * IPW + grp]
-#define B_(k) s.b[(k) * IPW + grp]
+#define AF_(k) reinterpret_cast<float2 *>(s.a)[(k) * IPW + grp]
+#define BF_(k) reinterpret_cast<float2 *>(s.b)[(k) * IPW + grp]
 #define D_(k) s.d32[(k) * IPW + grp]
 #define E_(k) s.e32[(k) * IPW + grp]
 #define X_(k) s.x32[(k) * IPW + grp]
@@ -370,14 +416,14 @@ __device__ void tri_check32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
   }
   if (p == 2) {
     float y0, y1;
-    exp2x2((float)A_(0), (float)A_(1), (float)B_(0), (float)dt, y0, y1);
+    exp2x2(AF_(0).x, AF_(1).x, BF_(0).x, (float)dt, y0, y1);
     ynorm = sqrtf(y0 * y0 + y1 * y1);
     ylast = fabsf(y1);
     return;
   }
   for (int i = gl; i < p; i += G) {
-    D_(i) = (float)A_(i);
-    E_(i) = (i + 1 < p) ? (float)B_(i) : 0.f;
+    D_(i) = AF_(i).x;
+    E_(i) = (i + 1 < p) ? BF_(i).x : 0.f;
   }
   __syncwarp(gm);
   tri_eig<float, G, PMAX>(s.d32, s.e32, s.S32, grp, gl, gm, p);
@@ -395,8 +441,8 @@ __device__ void tri_check32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
   ynorm = sqrtf(gsum<G>(yn, gm));
   __syncwarp(gm);
   ylast = fabsf(Y_(p - 1));
-#undef A_
-#undef B_
+#undef AF_
+#undef BF_
 #undef D_
 #undef E_
 #undef X_
@@ -404,71 +450,93 @@ __device__ void tri_check32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
 #undef S_
 }
 
-// FP32-path final step (p >= 3): every Ritz value is recomputed in FP64 as the
-// Rayleigh quotient of its FP32 Ritz vector with the FP64 T_p (the error is
-// quadratic in the vector's, ~1e-14); lambda_min enters the log-weight in
-// FP64. The relative weights exp(-dt (lambda_k - lambda_min)) in (0, 1] and
-// y = sum_k s_k s_k[0] w_k / |s_k|^2 are formed in FP32 (one Ritz pair per
+// FP32-path final step (p >= 3): every Ritz value is recomputed in double-float
+// arithmetic (about 44 bits, on the FP32 pipe) as the Rayleigh quotient of its FP32 Ritz
+// vector with the double-float T_p (the error is quadratic in the vector's, ~1e-14);
+// lambda_min enters the log-weight. The relative weights exp(-dt (lambda_k - lambda_min))
+// in (0, 1] and y = sum_k s_k s_k[0] w_k / |s_k|^2 are formed in FP32 (one Ritz pair per
 // lane), the precision of the Krylov vectors they multiply. y lands in y32.
 template <typename VT, int G, int DMAX, int PMAX>
 __device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
                             double &logfac) {
   constexpr int IPW = 32 / G;
-#define A_(k) s.a[(k) * IPW + grp]
-#define B_(k) s.b[(k) * IPW + grp]
-#define D_(k) s.dd[(k) * IPW + grp]
+#define AF_(k) reinterpret_cast<const float2 *>(s.a)[(k) * IPW + grp]
+#define BF_(k) reinterpret_cast<const float2 *>(s.b)[(k) * IPW + grp]
+#define DF_(k) reinterpret_cast<float2 *>(s.dd)[(k) * IPW + grp]
 #define X_(k) s.x32[(k) * IPW + grp]
 #define Y_(k) s.y32[(k) * IPW + grp]
 #define S_(k, i) s.S32[((k) * PMAX + (i)) * IPW + grp]
-  // lane-local Ritz pair k: FP64 Rayleigh quotient
-  float lmin32 = INFINITY;
+  // lane-local Ritz pair k: double-float Rayleigh quotient
+  DF lmin;
+  lmin.hi = INFINITY;
   int kmin = 0;
   for (int k = gl; k < p; k += G) {
-    double num = 0.0, den = 0.0, sprev = 0.0, scur = (double)S_(k, 0);
+    DF num, den;
+    float sprev = 0.f, scur = S_(k, 0);
     for (int i = 0; i < p; ++i) {
-      const double snext = (i + 1 < p) ? (double)S_(k, i + 1) : 0.0;
-      double ti = A_(i) * scur;
-      if (i > 0) ti = fma(B_(i - 1), sprev, ti);
-      if (i + 1 < p) ti = fma(B_(i), snext, ti);
-      num = fma(scur, ti, num);
-      den = fma(scur, scur, den);
+      const float snext = (i + 1 < p) ? S_(k, i + 1) : 0.f;
+      DF a, ti;
+      a.hi = AF_(i).x;
+      a.lo = AF_(i).y;
+      ti = df_mulf(a, scur);
+      if (i > 0) {
+        DF b;
+        b.hi = BF_(i - 1).x;
+        b.lo = BF_(i - 1).y;
+        ti = df_add(ti, df_mulf(b, sprev));
+      }
+      if (i + 1 < p) {
+        DF b;
+        b.hi = BF_(i).x;
+        b.lo = BF_(i).y;
+        ti = df_add(ti, df_mulf(b, snext));
+      }
+      num = df_add(num, df_mulf(ti, scur));
+      den.add_prod(scur, scur);
       sprev = scur;
       scur = snext;
     }
-    const double r0 = (double)(1.f / (float)den);
-    const double inv = r0 * fma(-den, r0, 2.0);  // one Newton step: 1/den to ~1e-14
-    const double lam = num * inv;
-    D_(k) = lam;
-    X_(k) = (float)inv;
-    if ((float)lam < lmin32) {
-      lmin32 = (float)lam;
+    den = df_norm(den.hi, den.lo);
+    const DF lam = df_div(num, den);
+    DF_(k) = make_float2(lam.hi, lam.lo);
+    X_(k) = 1.f / den.hi;
+    if (df_lt(lam, lmin)) {
+      lmin = lam;
       kmin = k;
     }
   }
-  // smallest Ritz value: argmin in FP32, its FP64 value from the owning lane
+  // smallest Ritz value over the group
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) {
-    const float ol = __shfl_xor_sync(gm, lmin32, o);
+    DF ol;
+    ol.hi = __shfl_xor_sync(gm, lmin.hi, o);
+    ol.lo = __shfl_xor_sync(gm, lmin.lo, o);
     const int ok = __shfl_xor_sync(gm, kmin, o);
-    if (ol < lmin32 || (ol == lmin32 && ok < kmin)) {
-      lmin32 = ol;
+    if (df_lt(ol, lmin) || (ol.hi == lmin.hi && ol.lo == lmin.lo && ok < kmin)) {
+      lmin = ol;
       kmin = ok;
     }
   }
   __syncwarp(gm);
-  const double lmin = D_(kmin);
-  for (int k = gl; k < p; k += G) X_(k) = expf(-(float)(dt * (D_(k) - lmin))) * S_(k, 0) * X_(k);
+  const float dtf = (float)dt;
+  for (int k = gl; k < p; k += G) {
+    DF lk;
+    lk.hi = DF_(k).x;
+    lk.lo = DF_(k).y;
+    const DF diff = df_add(lk, df_neg(lmin));
+    X_(k) = expf(-dtf * diff.hi) * S_(k, 0) * X_(k);
+  }
   __syncwarp(gm);
   for (int i = gl; i < p; i += G) {
     float acc = 0.f;
     for (int k = 0; k < p; ++k) acc = fmaf(S_(k, i), X_(k), acc);
     Y_(i) = acc;
   }
-  logfac = -dt * lmin;
+  logfac = -dt * ((double)lmin.hi + (double)lmin.lo);
   __syncwarp(gm);
-#undef A_
-#undef B_
-#undef D_
+#undef AF_
+#undef BF_
+#undef DF_
 #undef X_
 #undef Y_
 #undef S_
@@ -558,6 +626,7 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
   const double brk = M.brk_rel * fmax(__ldg(M.blk_norm + b), 1e-300);
   const int pcap = min(dim, M.pmax);
   const float tol32 = F32 ? (float)(0.5 * M.tol) : 0.f;  // safety factor 2 on FP32 estimates
+  const float brk32 = F32 ? (float)brk : 0.f;
   VT qc[R], qp[R];
 #pragma unroll
   for (int j = 0; j < R; ++j) {
@@ -565,7 +634,8 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
     qc[j] = (r < dim) ? u.Q(0, r) : VT(0);
     qp[j] = VT(0);
   }
-  double bprev = 0.0, logfac = 0.0;
+  double logfac = 0.0;
+  VT bprev = VT(0);
   int p = 0;
   bool conv = false, exact = false;
   for (int jj = 0; jj < pcap; ++jj) {
@@ -585,8 +655,14 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
       }
       wv[j] = a;
     }
-    const double al = da.value(gm);
-    const VT alv = VT(al), bpv = VT(bprev);
+    double al = 0.0;
+    DF al_df;
+    if constexpr (F32) {
+      al_df = da.value_df(gm);
+    } else {
+      al = da.value(gm);
+    }
+    const VT alv = F32 ? VT(al_df.hi) : VT(al), bpv = bprev;
 #pragma unroll
     for (int j = 0; j < R; ++j)
       if (gl + G * j < dim) wv[j] = wv[j] - alv * qc[j] - bpv * qp[j];
@@ -611,14 +687,25 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
 #pragma unroll
     for (int j = 0; j < R; ++j)
       if (gl + G * j < dim) db.add(wv[j], wv[j]);
-    const double bb = db.norm(gm);
+    double bb = 0.0;
+    DF bb_df;
+    if constexpr (F32) {
+      bb_df = db.norm_df(gm);
+    } else {
+      bb = db.norm(gm);
+    }
     p = jj + 1;
     if (gl == 0) {
-      A_(jj) = al;
-      B_(jj) = bb;
+      if constexpr (F32) {  // double-float alpha, beta in the slots of the FP64 ones
+        reinterpret_cast<float2 *>(s.a)[jj * IPW + grp] = make_float2(al_df.hi, al_df.lo);
+        reinterpret_cast<float2 *>(s.b)[jj * IPW + grp] = make_float2(bb_df.hi, bb_df.lo);
+      } else {
+        A_(jj) = al;
+        B_(jj) = bb;
+      }
     }
     __syncwarp(gm);
-    exact = (p == dim) || !(bb > brk);
+    exact = (p == dim) || !(F32 ? (bb_df.hi > brk32) : (bb > brk));
     bool stop = exact;
     // a-posteriori checks at every p up to 4, then on a geometric schedule
     // (6, 8, 11, 15, 20, 27): each check costs an eigendecomposition of T_p
@@ -627,7 +714,7 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
       if constexpr (F32) {
         float yn, yl;
         tri_check32(s, grp, gl, gm, p, dt, yn, yl);
-        stop = (float)bb * yl <= tol32 * yn;
+        stop = bb_df.hi * yl <= tol32 * yn;
       } else {
         if (!tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
         double yn = 0.0;
@@ -641,7 +728,7 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
       break;
     }
     if (p == pcap) break;
-    const VT ib = VT(1) / VT(bb);
+    const VT ib = F32 ? VT(1) / VT(bb_df.hi) : VT(1) / VT(bb);
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int r = gl + G * j;
@@ -649,7 +736,7 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
       qc[j] = wv[j] * ib;
       if (r < dim) u.Q(jj + 1, r) = qc[j];
     }
-    bprev = bb;
+    bprev = F32 ? VT(bb_df.hi) : VT(bb);
     __syncwarp(gm);
   }
   if (!conv) {
@@ -664,6 +751,14 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
       if constexpr (DMAX > 16) {
         // blocks beyond 16 rows (seven orbitals) hold close Ritz pairs whose FP32
         // vectors would leak rotation errors into y: full FP64 eigensolve at the final p
+        // (alpha, beta first widened in place from double-float to FP64)
+        for (int k = gl; k < p; k += G) {
+          const float2 av = reinterpret_cast<float2 *>(s.a)[k * IPW + grp];
+          const float2 bv = reinterpret_cast<float2 *>(s.b)[k * IPW + grp];
+          A_(k) = (double)av.x + (double)av.y;
+          B_(k) = (double)bv.x + (double)bv.y;
+        }
+        __syncwarp(gm);
         if (!tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
         for (int k = gl; k < p; k += G) s.y32[k * IPW + grp] = (float)Y_(k);
         __syncwarp(gm);
