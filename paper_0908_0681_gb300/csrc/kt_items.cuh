@@ -196,28 +196,40 @@ __device__ __forceinline__ float pow2_inv(float m) {
 }
 __device__ __forceinline__ double pow2_inv(double m) { return scalbn(1.0, -ilogb(m)); }
 
-// Scale the item's rows v to unit norm: an exact power-of-two prescale brings
-// the largest entry to [1, 2), then rsqrt of the sum of squares; the factor
-// actually applied is multiplied into `applied`. False if all rows are zero.
+// Scale the item's rows v to unit norm and multiply the factor actually applied into
+// `applied`. Usually one group reduction of the sum of squares and an rsqrt; when that
+// sum is tiny or huge, an exact power-of-two prescale first brings the largest entry to
+// [1, 2). False if all rows are zero.
 template <typename VT, int G, int R>
 __device__ __forceinline__ bool normalize_rows(VT (&v)[R], int gl, int dim, unsigned gm, LogScale &applied) {
-  VT m = VT(0);
-#pragma unroll
-  for (int j = 0; j < R; ++j)
-    if (gl + G * j < dim) m = fmax(m, fabs(v[j]));
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(gm, m, o));
-  if (!(m > VT(0))) return false;
-  const VT s1 = pow2_inv(m);
+  constexpr VT lo = sizeof(VT) == 4 ? VT(1e-30) : VT(1e-290), hi = sizeof(VT) == 4 ? VT(1e30) : VT(1e290);
   VT n2 = VT(0);
 #pragma unroll
   for (int j = 0; j < R; ++j)
-    if (gl + G * j < dim) {
-      const VT t = v[j] * s1;
-      n2 += t * t;
-    }
+    if (gl + G * j < dim) n2 += v[j] * v[j];
   n2 = gsum<G>(n2, gm);
-  const VT sc = s1 * rsq(n2);
+  VT sc;
+  if (n2 > lo && n2 < hi) {
+    sc = rsq(n2);
+  } else {
+    VT m = VT(0);
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (gl + G * j < dim) m = fmax(m, fabs(v[j]));
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(gm, m, o));
+    if (!(m > VT(0))) return false;
+    const VT s1 = pow2_inv(m);
+    n2 = VT(0);
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (gl + G * j < dim) {
+        const VT t = v[j] * s1;
+        n2 += t * t;
+      }
+    n2 = gsum<G>(n2, gm);
+    sc = s1 * rsq(n2);
+  }
 #pragma unroll
   for (int j = 0; j < R; ++j) v[j] *= sc;
   applied.mul((double)sc);
