@@ -368,7 +368,7 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     def unib(n, k):
         return torch.rand((n, nbig, k), dtype=torch.float64, device=dev, generator=g)
 
-    big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200)
+    big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200, measure_obs=True)
     big.set_configs(cand_big.subset(okb))
     for _ in range(0, therm, 500):
         big.run(unib(500, 6))
@@ -376,25 +376,31 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     for mode in ("plain", "da"):
         if mode == "da":
             big.set_surrogate(net)
+        big.reset_accumulators()
         u = unib(nsteps_big, 7 if mode == "da" else 6)
-        c0 = big.counters()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         if mode == "da":
-            big.run_da(u)
+            big.run_da(u, meas_every=meas)
         else:
-            big.run(u)
+            big.run(u, meas_every=meas)
         e1.record()
         torch.cuda.synchronize()
         c1 = big.counters()
         ms = e0.elapsed_time(e1)
+        ab = {k: v.cpu().numpy() for k, v in big.accumulators().items()}
+        docc_b = (ab["obs_sum"] / ab["sign_sum"][:, None])[:, 2 * spec.n_orb: 3 * spec.n_orb].mean(1)
+        order_b = ab["order_sum"].sum(1) / ab["sign_sum"]
         thr[mode] = {"proposals_per_s": nbig * nsteps_big / (ms / 1000.0), "ms_per_step": ms / nsteps_big,
-                     "trace_evaluations_per_proposal": (c1["trace_evaluations"] - c0["trace_evaluations"]) / (nbig * nsteps_big),
-                     "acceptance": (c1["insert_accepted"] + c1["remove_accepted"] - c0["insert_accepted"]
-                                    - c0["remove_accepted"]) / (nbig * nsteps_big)}
+                     "trace_evaluations_per_proposal": c1["trace_evaluations"] / (nbig * nsteps_big),
+                     "acceptance": (c1["insert_accepted"] + c1["remove_accepted"]) / (nbig * nsteps_big),
+                     "eff": {"docc": 1.0 / (docc_b.var(ddof=1) * ms / 1000.0),
+                             "order": 1.0 / (order_b.var(ddof=1) * ms / 1000.0)}}
     thr.update(chains=nbig, steps=nsteps_big,
-               speedup_da_over_plain=thr["da"]["proposals_per_s"] / thr["plain"]["proposals_per_s"])
+               speedup_da_over_plain=thr["da"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
+               speedup_da_over_plain_at_equal_error={k: thr["da"]["eff"][k] / thr["plain"]["eff"][k]
+                                                     for k in ("docc", "order")})
     del big
     return {"workload": f"five_orbital_sweep_beta{beta:g}_1024_chains", "metric": "Metropolis proposals/s (all chains)",
             "sweep_definition": "one sweep = as many proposals per chain as the chain holds operators on average",
@@ -580,7 +586,7 @@ def main():
             "config": {"workload": f"{a.workload}_{n}_walkers", "n_orb": w.model.n_orb, "U": w.model.U,
                        "J": w.model.J, "beta": w.model.beta,
                        "walkers_per_gpu": n, "mean_ops_per_walker": float(seqs.offsets[-1]) / n,
-                       "krylov_tol": w.model.krylov_tol, "trunc_eps": w.model.trunc_eps, "precision": "fp32-krylov (fp64 tridiagonal exp, norms, log-weights)",
+                       "krylov_tol": w.model.krylov_tol, "trunc_eps": w.model.trunc_eps, "precision": "fp32-krylov (double-float tridiagonal scalars and norms, fp64 log-weights)",
                        "blocks": "(n_up, n_dn, singly-occupied mask)", "n_blocks": info["n_blocks"],
                        "d_max": info["d_max"], "n_kept": info["n_kept"], "group_lanes": tuned, "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}"},

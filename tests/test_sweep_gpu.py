@@ -178,3 +178,29 @@ def test_seven_orbital_fp32_chain_weights():
         assert s == st["sign"][i] and sT == st["trace_sign"][i], i
         assert abs(math.expm1(st["trace_logabs"][i] - lT)) < 5e-5, i   # the FP32 ratio bound at seven orbitals
         assert abs(st["det_logabs"][i] - (lw - lT)) < 1e-8, i
+
+
+def test_five_orbital_fp64_chain_matches_oracle_from_given_configs():
+    """The bench's model (five orbitals, beta 50, semicircular bath), chains started from
+    Poisson(6) configurations: the FP64 chain reaches the oracle chain's configurations."""
+    w = workloads.five_orbital()
+    spec = w.model
+    om, gm = model_pair(spec, kt.KT_FP64)
+    table = workloads.semicircular_hybridization(spec.beta, 10, n_tau=2000)
+    hyb = Hyb(table, spec.beta)
+    cand = workloads.generate_sequences(w, 64, seed=12)
+    keep = [i for i in range(cand.n) if weight(om, hyb, list(zip(*[a.tolist() for a in cand.walker(i)])))[0] != 0][:12]
+    seqs = cand.subset(keep)
+    init = [list(zip(*[a.tolist() for a in seqs.walker(i)])) for i in range(seqs.n)]
+    nw, steps = len(init), 60
+    u = workloads.sweep_uniforms(steps, nw, seed=13)
+    sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=64, n_bins=10)
+    sw.set_configs(seqs)
+    sw.run(torch.as_tensor(u, device="cuda"))
+    ref = chain(om, hyb, init, u, k_cap=64)
+    assert sw.configs() == ref["configs"]
+    st = {k: v.cpu().numpy() for k, v in sw.state().items()}
+    assert (st["sign"] == ref["sign"]).all()
+    assert np.abs(st["trace_logabs"] - ref["trace_log"]).max() < 1e-8
+    assert np.abs(st["det_logabs"] - (ref["logw"] - ref["trace_log"])).max() < 1e-8
+    assert int((ref["accepted"] == 1).sum()) > 50
