@@ -60,6 +60,8 @@ def args_():
     p.add_argument("--sweep-beta", type=float, default=50.0)
     p.add_argument("--workload", choices=["five_orbital", "seven_orbital"], default="five_orbital",
                    help="five_orbital (4,096 walkers, the headline) or seven_orbital (256 walkers)")
+    p.add_argument("--trunc-eps", type=float, default=None,
+                   help="truncation threshold of the outer trace (default: the workload's, 1e-10)")
     return p.parse_args()
 
 
@@ -116,6 +118,12 @@ class ClockSampler:
 ITEMS_SOURCES = ("kt_internal.h", "kt_device.cuh", "kt_items.cuh", "kt_items_f32.cu")
 
 
+def trim_hist(h):
+    """Krylov-dimension histogram {p: propagations} without the empty bins (the last bin
+    counts every p at or above it)."""
+    return {str(p) if p < len(h) - 1 else f">={p}": c for p, c in enumerate(h) if c}
+
+
 def source_sha() -> str:
     """Hash of the sources the FP32 Krylov items kernel is compiled from (ties the committed
     ncu traffic record of that kernel to its code)."""
@@ -157,9 +165,9 @@ def aggregate(times_ms, n_per_rank: int, steps: int, world: int, reduce_max=None
     return world * n_per_rank * steps / (t[0] / 1000.0), t
 
 
-def make_workload(rank: int, rounds: int, name: str = "five_orbital"):
+def make_workload(rank: int, rounds: int, name: str = "five_orbital", trunc_eps: float | None = None):
     from paper_0908_0681_gb300 import workloads
-    w = workloads.WORKLOADS[name]()
+    w = workloads.WORKLOADS[name]() if trunc_eps is None else workloads.WORKLOADS[name](trunc_eps=trunc_eps)
     seq_seed, move_seeds = rank_seeds(rank, rounds)
     seqs = workloads.generate_sequences(w, WALKERS[name], seed=seq_seed)
     moves = [workloads.generate_moves(w, seqs, seed=sd) for sd in move_seeds]
@@ -208,7 +216,7 @@ def reference_arm(a):
     import numpy as np
     from oracle.oracle import Model, Params, SeqBatch, ratio
 
-    w, seqs, moves = make_workload(0, min(N_ROUNDS, a.warmup + a.steps), a.workload)
+    w, seqs, moves = make_workload(0, min(N_ROUNDS, a.warmup + a.steps), a.workload, a.trunc_eps)
     spec = w.model
     P = Params(spec.n_orb, spec.U, spec.J, Up=spec.up, mu=spec.mu, delta=spec.delta, beta=spec.beta,
                trunc_eps=spec.trunc_eps, deg_tol=spec.deg_tol)
@@ -304,6 +312,8 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
 
     out = {}
     per_chain = {}
+    steps = max(meas, steps - steps % meas)   # whole measurement blocks
+    n_blocks = steps // meas
     u_plain = uni(steps, 6)      # the FP32 and FP64 plain runs share their uniforms
     for name, model, mode, n_t in (("fp32", models["fp32"], "plain", steps), ("fp32_da", models["fp32"], "da", steps),
                                    ("fp64", models["fp64"], "plain", steps)):
@@ -315,14 +325,24 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        if mode == "da":
-            sw.run_da(u, meas_every=meas)
-        else:
-            sw.run(u, meas_every=meas)
+        blocks = sw.run_blocks(u, meas, n_blocks, delayed=(mode == "da"))
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         cnt = sw.counters()
+        # error bars: binning analysis over the measurement blocks of every chain
+        series = {"docc": [], "order": [], "G_beta_half": []}
+        for blk in blocks:
+            bs = blk["sign_sum"].cpu().numpy()
+            series["docc"].append((blk["obs_sum"].cpu().numpy()[:, 2 * spec.n_orb: 3 * spec.n_orb].mean(1)) / bs)
+            series["order"].append(blk["order_sum"].cpu().numpy().sum(1) / bs)
+            series["G_beta_half"].append((blk["g_tau"].cpu().numpy()[:, :, 95:105].mean(2) * (200 / beta ** 2)).mean(1) / bs)
+        binning = {}
+        for k, v in series.items():
+            b = engine.binning_analysis(np.stack(v, axis=1))
+            binning[k] = {"mean": float(np.mean(v)), "error": b["error"], "tau_int_measurements": b["tau_int"],
+                          "errors_by_bin_size": {str(sz): e for sz, e in b["errors"].items()}}
+        del blocks
         stt = sw.state()
         acc = {k: v.cpu().numpy() for k, v in sw.accumulators().items()}
         ssum = acc["sign_sum"]
@@ -347,7 +367,8 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
                      "docc": float(docc.mean()), "G_beta_half": float(gmid.mean()),
                      "n_f": float(obs[:, :2 * spec.n_orb].mean()), "S2": float(obs[:, 3 * spec.n_orb].mean()),
                      "eff": {"docc": 1.0 / (docc.var(ddof=1) * secs), "order": 1.0 / (order.var(ddof=1) * secs),
-                             "G_beta_half": 1.0 / (gmid.var(ddof=1) * secs)}}
+                             "G_beta_half": 1.0 / (gmid.var(ddof=1) * secs)},
+                     "error_bars_binning": binning}
     # FP32 against FP64 on the same uniforms: chains whose final configurations agree took
     # the same decisions all along, so their accumulators differ only by the trace arithmetic
     a32, a64 = per_chain["fp32"], per_chain["fp64"]
@@ -435,7 +456,7 @@ def main():
             torch.distributed.barrier()
 
     n_rounds = min(N_ROUNDS, a.warmup + a.steps)
-    w, seqs, moves = make_workload(rank, n_rounds, a.workload)
+    w, seqs, moves = make_workload(rank, n_rounds, a.workload, a.trunc_eps)
     dseq = engine.DeviceSeqs.from_host(seqs, dev)
     dmoves = [engine.DeviceMoves.from_host(m, dev) for m in moves]
     m32 = engine.model_from_spec(w.model, precision=kt.KT_FP32_KRYLOV)
@@ -499,10 +520,18 @@ def main():
 
     # algorithmic work of the timed FP32 steps (untimed stats pass over the same rounds)
     stats = engine.new_stats(dev)
+    nonzero = torch.zeros((), dtype=torch.int64, device=dev)
     for k in range(a.steps):
         step(m32, cur32, a.warmup + k, stats)
+        nonzero += (out_s != 0).sum()
     torch.cuda.synchronize()
     st = kt.stats_from_tensor(stats)
+    nonzero_frac = float(nonzero.item()) / (n * a.steps)
+    stats64 = engine.new_stats(dev)
+    for k in range(K64):
+        step(m64, cur64, a.warmup + k, stats64)
+    torch.cuda.synchronize()
+    st64 = kt.stats_from_tensor(stats64)
 
     # end to end through the C ABI from pinned host buffers
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
@@ -583,7 +612,7 @@ def main():
             "metric": METRIC if a.workload == "five_orbital" else METRIC_7, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": tot32 / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{a.workload}_{n}_walkers", "n_orb": w.model.n_orb, "U": w.model.U,
+            "config": {"workload": f"{a.workload}_{n}_walkers" + ("" if a.trunc_eps is None else f"_trunc{a.trunc_eps:g}"), "n_orb": w.model.n_orb, "U": w.model.U,
                        "J": w.model.J, "beta": w.model.beta,
                        "walkers_per_gpu": n, "mean_ops_per_walker": float(seqs.offsets[-1]) / n,
                        "krylov_tol": w.model.krylov_tol, "trunc_eps": w.model.trunc_eps, "precision": "fp32-krylov (double-float tridiagonal scalars and norms, fp64 log-weights)",
@@ -595,7 +624,11 @@ def main():
                          "speedup_fp32_over_fp64": value / value64},
             "work": {"items_alive_per_step": st["items_alive"] / a.steps, "intervals_per_step": st["intervals"] / a.steps,
                      "mean_krylov_dim": st["krylov_iters"] / max(st["intervals"], 1), "p_max": st["p_max"],
-                     "noconv": st["noconv"], "flops_vec_per_step": f32_per_launch},
+                     "noconv": st["noconv"], "flops_vec_per_step": f32_per_launch,
+                     "nonzero_fraction": nonzero_frac,
+                     "value_over_nonzero_proposals": value * nonzero_frac,
+                     "p_hist_fp32": trim_hist(st["p_hist"]), "p_hist_fp64": trim_hist(st64["p_hist"]),
+                     "mean_krylov_dim_fp64": st64["krylov_iters"] / max(st64["intervals"], 1)},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

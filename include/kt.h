@@ -62,8 +62,8 @@ typedef enum {
 
 /* precision */
 #define KT_FP64 0         /* FP64 Krylov vectors and scalars (plain FP64 path) */
-#define KT_FP32_KRYLOV 1  /* FP32 SpMV and Krylov vectors; FP64 tridiagonal exponential,
-                             Lanczos norms and log-weights */
+#define KT_FP32_KRYLOV 1  /* FP32 SpMV and Krylov vectors; FP64-accurate (double-float)
+                             Lanczos scalars, norms and Ritz values; FP64 log-weights */
 
 /* flags */
 #define KT_DENSITY_ONLY 1u   /* drop spin-flip and pair-hopping (density-density H_loc) */
@@ -108,6 +108,8 @@ typedef struct {
   size_t device_bytes;  /* device memory held by the model's tables */
 } kt_model_info;
 
+#define KT_P_HIST 32
+
 /* Per-call counters, accumulated on the device with atomics into a caller-owned
  * DEVICE struct (zero it before the call; pass NULL to skip counting). */
 typedef struct {
@@ -123,6 +125,8 @@ typedef struct {
   unsigned long long flops_vec;      /* algorithmic vector flops (SpMV, dots, axpys, assembly) */
   unsigned long long flops_tri;      /* FP64 flops of the small tridiagonal exponentials */
   unsigned long long bytes_apply;    /* bytes moved by c / c^+ gathers */
+  unsigned long long p_hist[KT_P_HIST]; /* propagations by stopping Krylov dimension p:
+                                            bin p for p < KT_P_HIST - 1, the last bin p >= KT_P_HIST - 1 */
 } kt_stats;
 
 /* CSR batch of operator sequences (Eq. (weight_strong): the time-ordered

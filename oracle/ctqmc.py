@@ -131,15 +131,20 @@ def bath_weight(hyb: Hyb, ops, nf: int):
     return sgn, lw
 
 
-def weight(model: Model, hyb: Hyb, ops):
-    """(sign, log|w|, sign_T, log|T|) of a configuration; sign 0 when w = 0."""
+def weight(model: Model, hyb: Hyb, ops, trace=None):
+    """(sign, log|w|, sign_T, log|T|) of a configuration; sign 0 when w = 0. `trace`, when
+    given, is a callable ops -> (sign, log|T|) that replaces model.trace (the segment
+    picture of oracle/segment.py for the density-density model)."""
     nf = 2 * model.p.n_orb
     for f in range(nf):
         cre, ann = flavor_times(ops, f)
         if len(cre) != len(ann):
             return 0, -math.inf, 0, -math.inf
-    sT, lT, _ = model.trace(SeqBatch.from_lists([ops]))
-    sT, lT = int(sT[0]), float(lT[0])
+    if trace is None:
+        sT, lT, _ = model.trace(SeqBatch.from_lists([ops]))
+        sT, lT = int(sT[0]), float(lT[0])
+    else:
+        sT, lT = trace(ops)
     if sT == 0:
         return 0, -math.inf, 0, -math.inf
     sgn, logw = sT * permutation_sign(ops, nf), lT
@@ -213,10 +218,11 @@ def propose(ops, u, nf, beta, k_cap):
 
 
 def chain(model: Model, hyb: Hyb, init, uniforms: np.ndarray, k_cap: int = 64, n_bins: int = 50,
-          meas_every: int = 0, observables: bool = False, surrogate=None):
+          meas_every: int = 0, observables: bool = False, surrogate=None, trace=None):
     """Run every walker's chain with the given uniforms [n_steps, n_walkers, 6] (7 with a
     surrogate: a callable (ops, kind, flavor, t_first, t_second, seg) -> predicted
-    log|T_new / T_old|, used for delayed acceptance).
+    log|T_new / T_old|, used for delayed acceptance). `trace` replaces model.trace in every
+    weight (see weight()).
 
     Returns a dict: accepted [n_steps, n_walkers] (1 accepted, 0 rejected, -1 null,
     -2 rejected at stage 1),
@@ -228,7 +234,7 @@ def chain(model: Model, hyb: Hyb, init, uniforms: np.ndarray, k_cap: int = 64, n
     nf = 2 * model.p.n_orb
     n_steps, nw, _ = uniforms.shape
     configs = [list(c) for c in init]
-    cur = [weight(model, hyb, c) for c in configs]
+    cur = [weight(model, hyb, c, trace) for c in configs]
     acc = np.zeros((n_steps, nw), dtype=np.int8)
     g_acc = np.zeros((nw, nf, n_bins))
     sign_sum = np.zeros(nw)
@@ -255,7 +261,7 @@ def chain(model: Model, hyb: Hyb, init, uniforms: np.ndarray, k_cap: int = 64, n
                     acc[step, w] = -2
                     continue
                 lstage1 = rt + bl_new - bl_old + lp
-            nw_ = weight(model, hyb, new)
+            nw_ = weight(model, hyb, new, trace)
             if nw_[0] == 0:
                 continue
             lr = nw_[1] - cur[w][1] + lp - lstage1

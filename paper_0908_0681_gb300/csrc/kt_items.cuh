@@ -620,7 +620,8 @@ __device__ bool apply_op(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, int f, i
 // a-posteriori stop; the scalars taken out go to the log-weight.
 // False if the propagated vector is exactly zero.
 template <typename VT, int G, int DMAX, int PMAX>
-__device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double dt, bool with_stats) {
+__device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double dt, kt_stats *stats) {
+  const bool with_stats = stats != nullptr;
   constexpr bool F32 = sizeof(VT) == 4;
   constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
   constexpr int IPW = 32 / G;
@@ -813,6 +814,7 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
   u.acc.iters += p;
   u.acc.pmax = u.acc.pmax > (unsigned long long)p ? u.acc.pmax : (unsigned long long)p;
   if (with_stats) {
+    if (gl == 0) atomicAdd(&stats->p_hist[p < KT_P_HIST - 1 ? p : KT_P_HIST - 1], 1ull);
     u.acc.flops_tri += (p <= 2) ? 30ull : (unsigned long long)(12 * p * p * p + 40 * p);
     int cnt = 0;
 #pragma unroll
@@ -918,7 +920,7 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
         const double tn = last ? t_s : nx.t;
         const double dt = half == 0 ? tn - op.t : op.t - tn;
         if (!last) op = nx;
-        if (dt > 0.0 && !propagate(M, u, dt, stats != nullptr)) {
+        if (dt > 0.0 && !propagate(M, u, dt, stats)) {
           vanished = true;
           break;
         }

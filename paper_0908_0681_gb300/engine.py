@@ -69,7 +69,7 @@ def model_from_spec(spec, precision=kt.KT_FP32_KRYLOV, flags=0, krylov_pmax=0, t
 
 
 def new_stats(device="cuda") -> torch.Tensor:
-    return torch.zeros(len(kt.STATS_FIELDS), dtype=torch.int64, device=device)
+    return torch.zeros(kt.STATS_WORDS, dtype=torch.int64, device=device)
 
 
 def workspace(model: kt.KtModel, n: int, device="cuda") -> torch.Tensor:
@@ -121,6 +121,36 @@ def trace_ratio(model: kt.KtModel, seqs: DeviceSeqs, cur_sign: torch.Tensor, cur
     ws = workspace(model, n, dev) if ws is None else ws
     kt.kt_trace_ratio(model, seqs.batch(), cur_sign, cur_logabs, moves.batch(), sign, lr, st, stats, ws)
     return sign, lr, st
+
+
+def binning_analysis(x) -> dict:
+    """Standard error of the mean of correlated measurements by binning.
+
+    x: [n_chains, n_t] series (or [n_t] for one chain), consecutive in Monte Carlo time.
+    For every bin size b dividing n_t the series is cut into bins of b consecutive values,
+    and the error of the grand mean is sqrt(var(bin means) / number of bins), pooled over
+    the independent chains. For uncorrelated data every b gives the same error; with
+    autocorrelation the error grows with b until the bins are longer than the
+    autocorrelation time, where it levels off (the plateau is the error bar). Returns
+    {"errors": {b: error}, "error": the error at the largest b with at least 8 bins per
+    chain (or 2 bins in all), "tau_int": half the squared ratio of that error to the b = 1
+    error (the integrated autocorrelation time, in measurements)}."""
+    x = np.asarray(x, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[None, :]
+    nc, nt = x.shape
+    errs = {}
+    for b in range(1, nt + 1):
+        if nt % b:
+            continue
+        y = x.reshape(nc, nt // b, b).mean(axis=2).ravel()
+        if y.size < 2:
+            continue
+        errs[b] = float(np.sqrt(y.var(ddof=1) / y.size))
+    ok = [b for b in errs if nt // b >= 8] or list(errs)
+    bmax = max(ok)
+    e1 = errs[min(errs)]
+    return {"errors": errs, "error": errs[bmax], "tau_int": 0.5 * (errs[bmax] / e1) ** 2 if e1 > 0 else 0.5}
 
 
 class Sweep:
@@ -208,6 +238,21 @@ class Sweep:
 
     def reset_accumulators(self) -> None:
         kt.kt_sweep_reset_accumulators(self.h)
+
+    def run_blocks(self, uniforms: torch.Tensor, meas_every: int, n_blocks: int, delayed: bool = False) -> list:
+        """Run the steps as n_blocks consecutive equal blocks (plain, or delayed acceptance
+        with 7 uniforms per step) and return each block's own accumulator sums (device
+        tensors), for binning analyses over time. The running accumulators and counters
+        keep their totals; the per-block sums are differences of device snapshots, so no
+        block waits for the host."""
+        n = uniforms.shape[0]
+        assert n_blocks > 0 and n % n_blocks == 0 and meas_every > 0 and (n // n_blocks) % meas_every == 0
+        step = n // n_blocks
+        snaps = [self.accumulators()]
+        for b in range(n_blocks):
+            (self.run_da if delayed else self.run)(uniforms[b * step:(b + 1) * step], meas_every)
+            snaps.append(self.accumulators())
+        return [{k: snaps[b + 1][k] - snaps[b][k] for k in snaps[0]} for b in range(n_blocks)]
 
     def green_function(self, acc: dict | None = None) -> torch.Tensor:
         """G_f(tau) at the bin centres, pooled over walkers: [n_flavors, n_bins]."""

@@ -41,8 +41,12 @@ STATS_FIELDS = ["walkers", "items", "items_alive", "items_vanished", "ops_applie
                 "p_max", "noconv", "flops_vec", "flops_tri", "bytes_apply"]
 
 
+KT_P_HIST = 32
+STATS_WORDS = len(STATS_FIELDS) + KT_P_HIST
+
+
 class kt_stats(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_ulonglong) for f in STATS_FIELDS]
+    _fields_ = [(f, ctypes.c_ulonglong) for f in STATS_FIELDS] + [("p_hist", ctypes.c_ulonglong * KT_P_HIST)]
 
 
 class kt_sweep_params(ctypes.Structure):
@@ -465,6 +469,9 @@ def kt_trace_ratio_static(m: KtModel, cur: kt_seq_batch, cur_sign, cur_logabs, m
 
 
 def stats_from_tensor(t) -> dict:
-    """Decode a kt_stats held in a uint64 tensor of len(STATS_FIELDS)."""
+    """Decode a kt_stats held in a uint64 tensor of STATS_WORDS words. `p_hist` is the list of
+    propagations by stopping Krylov dimension p (index p; the last entry counts p >= KT_P_HIST - 1)."""
     v = t.cpu().numpy().astype(np.uint64)
-    return {f: int(v[i]) for i, f in enumerate(STATS_FIELDS)}
+    d = {f: int(v[i]) for i, f in enumerate(STATS_FIELDS)}
+    d["p_hist"] = [int(x) for x in v[len(STATS_FIELDS):STATS_WORDS]]
+    return d

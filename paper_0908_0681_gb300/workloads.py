@@ -65,16 +65,18 @@ class Workload:
     extra: dict = field(default_factory=dict)
 
 
-def three_orbital() -> Workload:
+def three_orbital(trunc_eps: float = 1e-10) -> Workload:
     U, J = 4.0, 1.0
-    return Workload("three_orbital", ModelSpec(3, U, J, mu=2.5 * U - 5 * J, delta=(0.0,) * 3, beta=10.0),
+    return Workload("three_orbital", ModelSpec(3, U, J, mu=2.5 * U - 5 * J, delta=(0.0,) * 3, beta=10.0,
+                                               trunc_eps=trunc_eps),
                     start="coin", order="uniform8")
 
 
-def five_orbital() -> Workload:
+def five_orbital(trunc_eps: float = 1e-10) -> Workload:
     U, J = 4.0, 1.0
     delta = tuple(np.random.default_rng(2).uniform(-0.05, 0.05, 5).tolist())
-    return Workload("five_orbital", ModelSpec(5, U, J, mu=4.5 * U - 10 * J, delta=delta, beta=50.0),
+    return Workload("five_orbital", ModelSpec(5, U, J, mu=4.5 * U - 10 * J, delta=delta, beta=50.0,
+                                              trunc_eps=trunc_eps),
                     start="pattern", order="poisson", lam=6.0, pattern_singles=5)
 
 

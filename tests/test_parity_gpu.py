@@ -303,3 +303,26 @@ def test_seven_orbital_traces_and_ratios(seven, prec):
     idx = np.nonzero(reg)[0]
     parity.compare(ncls[idx], nsx[idx] * cur_s[idx], nlx[idx] - lx[idx], rs[idx], rl[idx], prec, ox.nkept,
                    w.model.beta * ox.E0 + lx[idx], "7-orbital ratios")
+
+
+def test_seven_orbital_energy_window_1e4():
+    """The seven-orbital model with the wider truncation threshold trunc_eps = 1e-4 (Sec. IV.C's
+    energy window): fewer kept multiplets, the same parity bar for traces and ratios."""
+    w = workloads.seven_orbital(trunc_eps=1e-4)
+    seqs = workloads.generate_sequences(w, 48, seed=2)
+    o64, ox = parity.oracle_pair(w.model)
+    cls, sx, lx = parity.oracle_traces(o64, ox, seqs)
+    m = engine.model_from_spec(w.model, precision=kt.KT_FP32_KRYLOV)
+    info = kt.kt_model_query(m)
+    assert info["n_kept"] == ox.nkept < 63
+    s, l, st = gpu_trace(m, seqs)
+    assert (st == kt.KT_OK).all(), np.unique(st, return_counts=True)
+    parity.compare(cls, sx, lx, s, l, kt.KT_FP32_KRYLOV, ox.nkept, w.model.beta * ox.E0, "7-orbital 1e-4 traces")
+    moves = workloads.generate_moves(w, seqs, seed=1001)
+    cur_s = np.where(cls == 2, sx, 0).astype(np.int8)
+    ncls, nsx, nlx = parity.oracle_ratios(o64, ox, seqs, cur_s, lx, moves)
+    rs, rl, rst = gpu_ratio(m, seqs, cur_s, lx, moves)
+    idx = np.nonzero(cls == 2)[0]
+    assert (rst[idx] == kt.KT_OK).all()
+    parity.compare(ncls[idx], nsx[idx] * cur_s[idx], nlx[idx] - lx[idx], rs[idx], rl[idx], kt.KT_FP32_KRYLOV,
+                   ox.nkept, w.model.beta * ox.E0 + lx[idx], "7-orbital 1e-4 ratios")

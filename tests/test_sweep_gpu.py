@@ -204,3 +204,62 @@ def test_five_orbital_fp64_chain_matches_oracle_from_given_configs():
     assert np.abs(st["trace_logabs"] - ref["trace_log"]).max() < 1e-8
     assert np.abs(st["det_logabs"] - (ref["logw"] - ref["trace_log"])).max() < 1e-8
     assert int((ref["accepted"] == 1).sum()) > 50
+
+
+def test_density_only_chain_matches_segment_picture():
+    """Density-density H_loc (KT_DENSITY_ONLY): the GPU chain (Krylov traces) against an
+    oracle chain whose traces come from the segment picture (segment lengths and
+    overlaps, oracle/segment.py), on the same uniforms: the same decisions and final
+    configurations, the same trace and determinant weights."""
+    from oracle.segment import SegmentTrace
+    w = workloads.three_orbital()
+    spec = w.model
+    nw, steps = 16, 400
+    P = Params(spec.n_orb, spec.U, spec.J, Up=spec.up, mu=spec.mu, delta=spec.delta, beta=spec.beta,
+               trunc_eps=spec.trunc_eps, deg_tol=spec.deg_tol, density_only=True)
+    om = Model(P)
+    seg = SegmentTrace(spec.n_orb, spec.U, spec.J, spec.mu, spec.delta, spec.beta, Up=spec.up,
+                       trunc_eps=spec.trunc_eps, deg_tol=spec.deg_tol)
+    gm = engine.model_from_spec(spec, precision=kt.KT_FP64, flags=kt.KT_DENSITY_ONLY)
+    assert kt.kt_model_query(gm)["n_kept"] == seg.n_kept
+    table = workloads.semicircular_hybridization(spec.beta, 6, n_tau=2000)
+    u = workloads.sweep_uniforms(steps, nw, seed=23)
+    sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=32, n_bins=20, measure_obs=False)
+    sw.run(torch.as_tensor(u, device="cuda"), meas_every=8)
+    ref = chain(om, Hyb(table, spec.beta), [[] for _ in range(nw)], u, k_cap=32, n_bins=20, meas_every=8,
+                trace=seg)
+    cnt = sw.counters()
+    assert cnt["trace_errors"] == 0
+    assert cnt["insert_accepted"] + cnt["remove_accepted"] == int((ref["accepted"] == 1).sum()) > 100
+    cfg = sw.configs()
+    for i in range(nw):
+        assert cfg[i] == ref["configs"][i], i
+    st = {k: v.cpu().numpy() for k, v in sw.state().items()}
+    assert (st["sign"] == ref["sign"]).all() and (st["trace_sign"] == ref["trace_sign"]).all()
+    assert np.abs(st["trace_logabs"] - ref["trace_log"]).max() < 1e-9
+    assert np.abs(st["det_logabs"] - (ref["logw"] - ref["trace_log"])).max() < 1e-8
+    a = {k: v.cpu().numpy() for k, v in sw.accumulators().items()}
+    assert np.allclose(a["order_sum"], ref["order_sum"])
+    assert np.abs(a["g_tau"] - ref["g_acc"]).max() <= 1e-9 * max(1.0, np.abs(ref["g_acc"]).max())
+
+
+def test_run_blocks_partition_the_accumulators():
+    """run_blocks: the per-block sums add up to the running accumulators, the counters keep
+    their totals, and the blocks feed a binning analysis of the double occupancy."""
+    w = workloads.three_orbital()
+    spec = w.model
+    gm = engine.model_from_spec(spec, precision=kt.KT_FP32_KRYLOV)
+    nw, steps, meas, nb = 64, 400, 10, 8
+    table = workloads.semicircular_hybridization(spec.beta, 6, n_tau=2000)
+    sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=64, n_bins=20, measure_obs=True)
+    u = torch.as_tensor(workloads.sweep_uniforms(steps, nw, seed=41), device="cuda")
+    blocks = sw.run_blocks(u, meas, nb)
+    tot = sw.accumulators()
+    for k in tot:
+        s = sum(b[k] for b in blocks)
+        assert torch.allclose(s, tot[k], rtol=1e-12, atol=1e-9), k
+    cnt = sw.counters()
+    assert cnt["measurements"] == steps // meas and cnt["insert_proposed"] + cnt["remove_proposed"] == nw * steps
+    docc = np.stack([(b["obs_sum"][:, 6:9].mean(1) / b["sign_sum"]).cpu().numpy() for b in blocks], axis=1)
+    r = engine.binning_analysis(docc)
+    assert np.isfinite(r["error"]) and r["error"] > 0 and set(r["errors"]) >= {1, 2, 4}
