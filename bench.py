@@ -247,6 +247,9 @@ def reference_arm(a):
     print(json.dumps(line), flush=True)
 
 
+CACHE_OPS = 512   # partial-state cache length of the cached sweeps (operators per walker)
+
+
 def sweep_bench(dev, steps: int, beta: float, seed: int):
     """Full CT-HYB sweeps of the five-orbital model (semicircular bath, 2,000 tau points,
     1,024 chains). Chains start from Poisson(6) configurations and thermalise untimed
@@ -315,13 +318,18 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     steps = max(meas, steps - steps % meas)   # whole measurement blocks
     n_blocks = steps // meas
     u_plain = uni(steps, 6)      # the FP32 and FP64 plain runs share their uniforms
-    for name, model, mode, n_t in (("fp32", models["fp32"], "plain", steps), ("fp32_da", models["fp32"], "da", steps),
-                                   ("fp64", models["fp64"], "plain", steps)):
-        sw = engine.Sweep(model, table, beta, nw, k_cap=128, n_bins=200, measure_obs=True)
+    u_da = uni(steps, 7)         # and so do the delayed-acceptance runs
+    for name, model, mode, n_t, cache in (("fp32", models["fp32"], "plain", steps, 0),
+                                          ("fp32_da", models["fp32"], "da", steps, 0),
+                                          ("fp64", models["fp64"], "plain", steps, 0),
+                                          ("fp32_cached", models["fp32"], "plain", steps, CACHE_OPS),
+                                          ("fp32_da_cached", models["fp32"], "da", steps, CACHE_OPS),
+                                          ("fp64_cached", models["fp64"], "plain", steps, CACHE_OPS)):
+        sw = engine.Sweep(model, table, beta, nw, k_cap=128, n_bins=200, measure_obs=True, cache_ops=cache)
         sw.set_configs(thermal)
         if mode == "da":
             sw.set_surrogate(net)
-        u = uni(n_t, 7) if mode == "da" else u_plain
+        u = u_da if mode == "da" else u_plain
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -341,6 +349,7 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         for k, v in series.items():
             b = engine.binning_analysis(np.stack(v, axis=1))
             binning[k] = {"mean": float(np.mean(v)), "error": b["error"], "tau_int_measurements": b["tau_int"],
+                          "plateau": b["plateau"],
                           "errors_by_bin_size": {str(sz): e for sz, e in b["errors"].items()}}
         del blocks
         stt = sw.state()
@@ -351,6 +360,7 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         order = acc["order_sum"].sum(1) / ssum
         gmid = (acc["g_tau"][:, :, 95:105].mean(2) * (200 / beta ** 2) / ssum[:, None]).mean(1)
         K = stt["lens"].double().mean().item()
+        del sw
         per_chain[name] = {"docc": docc, "order": order, "G_beta_half": gmid,
                            "n_f": obs[:, :2 * spec.n_orb].mean(1), "S2": obs[:, 3 * spec.n_orb],
                            "lens": stt["lens"].cpu().numpy(), "tau": stt["tau"].cpu().numpy()}
@@ -378,8 +388,16 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     for k in ("docc", "order", "G_beta_half", "n_f", "S2"):
         d = np.abs(a32[k][same] - a64[k][same])
         err32[f"max_abs_diff_{k}"] = float(d.max()) if d.size else None
+
+    def identical(p, q):
+        a, b = per_chain[p], per_chain[q]
+        return int(sum(a["lens"][i] == b["lens"][i] and np.array_equal(a["tau"][i, :a["lens"][i]], b["tau"][i, :b["lens"][i]])
+                       for i in range(nw)))
+    cache_same = {f"{c}_vs_{p}": identical(c, p) for c, p in (("fp32_cached", "fp32"), ("fp32_da_cached", "fp32_da"),
+                                                            ("fp64_cached", "fp64"))}
     speed = {f"{a}_over_{b}": {k: out[a]["eff"][k] / out[b]["eff"][k] for k in out[a]["eff"]}
-             for a, b in (("fp32", "fp64"), ("fp32_da", "fp64"), ("fp32_da", "fp32"))}
+             for a, b in (("fp32", "fp64"), ("fp32_da", "fp64"), ("fp32_da", "fp32"), ("fp32_cached", "fp64"),
+                          ("fp32_da_cached", "fp64"), ("fp32_cached", "fp32"), ("fp64_cached", "fp64"))}
     # throughput-bound batch: 8,192 chains (the 1,024-chain batch is bound by its longest chains)
     nbig, nsteps_big = 8192, max(steps // 4, 100)
     cand_big = workloads.generate_sequences(gen, int(1.3 * nbig), seed=seed + 1)
@@ -393,16 +411,26 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     big.set_configs(cand_big.subset(okb))
     for _ in range(0, therm, 500):
         big.run(unib(500, 6))
+    stb = {k: v.cpu().numpy() for k, v in big.state().items()}
+    lb = stb["lens"]
+    thermal_big = workloads.Sequences(np.concatenate([[0], np.cumsum(lb)]).astype(np.int32),
+                                      np.concatenate([stb["tau"][i, :lb[i]] for i in range(nbig)]),
+                                      np.concatenate([stb["flavor"][i, :lb[i]] for i in range(nbig)]),
+                                      np.concatenate([stb["dagger"][i, :lb[i]] for i in range(nbig)]))
+    del big
     thr = {}
-    for mode in ("plain", "da"):
-        if mode == "da":
+    ub = {6: unib(nsteps_big, 6), 7: unib(nsteps_big, 7)}
+    for mode in ("plain", "da", "plain_cached", "da_cached"):
+        big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200, measure_obs=True,
+                           cache_ops=CACHE_OPS if mode.endswith("cached") else 0)
+        big.set_configs(thermal_big)
+        if mode.startswith("da"):
             big.set_surrogate(net)
-        big.reset_accumulators()
-        u = unib(nsteps_big, 7 if mode == "da" else 6)
+        u = ub[7 if mode.startswith("da") else 6]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        if mode == "da":
+        if mode.startswith("da"):
             big.run_da(u, meas_every=meas)
         else:
             big.run(u, meas_every=meas)
@@ -410,25 +438,42 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         torch.cuda.synchronize()
         c1 = big.counters()
         ms = e0.elapsed_time(e1)
+        # trace-pipeline work of 50 more (untimed) steps
+        wst = engine.new_stats(dev)
+        big.set_stats(wst)
+        if mode.startswith("da"):
+            big.run_da(u[:50])
+        else:
+            big.run(u[:50])
+        big.set_stats(None)
+        wk = kt.stats_from_tensor(wst)
         ab = {k: v.cpu().numpy() for k, v in big.accumulators().items()}
         docc_b = (ab["obs_sum"] / ab["sign_sum"][:, None])[:, 2 * spec.n_orb: 3 * spec.n_orb].mean(1)
         order_b = ab["order_sum"].sum(1) / ab["sign_sum"]
         thr[mode] = {"proposals_per_s": nbig * nsteps_big / (ms / 1000.0), "ms_per_step": ms / nsteps_big,
+                     "work_per_proposal": {"intervals": wk["intervals"] / (50 * nbig),
+                                           "ops_applied": wk["ops_applied"] / (50 * nbig),
+                                           "krylov_iters": wk["krylov_iters"] / (50 * nbig),
+                                           "items_alive": wk["items_alive"] / (50 * nbig)},
                      "trace_evaluations_per_proposal": c1["trace_evaluations"] / (nbig * nsteps_big),
                      "acceptance": (c1["insert_accepted"] + c1["remove_accepted"]) / (nbig * nsteps_big),
                      "eff": {"docc": 1.0 / (docc_b.var(ddof=1) * ms / 1000.0),
                              "order": 1.0 / (order_b.var(ddof=1) * ms / 1000.0)}}
-    thr.update(chains=nbig, steps=nsteps_big,
+        del big
+    thr.update(chains=nbig, steps=nsteps_big, cache_ops=CACHE_OPS,
                speedup_da_over_plain=thr["da"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
-               speedup_da_over_plain_at_equal_error={k: thr["da"]["eff"][k] / thr["plain"]["eff"][k]
-                                                     for k in ("docc", "order")})
-    del big
+               speedup_cached_over_plain=thr["plain_cached"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
+               speedup_da_cached_over_plain=thr["da_cached"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
+               speedup_at_equal_error_over_plain={m: {k: thr[m]["eff"][k] / thr["plain"]["eff"][k]
+                                                         for k in ("docc", "order")}
+                                                      for m in ("da", "plain_cached", "da_cached")})
     return {"workload": f"five_orbital_sweep_beta{beta:g}_1024_chains", "metric": "Metropolis proposals/s (all chains)",
             "sweep_definition": "one sweep = as many proposals per chain as the chain holds operators on average",
             "bath": "semicircular DOS, bandwidth 4, 2000 tau points", "thermalisation_steps": therm,
-            "measure_every": meas, "fp32": out["fp32"], "fp32_da": out["fp32_da"], "fp64": out["fp64"],
+            "measure_every": meas, **out,
             "speedup_fp32_over_fp64": out["fp32"]["proposals_per_s"] / out["fp64"]["proposals_per_s"],
             "speedup_at_equal_error": speed, "throughput_8192_chains": thr, "fp32_vs_fp64_same_uniforms": err32,
+            "cached_vs_uncached_identical_paths": cache_same, "cache_ops": CACHE_OPS,
             "surrogate": {"training_samples": int(X.shape[0]), "collect_s": t_collect, "train_s": t_train,
                           "epochs": len(hist), "loss_per_epoch": hist, "rms_residual_log_ratio": resid,
                           "target_std": spread, "network": "n_in-256-256-1 ReLU, BF16 tcgen05, FP32 accumulate"}}

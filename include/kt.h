@@ -287,6 +287,20 @@ kt_status kt_trace_ratio_static(kt_model *m, const kt_seq_batch *cur, const int8
  *   the expansion order of every flavor;
  *   optionally the observables of kt_measure at beta/2.
  * Every chain starts from the empty configuration.
+ *
+ * Partial-state cache (cache_ops > 0; Sec. III's forward and backward propagation,
+ * kept between steps). For every walker and kept state the sweep stores, for its
+ * current configuration of K operators, the normalised forward states after each
+ * operator (times their log-weights) and the backward states from beta down to each
+ * operator, each over a valid prefix and suffix of positions. A proposal edits the
+ * window between its first and last changed operator; its trace ratio propagates
+ * only from the last valid forward state before the window to the first valid
+ * backward state after it (split in the middle, forward and backward concurrently),
+ * writing the states it passes: positions outside the window extend the valid
+ * prefix or suffix at once, positions inside it are kept aside and committed only if
+ * the move is accepted. The Markov chain and its uniforms are unchanged; the ratios
+ * differ from the full evaluation by rounding only. Memory: 4 * n_walkers * n_kept *
+ * (cache_ops + 1) * (d_max * element size + 20) bytes.
  */
 typedef struct kt_sweep kt_sweep;
 
@@ -297,6 +311,9 @@ typedef struct {
   const double *hyb;    /* HOST [n_flavors][n_tau + 1]: F_f(i beta / n_tau) */
   int32_t n_bins;       /* G(tau) bins (>= 1) */
   int32_t measure_obs;  /* nonzero: accumulate the kt_measure observables at each measurement */
+  int32_t cache_ops;    /* 0: every trace ratio is evaluated from scratch, split at the middle
+                           operator. > 0: partial-state cache (see below) for walkers of up to
+                           cache_ops operators (longer ones fall back to the full evaluation) */
 } kt_sweep_params;
 
 /* Caller-owned DEVICE destinations for kt_sweep_get_state; NULL entries are skipped. */
@@ -342,6 +359,9 @@ kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int
  * Synchronises. On KT_EINVAL (a malformed sequence, too many pairs, a singular
  * bath matrix or a zero trace) every walker is back at the empty configuration. */
 kt_status kt_sweep_set_configs(kt_sweep *s, const kt_seq_batch *host_batch);
+/* Count the trace pipeline's work of the following steps into a caller-owned DEVICE
+ * kt_stats (as kt_trace_ratio does; zero it first). NULL stops counting. */
+kt_status kt_sweep_set_stats(kt_sweep *s, kt_stats *stats);
 kt_status kt_sweep_get_state(kt_sweep *s, const kt_sweep_state *dst, void *stream);
 kt_status kt_sweep_get_accumulators(kt_sweep *s, const kt_sweep_accum *dst, void *stream);
 /* Synchronises the device and copies the counters to out[KT_SWEEP_NCOUNTERS]. */

@@ -89,6 +89,36 @@ struct Workspace {
   int32_t *item_blk;   // [n * n_kept] block of the item at tau = beta/2
 };
 
+// Partial-state cache of the sweep: for every (walker, kept state) item of the
+// current configuration (K operators), forward states at slot i = position i (the
+// state right after operator i-1, at its time; position 0 is the kept state at
+// tau = 0 and is not stored) and backward states at reverse slot K - e (the bra
+// including operators e .. K-1, at the time of operator e; reverse slot 0 is the kept
+// state at beta). Entries are normalised vectors with a log-weight and their block
+// (-1: the state is zero). f[item] and gr[item] bound the valid forward slots
+// [0, f] and reverse slots [0, gr]. The scratch arrays hold one step's tentative
+// states (inside the edited window) until the accept decision.
+struct CacheView {
+  int P;              // positions per direction; walkers with more operators are not cached
+  int dv;             // vector stride (rows) of an entry
+  void *fvec, *bvec;  // [n_items][P + 1][dv] elements of the model's precision
+  double2 *flog, *blog;  // log-weight = x - log(y) (y: mantissa of the normalisation product)
+  int32_t *fblk, *bblk;
+  void *sfvec, *sbvec;
+  double2 *sflog, *sblog;
+  int32_t *sfblk, *sbblk;
+  int32_t *f, *gr;    // [n_items]
+  int4 *plan;         // [n_items] this step: {y, x_new, m, flags}: bit 0 cached, bit 1 unit run
+};
+
+// Edited window of a move in the new sequence: positions [lo, hi_new) differ from
+// the old sequence, positions < lo equal it, positions >= hi_new are old ones shifted
+// by K_new - K_old.
+__host__ __device__ inline void edit_window(int4 d, int &lo, int &hi_new) {
+  lo = d.y;
+  hi_new = d.x == 0 ? d.z + 2 : d.z - 1;
+}
+
 // n_obs_item = 0: trace and ratio calls; nf + n_orb + 1: measurement calls.
 size_t workspace_bytes(int n_walkers, int n_kept, int d_max, int n_obs_item = 0);
 Workspace carve_workspace(void *base, int n_walkers, int n_kept, int d_max, int n_obs_item = 0);
@@ -118,6 +148,14 @@ int launch_pipeline(const DevModel &m, int precision, int kernel_dmax, int group
                     const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv, int32_t *status,
                     kt_stats *stats, const Workspace &ws, void *stream, const StageEvents *timing,
                     double *obs = nullptr);
+
+// The trace-ratio pipeline of the sweep's cached mode: validation and edit, the
+// per-item plan (pruning, the stretch between valid cached states), the cached
+// Krylov items and the reduction. The items use the default lane-group size.
+int launch_cached_pipeline(const DevModel &m, int precision, int kernel_dmax, const SeqView &seq,
+                           const MoveView &moves, const int8_t *cur_sign, const double *cur_logabs, int8_t *sign,
+                           double *logv, int32_t *status, const Workspace &ws, const CacheView &cache, kt_stats *stats,
+                           void *stream);
 
 // Tensor-core GEMM C = A . B^T (BF16 in, FP32 out) and the surrogate network's
 // forward pass (kt_mlp.cu), for the delayed-acceptance sweep.

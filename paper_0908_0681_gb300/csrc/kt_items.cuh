@@ -1037,6 +1037,227 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
   }
 }
 
+// One cache entry: the unit's normalised vector, its log-weight as (additive part
+// less the binary exponent of the normalisation product, mantissa of that product)
+// so that no logarithm is taken per operator, and its block (-1: the state is zero).
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ __forceinline__ void store_entry(VT *vec, double2 *lg, int32_t *bk, size_t e, int dv,
+                                            Unit<VT, G, DMAX, PMAX> &u, bool zero) {
+  constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
+  if (!zero) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = u.gl + G * j;
+      if (r < u.dim) vec[e * dv + r] = u.Q(0, r);
+    }
+  }
+  if (u.gl == 0) {
+    bk[e] = zero ? -1 : u.b;
+    lg[e] = zero ? make_double2(0.0, 1.0) : make_double2(fma(-(double)u.Linv.e, 0.69314718055994530942, u.Ladd), u.Linv.m);
+  }
+}
+
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ __forceinline__ bool load_entry(const DevModel &M, const VT *vec, const double2 *lg, const int32_t *bk,
+                                           size_t e, int dv, Unit<VT, G, DMAX, PMAX> &u) {
+  constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
+  const int b = __ldcg(bk + e);
+  if (b < 0) return false;
+  u.b = b;
+  u.dim = __ldg(M.blk_dim + b);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = u.gl + G * j;
+    if (r < u.dim) u.Q(0, r) = __ldcg(vec + e * dv + r);
+  }
+  const double2 l = __ldcg(lg + e);
+  u.Ladd = l.x;
+  u.Linv.m = l.y;
+  u.Linv.e = 0;
+  __syncwarp(u.gm);
+  return true;
+}
+
+// Cached-mode work units (the sweep's partial-state cache). Every planned item
+// has a forward unit, ops y .. m-1 of the edited sequence starting from the cached
+// state after op y-1 (the kept state at tau = 0 when y = 0), and a backward unit,
+// the adjoints of ops x-1 .. m starting from the cached bra at op x (the kept state
+// at beta when x = K) and then the interval down to op m-1 (Sec. III step 3, over
+// the stretch that the cache does not cover). Each state passed is written to the
+// cache when its position lies outside the edited window, else to the scratch
+// arrays. The halves meet as in items_kernel.
+template <typename VT, int G, int DMAX, int PMAX>
+__global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws,
+                                                           CacheView C, kt_stats *stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int R = (DMAX + G - 1) / G;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane % G;
+  const unsigned gm = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
+  WarpTile<VT, G, DMAX, PMAX> &tile = reinterpret_cast<WarpTile<VT, G, DMAX, PMAX> *>(smem_raw)[wib];
+  const VT *__restrict__ tkept = Tab<VT>::kept(M);
+  const int n_units = 2 * ws.counters[0];
+  const int nk = M.n_kept;
+  const int vstride = M.d_max, dv = C.dv;
+  VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
+  const size_t P1 = (size_t)C.P + 1;
+
+  for (;;) {
+    int uix = 0;
+    if (gl == 0) uix = atomicAdd(&ws.counters[1], 1);
+    uix = __shfl_sync(gm, uix, grp * G);
+    if (uix >= n_units) break;
+    const int it = uix >> 1, half = uix & 1;
+    const int item = ws.worklist[it];
+    const int w = item / nk, q = item - w * nk;
+    const Cursor cur = make_cursor(S, mv, true, ws.desc, w);
+    const int Kn = cur.d.w;
+    const int4 pl = C.plan[item];
+    const bool cached = (pl.w & 1) != 0;
+    int lo, hi;
+    edit_window(cur.d, lo, hi);
+    const int b_kept = __ldg(M.kept_blk + q);
+    const double Ek = __ldg(M.kept_e + q);
+    const int koff = __ldg(M.kept_off + q);
+    Unit<VT, G, DMAX, PMAX> u{tile, grp, gl, gm, b_kept, __ldg(M.blk_dim + b_kept), 0.0, LogScale(), KT_OK, ItemAcc{}};
+    const size_t eb = (size_t)item * P1;
+    const int m = pl.z;
+    bool eigen = true, vanished = false;
+    double t;
+    if (half == 0) {
+      const int y = pl.x;
+      if (y == 0) {
+        t = 0.0;
+      } else {
+        t = cur.get(y - 1).t;
+        eigen = false;
+        vanished = !load_entry(M, (const VT *)C.fvec, C.flog, C.fblk, eb + y, dv, u);
+      }
+      if (eigen) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int r = gl + G * j;
+          if (r < u.dim) u.Q(0, r) = __ldg(tkept + koff + r);
+        }
+        __syncwarp(gm);
+      }
+      for (int i = y; i < m; ++i) {
+        const Op op = cur.get(i);
+        if (!vanished) {
+          const double dt = op.t - t;
+          if (eigen) u.Ladd -= dt * Ek;
+          else if (dt > 0.0 && !propagate(M, u, dt, stats)) vanished = true;
+          if (!vanished && !apply_op(M, u, op.f, op.dag)) vanished = true;
+          eigen = false;
+        }
+        t = op.t;
+        if (cached) {
+          const bool out = i + 1 <= lo;  // outside the window: valid for the current configuration too
+          store_entry((VT *)(out ? C.fvec : C.sfvec), out ? C.flog : C.sflog, out ? C.fblk : C.sfblk, eb + i + 1, dv,
+                      u, vanished);
+        }
+      }
+    } else {
+      const int x = pl.y;
+      if (x == Kn) {
+        t = M.beta;
+      } else {
+        t = cur.get(x).t;
+        eigen = false;
+        vanished = !load_entry(M, (const VT *)C.bvec, C.blog, C.bblk, eb + (Kn - x), dv, u);
+      }
+      if (eigen) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int r = gl + G * j;
+          if (r < u.dim) u.Q(0, r) = __ldg(tkept + koff + r);
+        }
+        __syncwarp(gm);
+      }
+      for (int i = x - 1; i >= m; --i) {
+        const Op op = cur.get(i);
+        if (!vanished) {
+          const double dt = t - op.t;
+          if (eigen) u.Ladd -= dt * Ek;
+          else if (dt > 0.0 && !propagate(M, u, dt, stats)) vanished = true;
+          if (!vanished && !apply_op(M, u, op.f, 1 - op.dag)) vanished = true;
+          eigen = false;
+        }
+        t = op.t;
+        if (cached) {
+          const bool out = i >= hi;
+          store_entry((VT *)(out ? C.bvec : C.sbvec), out ? C.blog : C.sblog, out ? C.bblk : C.sbblk, eb + (Kn - i), dv,
+                      u, vanished);
+        }
+      }
+      // the interval down to the forward unit's last operator
+      if (!vanished) {
+        const double tf = m >= 1 ? cur.get(m - 1).t : 0.0;
+        const double dt = t - tf;
+        if (eigen) u.Ladd -= dt * Ek;
+        else if (dt > 0.0 && !propagate(M, u, dt, stats)) vanished = true;
+      }
+    }
+    // publish this half; the second to finish forms the overlap
+    const int hslot = 2 * item + half;
+    if (!vanished) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int r = gl + G * j;
+        if (r < u.dim) hvec[(size_t)hslot * vstride + r] = u.Q(0, r);
+      }
+    }
+    const double Lh = vanished ? 0.0 : u.Ladd - u.Linv.log_value();
+    if (gl == 0) {
+      ws.half_log[hslot] = Lh;
+      ws.half_info[hslot] = vanished ? -1 : (u.b | (u.status << 24));
+    }
+    __threadfence();
+    __syncwarp(gm);
+    int old = 0;
+    if (gl == 0) old = atomicAdd(&ws.pair_flag[item], 1);
+    old = __shfl_sync(gm, old, grp * G);
+    if (old == 1) {
+      __threadfence();
+      const int oslot = 2 * item + (1 - half);
+      const int oinfo = __ldcg(ws.half_info + oslot);
+      const double Lo = __ldcg(ws.half_log + oslot);
+      bool zero = vanished || oinfo < 0 || (oinfo & 0xffffff) != u.b;
+      double ov = 0.0;
+      if (!zero) {
+        GroupDot<VT, G> d;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int r = gl + G * j;
+          if (r < u.dim) d.add(u.Q(0, r), __ldcg(hvec + (size_t)oslot * vstride + r));
+        }
+        ov = d.value(gm);
+        zero = (ov == 0.0);
+      }
+      int st = u.status;
+      if (oinfo >= 0 && (oinfo >> 24) > st) st = oinfo >> 24;
+      const double L = Lh + Lo + (zero ? 0.0 : log(fabs(ov)));
+      if (!zero && !isfinite(L)) st = KT_ENUMERIC;
+      if (gl == 0) {
+        ws.item_sign[item] = zero ? 0 : (ov > 0.0 ? 1 : -1);
+        ws.item_log[item] = zero ? -INFINITY : L;
+        ws.item_status[item] = st;
+      }
+    }
+    if (gl == 0 && stats) {
+      stat_add(&stats->ops_applied, u.acc.ops);
+      stat_add(&stats->intervals, u.acc.intervals);
+      stat_add(&stats->krylov_iters, u.acc.iters);
+      if (u.acc.pmax) atomicMax(&stats->p_max, u.acc.pmax);
+      stat_add(&stats->noconv, u.acc.noconv);
+      stat_add(&stats->flops_vec, u.acc.flops_vec);
+      stat_add(&stats->flops_tri, u.acc.flops_tri);
+      stat_add(&stats->bytes_apply, u.acc.bytes_apply);
+    }
+    __syncwarp(gm);
+  }
+}
+
 // launch helpers
 template <typename VT, int G, int DMAX, int PMAX>
 int launch_items(const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves, const Workspace &ws,
@@ -1062,6 +1283,31 @@ int launch_items(const DevModel &M, const SeqView &S, const MoveView &mv, int ha
   return (int)cudaGetLastError();
 }
 
+
+template <typename VT, int G, int DMAX, int PMAX>
+int launch_items_cached(const DevModel &M, const SeqView &S, const MoveView &mv, const Workspace &ws,
+                        const CacheView &C, kt_stats *stats, cudaStream_t st) {
+  using Tile = WarpTile<VT, G, DMAX, PMAX>;
+  static int cached_grid = 0, cached_wpb = 0;
+  if (cached_grid == 0) {
+    int wpb = (int)((200 * 1024) / sizeof(Tile));
+    wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
+    const size_t smem = (size_t)wpb * sizeof(Tile);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(items_cached_kernel<VT, G, DMAX, PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, items_cached_kernel<VT, G, DMAX, PMAX>, wpb * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    cached_wpb = wpb;
+    cached_grid = sms * per_sm;
+  }
+  const size_t smem = (size_t)cached_wpb * sizeof(Tile);
+  items_cached_kernel<VT, G, DMAX, PMAX><<<cached_grid, cached_wpb * 32, smem, st>>>(M, S, mv, ws, C, stats);
+  return (int)cudaGetLastError();
+}
 
 template <typename VT>
 int dispatch_items(int kd, int G, const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves,

@@ -35,6 +35,10 @@ int dispatch_items_f32(int kd, int G, const DevModel &M, const SeqView &S, const
                        const Workspace &ws, kt_stats *stats, cudaStream_t st);
 int dispatch_items_f64(int kd, int G, const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves,
                        const Workspace &ws, kt_stats *stats, cudaStream_t st);
+int dispatch_items_cached_f32(int kd, const DevModel &M, const SeqView &S, const MoveView &mv, const Workspace &ws,
+                              const CacheView &C, kt_stats *stats, cudaStream_t st);
+int dispatch_items_cached_f64(int kd, const DevModel &M, const SeqView &S, const MoveView &mv, const Workspace &ws,
+                              const CacheView &C, kt_stats *stats, cudaStream_t st);
 
 namespace {
 using namespace dev;
@@ -129,6 +133,55 @@ __global__ void prune_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, 
     b = __ldg(M.blk_target + ((size_t)b * M.nf + op.f) * 2 + op.dag);
   }
   const bool alive = (b == b0);
+  if (alive) {
+    const int slot = atomicAdd(&ws.counters[0], 1);
+    ws.worklist[slot] = item;
+  }
+  if (stats) {
+    atomicAdd(&stats->items, 1ull);
+    if (alive) atomicAdd(&stats->items_alive, 1ull);
+  }
+}
+
+// Cached mode: structural pruning as above, and for the surviving items the
+// stretch of the edited sequence that the partial-state cache does not cover: the
+// forward unit starts after op y-1 with y = min(lo, f) (the last valid forward state
+// before the window), the backward unit at op x with x the first position at or
+// after the window whose backward state is valid; they meet at m, the middle of
+// [y, x]. Walkers longer than the cache (before or after the edit) use y = 0,
+// x = K_new without writing states.
+__global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, CacheView C, kt_stats *stats) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nk = M.n_kept;
+  if (item >= S.n * nk) return;
+  const int w = item / nk, q = item - w * nk;
+  ws.item_sign[item] = 0;
+  ws.item_status[item] = KT_OK;
+  ws.item_log[item] = -INFINITY;
+  ws.pair_flag[item] = 0;
+  C.plan[item] = make_int4(0, 0, 0, 0);
+  if (ws.wstatus[w] != KT_OK) return;
+  const Cursor c = make_cursor(S, mv, true, ws.desc, w);
+  const int b0 = __ldg(M.kept_blk + q);
+  int b = b0;
+  for (int i = 0; i < c.d.w && b >= 0; ++i) {
+    const Op op = c.get(i);
+    b = __ldg(M.blk_target + ((size_t)b * M.nf + op.f) * 2 + op.dag);
+  }
+  const bool alive = (b == b0);
+  const int Kn = c.d.w, Ko = c.d.x == 0 ? Kn - 2 : Kn + 2;
+  const bool cached = Kn <= C.P && Ko <= C.P;
+  int lo, hi;
+  edit_window(c.d, lo, hi);
+  int y = 0, x = Kn;
+  if (cached) {
+    const int f = C.f[item], gr = C.gr[item];
+    y = lo < f ? lo : f;
+    const int x_old = max(hi - (Kn - Ko), Ko - gr);
+    x = x_old + (Kn - Ko);
+  }
+  const int m = y + (x - y) / 2;
+  C.plan[item] = make_int4(y, x, m, (cached ? 1 : 0) | (alive ? 2 : 0));
   if (alive) {
     const int slot = atomicAdd(&ws.counters[0], 1);
     ws.worklist[slot] = item;
@@ -284,6 +337,26 @@ int launch_pipeline(const DevModel &M, int precision, int kd, int G, const SeqVi
   reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, has_moves, cur_sign, cur_logabs, ws, sign, logv, status);
   if (obs) measure_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, ws, obs);
   mark(4);
+  return (int)cudaGetLastError();
+}
+
+int launch_cached_pipeline(const DevModel &M, int precision, int kd, const SeqView &S, const MoveView &mv,
+                           const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv,
+                           int32_t *status, const Workspace &ws, const CacheView &C, kt_stats *stats, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = S.n;
+  cudaGetLastError();
+  prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, mv, 1, cur_sign, ws, stats);
+  const long long items = (long long)n * M.n_kept;
+  if (items > 0) plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, ws, C, stats);
+  int rc = (int)cudaGetLastError();
+  if (rc) return rc;
+  if (items > 0) {
+    rc = (precision == KT_FP64) ? dispatch_items_cached_f64(kd, M, S, mv, ws, C, stats, st)
+                                : dispatch_items_cached_f32(kd, M, S, mv, ws, C, stats, st);
+    if (rc) return rc;
+  }
+  reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, 1, cur_sign, cur_logabs, ws, sign, logv, status);
   return (int)cudaGetLastError();
 }
 

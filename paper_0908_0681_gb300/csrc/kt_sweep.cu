@@ -82,6 +82,7 @@ struct SweepView {
   double *p_t1, *p_t2;  // the move's first operator time and its partner's
   int8_t *p_seg;      // 1 if the first operator is a c^+
   int32_t *p_pair;    // [2 nw] sequence indices of a removal's pair (-1 for insertions)
+  int8_t *p_acc;      // 1 if this step's move was accepted
   // delayed acceptance
   int n_in;           // feature length
   __nv_bfloat16 *X;   // [nw][n_in] features of the proposals
@@ -169,6 +170,7 @@ __global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni
     S.p_seg[w] = 0;
     S.p_pair[2 * w] = -1;
     S.p_pair[2 * w + 1] = -1;
+    S.p_acc[w] = 0;
   }
   const double *tau = S.tau + o;
   const uint8_t *fl = S.flv + o, *dg = S.dag + o;
@@ -337,6 +339,7 @@ __global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni,
   const double u5 = uni[(size_t)w * ustride + 5];
   const bool accept = (u5 > 0.0 ? log(u5) : -INFINITY) < logR;
   if (!accept) return;
+  if (lane == 0) S.p_acc[w] = 1;
   const int nf = S.nf, f = S.mv_flv[w], kind = S.mv_kind[w];
   const int o = S.offsets[w];
   double *tau = S.tau + o;
@@ -590,6 +593,74 @@ __global__ void sweep_obs_accumulate_kernel(SweepView S) {
   if (isfinite(v)) S.obs_sum[t] += (double)S.w_sign[w] * v;
 }
 
+// After the accept decision of a cached-mode step, one warp per (walker, kept state)
+// item: an accepted move makes its tentative states (scratch) the cache's and the
+// valid ranges meet at m; a rejected one keeps the cache and only extends the valid
+// ranges by the states written outside the window; a pruned item (zero in the new
+// configuration) keeps the unchanged prefix and suffix if the move is accepted.
+__global__ void sweep_cache_commit_kernel(SweepView S, CacheView C, const int4 *__restrict__ desc,
+                                          const int32_t *__restrict__ wstatus, int nk, int words) {
+  const int lane = threadIdx.x & 31;
+  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (item >= S.nw * nk) return;
+  const int w = item / nk;
+  if (!S.p_valid[w] || wstatus[w] != KT_OK) return;
+  const int4 pl = C.plan[item];
+  const bool acc = S.p_acc[w] != 0;
+  if (!(pl.w & 1)) {
+    if (acc && lane == 0) {
+      C.f[item] = 0;
+      C.gr[item] = 0;
+    }
+    return;
+  }
+  const int4 d = desc[w];
+  int lo, hi;
+  edit_window(d, lo, hi);
+  const int Kn = d.w, Ko = d.x == 0 ? Kn - 2 : Kn + 2;
+  const int y = pl.x, x = pl.y, m = pl.z;
+  if (!(pl.w & 2)) {
+    if (acc && lane == 0) {
+      C.f[item] = min(C.f[item], lo);
+      C.gr[item] = min(C.gr[item], Ko - (hi - (Kn - Ko)));
+    }
+    return;
+  }
+  if (!acc) {
+    if (lane == 0 && S.r_status[w] == KT_OK) {
+      C.f[item] = max(C.f[item], min(m, lo));
+      C.gr[item] = max(C.gr[item], Kn - max(m, hi));
+    }
+    return;
+  }
+  const size_t eb = (size_t)item * ((size_t)C.P + 1);
+  const uint32_t *sfv = (const uint32_t *)C.sfvec, *sbv = (const uint32_t *)C.sbvec;
+  uint32_t *fv = (uint32_t *)C.fvec, *bv = (uint32_t *)C.bvec;
+  // forward slots (max(y, lo), m] and backward reverse slots of positions [m, min(x, hi))
+  const int f0 = max(y, lo) + 1, nfw = m - f0 + 1;
+  const int r0 = Kn - min(x, hi) + 1, nbw = (Kn - m) - r0 + 1;
+  for (int k = lane; k < nfw * words; k += 32) {
+    const size_t e = eb + f0 + k / words;
+    fv[e * words + k % words] = sfv[e * words + k % words];
+  }
+  for (int k = lane; k < nbw * words; k += 32) {
+    const size_t e = eb + r0 + k / words;
+    bv[e * words + k % words] = sbv[e * words + k % words];
+  }
+  for (int k = lane; k < nfw; k += 32) {
+    C.fblk[eb + f0 + k] = C.sfblk[eb + f0 + k];
+    C.flog[eb + f0 + k] = C.sflog[eb + f0 + k];
+  }
+  for (int k = lane; k < nbw; k += 32) {
+    C.bblk[eb + r0 + k] = C.sbblk[eb + r0 + k];
+    C.blog[eb + r0 + k] = C.sblog[eb + r0 + k];
+  }
+  if (lane == 0) {
+    C.f[item] = m;
+    C.gr[item] = Kn - m;
+  }
+}
+
 __global__ void sweep_init_kernel(SweepView S, const int8_t *sg, const double *lg) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= S.nw) return;
@@ -620,6 +691,10 @@ struct kt_sweep {
   bool measure_obs = false;
   std::vector<double> hyb_host;
   kt_mlp *net = nullptr;
+  kt::CacheView cache{};  // partial-state cache (cache.P == 0: off)
+  kt_stats *stats = nullptr;  // device counters of the trace pipeline (kt_sweep_set_stats)
+  void *cache_mem = nullptr;
+  int cache_words = 0;    // 32-bit words per cached vector
 };
 
 namespace {
@@ -644,7 +719,7 @@ kt_status carve_and_alloc(kt_sweep *s) {
                o_obs = take(nw * v.nobs * 8), o_obt = take(nw * v.nobs * 8), o_msg = take(nw), o_mlg = take(nw * 8),
                o_mst = take(nw * 4), o_cnt = take(KT_SWEEP_NCOUNTERS * 8), o_pk = take(nw), o_pt1 = take(nw * 8),
                o_pt2 = take(nw * 8), o_pseg = take(nw), o_X = take(nw * (size_t)v.n_in * 2), o_yt = take(nw * 4),
-               o_ppair = take(nw * 2 * 4);
+               o_ppair = take(nw * 2 * 4), o_pacc = take(nw);
   if (cudaMalloc(&s->mem, b) != cudaSuccess) {
     cudaGetLastError();
     s->mem = nullptr;
@@ -697,6 +772,63 @@ kt_status carve_and_alloc(kt_sweep *s) {
   v.X = (__nv_bfloat16 *)(p + o_X);
   v.ytil = (float *)(p + o_yt);
   v.p_pair = (int32_t *)(p + o_ppair);
+  v.p_acc = (int8_t *)(p + o_pacc);
+  return KT_OK;
+}
+
+// The partial-state cache: P + 1 slots per direction for every (walker, kept state)
+// item, cache and scratch, plus the valid ranges and the per-step plan.
+kt_status alloc_cache(kt_sweep *s, int P) {
+  const kt::DevModel &M = *s->mv.dev;
+  const size_t items = (size_t)s->v.nw * M.n_kept, slots = items * ((size_t)P + 1);
+  const size_t esz = s->mv.precision == KT_FP64 ? 8 : 4, dv = (size_t)M.d_max;
+  size_t b = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = b;
+    b += kt::up256(bytes);
+    return at;
+  };
+  size_t o_vec[4], o_log[4], o_blk[4];
+  for (int k = 0; k < 4; ++k) {
+    o_vec[k] = take(slots * dv * esz);
+    o_log[k] = take(slots * 16);
+    o_blk[k] = take(slots * 4);
+  }
+  const size_t o_f = take(items * 4), o_gr = take(items * 4), o_plan = take(items * 16);
+  if (cudaMalloc(&s->cache_mem, b) != cudaSuccess) {
+    cudaGetLastError();
+    s->cache_mem = nullptr;
+    return KT_ENOMEM;
+  }
+  char *p = (char *)s->cache_mem;
+  kt::CacheView &C = s->cache;
+  C.P = P;
+  C.dv = (int)dv;
+  C.fvec = p + o_vec[0];
+  C.bvec = p + o_vec[1];
+  C.sfvec = p + o_vec[2];
+  C.sbvec = p + o_vec[3];
+  C.flog = (double2 *)(p + o_log[0]);
+  C.blog = (double2 *)(p + o_log[1]);
+  C.sflog = (double2 *)(p + o_log[2]);
+  C.sblog = (double2 *)(p + o_log[3]);
+  C.fblk = (int32_t *)(p + o_blk[0]);
+  C.bblk = (int32_t *)(p + o_blk[1]);
+  C.sfblk = (int32_t *)(p + o_blk[2]);
+  C.sbblk = (int32_t *)(p + o_blk[3]);
+  C.f = (int32_t *)(p + o_f);
+  C.gr = (int32_t *)(p + o_gr);
+  C.plan = (int4 *)(p + o_plan);
+  s->cache_words = (int)(dv * esz / 4);
+  return cudaMemset(s->cache_mem, 0, b) == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+// Nothing cached is valid for new configurations.
+kt_status invalidate_cache(kt_sweep *s) {
+  if (!s->cache_mem) return KT_OK;
+  const size_t items = (size_t)s->v.nw * s->mv.dev->n_kept;
+  if (cudaMemset(s->cache.f, 0, items * 4) != cudaSuccess || cudaMemset(s->cache.gr, 0, items * 4) != cudaSuccess)
+    return KT_ECUDA;
   return KT_OK;
 }
 
@@ -720,6 +852,7 @@ kt_status reset_empty(kt_sweep *s) {
   kt::SweepView &v = s->v;
   const size_t nw = v.nw, nf = v.nf;
   if (cudaMemset(v.lens, 0, nw * 4) != cudaSuccess || cudaMemset(v.kf, 0, nw * nf * 4) != cudaSuccess) return KT_ECUDA;
+  if (invalidate_cache(s) != KT_OK) return KT_ECUDA;
   if (current_traces(s, v.m_sign, v.m_log, v.m_status, nullptr, 0) != 0) return KT_ECUDA;
   kt::sweep_init_kernel<<<(v.nw + 255) / 256, 256>>>(v, v.m_sign, v.m_log);
   return cudaDeviceSynchronize() == cudaSuccess ? KT_OK : KT_ECUDA;
@@ -786,7 +919,8 @@ kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out)
   *out = nullptr;
   const kt::ModelView mv = kt::model_view(m);
   if (mv.host_only) return KT_EINVAL;
-  if (p->n_walkers < 1 || p->k_cap < 1 || p->k_cap > 128 || p->n_tau < 1 || p->n_bins < 1) return KT_EINVAL;
+  if (p->n_walkers < 1 || p->k_cap < 1 || p->k_cap > 128 || p->n_tau < 1 || p->n_bins < 1 || p->cache_ops < 0)
+    return KT_EINVAL;
   const int nf = mv.dev->nf;
   for (long long i = 0; i < (long long)nf * (p->n_tau + 1); ++i)
     if (!std::isfinite(p->hyb[i])) return KT_EINVAL;
@@ -806,6 +940,7 @@ kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out)
   v.n_in = (35 * nf + 3 + 15) / 16 * 16;
   v.beta = mv.dev->beta;
   kt_status rc = carve_and_alloc(s);
+  if (rc == KT_OK && p->cache_ops > 0) rc = alloc_cache(s, std::min(p->cache_ops, v.cap));
   if (rc == KT_OK) {
     s->ws_bytes = kt::workspace_bytes(v.nw, mv.dev->n_kept, mv.dev->d_max, nf + mv.dev->n_orb + 1);
     if (cudaMalloc(&s->ws, s->ws_bytes) != cudaSuccess) {
@@ -865,11 +1000,21 @@ static kt_status run_steps(kt_sweep *s, int32_t n_steps, const double *uniforms,
       if (kt::mlp_forward(s->net, v.X, v.nw, v.ytil, false, st) != 0) return KT_ECUDA;
       kt::sweep_stage1_kernel<<<(v.nw + 255) / 256, 256, 0, st>>>(v, u);
     }
-    if (kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, sv, &mvv, v.tr_sign, v.tr_log,
-                            v.r_sign, v.r_log, v.r_status, nullptr, w, st, nullptr) != 0)
+    if (s->cache_mem) {
+      if (kt::launch_cached_pipeline(M, s->mv.precision, s->mv.kernel_dmax, sv, mvv, v.tr_sign, v.tr_log, v.r_sign,
+                                     v.r_log, v.r_status, w, s->cache, s->stats, st) != 0)
+        return KT_ECUDA;
+    } else if (kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, sv, &mvv, v.tr_sign,
+                                   v.tr_log, v.r_sign, v.r_log, v.r_status, s->stats, w, st, nullptr) != 0) {
       return KT_ECUDA;
+    }
     if (mode == 2) kt::sweep_record_kernel<<<grid, wpb * 32, 0, st>>>(v, feat, targ, count, cap);
     kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, u, ustride, w.desc, mode == 1);
+    if (s->cache_mem) {
+      const long long nitems = (long long)v.nw * M.n_kept;
+      kt::sweep_cache_commit_kernel<<<(unsigned)((nitems * 32 + 255) / 256), 256, 0, st>>>(
+          v, s->cache, w.desc, w.wstatus, M.n_kept, s->cache_words);
+    }
     if (meas_every > 0 && (step + 1) % meas_every == 0) {
       kt::sweep_measure_kernel<<<grid, wpb * 32, 0, st>>>(v);
       if (s->measure_obs) {
@@ -895,6 +1040,12 @@ kt_status kt_sweep_collect(kt_sweep *s, int32_t n_steps, const double *uniforms,
                            int32_t *count, int32_t capacity, void *stream) {
   if (!s || !features || !targets || !count || capacity < 0) return KT_EINVAL;
   return run_steps(s, n_steps, uniforms, 0, stream, 2, (__nv_bfloat16 *)features, targets, count, capacity);
+}
+
+kt_status kt_sweep_set_stats(kt_sweep *s, kt_stats *stats) {
+  if (!s) return KT_EINVAL;
+  s->stats = stats;
+  return KT_OK;
 }
 
 kt_status kt_sweep_feature_size(const kt_sweep *s, int32_t *n_in) {
@@ -1047,7 +1198,7 @@ static kt_status set_configs_impl(kt_sweep *s, const kt_seq_batch *b) {
   if (cudaMemcpy(v.w_sign, ws.data(), nw, cudaMemcpyHostToDevice) != cudaSuccess) {
     return KT_ECUDA;
   }
-  return KT_OK;
+  return invalidate_cache(s);
 }
 
 kt_status kt_sweep_get_state(kt_sweep *s, const kt_sweep_state *d, void *stream) {
@@ -1111,6 +1262,7 @@ void kt_sweep_destroy(kt_sweep *s) {
   if (!s) return;
   if (s->ws) cudaFree(s->ws);
   if (s->mem) cudaFree(s->mem);
+  if (s->cache_mem) cudaFree(s->cache_mem);
   delete s;
 }
 

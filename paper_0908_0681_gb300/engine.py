@@ -131,10 +131,13 @@ def binning_analysis(x) -> dict:
     and the error of the grand mean is sqrt(var(bin means) / number of bins), pooled over
     the independent chains. For uncorrelated data every b gives the same error; with
     autocorrelation the error grows with b until the bins are longer than the
-    autocorrelation time, where it levels off (the plateau is the error bar). Returns
-    {"errors": {b: error}, "error": the error at the largest b with at least 8 bins per
-    chain (or 2 bins in all), "tau_int": half the squared ratio of that error to the b = 1
-    error (the integrated autocorrelation time, in measurements)}."""
+    autocorrelation time, where it levels off (the plateau is the error bar). With many
+    independent chains the largest bin is a whole chain, whose mean is independent of the
+    others whatever the autocorrelation. Returns {"errors": {b: error}, "error": the error
+    at the largest b that leaves at least 8 bins in all, "tau_int": half the squared ratio
+    of that error to the b = 1 error (the integrated autocorrelation time, in
+    measurements), "plateau": whether that error is within 10% of the one at the next
+    smaller b (else the series is too short for a single chain's error bar)}."""
     x = np.asarray(x, dtype=np.float64)
     if x.ndim == 1:
         x = x[None, :]
@@ -147,10 +150,13 @@ def binning_analysis(x) -> dict:
         if y.size < 2:
             continue
         errs[b] = float(np.sqrt(y.var(ddof=1) / y.size))
-    ok = [b for b in errs if nt // b >= 8] or list(errs)
+    ok = [b for b in errs if nc * (nt // b) >= 8] or list(errs)
     bmax = max(ok)
     e1 = errs[min(errs)]
-    return {"errors": errs, "error": errs[bmax], "tau_int": 0.5 * (errs[bmax] / e1) ** 2 if e1 > 0 else 0.5}
+    smaller = [b for b in errs if b < bmax]
+    plateau = bool(smaller) and errs[bmax] <= 1.1 * errs[max(smaller)]
+    return {"errors": errs, "error": errs[bmax], "tau_int": 0.5 * (errs[bmax] / e1) ** 2 if e1 > 0 else 0.5,
+            "plateau": plateau}
 
 
 class Sweep:
@@ -158,8 +164,12 @@ class Sweep:
     removal of c^+/c pairs with FP64 determinant updates and the library's trace ratios."""
 
     def __init__(self, model: kt.KtModel, hyb: np.ndarray, beta: float, n_walkers: int, k_cap: int = 64,
-                 n_bins: int = 100, measure_obs: bool = False):
-        self.h = kt.KtSweep(model, hyb, n_walkers, k_cap=k_cap, n_bins=n_bins, measure_obs=measure_obs)
+                 n_bins: int = 100, measure_obs: bool = False, cache_ops: int = 0):
+        """cache_ops > 0 keeps the partial-state cache for walkers of up to cache_ops
+        operators: each proposal's trace ratio then propagates only the stretch around its
+        edit that the cache does not cover."""
+        self.h = kt.KtSweep(model, hyb, n_walkers, k_cap=k_cap, n_bins=n_bins, measure_obs=measure_obs,
+                            cache_ops=cache_ops)
         info = kt.kt_model_query(model)
         self.nf, self.n_orb = info["n_flavors"], info["n_orb"]
         self.beta = float(beta)
@@ -238,6 +248,12 @@ class Sweep:
 
     def reset_accumulators(self) -> None:
         kt.kt_sweep_reset_accumulators(self.h)
+
+    def set_stats(self, stats: torch.Tensor | None) -> None:
+        """Accumulate the trace pipeline's kt_stats of the following steps into `stats`
+        (engine.new_stats()); None stops."""
+        self._stats = stats
+        kt.kt_sweep_set_stats(self.h, stats)
 
     def run_blocks(self, uniforms: torch.Tensor, meas_every: int, n_blocks: int, delayed: bool = False) -> list:
         """Run the steps as n_blocks consecutive equal blocks (plain, or delayed acceptance

@@ -51,7 +51,8 @@ class kt_stats(ctypes.Structure):
 
 class kt_sweep_params(ctypes.Structure):
     _fields_ = [("n_walkers", ctypes.c_int32), ("k_cap", ctypes.c_int32), ("n_tau", ctypes.c_int32),
-                ("hyb", ctypes.c_void_p), ("n_bins", ctypes.c_int32), ("measure_obs", ctypes.c_int32)]
+                ("hyb", ctypes.c_void_p), ("n_bins", ctypes.c_int32), ("measure_obs", ctypes.c_int32),
+                ("cache_ops", ctypes.c_int32)]
 
 
 class kt_sweep_state(ctypes.Structure):
@@ -83,7 +84,7 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_sweep_set_configs", "kt_gemm_bf16", "kt_mlp_create", "kt_mlp_num_params",
                  "kt_mlp_set_params", "kt_mlp_get_params", "kt_mlp_forward", "kt_mlp_backward", "kt_mlp_get_grads",
                  "kt_mlp_adam", "kt_mlp_error", "kt_mlp_destroy", "kt_sweep_feature_size", "kt_sweep_collect",
-                 "kt_sweep_set_surrogate", "kt_sweep_run_da"]
+                 "kt_sweep_set_surrogate", "kt_sweep_run_da", "kt_sweep_set_stats"]
 
 KT_SWEEP_NCOUNTERS = 10
 KT_MLP_HIDDEN = 256
@@ -140,6 +141,7 @@ def load():
     lib.kt_sweep_collect.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
     lib.kt_sweep_set_surrogate.argtypes = [vp, vp]
     lib.kt_sweep_run_da.argtypes = [vp, i32, vp, i32, vp]
+    lib.kt_sweep_set_stats.argtypes = [vp, vp]
     lib.kt_sweep_get_state.argtypes = [vp, ctypes.POINTER(kt_sweep_state), vp]
     lib.kt_sweep_get_accumulators.argtypes = [vp, ctypes.POINTER(kt_sweep_accum), vp]
     lib.kt_sweep_counters.argtypes = [vp, vp]
@@ -293,11 +295,12 @@ class KtSweep:
     """Owning handle of a kt_sweep (destroyed with the object); keeps its model alive."""
 
     def __init__(self, model: KtModel, hyb: np.ndarray, n_walkers: int, k_cap: int = 64, n_bins: int = 100,
-                 measure_obs: bool = False):
+                 measure_obs: bool = False, cache_ops: int = 0):
         self.model = model
         self._hyb = np.ascontiguousarray(hyb, dtype=np.float64)
         p = kt_sweep_params(int(n_walkers), int(k_cap), int(self._hyb.shape[1] - 1),
-                            self._hyb.ctypes.data_as(ctypes.c_void_p), int(n_bins), 1 if measure_obs else 0)
+                            self._hyb.ctypes.data_as(ctypes.c_void_p), int(n_bins), 1 if measure_obs else 0,
+                            int(cache_ops))
         h = ctypes.c_void_p()
         _check(load().kt_sweep_create(model.handle, ctypes.byref(p), ctypes.byref(h)), "kt_sweep_create")
         self.handle = h
@@ -308,6 +311,12 @@ class KtSweep:
         if h is not None and _lib is not None:
             _lib.kt_sweep_destroy(h)
             self.handle = None
+
+
+def kt_sweep_set_stats(s: KtSweep, stats) -> None:
+    """Count the trace pipeline's work of the following steps into a device kt_stats
+    tensor (engine.new_stats); None stops counting."""
+    _check(load().kt_sweep_set_stats(s.handle, _ptr(stats)), "kt_sweep_set_stats")
 
 
 def kt_sweep_run(s: KtSweep, n_steps: int, uniforms, meas_every: int = 0, stream=None) -> None:

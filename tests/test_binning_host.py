@@ -37,6 +37,23 @@ def test_ar1_error_reaches_the_exact_variance_of_the_mean():
     assert r["errors"][1] < 0.5 * exact
     assert abs(r["error"] / exact - 1) < 0.15, (r["error"], exact)
     assert abs(r["tau_int"] / ((1 + rho) / (2 * (1 - rho))) - 1) < 0.3
+    assert r["plateau"]
+
+
+def test_chains_shorter_than_the_autocorrelation_time():
+    """Many independent chains, each shorter than its autocorrelation time: the whole-chain
+    bins still give the right error, and the missing plateau is reported."""
+    rho = 0.995
+    rng = np.random.default_rng(4)
+    x = _ar1(rng, 2000, 64, rho)
+    r = binning_analysis(x)
+    assert not r["plateau"]
+    # exact variance of a 64-step AR(1) mean started in equilibrium
+    n = x.shape[1]
+    k = np.arange(1, n)
+    var1 = (1 + 2 * np.sum((1 - k / n) * rho ** k)) / n
+    exact = math.sqrt(var1 / x.shape[0])
+    assert abs(r["error"] / exact - 1) < 0.1, (r["error"], exact)
 
 
 def test_single_chain_and_short_series():

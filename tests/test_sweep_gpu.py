@@ -33,23 +33,27 @@ def model_pair(spec, precision):
     return Model(P), engine.model_from_spec(spec, precision=precision)
 
 
-def run_both(spec, nw, steps, k_cap, n_bins, meas_every, seed, precision=kt.KT_FP64, observables=True):
+def run_both(spec, nw, steps, k_cap, n_bins, meas_every, seed, precision=kt.KT_FP64, observables=True,
+             cache_ops=0):
     om, gm = model_pair(spec, precision)
     table = workloads.semicircular_hybridization(spec.beta, 2 * spec.n_orb, n_tau=2000)
     u = workloads.sweep_uniforms(steps, nw, seed=seed)
-    sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=k_cap, n_bins=n_bins, measure_obs=observables)
+    sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=k_cap, n_bins=n_bins, measure_obs=observables,
+                      cache_ops=cache_ops)
     sw.run(torch.as_tensor(u, device="cuda"), meas_every=meas_every)
     ref = chain(om, Hyb(table, spec.beta), [[] for _ in range(nw)], u, k_cap=k_cap, n_bins=n_bins,
                 meas_every=meas_every, observables=observables)
     return om, Hyb(table, spec.beta), sw, ref
 
 
-@pytest.mark.parametrize("k_cap", [64, 2])
-def test_three_orbital_chain_matches_oracle(k_cap):
+@pytest.mark.parametrize("k_cap,cache_ops", [(64, 0), (2, 0), (64, 64), (64, 12)])
+def test_three_orbital_chain_matches_oracle(k_cap, cache_ops):
+    """cache_ops > 0: the ratios come from the partial-state cache; with 12 the walkers
+    move in and out of the cached length."""
     w = workloads.three_orbital()
     spec = w.model
     nw, steps = 16, 400
-    om, hyb, sw, ref = run_both(spec, nw, steps, k_cap, n_bins=20, meas_every=8, seed=21)
+    om, hyb, sw, ref = run_both(spec, nw, steps, k_cap, n_bins=20, meas_every=8, seed=21, cache_ops=cache_ops)
     cnt = sw.counters()
     acc = ref["accepted"]
     assert cnt["trace_errors"] == 0
@@ -263,3 +267,83 @@ def test_run_blocks_partition_the_accumulators():
     docc = np.stack([(b["obs_sum"][:, 6:9].mean(1) / b["sign_sum"]).cpu().numpy() for b in blocks], axis=1)
     r = engine.binning_analysis(docc)
     assert np.isfinite(r["error"]) and r["error"] > 0 and set(r["errors"]) >= {1, 2, 4}
+
+
+def _thermal_five_orbital(nw, beta, seed):
+    """Five-orbital configurations after 300 plain steps from Poisson(6) starts."""
+    w = workloads.five_orbital()
+    spec = workloads.five_orbital_sweep(beta).model
+    gen = workloads.Workload(w.name, spec, start=w.start, order=w.order, lam=w.lam, cap=w.cap,
+                             pattern_singles=w.pattern_singles)
+    cand = workloads.generate_sequences(gen, 2 * nw, seed=seed)
+    m = engine.model_from_spec(spec, precision=kt.KT_FP64)
+    sg, _, _ = engine.trace(m, engine.DeviceSeqs.from_host(cand))
+    ok = np.nonzero(sg.cpu().numpy() != 0)[0][:nw]
+    table = workloads.semicircular_hybridization(beta, 10, n_tau=2000)
+    sw = engine.Sweep(m, table, beta, nw, k_cap=128, n_bins=20)
+    sw.set_configs(cand.subset(ok))
+    sw.run(torch.as_tensor(workloads.sweep_uniforms(300, nw, seed=seed + 1), device="cuda"))
+    st = {k: v.cpu().numpy() for k, v in sw.state().items()}
+    lens = st["lens"]
+    seqs = workloads.Sequences(np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
+                               np.concatenate([st["tau"][i, :lens[i]] for i in range(nw)]),
+                               np.concatenate([st["flavor"][i, :lens[i]] for i in range(nw)]),
+                               np.concatenate([st["dagger"][i, :lens[i]] for i in range(nw)]))
+    return spec, table, seqs
+
+
+@pytest.mark.parametrize("precision", [kt.KT_FP64, kt.KT_FP32_KRYLOV])
+def test_cached_five_orbital_chains_match_uncached(precision):
+    """Five orbitals at beta = 50 from thermalised configurations (about 160 operators):
+    the cached chains take the decisions of the uncached ones on the same uniforms (FP64:
+    every chain; FP32: the ratios differ by rounding, so a rare near-tie may flip) and
+    track the same weights; the cached FP32 weights match the oracle's from scratch."""
+    nw, steps, beta = 128, 300, 50.0
+    spec, table, seqs = _thermal_five_orbital(nw, beta, seed=11)
+    u = torch.as_tensor(workloads.sweep_uniforms(steps, nw, seed=12), device="cuda")
+    gm = engine.model_from_spec(spec, precision=precision)
+    runs = {}
+    for c in (0, 512):
+        sw = engine.Sweep(gm, table, beta, nw, k_cap=128, n_bins=20, cache_ops=c)
+        sw.set_configs(seqs)
+        sw.run(u, meas_every=10)
+        runs[c] = (sw, {k: v.cpu().numpy() for k, v in sw.state().items()}, sw.counters())
+    (a, sa, ca), (b, sb, cb) = runs[0], runs[512]
+    assert ca["trace_errors"] == 0 and cb["trace_errors"] == 0
+    assert cb["insert_accepted"] + cb["remove_accepted"] > nw * steps // 10
+    same = np.array([sa["lens"][i] == sb["lens"][i] and
+                     np.array_equal(sa["tau"][i, :sa["lens"][i]], sb["tau"][i, :sb["lens"][i]]) for i in range(nw)])
+    if precision == kt.KT_FP64:
+        assert same.all()
+        assert np.abs(sa["trace_logabs"] - sb["trace_logabs"]).max() < 1e-9
+    else:
+        assert same.mean() >= 0.95
+        assert np.abs(sa["trace_logabs"][same] - sb["trace_logabs"][same]).max() < 1e-4
+        om, _ = model_pair(spec, kt.KT_FP64)
+        hyb = Hyb(table, beta)
+        cfg = b.configs()
+        for i in range(0, nw, 8):
+            s_, lw, sT, lT = weight(om, hyb, cfg[i])
+            assert sT == sb["trace_sign"][i] and abs(math.expm1(sb["trace_logabs"][i] - lT)) < 1e-4, i
+
+
+def test_cached_delayed_acceptance_matches_uncached():
+    """Delayed acceptance with the cache: the same surrogate and uniforms give the same
+    chain as without it (three orbitals, FP64)."""
+    w = workloads.three_orbital()
+    spec = w.model
+    nw, steps = 64, 300
+    gm = engine.model_from_spec(spec, precision=kt.KT_FP64)
+    table = workloads.semicircular_hybridization(spec.beta, 6, n_tau=2000)
+    u = torch.rand((steps, nw, 7), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    out = []
+    for c in (0, 256):
+        sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=64, n_bins=10, cache_ops=c)
+        net = engine.Surrogate(sw.n_features, max_batch=nw, seed=3)
+        sw.set_surrogate(net)
+        sw.run_da(u, meas_every=10)
+        out.append((sw.configs(), sw.counters(), sw.state()["trace_logabs"].cpu().numpy()))
+    assert out[0][0] == out[1][0]
+    assert out[0][1] == out[1][1]
+    assert out[0][1]["stage1_rejected"] > 0 and out[0][1]["insert_accepted"] > 0
+    assert np.abs(out[0][2] - out[1][2]).max() < 1e-9
