@@ -73,7 +73,9 @@ struct MoveView {
 
 // Workspace layout (device), sized for n walkers and n_kept kept states.
 struct Workspace {
-  int32_t *counters;   // [4]: 0 = number of alive items, 1 = next item to claim
+  int32_t *counters;   // [4]: 0 = number of alive items, 1 = next item to claim; cached mode:
+                       // 2 = items with long stretches (worklist from the front), 3 = the others
+                       // (worklist from the back)
   int4 *desc;          // [n] per-walker edit descriptor {kind, p1, p2, K_new}
   int32_t *wstatus;    // [n] per-walker status from validation
   int32_t *worklist;   // [n * n_kept] alive items (walker * n_kept + kept)
@@ -110,6 +112,9 @@ struct CacheView {
   int32_t *f, *gr;    // [n_items]
   int4 *plan;         // [n_items] this step: {y, x_new, m, flags}: bit 0 cached, bit 1 unit run
 };
+
+// Cached mode: stretches of at least this many operators are scheduled first.
+#define KT_LONG_STRETCH 48
 
 // Edited window of a move in the new sequence: positions [lo, hi_new) differ from
 // the old sequence, positions < lo equal it, positions >= hi_new are old ones shifted

@@ -1096,8 +1096,9 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
   const unsigned gm = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
   WarpTile<VT, G, DMAX, PMAX> &tile = reinterpret_cast<WarpTile<VT, G, DMAX, PMAX> *>(smem_raw)[wib];
   const VT *__restrict__ tkept = Tab<VT>::kept(M);
-  const int n_units = 2 * ws.counters[0];
+  const int n_units = 2 * ws.counters[0], n_long = ws.counters[2];
   const int nk = M.n_kept;
+  const int last = S.n * nk - 1;
   const int vstride = M.d_max, dv = C.dv;
   VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
   const size_t P1 = (size_t)C.P + 1;
@@ -1108,7 +1109,7 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
     uix = __shfl_sync(gm, uix, grp * G);
     if (uix >= n_units) break;
     const int it = uix >> 1, half = uix & 1;
-    const int item = ws.worklist[it];
+    const int item = ws.worklist[it < n_long ? it : last - (it - n_long)];
     const int w = item / nk, q = item - w * nk;
     const Cursor cur = make_cursor(S, mv, true, ws.desc, w);
     const int Kn = cur.d.w;
@@ -1121,81 +1122,54 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
     const int koff = __ldg(M.kept_off + q);
     Unit<VT, G, DMAX, PMAX> u{tile, grp, gl, gm, b_kept, __ldg(M.blk_dim + b_kept), 0.0, LogScale(), KT_OK, ItemAcc{}};
     const size_t eb = (size_t)item * P1;
-    const int m = pl.z;
-    bool eigen = true, vanished = false;
-    double t;
-    if (half == 0) {
-      const int y = pl.x;
-      if (y == 0) {
-        t = 0.0;
-      } else {
-        t = cur.get(y - 1).t;
-        eigen = false;
-        vanished = !load_entry(M, (const VT *)C.fvec, C.flog, C.fblk, eb + y, dv, u);
-      }
-      if (eigen) {
+    const int y = pl.x, x = pl.y, m = pl.z;
+    // One loop for both halves (a single inlined copy of propagate and apply_op):
+    // forward, steps s = 0 .. m-y-1 take op i = y+s: the interval up to it, then the op;
+    // backward, steps s = 0 .. x-m-1 take op i = x-1-s: the interval down to it, then
+    // its adjoint; a last step without op takes the interval down to op m-1.
+    const bool fwd = half == 0;
+    const int start = fwd ? y : x;
+    const bool from_kept = fwd ? (y == 0) : (x == Kn);
+    double t = fwd ? (y == 0 ? 0.0 : cur.get(y - 1).t) : (x == Kn ? M.beta : cur.get(x).t);
+    bool eigen = from_kept, vanished = false;
+    if (from_kept) {
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int r = gl + G * j;
-          if (r < u.dim) u.Q(0, r) = __ldg(tkept + koff + r);
-        }
-        __syncwarp(gm);
+      for (int j = 0; j < R; ++j) {
+        const int r = gl + G * j;
+        if (r < u.dim) u.Q(0, r) = __ldg(tkept + koff + r);
       }
-      for (int i = y; i < m; ++i) {
-        const Op op = cur.get(i);
-        if (!vanished) {
-          const double dt = op.t - t;
-          if (eigen) u.Ladd -= dt * Ek;
-          else if (dt > 0.0 && !propagate(M, u, dt, stats)) vanished = true;
-          if (!vanished && !apply_op(M, u, op.f, op.dag)) vanished = true;
-          eigen = false;
-        }
-        t = op.t;
-        if (cached) {
-          const bool out = i + 1 <= lo;  // outside the window: valid for the current configuration too
-          store_entry((VT *)(out ? C.fvec : C.sfvec), out ? C.flog : C.sflog, out ? C.fblk : C.sfblk, eb + i + 1, dv,
-                      u, vanished);
-        }
-      }
+      __syncwarp(gm);
     } else {
-      const int x = pl.y;
-      if (x == Kn) {
-        t = M.beta;
-      } else {
-        t = cur.get(x).t;
-        eigen = false;
-        vanished = !load_entry(M, (const VT *)C.bvec, C.blog, C.bblk, eb + (Kn - x), dv, u);
-      }
-      if (eigen) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int r = gl + G * j;
-          if (r < u.dim) u.Q(0, r) = __ldg(tkept + koff + r);
-        }
-        __syncwarp(gm);
-      }
-      for (int i = x - 1; i >= m; --i) {
-        const Op op = cur.get(i);
-        if (!vanished) {
-          const double dt = t - op.t;
-          if (eigen) u.Ladd -= dt * Ek;
-          else if (dt > 0.0 && !propagate(M, u, dt, stats)) vanished = true;
-          if (!vanished && !apply_op(M, u, op.f, 1 - op.dag)) vanished = true;
-          eigen = false;
-        }
-        t = op.t;
-        if (cached) {
-          const bool out = i >= hi;
-          store_entry((VT *)(out ? C.bvec : C.sbvec), out ? C.blog : C.sblog, out ? C.bblk : C.sbblk, eb + (Kn - i), dv,
-                      u, vanished);
-        }
-      }
-      // the interval down to the forward unit's last operator
+      vanished = !load_entry(M, (const VT *)(fwd ? C.fvec : C.bvec), fwd ? C.flog : C.blog, fwd ? C.fblk : C.bblk,
+                             eb + (fwd ? start : Kn - start), dv, u);
+    }
+    const int n_ops = fwd ? m - y : x - m;
+    const int n_steps = fwd ? n_ops : n_ops + 1;
+    const double tf = m >= 1 ? cur.get(m - 1).t : 0.0;
+    for (int s = 0; s < n_steps; ++s) {
+      const bool has_op = s < n_ops;
+      const int i = fwd ? y + s : x - 1 - s;
+      Op op{tf, 0, 0};
+      if (has_op) op = cur.get(i);
       if (!vanished) {
-        const double tf = m >= 1 ? cur.get(m - 1).t : 0.0;
-        const double dt = t - tf;
+        const double dt = fwd ? op.t - t : t - op.t;
         if (eigen) u.Ladd -= dt * Ek;
         else if (dt > 0.0 && !propagate(M, u, dt, stats)) vanished = true;
+        if (has_op) {
+          if (!vanished && !apply_op(M, u, op.f, fwd ? op.dag : 1 - op.dag)) vanished = true;
+          eigen = false;
+        }
+      }
+      t = op.t;
+      if (has_op && cached) {
+        // forward slot i+1 / backward reverse slot K-i; outside the window the state is
+        // valid for the current configuration too and goes to the cache itself
+        const bool out = fwd ? i + 1 <= lo : i >= hi;
+        const size_t e = eb + (fwd ? i + 1 : Kn - i);
+        VT *vec = (VT *)(fwd ? (out ? C.fvec : C.sfvec) : (out ? C.bvec : C.sbvec));
+        double2 *lg = fwd ? (out ? C.flog : C.sflog) : (out ? C.blog : C.sblog);
+        int32_t *bk = fwd ? (out ? C.fblk : C.sfblk) : (out ? C.bblk : C.sbblk);
+        store_entry(vec, lg, bk, e, dv, u, vanished);
       }
     }
     // publish this half; the second to finish forms the overlap

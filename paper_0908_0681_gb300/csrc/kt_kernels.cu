@@ -52,6 +52,8 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
   if (w == 0) {
     ws.counters[0] = 0;
     ws.counters[1] = 0;
+    ws.counters[2] = 0;
+    ws.counters[3] = 0;
   }
   if (w >= S.n) return;
   const int o = S.offsets[w], K = S.lens ? S.lens[w] : S.offsets[w + 1] - o;
@@ -183,8 +185,13 @@ __global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, Ca
   const int m = y + (x - y) / 2;
   C.plan[item] = make_int4(y, x, m, (cached ? 1 : 0) | (alive ? 2 : 0));
   if (alive) {
-    const int slot = atomicAdd(&ws.counters[0], 1);
-    ws.worklist[slot] = item;
+    // longest stretches first: they bound the launch, the short ones fill in around them
+    atomicAdd(&ws.counters[0], 1);
+    if (x - y >= KT_LONG_STRETCH) {
+      ws.worklist[atomicAdd(&ws.counters[2], 1)] = item;
+    } else {
+      ws.worklist[S.n * nk - 1 - atomicAdd(&ws.counters[3], 1)] = item;
+    }
   }
   if (stats) {
     atomicAdd(&stats->items, 1ull);

@@ -1,13 +1,15 @@
 """A fixed invocation of the CT-HYB sweep for profiler captures.
 
     python -m paper_0908_0681_gb300.profile_sweep [--beta 50] [--chains 1024] [--steps 20]
-           [--therm 200] [--collect 100] [--mode plain|da|both]
+           [--therm 200] [--collect 100] [--mode plain|da|both] [--cache-ops 0] [--precision fp32|fp64]
+           [--k-cap 128]
 
 Five-orbital model with the semicircular bath (2,000 tau points); the chains start from
 Poisson(6) configurations (kt_sweep_set_configs) and thermalise `therm` steps. For
 `da`, a surrogate is trained for one epoch on `collect` steps of the chains' own ratios.
-Then `steps` plain and/or delayed-acceptance steps run, measuring every 10 steps.
-Exits 0 when no chain reported a trace error.
+Then `steps` plain and/or delayed-acceptance steps run, measuring every 10 steps, with
+the partial-state cache when --cache-ops > 0. Prints the CUDA-event time per step and
+the trace pipeline's work per proposal. Exits 0 when no chain reported a trace error.
 """
 from __future__ import annotations
 
@@ -28,6 +30,9 @@ def main():
     p.add_argument("--therm", type=int, default=200)
     p.add_argument("--mode", choices=["plain", "da", "both"], default="both")
     p.add_argument("--collect", type=int, default=100, help="steps of training data for the surrogate")
+    p.add_argument("--cache-ops", type=int, default=0)
+    p.add_argument("--k-cap", type=int, default=128)
+    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     a = p.parse_args()
     import numpy as np
     import torch
@@ -40,11 +45,11 @@ def main():
     gen = workloads.Workload(w.name, spec, start=w.start, order=w.order, lam=w.lam, cap=w.cap,
                              pattern_singles=w.pattern_singles)
     cand = workloads.generate_sequences(gen, 2 * nw, seed=7)
-    model = engine.model_from_spec(spec, precision=kt.KT_FP32_KRYLOV)
+    model = engine.model_from_spec(spec, precision=kt.KT_FP32_KRYLOV if a.precision == "fp32" else kt.KT_FP64)
     sg, _, _ = engine.trace(model, engine.DeviceSeqs.from_host(cand))
     ok = np.nonzero(sg.cpu().numpy() != 0)[0][:nw]
     table = workloads.semicircular_hybridization(a.beta, 2 * spec.n_orb, n_tau=2000)
-    sw = engine.Sweep(model, table, a.beta, nw, k_cap=128, n_bins=200, measure_obs=True)
+    sw = engine.Sweep(model, table, a.beta, nw, k_cap=a.k_cap, n_bins=200, measure_obs=True, cache_ops=a.cache_ops)
     sw.set_configs(cand.subset(ok))
     g = torch.Generator(device="cuda").manual_seed(3)
 
@@ -52,17 +57,35 @@ def main():
         return torch.rand((n, nw, k), dtype=torch.float64, device="cuda", generator=g)
 
     sw.run(uni(a.therm, 6))
+
+    def timed(fn, u):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn(u, meas_every=10)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / u.shape[0]
+        st = engine.new_stats()
+        sw.set_stats(st)
+        fn(u[:10])
+        sw.set_stats(None)
+        w = kt.stats_from_tensor(st)
+        per = {k: round(w[k] / (10 * nw), 3) for k in ("intervals", "ops_applied", "krylov_iters", "items_alive")}
+        print(f"  {fn.__name__}: {ms:.3f} ms/step, {nw / ms * 1e3:.0f} proposals/s, work per proposal {per}")
+
     if a.mode in ("plain", "both"):
-        sw.run(uni(a.steps, 6), meas_every=10)
+        timed(sw.run, uni(a.steps, 6))
     if a.mode in ("da", "both"):
         X, t = sw.collect(uni(a.collect, 6), capacity=a.collect * nw)
-        net = engine.Surrogate(sw.n_features, max_batch=4096, seed=1)
+        net = engine.Surrogate(sw.n_features, max_batch=max(4096, nw), seed=1)
         net.train(X, t.clamp(-25.0, 10.0), epochs=1, batch=4096, lr=3e-3)
         sw.set_surrogate(net)
-        sw.run_da(uni(a.steps, 7), meas_every=10)
+        timed(sw.run_da, uni(a.steps, 7))
     torch.cuda.synchronize()
     c = sw.counters()
-    print(f"profile_sweep beta={a.beta:g} chains={nw} steps={a.steps} mode={a.mode} counters={c}")
+    print(f"profile_sweep beta={a.beta:g} chains={nw} steps={a.steps} mode={a.mode} cache_ops={a.cache_ops} "
+          f"precision={a.precision} counters={c}")
     return 0 if c["trace_errors"] == 0 else 1
 
 
