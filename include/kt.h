@@ -248,6 +248,37 @@ kt_status kt_trace_ratio_static(kt_model *m, const kt_seq_batch *cur, const int8
                                 double *logratio, int32_t *status, kt_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Trace ratios from cached partial states (Sec. III step 3: the forward and */
+/* backward propagation, kept between calls).                                */
+/* ------------------------------------------------------------------------ */
+/*
+ * For fixed current configurations evaluated against many proposed updates,
+ * kt_ratio_cache_build stores, for every walker and kept state, the normalised
+ * forward state after each operator and the backward state from beta down to each
+ * operator, with their log-weights. kt_trace_ratio_cached then propagates only the
+ * window that an update edits: from the cached forward state before its first
+ * changed operator to the cached backward state after its last one, split in the
+ * middle. Results, per-walker statuses and tolerances are those of kt_trace_ratio
+ * (the values differ by rounding only); the cache is only read. The batch passed to
+ * kt_trace_ratio_cached must hold the configurations of the last build (the library
+ * does not check this). Walkers longer than max_ops operators, before or after their
+ * update, are evaluated from scratch.
+ * Device memory: 2 * n_walkers * n_kept * (max_ops + 1) * (d_max * element size + 20)
+ * bytes plus a kt_trace workspace; errors KT_EINVAL (bad arguments, n != n_walkers),
+ * KT_ENOMEM, KT_ECUDA. Calls are enqueued on the stream; build and ratio calls on one
+ * cache must not overlap.
+ */
+typedef struct kt_ratio_cache kt_ratio_cache;
+kt_status kt_ratio_cache_create(kt_model *m, int32_t n_walkers, int32_t max_ops, kt_ratio_cache **out);
+/* DEVICE batch of n_walkers current configurations, layout and validation as kt_trace. */
+kt_status kt_ratio_cache_build(kt_ratio_cache *c, const kt_seq_batch *cur, void *stream);
+kt_status kt_trace_ratio_cached(kt_ratio_cache *c, const kt_seq_batch *cur, const int8_t *cur_sign,
+                                const double *cur_logabs, const kt_move_batch *moves, int8_t *sign,
+                                double *logratio, int32_t *status, kt_stats *stats, void *stream);
+/* No-op on NULL. Not stream-ordered: call it after the cache's work has completed. */
+void kt_ratio_cache_destroy(kt_ratio_cache *c);
+
+/* ------------------------------------------------------------------------ */
 /* Batched CT-HYB Markov chains (Sec. II): Metropolis insertion and removal  */
 /* of c^+/c pairs with the weight of Eq. (weight_strong) for a hybridization */
 /* that is diagonal in the flavors.                                          */

@@ -110,7 +110,8 @@ struct CacheView {
   double2 *sflog, *sblog;
   int32_t *sfblk, *sbblk;
   int32_t *f, *gr;    // [n_items]
-  int4 *plan;         // [n_items] this step: {y, x_new, m, flags}: bit 0 cached, bit 1 unit run
+  int4 *plan;         // [n_items] this step: {y, x_new, m, flags}: bit 0 store states, bit 1 unit run,
+                      // bit 2 cache build (both units cover the whole sequence)
 };
 
 // Cached mode: stretches of at least this many operators are scheduled first.
@@ -159,8 +160,12 @@ int launch_pipeline(const DevModel &m, int precision, int kernel_dmax, int group
 // Krylov items and the reduction. The items use the default lane-group size.
 int launch_cached_pipeline(const DevModel &m, int precision, int kernel_dmax, const SeqView &seq,
                            const MoveView &moves, const int8_t *cur_sign, const double *cur_logabs, int8_t *sign,
-                           double *logv, int32_t *status, const Workspace &ws, const CacheView &cache, kt_stats *stats,
-                           void *stream);
+                           double *logv, int32_t *status, const Workspace &ws, const CacheView &cache, bool write,
+                           kt_stats *stats, void *stream);
+// Store every forward and backward state of the current configurations (plan flags
+// bit 2: whole sequences, no overlap) and mark them valid.
+int launch_cache_build(const DevModel &m, int precision, int kernel_dmax, const SeqView &seq, const Workspace &ws,
+                       const CacheView &cache, void *stream);
 
 // Tensor-core GEMM C = A . B^T (BF16 in, FP32 out) and the surrogate network's
 // forward pass (kt_mlp.cu), for the delayed-acceptance sweep.

@@ -1128,6 +1128,7 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
     // backward, steps s = 0 .. x-m-1 take op i = x-1-s: the interval down to it, then
     // its adjoint; a last step without op takes the interval down to op m-1.
     const bool fwd = half == 0;
+    const bool build = (pl.w & 4) != 0;  // cache build: each half covers the whole sequence
     const int start = fwd ? y : x;
     const bool from_kept = fwd ? (y == 0) : (x == Kn);
     double t = fwd ? (y == 0 ? 0.0 : cur.get(y - 1).t) : (x == Kn ? M.beta : cur.get(x).t);
@@ -1143,8 +1144,8 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
       vanished = !load_entry(M, (const VT *)(fwd ? C.fvec : C.bvec), fwd ? C.flog : C.blog, fwd ? C.fblk : C.bblk,
                              eb + (fwd ? start : Kn - start), dv, u);
     }
-    const int n_ops = fwd ? m - y : x - m;
-    const int n_steps = fwd ? n_ops : n_ops + 1;
+    const int n_ops = build ? Kn : (fwd ? m - y : x - m);
+    const int n_steps = fwd || build ? n_ops : n_ops + 1;
     const double tf = m >= 1 ? cur.get(m - 1).t : 0.0;
     for (int s = 0; s < n_steps; ++s) {
       const bool has_op = s < n_ops;
@@ -1164,7 +1165,7 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
       if (has_op && cached) {
         // forward slot i+1 / backward reverse slot K-i; outside the window the state is
         // valid for the current configuration too and goes to the cache itself
-        const bool out = fwd ? i + 1 <= lo : i >= hi;
+        const bool out = build || (fwd ? i + 1 <= lo : i >= hi);
         const size_t e = eb + (fwd ? i + 1 : Kn - i);
         VT *vec = (VT *)(fwd ? (out ? C.fvec : C.sfvec) : (out ? C.bvec : C.sbvec));
         double2 *lg = fwd ? (out ? C.flog : C.sflog) : (out ? C.blog : C.sblog);
@@ -1172,50 +1173,52 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
         store_entry(vec, lg, bk, e, dv, u, vanished);
       }
     }
-    // publish this half; the second to finish forms the overlap
-    const int hslot = 2 * item + half;
-    if (!vanished) {
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int r = gl + G * j;
-        if (r < u.dim) hvec[(size_t)hslot * vstride + r] = u.Q(0, r);
-      }
-    }
-    const double Lh = vanished ? 0.0 : u.Ladd - u.Linv.log_value();
-    if (gl == 0) {
-      ws.half_log[hslot] = Lh;
-      ws.half_info[hslot] = vanished ? -1 : (u.b | (u.status << 24));
-    }
-    __threadfence();
-    __syncwarp(gm);
-    int old = 0;
-    if (gl == 0) old = atomicAdd(&ws.pair_flag[item], 1);
-    old = __shfl_sync(gm, old, grp * G);
-    if (old == 1) {
-      __threadfence();
-      const int oslot = 2 * item + (1 - half);
-      const int oinfo = __ldcg(ws.half_info + oslot);
-      const double Lo = __ldcg(ws.half_log + oslot);
-      bool zero = vanished || oinfo < 0 || (oinfo & 0xffffff) != u.b;
-      double ov = 0.0;
-      if (!zero) {
-        GroupDot<VT, G> d;
+    // publish this half; the second to finish forms the overlap (not for a build)
+    if (!build) {
+      const int hslot = 2 * item + half;
+      if (!vanished) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           const int r = gl + G * j;
-          if (r < u.dim) d.add(u.Q(0, r), __ldcg(hvec + (size_t)oslot * vstride + r));
+          if (r < u.dim) hvec[(size_t)hslot * vstride + r] = u.Q(0, r);
         }
-        ov = d.value(gm);
-        zero = (ov == 0.0);
       }
-      int st = u.status;
-      if (oinfo >= 0 && (oinfo >> 24) > st) st = oinfo >> 24;
-      const double L = Lh + Lo + (zero ? 0.0 : log(fabs(ov)));
-      if (!zero && !isfinite(L)) st = KT_ENUMERIC;
+      const double Lh = vanished ? 0.0 : u.Ladd - u.Linv.log_value();
       if (gl == 0) {
-        ws.item_sign[item] = zero ? 0 : (ov > 0.0 ? 1 : -1);
-        ws.item_log[item] = zero ? -INFINITY : L;
-        ws.item_status[item] = st;
+        ws.half_log[hslot] = Lh;
+        ws.half_info[hslot] = vanished ? -1 : (u.b | (u.status << 24));
+      }
+      __threadfence();
+      __syncwarp(gm);
+      int old = 0;
+      if (gl == 0) old = atomicAdd(&ws.pair_flag[item], 1);
+      old = __shfl_sync(gm, old, grp * G);
+      if (old == 1) {
+        __threadfence();
+        const int oslot = 2 * item + (1 - half);
+        const int oinfo = __ldcg(ws.half_info + oslot);
+        const double Lo = __ldcg(ws.half_log + oslot);
+        bool zero = vanished || oinfo < 0 || (oinfo & 0xffffff) != u.b;
+        double ov = 0.0;
+        if (!zero) {
+          GroupDot<VT, G> d;
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const int r = gl + G * j;
+            if (r < u.dim) d.add(u.Q(0, r), __ldcg(hvec + (size_t)oslot * vstride + r));
+          }
+          ov = d.value(gm);
+          zero = (ov == 0.0);
+        }
+        int st = u.status;
+        if (oinfo >= 0 && (oinfo >> 24) > st) st = oinfo >> 24;
+        const double L = Lh + Lo + (zero ? 0.0 : log(fabs(ov)));
+        if (!zero && !isfinite(L)) st = KT_ENUMERIC;
+        if (gl == 0) {
+          ws.item_sign[item] = zero ? 0 : (ov > 0.0 ? 1 : -1);
+          ws.item_log[item] = zero ? -INFINITY : L;
+          ws.item_status[item] = st;
+        }
       }
     }
     if (gl == 0 && stats) {

@@ -151,8 +151,10 @@ __global__ void prune_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, 
 // before the window), the backward unit at op x with x the first position at or
 // after the window whose backward state is valid; they meet at m, the middle of
 // [y, x]. Walkers longer than the cache (before or after the edit) use y = 0,
-// x = K_new without writing states.
-__global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, CacheView C, kt_stats *stats) {
+// x = K_new without writing states. write = 0: the cache is only read (no state of
+// this call is stored).
+__global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, CacheView C, int write,
+                            kt_stats *stats) {
   const int item = blockIdx.x * blockDim.x + threadIdx.x;
   const int nk = M.n_kept;
   if (item >= S.n * nk) return;
@@ -183,7 +185,7 @@ __global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, Ca
     x = x_old + (Kn - Ko);
   }
   const int m = y + (x - y) / 2;
-  C.plan[item] = make_int4(y, x, m, (cached ? 1 : 0) | (alive ? 2 : 0));
+  C.plan[item] = make_int4(y, x, m, (cached && write ? 1 : 0) | (alive ? 2 : 0));
   if (alive) {
     // longest stretches first: they bound the launch, the short ones fill in around them
     atomicAdd(&ws.counters[0], 1);
@@ -196,6 +198,27 @@ __global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, Ca
   if (stats) {
     atomicAdd(&stats->items, 1ull);
     if (alive) atomicAdd(&stats->items_alive, 1ull);
+  }
+}
+
+// Cache build for the current configurations: every (walker, kept state) item of a
+// walker within the cache length gets a forward unit over all its operators and a
+// backward unit over all of them, storing every state (zero states included, so that
+// a later edit that revives the item finds its prefix and suffix).
+__global__ void build_plan_kernel(DevModel M, SeqView S, Workspace ws, CacheView C) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nk = M.n_kept;
+  if (item >= S.n * nk) return;
+  const int w = item / nk;
+  ws.pair_flag[item] = 0;
+  const int K = ws.desc[w].w;
+  const bool ok = ws.wstatus[w] == KT_OK && K <= C.P;
+  C.f[item] = ok ? K : 0;
+  C.gr[item] = ok ? K : 0;
+  C.plan[item] = make_int4(0, K, 0, ok ? 1 | 2 | 4 : 0);
+  if (ok) {
+    atomicAdd(&ws.counters[0], 1);
+    ws.worklist[atomicAdd(&ws.counters[2], 1)] = item;
   }
 }
 
@@ -349,13 +372,14 @@ int launch_pipeline(const DevModel &M, int precision, int kd, int G, const SeqVi
 
 int launch_cached_pipeline(const DevModel &M, int precision, int kd, const SeqView &S, const MoveView &mv,
                            const int8_t *cur_sign, const double *cur_logabs, int8_t *sign, double *logv,
-                           int32_t *status, const Workspace &ws, const CacheView &C, kt_stats *stats, void *stream) {
+                           int32_t *status, const Workspace &ws, const CacheView &C, bool write, kt_stats *stats,
+                           void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int n = S.n;
   cudaGetLastError();
   prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, mv, 1, cur_sign, ws, stats);
   const long long items = (long long)n * M.n_kept;
-  if (items > 0) plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, ws, C, stats);
+  if (items > 0) plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, ws, C, write ? 1 : 0, stats);
   int rc = (int)cudaGetLastError();
   if (rc) return rc;
   if (items > 0) {
@@ -364,6 +388,23 @@ int launch_cached_pipeline(const DevModel &M, int precision, int kd, const SeqVi
     if (rc) return rc;
   }
   reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, 1, cur_sign, cur_logabs, ws, sign, logv, status);
+  return (int)cudaGetLastError();
+}
+
+int launch_cache_build(const DevModel &M, int precision, int kd, const SeqView &S, const Workspace &ws,
+                       const CacheView &C, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = S.n;
+  cudaGetLastError();
+  prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, MoveView{}, 0, nullptr, ws, nullptr);
+  const long long items = (long long)n * M.n_kept;
+  if (items == 0) return (int)cudaGetLastError();
+  build_plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, ws, C);
+  int rc = (int)cudaGetLastError();
+  if (rc) return rc;
+  rc = (precision == KT_FP64) ? dispatch_items_cached_f64(kd, M, S, MoveView{}, ws, C, nullptr, st)
+                              : dispatch_items_cached_f32(kd, M, S, MoveView{}, ws, C, nullptr, st);
+  if (rc) return rc;
   return (int)cudaGetLastError();
 }
 

@@ -1002,7 +1002,7 @@ static kt_status run_steps(kt_sweep *s, int32_t n_steps, const double *uniforms,
     }
     if (s->cache_mem) {
       if (kt::launch_cached_pipeline(M, s->mv.precision, s->mv.kernel_dmax, sv, mvv, v.tr_sign, v.tr_log, v.r_sign,
-                                     v.r_log, v.r_status, w, s->cache, s->stats, st) != 0)
+                                     v.r_log, v.r_status, w, s->cache, true, s->stats, st) != 0)
         return KT_ECUDA;
     } else if (kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, sv, &mvv, v.tr_sign,
                                    v.tr_log, v.r_sign, v.r_log, v.r_status, s->stats, w, st, nullptr) != 0) {

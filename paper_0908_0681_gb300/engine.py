@@ -123,6 +123,29 @@ def trace_ratio(model: kt.KtModel, seqs: DeviceSeqs, cur_sign: torch.Tensor, cur
     return sign, lr, st
 
 
+class RatioCache:
+    """Partial-state cache of fixed current configurations (kt_ratio_cache_*): build it once
+    for a batch, then evaluate trace ratios of updates against those configurations by
+    propagating only each update's edited window."""
+
+    def __init__(self, model: kt.KtModel, n_walkers: int, max_ops: int = 512):
+        self.h = kt.KtRatioCache(model, n_walkers, max_ops)
+
+    def build(self, seqs: DeviceSeqs) -> None:
+        kt.kt_ratio_cache_build(self.h, seqs.batch())
+
+    def ratio(self, seqs: DeviceSeqs, cur_sign: torch.Tensor, cur_logabs: torch.Tensor, moves: DeviceMoves,
+              out=None, stats: torch.Tensor | None = None):
+        """(sign int8, log|ratio| float64, status int32) device tensors, as trace_ratio."""
+        n = seqs.n
+        dev = seqs.offsets.device
+        if out is None:
+            out = (torch.empty(n, dtype=torch.int8, device=dev), torch.empty(n, dtype=torch.float64, device=dev),
+                   torch.empty(n, dtype=torch.int32, device=dev))
+        kt.kt_trace_ratio_cached(self.h, seqs.batch(), cur_sign, cur_logabs, moves.batch(), *out, stats)
+        return out
+
+
 def binning_analysis(x) -> dict:
     """Standard error of the mean of correlated measurements by binning.
 

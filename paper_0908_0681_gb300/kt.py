@@ -84,7 +84,8 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_sweep_set_configs", "kt_gemm_bf16", "kt_mlp_create", "kt_mlp_num_params",
                  "kt_mlp_set_params", "kt_mlp_get_params", "kt_mlp_forward", "kt_mlp_backward", "kt_mlp_get_grads",
                  "kt_mlp_adam", "kt_mlp_error", "kt_mlp_destroy", "kt_sweep_feature_size", "kt_sweep_collect",
-                 "kt_sweep_set_surrogate", "kt_sweep_run_da", "kt_sweep_set_stats"]
+                 "kt_sweep_set_surrogate", "kt_sweep_run_da", "kt_sweep_set_stats", "kt_ratio_cache_create",
+                 "kt_ratio_cache_build", "kt_trace_ratio_cached", "kt_ratio_cache_destroy"]
 
 KT_SWEEP_NCOUNTERS = 10
 KT_MLP_HIDDEN = 256
@@ -142,6 +143,12 @@ def load():
     lib.kt_sweep_set_surrogate.argtypes = [vp, vp]
     lib.kt_sweep_run_da.argtypes = [vp, i32, vp, i32, vp]
     lib.kt_sweep_set_stats.argtypes = [vp, vp]
+    lib.kt_ratio_cache_create.argtypes = [vp, i32, i32, ctypes.POINTER(vp)]
+    lib.kt_ratio_cache_build.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp]
+    lib.kt_trace_ratio_cached.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
+                                          vp, vp, vp, vp, vp]
+    lib.kt_ratio_cache_destroy.argtypes = [vp]
+    lib.kt_ratio_cache_destroy.restype = None
     lib.kt_sweep_get_state.argtypes = [vp, ctypes.POINTER(kt_sweep_state), vp]
     lib.kt_sweep_get_accumulators.argtypes = [vp, ctypes.POINTER(kt_sweep_accum), vp]
     lib.kt_sweep_counters.argtypes = [vp, vp]
@@ -156,7 +163,8 @@ def load():
                                 ctypes.POINTER(ctypes.c_int32)]
     lib.kt_timing_end.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
     for f in ABI_FUNCTIONS:
-        if f not in ("kt_status_string", "kt_model_destroy", "kt_sweep_destroy", "kt_mlp_destroy"):
+        if f not in ("kt_status_string", "kt_model_destroy", "kt_sweep_destroy", "kt_mlp_destroy",
+                     "kt_ratio_cache_destroy"):
             getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -311,6 +319,35 @@ class KtSweep:
         if h is not None and _lib is not None:
             _lib.kt_sweep_destroy(h)
             self.handle = None
+
+
+class KtRatioCache:
+    """Owning handle of a kt_ratio_cache (destroyed with the object); keeps its model alive."""
+
+    def __init__(self, model: KtModel, n_walkers: int, max_ops: int):
+        self.model = model
+        h = ctypes.c_void_p()
+        _check(load().kt_ratio_cache_create(model.handle, int(n_walkers), int(max_ops), ctypes.byref(h)),
+               "kt_ratio_cache_create")
+        self.handle = h
+        self.n_walkers, self.max_ops = int(n_walkers), int(max_ops)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.kt_ratio_cache_destroy(h)
+            self.handle = None
+
+
+def kt_ratio_cache_build(c: KtRatioCache, batch: kt_seq_batch, stream=None) -> None:
+    _check(load().kt_ratio_cache_build(c.handle, ctypes.byref(batch), _stream_handle(stream)), "kt_ratio_cache_build")
+
+
+def kt_trace_ratio_cached(c: KtRatioCache, cur: kt_seq_batch, cur_sign, cur_logabs, moves: kt_move_batch, sign,
+                          logratio, status, stats=None, stream=None) -> None:
+    _check(load().kt_trace_ratio_cached(c.handle, ctypes.byref(cur), _ptr(cur_sign), _ptr(cur_logabs),
+                                        ctypes.byref(moves), _ptr(sign), _ptr(logratio), _ptr(status), _ptr(stats),
+                                        _stream_handle(stream)), "kt_trace_ratio_cached")
 
 
 def kt_sweep_set_stats(s: KtSweep, stats) -> None:

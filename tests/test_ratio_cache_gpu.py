@@ -1,0 +1,155 @@
+"""Trace ratios from cached partial states (kt_ratio_cache_*) against the oracle and
+against the from-scratch kt_trace_ratio, element by element.
+
+One build of the cache serves several rounds of proposed updates against the same
+current configurations. The cached ratio propagates only the edited window between
+cached states, so it is the same trace ratio up to rounding: the oracle bars of the
+parity tests apply (1e-10 relative FP64, 1e-5 FP32, structural zeros exact), and the
+two GPU evaluations differ by at most the sum of their errors. A short cache length
+(24 operators) makes most walkers fall back to the full evaluation.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0908_0681_gb300 import engine, kt, workloads  # noqa: E402
+from tests import parity  # noqa: E402
+
+PRECS = [kt.KT_FP64, kt.KT_FP32_KRYLOV]
+PAIR_TOL = {kt.KT_FP64: 2e-10, kt.KT_FP32_KRYLOV: 2e-5}
+
+
+def dev(a, dt):
+    return torch.as_tensor(np.asarray(a, dt), device="cuda")
+
+
+def both_ratios(model, seqs, cur_s, cur_l, moves_list, max_ops):
+    d = engine.DeviceSeqs.from_host(seqs)
+    cache = engine.RatioCache(model, seqs.n, max_ops)
+    cache.build(d)
+    cs, cl = dev(cur_s, np.int8), dev(cur_l, np.float64)
+    out = []
+    for mv in moves_list:
+        dm = engine.DeviceMoves.from_host(mv)
+        c = [t.cpu().numpy() for t in cache.ratio(d, cs, cl, dm)]
+        f = [t.cpu().numpy() for t in engine.trace_ratio(model, d, cs, cl, dm)]
+        out.append((c, f))
+    return out
+
+
+def check_round(w, seqs, o64, ox, cls, sx, lx, prec, mv, cached, full, label):
+    cur_s = np.where(cls == 2, sx, 0).astype(np.int8)
+    reg = cls == 2
+    cs, cl, cst = cached
+    fs, fl, fst = full
+    assert (cst[reg] == kt.KT_OK).all() and (fst[reg] == kt.KT_OK).all(), label
+    assert (cst[~reg] == kt.KT_EZEROWEIGHT).all(), label
+    ncls, nsx, nlx = parity.oracle_ratios(o64, ox, seqs, cur_s, lx, mv)
+    both = reg & (ncls == 2)
+    assert (cs[both] == fs[both]).all(), label
+    d = np.abs(cl[both] - fl[both])
+    assert d.max(initial=0.0) <= PAIR_TOL[prec], (label, float(d.max(initial=0.0)))
+    zero = reg & (ncls == 0)
+    assert (cs[zero] == 0).all() and (fs[zero] == 0).all(), label
+    idx = np.nonzero(reg)[0]
+    parity.compare(ncls[idx], nsx[idx] * cur_s[idx], nlx[idx] - lx[idx], cs[idx], cl[idx], prec, ox.nkept,
+                   w.model.beta * ox.E0 + lx[idx], label)
+
+
+@pytest.fixture(scope="module")
+def three():
+    w = workloads.three_orbital()
+    seqs = workloads.generate_sequences(w, 600, seed=5)
+    o64, ox = parity.oracle_pair(w.model)
+    cls, sx, lx = parity.oracle_traces(o64, ox, seqs)
+    return w, seqs, o64, ox, cls, sx, lx
+
+
+@pytest.fixture(scope="module")
+def five():
+    w = workloads.five_orbital()
+    seqs = workloads.generate_sequences(w, 192, seed=6)
+    o64, ox = parity.oracle_pair(w.model)
+    cls, sx, lx = parity.oracle_traces(o64, ox, seqs)
+    return w, seqs, o64, ox, cls, sx, lx
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("max_ops", [512, 24])
+def test_three_orbital_cached_ratios(three, prec, max_ops):
+    w, seqs, o64, ox, cls, sx, lx = three
+    m = engine.model_from_spec(w.model, precision=prec)
+    cur_s = np.where(cls == 2, sx, 0).astype(np.int8)
+    moves = [workloads.generate_moves(w, seqs, seed=900 + r) for r in range(3)]
+    for r, (c, f) in enumerate(both_ratios(m, seqs, cur_s, lx, moves, max_ops)):
+        check_round(w, seqs, o64, ox, cls, sx, lx, prec, moves[r], c, f, f"3-orbital round {r} cache {max_ops}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_five_orbital_cached_ratios(five, prec):
+    w, seqs, o64, ox, cls, sx, lx = five
+    m = engine.model_from_spec(w.model, precision=prec)
+    cur_s = np.where(cls == 2, sx, 0).astype(np.int8)
+    moves = [workloads.generate_moves(w, seqs, seed=950 + r) for r in range(2)]
+    for r, (c, f) in enumerate(both_ratios(m, seqs, cur_s, lx, moves, 512)):
+        check_round(w, seqs, o64, ox, cls, sx, lx, prec, moves[r], c, f, f"5-orbital round {r}")
+
+
+def test_cached_window_edge_cases(five):
+    """Updates whose window touches the ends of the sequence: an insertion that wraps
+    around beta, insertions at the very start and end, the removal of two adjacent
+    operators (an empty window), and a removal that wraps (the pair's second operator
+    is the first of the sequence)."""
+    w, seqs, o64, ox, cls, sx, lx = five
+    b = w.model.beta
+    m = engine.model_from_spec(w.model, precision=kt.KT_FP64)
+    mv = workloads.generate_moves(w, seqs, seed=977)
+    n = seqs.n
+    for i in range(n):
+        tau, fl, dg = seqs.walker(i)
+        case = i % 5
+        f = int(fl[0]) if len(fl) else 0
+        if case == 0:    # wrapping insertion
+            mv.kind[i], mv.flavor[i], mv.t_dag[i], mv.t_ann[i] = 0, f, b - 1e-3, 1e-3
+        elif case == 1:  # both operators before the first existing one
+            t0 = tau[0] if len(tau) else b
+            mv.kind[i], mv.flavor[i], mv.t_dag[i], mv.t_ann[i] = 0, f, 0.25 * t0, 0.5 * t0
+        elif case == 2:  # both after the last one
+            t1 = tau[-1] if len(tau) else 0.0
+            mv.kind[i], mv.flavor[i], mv.t_dag[i], mv.t_ann[i] = 0, f, t1 + 0.5 * (b - t1), t1 + 0.25 * (b - t1)
+        elif case == 3:  # adjacent pair
+            adj = [j for j in range(len(fl) - 1) if fl[j] == fl[j + 1] and dg[j] != dg[j + 1]]
+            if adj:
+                mv.kind[i], mv.flavor[i], mv.rem_idx[i] = 1, int(fl[adj[0]]), adj[0]
+        else:            # the last operator of a flavor with its cyclic successor (wraps)
+            g = int(fl[-1])
+            last = max(j for j in range(len(fl)) if fl[j] == g)
+            firsts = [j for j in range(len(fl)) if fl[j] == g]
+            if len(firsts) >= 2 and dg[firsts[0]] != dg[last]:
+                mv.kind[i], mv.flavor[i], mv.rem_idx[i] = 1, g, last
+    cur_s = np.where(cls == 2, sx, 0).astype(np.int8)
+    (c, f), = both_ratios(m, seqs, cur_s, lx, [mv], 512)
+    check_round(w, seqs, o64, ox, cls, sx, lx, kt.KT_FP64, mv, c, f, "window edge cases")
+
+
+def test_rebuild_for_new_configurations(three):
+    """One cache object rebuilt for other configurations gives their ratios."""
+    w, seqs, o64, ox, cls, sx, lx = three
+    m = engine.model_from_spec(w.model, precision=kt.KT_FP64)
+    cache = engine.RatioCache(m, 200, 512)
+    for part in (range(0, 200), range(200, 400)):
+        sub = seqs.subset(list(part))
+        c_sub, s_sub, l_sub = cls[list(part)], sx[list(part)], lx[list(part)]
+        d = engine.DeviceSeqs.from_host(sub)
+        cache.build(d)
+        mv = workloads.generate_moves(w, sub, seed=31)
+        cur_s = np.where(c_sub == 2, s_sub, 0).astype(np.int8)
+        res = [t.cpu().numpy() for t in cache.ratio(d, dev(cur_s, np.int8), dev(l_sub, np.float64),
+                                                      engine.DeviceMoves.from_host(mv))]
+        full = [t.cpu().numpy() for t in engine.trace_ratio(m, d, dev(cur_s, np.int8), dev(l_sub, np.float64),
+                                                             engine.DeviceMoves.from_host(mv))]
+        check_round(w, sub, o64, ox, c_sub, s_sub, l_sub, kt.KT_FP64, mv, res, full, "rebuild")
