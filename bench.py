@@ -558,7 +558,9 @@ def main():
     ms32, stage32, nl32 = timed_loop(m32, cur32, a.steps, a.warmup)
     clocks = sampler.stop()
     if st_bad := int((out_st != 0).sum().item()):
-        print(f"warning: {st_bad} walkers with non-OK status in the last step", file=sys.stderr)
+        vals, cnts = torch.unique(out_st, return_counts=True)
+        hist = {kt.status_name(int(v)): int(c) for v, c in zip(vals.tolist(), cnts.tolist())}
+        print(f"warning: {st_bad} walkers with non-OK status in the last step: {hist}", file=sys.stderr)
 
     K64 = a.fp64_steps if a.fp64_steps > 0 else min(a.steps, 100)
     ms64, stage64, _ = timed_loop(m64, cur64, K64, a.warmup)

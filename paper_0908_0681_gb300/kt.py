@@ -17,6 +17,14 @@ import numpy as np
 from . import build as _build
 
 KT_OK, KT_EINVAL, KT_ENOMEM, KT_ECUDA, KT_ENOCONV, KT_ENUMERIC, KT_EZEROWEIGHT, KT_ETIMEOUT, KT_EUNSUPPORTED = range(9)
+STATUS_NAMES = ["KT_OK", "KT_EINVAL", "KT_ENOMEM", "KT_ECUDA", "KT_ENOCONV", "KT_ENUMERIC", "KT_EZEROWEIGHT",
+                "KT_ETIMEOUT", "KT_EUNSUPPORTED"]
+
+
+def status_name(code: int) -> str:
+    return STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else f"status {code}"
+
+
 KT_FP64, KT_FP32_KRYLOV = 0, 1
 KT_DENSITY_ONLY, KT_SECTOR_BLOCKS, KT_HOST_ONLY = 1, 2, 256
 

@@ -326,3 +326,29 @@ def test_seven_orbital_energy_window_1e4():
     assert (rst[idx] == kt.KT_OK).all()
     parity.compare(ncls[idx], nsx[idx] * cur_s[idx], nlx[idx] - lx[idx], rs[idx], rl[idx], kt.KT_FP32_KRYLOV,
                    ox.nkept, w.model.beta * ox.E0 + lx[idx], "7-orbital 1e-4 ratios")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_repeated_evaluations_are_bitwise_identical(prec):
+    """The full five-orbital batch (4,096 walkers) evaluated four times, with other work
+    between the calls: signs, log-ratios and statuses must be bit for bit the same (no
+    result may depend on which unit of an item finishes first or on what a warp slot held
+    before)."""
+    w = workloads.five_orbital()
+    seqs = workloads.generate_sequences(w, 4096, seed=1)
+    m = engine.model_from_spec(w.model, precision=prec)
+    d = engine.DeviceSeqs.from_host(seqs)
+    cs, cl, cst = engine.trace(m, d)
+    assert int((cst != 0).sum()) == 0
+    mv = engine.DeviceMoves.from_host(workloads.generate_moves(w, seqs, seed=1003))
+    ref = None
+    for k in range(4):
+        if k % 2:
+            engine.trace(m, engine.DeviceSeqs.from_host(seqs.subset(list(range(0, 4096, 3)))))
+        out = [t.cpu().numpy() for t in engine.trace_ratio(m, d, cs, cl, mv)]
+        if ref is None:
+            ref = out
+            assert (out[2] == kt.KT_OK).all(), np.unique(out[2], return_counts=True)
+        else:
+            for a, b in zip(ref, out):
+                assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), k
