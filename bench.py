@@ -565,6 +565,35 @@ def main():
     K64 = a.fp64_steps if a.fp64_steps > 0 else min(a.steps, 100)
     ms64, stage64, _ = timed_loop(m64, cur64, K64, a.warmup)
 
+    # Latency floor: the walkers with the longest edited sequences of the last timed round,
+    # each evaluated alone (a batch of one: no other work on the GPU). The batch cannot finish
+    # before its longest unit, so single_ms bounds items_ms from below.
+    r_last = (a.warmup + a.steps - 1) % n_rounds
+    lens = np.diff(seqs.offsets) + np.where(moves[r_last].kind == 0, 2, -2)
+    longest = np.argsort(-lens, kind="stable")[:4]
+    single = []
+    for i in longest:
+        s1 = engine.DeviceSeqs.from_host(seqs.subset([int(i)]), dev)
+        m1 = engine.DeviceMoves.from_host(moves[r_last].subset([int(i)]), dev)
+        c1 = (cur32[0][int(i):int(i) + 1].contiguous(), cur32[1][int(i):int(i) + 1].contiguous())
+        o1 = (torch.empty(1, dtype=torch.int8, device=dev), torch.empty(1, dtype=torch.float64, device=dev),
+              torch.empty(1, dtype=torch.int32, device=dev))
+        w1 = engine.workspace(m32, 1, dev)
+        ts = []
+        for k in range(12):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            kt.kt_trace_ratio(m32, s1.batch(), c1[0], c1[1], m1.batch(), *o1, None, w1, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 2:
+                ts.append(e0.elapsed_time(e1))
+        single.append(float(np.median(ts)))
+    latency_floor = {"longest_edited_lengths": [int(lens[i]) for i in longest], "single_walker_ms": single,
+                     "items_ms_per_launch": stage32["items"] / max(nl32, 1),
+                     "step_ms": sum(ms32) / a.steps,
+                     "step_over_longest_single": (sum(ms32) / a.steps) / max(single)}
+
     # Ratios from cached partial states of the same fixed configurations (kt_ratio_cache):
     # the build stores every forward and backward state once (timed apart); each step
     # then propagates only the window that its update edits.
@@ -718,6 +747,7 @@ def main():
                      "mean_krylov_dim_fp64": st64["krylov_iters"] / max(st64["intervals"], 1)},
             "roofline": roofline,
             "cached_ratio": cached_ratio,
+            "latency_floor": latency_floor,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "sweep": sweep,

@@ -208,6 +208,10 @@ class Moves:
     def as_dict(self):
         return {"kind": self.kind, "flavor": self.flavor, "t_dag": self.t_dag, "t_ann": self.t_ann, "rem_idx": self.rem_idx}
 
+    def subset(self, idx) -> "Moves":
+        idx = np.asarray(idx, dtype=np.int64)
+        return Moves(self.kind[idx], self.flavor[idx], self.t_dag[idx], self.t_ann[idx], self.rem_idx[idx])
+
 
 def generate_moves(w: Workload, seqs: Sequences, seed: int) -> Moves:
     """One proposed local update per walker."""
