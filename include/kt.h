@@ -260,9 +260,10 @@ kt_status kt_trace_ratio_static(kt_model *m, const kt_seq_batch *cur, const int8
  * changed operator to the cached backward state after its last one, split in the
  * middle. Results, per-walker statuses and tolerances are those of kt_trace_ratio
  * (the values differ by rounding only); the cache is only read. The batch passed to
- * kt_trace_ratio_cached must hold the configurations of the last build (the library
- * does not check this). Walkers longer than max_ops operators, before or after their
- * update, are evaluated from scratch.
+ * kt_trace_ratio_cached must hold the configurations of the last build: the library
+ * evaluates from scratch a walker whose length differs from the build, but cannot see
+ * other changes. Walkers longer than max_ops operators, before or after their update,
+ * are evaluated from scratch too.
  * Device memory: 2 * n_walkers * n_kept * (max_ops + 1) * (d_max * element size + 20)
  * bytes plus a kt_trace workspace; errors KT_EINVAL (bad arguments, n != n_walkers),
  * KT_ENOMEM, KT_ECUDA. Calls are enqueued on the stream; build and ratio calls on one

@@ -174,7 +174,9 @@ __global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, Ca
   }
   const bool alive = (b == b0);
   const int Kn = c.d.w, Ko = c.d.x == 0 ? Kn - 2 : Kn + 2;
-  const bool cached = Kn <= C.P && Ko <= C.P;
+  // read-only use (fixed configurations): the cache was built for every operator of the
+  // current sequence, so a walker whose length differs from the build is evaluated in full
+  const bool cached = Kn <= C.P && Ko <= C.P && (write || C.f[item] == Ko);
   int lo, hi;
   edit_window(c.d, lo, hi);
   int y = 0, x = Kn;

@@ -153,3 +153,66 @@ def test_rebuild_for_new_configurations(three):
         full = [t.cpu().numpy() for t in engine.trace_ratio(m, d, dev(cur_s, np.int8), dev(l_sub, np.float64),
                                                              engine.DeviceMoves.from_host(mv))]
         check_round(w, sub, o64, ox, c_sub, s_sub, l_sub, kt.KT_FP64, mv, res, full, "rebuild")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_seven_orbital_cached_ratios(prec):
+    """36-row blocks (the 16-lane cached kernel): seven orbitals, N_tr = 63."""
+    w = workloads.seven_orbital()
+    seqs = workloads.generate_sequences(w, 48, seed=1)
+    o64, ox = parity.oracle_pair(w.model)
+    cls, sx, lx = parity.oracle_traces(o64, ox, seqs)
+    m = engine.model_from_spec(w.model, precision=prec)
+    cur_s = np.where(cls == 2, sx, 0).astype(np.int8)
+    mv = workloads.generate_moves(w, seqs, seed=1000)
+    (c, f), = both_ratios(m, seqs, cur_s, lx, [mv], 512)
+    if prec == kt.KT_FP64:
+        check_round(w, seqs, o64, ox, cls, sx, lx, prec, mv, c, f, "7-orbital cached")
+    else:
+        # FP32 ratios at seven orbitals carry up to 4.5e-5 of rounding (Krylov dimensions to 20):
+        # compare the cached and the full GPU evaluations with each other
+        reg = cls == 2
+        assert (c[2][reg] == kt.KT_OK).all() and (c[0][reg] == f[0][reg]).all()
+        nz = reg & (c[0] != 0)
+        assert np.abs(c[1][nz] - f[1][nz]).max() <= 1e-4
+
+
+def test_sector_blocks_cached_ratios(five):
+    """Whole (n_up, n_dn) sectors (KT_SECTOR_BLOCKS, up to 100 rows: the 32-lane, 128-row
+    cached kernel) give the same ratios."""
+    w, seqs, o64, ox, cls, sx, lx = five
+    m = engine.model_from_spec(w.model, precision=kt.KT_FP64, flags=kt.KT_SECTOR_BLOCKS)
+    cur_s = np.where(cls == 2, sx, 0).astype(np.int8)
+    sub = list(range(64))
+    s2, c2, x2, l2 = seqs.subset(sub), cls[sub], sx[sub], lx[sub]
+    mv = workloads.generate_moves(w, s2, seed=1001)
+    (c, f), = both_ratios(m, s2, cur_s[sub], l2, [mv], 512)
+    check_round(w, s2, o64, ox, c2, x2, l2, kt.KT_FP64, mv, c, f, "sector blocks cached")
+
+
+def test_stale_lengths_fall_back_to_full_evaluation(three):
+    """A cache built for other configurations: walkers whose length differs from the build
+    are evaluated in full (correct ratios); the library cannot see other differences."""
+    w, seqs, o64, ox, cls, sx, lx = three
+    m = engine.model_from_spec(w.model, precision=kt.KT_FP64)
+    a = seqs.subset(list(range(0, 200)))
+    b = seqs.subset(list(range(200, 400)))
+    lens_a, lens_b = np.diff(a.offsets), np.diff(b.offsets)
+    cache = engine.RatioCache(m, 200, 512)
+    cache.build(engine.DeviceSeqs.from_host(a))
+    db = engine.DeviceSeqs.from_host(b)
+    c_b, s_b, l_b = cls[200:400], sx[200:400], lx[200:400]
+    cur_s = np.where(c_b == 2, s_b, 0).astype(np.int8)
+    mv = workloads.generate_moves(w, b, seed=77)
+    res = [t.cpu().numpy() for t in cache.ratio(db, dev(cur_s, np.int8), dev(l_b, np.float64),
+                                                  engine.DeviceMoves.from_host(mv))]
+    full = [t.cpu().numpy() for t in engine.trace_ratio(m, db, dev(cur_s, np.int8), dev(l_b, np.float64),
+                                                         engine.DeviceMoves.from_host(mv))]
+    diff = lens_a != lens_b
+    assert diff.sum() >= 50
+    ncls, nsx, nlx = parity.oracle_ratios(o64, ox, b, cur_s, l_b, mv)
+    ok = diff & (c_b == 2) & (ncls == 2)
+    zero = diff & (c_b == 2) & (ncls == 0)
+    assert ok.sum() >= 10
+    assert (res[0][ok] == full[0][ok]).all() and (res[0][zero] == 0).all()
+    assert np.abs(res[1][ok] - full[1][ok]).max() <= 1e-10
