@@ -170,7 +170,10 @@ int launch_cache_build(const DevModel &m, int precision, int kernel_dmax, const 
 // Tensor-core GEMM C = A . B^T (BF16 in, FP32 out) and the surrogate network's
 // forward pass (kt_mlp.cu), for the delayed-acceptance sweep.
 int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc, int M, int N, int K, int *err,
-              void *st_);
+              void *st_, int splits = 1);
+// Number of K slices gemm_bf16 uses for `splits` (each slice a multiple of 64 columns); with
+// more than one, slice z writes its partial product to C + z * M * ldc.
+int gemm_splits(int K, int splits);
 int mlp_forward(kt_mlp *n, const void *X, int B, float *y, bool train, void *st_);
 int mlp_inputs(const kt_mlp *n);
 int mlp_max_batch(const kt_mlp *n);

@@ -26,6 +26,7 @@ namespace mlp {
 constexpr int BM = 128;       // rows per CTA (TMEM lanes)
 constexpr int BK = 64;        // K columns per shared-memory stage
 constexpr int MAX_BN = 256;   // accumulator columns
+constexpr int MAX_SPLITS = 16;  // K slices of the weight-gradient products (K = batch)
 constexpr int WAIT_LIMIT = 1 << 21;  // polls of 32+ ns each: the wait gives up after ~0.1-1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,7 +92,7 @@ __device__ __forceinline__ void stage_tile(uint8_t *dst, const __nv_bfloat16 *sr
 
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__restrict__ A, int lda,
                                                         const __nv_bfloat16 *__restrict__ B, int ldb, float *C, int ldc,
-                                                        int M, int N, int K, int BN, int *err) {
+                                                        int M, int N, int K, int BN, int kslice, int *err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *sA = smem;                      // 128 x 64 BF16 = 16 KB
   uint8_t *sB = smem + BM * BK * 2;        // BN x 64 BF16 <= 32 KB
@@ -100,6 +101,12 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__r
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // split K: this CTA reduces over [kb, K) of its slice and writes partial sums to slab z of C
+  const int kb = blockIdx.z * kslice;
+  A += kb;
+  B += kb;
+  C += (size_t)blockIdx.z * M * ldc;
+  K = min(K - kb, kslice);
   const int bn = (N - n0) < BN ? (N - n0) : BN;  // multiple of 16 (N is)
   const uint32_t ncols = 256;                    // power of two >= bn
   const uint32_t mb = smem_u32(&mbar);
@@ -188,8 +195,13 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__r
 }  // namespace mlp
 
 // C = A . B^T; requirements checked by the caller-facing entry point.
+int gemm_splits(int K, int splits) {
+  const int kslice = ((K + splits - 1) / splits + mlp::BK - 1) / mlp::BK * mlp::BK;
+  return (K + kslice - 1) / kslice;
+}
+
 int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc, int M, int N, int K, int *err,
-              void *st_) {
+              void *st_, int splits) {
   cudaStream_t st = (cudaStream_t)st_;
   const int BN = N <= mlp::MAX_BN ? N : 128;
   const size_t smem = (size_t)mlp::BM * mlp::BK * 2 + (size_t)BN * mlp::BK * 2;
@@ -198,9 +210,11 @@ int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc,
     cudaFuncSetAttribute(mlp::gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     attr = true;
   }
-  dim3 grid((unsigned)((M + mlp::BM - 1) / mlp::BM), (unsigned)((N + BN - 1) / BN));
+  // every slice holds at least one 64-column chunk of K (its offset keeps rows 16-byte aligned)
+  const int kslice = ((K + splits - 1) / splits + mlp::BK - 1) / mlp::BK * mlp::BK;
+  dim3 grid((unsigned)((M + mlp::BM - 1) / mlp::BM), (unsigned)((N + BN - 1) / BN), (unsigned)((K + kslice - 1) / kslice));
   mlp::gemm_bf16_kernel<<<grid, 128, smem, st>>>((const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb, C, ldc,
-                                                 M, N, K, BN, err);
+                                                 M, N, K, BN, kslice, err);
   return (int)cudaGetLastError();
 }
 
@@ -290,26 +304,53 @@ __global__ void dz2_kernel(const float *__restrict__ Z2, const float *__restrict
   dZ2T[(size_t)j * B + b] = v;
 }
 
-// column sums over the batch: gw3_j = sum_b dy_b H2_bj, gb2_j = sum_b dZ2_bj (FP32), gb3 = sum_b dy_b
-__global__ void out_grads_kernel(const float *__restrict__ Z2, const float *__restrict__ b2,
-                                 const float *__restrict__ w3, const float *__restrict__ H2,
-                                 const float *__restrict__ dy, float *gw3, float *gb2, float *gb3, int B) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < H) {
-    float a = 0.f, c = 0.f;
-    for (int b = 0; b < B; ++b) {
-      const float d = dy[b];
-      a = fmaf(d, H2[(size_t)b * H + j], a);
-      if (Z2[(size_t)b * H + j] + b2[j] > 0.f) c = fmaf(d, w3[j], c);
-    }
-    gw3[j] = a;
-    gb2[j] = c;
+// Column sums over the batch, gw3_j = sum_b dy_b H2_bj, gb2_j = sum_b dZ2_bj and
+// gb3 = sum_b dy_b (FP32), in two deterministic passes: one block of H threads per chunk
+// of ROWS rows writes the chunk's sums, then one block adds the chunks in order.
+constexpr int ROWS = 128;
+__global__ void out_grads_part_kernel(const float *__restrict__ Z2, const float *__restrict__ b2,
+                                      const float *__restrict__ w3, const float *__restrict__ H2,
+                                      const float *__restrict__ dy, float *pw3, float *pb2, float *pb3, int B) {
+  __shared__ float sh[H];
+  const int c = blockIdx.x, j = threadIdx.x;
+  const int r0 = c * ROWS, r1 = min(B, r0 + ROWS);
+  float a = 0.f, s = 0.f;
+  for (int b = r0; b < r1; ++b) {
+    const float d = dy[b];
+    a = fmaf(d, H2[(size_t)b * H + j], a);
+    if (Z2[(size_t)b * H + j] + b2[j] > 0.f) s = fmaf(d, w3[j], s);
   }
-  if (j == 0) {
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) s += dy[b];
-    gb3[0] = s;
+  pw3[(size_t)c * H + j] = a;
+  pb2[(size_t)c * H + j] = s;
+  sh[j] = (j < ROWS && r0 + j < r1) ? dy[r0 + j] : 0.f;
+  __syncthreads();
+  for (int o = H / 2; o > 0; o >>= 1) {
+    if (j < o) sh[j] += sh[j + o];
+    __syncthreads();
   }
+  if (j == 0) pb3[c] = sh[0];
+}
+__global__ void out_grads_sum_kernel(const float *__restrict__ pw3, const float *__restrict__ pb2,
+                                     const float *__restrict__ pb3, float *gw3, float *gb2, float *gb3, int nc) {
+  const int j = threadIdx.x;
+  float a = 0.f, s = 0.f, t = 0.f;
+  for (int c = 0; c < nc; ++c) {
+    a += pw3[(size_t)c * H + j];
+    s += pb2[(size_t)c * H + j];
+    if (j == 0) t += pb3[c];
+  }
+  gw3[j] = a;
+  gb2[j] = s;
+  if (j == 0) gb3[0] = t;
+}
+
+// Sum of split-K partial products: out[i] = sum over slabs s of part[s n + i], in order.
+__global__ void splitk_sum_kernel(const float *__restrict__ part, float *out, int S, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float a = 0.f;
+  for (int s = 0; s < S; ++s) a += part[(size_t)s * n + i];
+  out[i] = a;
 }
 
 // dZ1 = dH1 masked by relu'(Z1 + b1): BF16 transposed [H][B]; gb1 column sums (FP32)
@@ -321,14 +362,14 @@ __global__ void dz1_kernel(const float *__restrict__ dH1, const float *__restric
   const float d = (Z1[i] + b1[j] > 0.f) ? dH1[i] : 0.f;
   dZ1T[(size_t)j * B + b] = __float2bfloat16_rn(d);
 }
-__global__ void gb1_kernel(const float *__restrict__ dH1, const float *__restrict__ Z1, const float *__restrict__ b1,
-                           float *gb1, int B) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= H) return;
-  float c = 0.f;
-  for (int b = 0; b < B; ++b)
-    if (Z1[(size_t)b * H + j] + b1[j] > 0.f) c += dH1[(size_t)b * H + j];
-  gb1[j] = c;
+__global__ void gb1_part_kernel(const float *__restrict__ dH1, const float *__restrict__ Z1,
+                                const float *__restrict__ b1, float *pb1, int B) {
+  const int c = blockIdx.x, j = threadIdx.x;
+  const int r0 = c * ROWS, r1 = min(B, r0 + ROWS);
+  float s = 0.f;
+  for (int b = r0; b < r1; ++b)
+    if (Z1[(size_t)b * H + j] + b1[j] > 0.f) s += dH1[(size_t)b * H + j];
+  pb1[(size_t)c * H + j] = s;
 }
 
 // Adam (Kingma & Ba 2015, Algorithm 1) on the packed FP32 parameters
@@ -359,6 +400,8 @@ struct kt_mlp {
   __nv_bfloat16 *W1b, *W2b, *W2Tb;
   float *Z1, *Z2, *H2, *dH1, *y, *dy, *loss;
   __nv_bfloat16 *H1b, *H1Tb, *dZ2b, *dZ2Tb, *dZ1Tb, *XTb;
+  float *part;               // split-K slabs of the weight gradients
+  float *pw3, *pb2, *pb3, *pb1;  // per-chunk column sums
   int *err;
 };
 
@@ -413,7 +456,10 @@ kt_status kt_mlp_create(int32_t n_in, int32_t max_batch, kt_mlp **out) {
                o_z1 = take(B * H * 4), o_z2 = take(B * H * 4), o_h2 = take(B * H * 4), o_dh1 = take(B * H * 4),
                o_y = take(B * 4), o_dy = take(B * 4), o_loss = take(4), o_h1 = take(B * H * 2), o_h1t = take(B * H * 2),
                o_dz2 = take(B * H * 2), o_dz2t = take(B * H * 2), o_dz1t = take(B * H * 2),
-               o_xt = take(B * (size_t)n_in * 2), o_err = take(4);
+               o_xt = take(B * (size_t)n_in * 2), o_err = take(4),
+               o_part = take((size_t)kt::mlp::MAX_SPLITS * H * (n_in > H ? n_in : H) * 4),
+               o_pw3 = take((B / ROWS + 1) * H * 4), o_pb2 = take((B / ROWS + 1) * H * 4), o_pb3 = take((B / ROWS + 1) * 4),
+               o_pb1 = take((B / ROWS + 1) * H * 4);
   if (cudaMalloc(&n->mem, off) != cudaSuccess) {
     cudaGetLastError();
     delete n;
@@ -432,6 +478,11 @@ kt_status kt_mlp_create(int32_t n_in, int32_t max_batch, kt_mlp **out) {
   n->b2 = q; n->gb2 = r; q += H; r += H;
   n->w3 = q; n->gw3 = r; q += H; r += H;
   n->b3 = q; n->gb3 = r;
+  n->part = (float *)(b + o_part);
+  n->pw3 = (float *)(b + o_pw3);
+  n->pb2 = (float *)(b + o_pb2);
+  n->pb3 = (float *)(b + o_pb3);
+  n->pb1 = (float *)(b + o_pb1);
   n->W1b = (__nv_bfloat16 *)(b + o_w1b);
   n->W2b = (__nv_bfloat16 *)(b + o_w2b);
   n->W2Tb = (__nv_bfloat16 *)(b + o_w2t);
@@ -498,16 +549,23 @@ kt_status kt_mlp_backward(kt_mlp *n, const void *X, const float *t, int32_t B, f
   cudaMemsetAsync(n->loss, 0, 4, st);
   loss_kernel<<<blocks(B), 256, 0, st>>>(n->y, t, n->dy, n->loss, B);
   dz2_kernel<<<blocks((long long)B * H), 256, 0, st>>>(n->Z2, n->b2, n->w3, n->dy, n->dZ2b, n->dZ2Tb, B);
-  out_grads_kernel<<<1, H, 0, st>>>(n->Z2, n->b2, n->w3, n->H2, n->dy, n->gw3, n->gb2, n->gb3, B);
+  const int nc = (B + ROWS - 1) / ROWS;
+  out_grads_part_kernel<<<nc, H, 0, st>>>(n->Z2, n->b2, n->w3, n->H2, n->dy, n->pw3, n->pb2, n->pb3, B);
+  out_grads_sum_kernel<<<1, H, 0, st>>>(n->pw3, n->pb2, n->pb3, n->gw3, n->gb2, n->gb3, nc);
+  // weight gradients reduce over the batch: split K = B over several CTAs, then sum the slabs
+  const int S = kt::gemm_splits(B, MAX_SPLITS);
   // dW2 = dZ2^T H1: A = dZ2T [H][B], B-operand = H1T [H][B]
-  if (kt::gemm_bf16(n->dZ2Tb, B, n->H1Tb, B, n->gW2, H, H, H, B, n->err, st)) return KT_ECUDA;
+  if (kt::gemm_bf16(n->dZ2Tb, B, n->H1Tb, B, n->part, H, H, H, B, n->err, st, MAX_SPLITS)) return KT_ECUDA;
+  splitk_sum_kernel<<<blocks((long long)H * H), 256, 0, st>>>(n->part, n->gW2, S, (long long)H * H);
   // dH1 = dZ2 W2: A = dZ2 [B][H], B-operand = W2T [H(in)][H(out)]
   if (kt::gemm_bf16(n->dZ2b, H, n->W2Tb, H, n->dH1, H, B, H, H, n->err, st)) return KT_ECUDA;
   dz1_kernel<<<blocks((long long)B * H), 256, 0, st>>>(n->dH1, n->Z1, n->b1, n->dZ1Tb, B);
-  gb1_kernel<<<1, H, 0, st>>>(n->dH1, n->Z1, n->b1, n->gb1, B);
+  gb1_part_kernel<<<nc, H, 0, st>>>(n->dH1, n->Z1, n->b1, n->pb1, B);
+  splitk_sum_kernel<<<1, H, 0, st>>>(n->pb1, n->gb1, nc, H);
   // dW1 = dZ1^T X: A = dZ1T [H][B], B-operand = XT [n_in][B]
   transpose_b16_kernel<<<blocks((long long)B * nin), 256, 0, st>>>((const __nv_bfloat16 *)X, n->XTb, B, nin);
-  if (kt::gemm_bf16(n->dZ1Tb, B, n->XTb, B, n->gW1, nin, H, nin, B, n->err, st)) return KT_ECUDA;
+  if (kt::gemm_bf16(n->dZ1Tb, B, n->XTb, B, n->part, nin, H, nin, B, n->err, st, MAX_SPLITS)) return KT_ECUDA;
+  splitk_sum_kernel<<<blocks((long long)H * nin), 256, 0, st>>>(n->part, n->gW1, S, (long long)H * nin);
   if (loss) cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToDevice, st);
   return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ECUDA;
 }
