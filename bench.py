@@ -305,7 +305,8 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     t = t.clamp(-25.0, 10.0)
     net = engine.Surrogate(base.n_features, max_batch=8192, seed=seed)
     t0 = time.time()
-    hist = net.train(X, t, epochs=6, batch=4096, lr=3e-3, seed=seed)
+    hist = net.train(X, t, epochs=10, batch=4096, lr=3e-3, seed=seed)
+    hist += net.train(X, t, epochs=10, batch=4096, lr=1e-3, seed=seed + 1)
     torch.cuda.synchronize()
     t_train = time.time() - t0
     pred = net.predict(X[:65536]).double()
