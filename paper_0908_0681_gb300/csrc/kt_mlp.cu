@@ -203,7 +203,12 @@ int gemm_splits(int K, int splits) {
 int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc, int M, int N, int K, int *err,
               void *st_, int splits) {
   cudaStream_t st = (cudaStream_t)st_;
-  const int BN = N <= mlp::MAX_BN ? N : 128;
+  // column tile: the whole N when it fits the accumulator, narrower (128, then 64 columns)
+  // while the grid would have fewer than 64 CTAs, so that small batches still spread out
+  const int gm = (M + mlp::BM - 1) / mlp::BM, gz = gemm_splits(K, splits);
+  int BN = N <= mlp::MAX_BN ? N : 128;
+  for (const int w : {128, 64})
+    if (BN > w && gm * ((N + BN - 1) / BN) * gz < 64) BN = w;
   const size_t smem = (size_t)mlp::BM * mlp::BK * 2 + (size_t)BN * mlp::BK * 2;
   static bool attr = false;
   if (!attr) {

@@ -15,7 +15,8 @@ from paper_0908_0681_gb300 import kt  # noqa: E402
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 16, 16), (128, 256, 64), (256, 256, 352), (200, 48, 64), (1024, 256, 256),
-                                   (256, 352, 4096), (384, 96, 80)])
+                                   (256, 352, 4096), (384, 96, 80), (1024, 256, 368), (4096, 256, 368),
+                                   (8192, 256, 256), (1000, 144, 368)])
 def test_gemm_bf16_matches_fp64(M, N, K):
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N * 3 + K)
     A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
