@@ -10,6 +10,8 @@
 // and every wait on that mbarrier is bounded (on timeout the kernel records an
 // error flag and stops issuing). The epilogue reads TMEM with tcgen05.ld (each
 // warp its 32 lanes = 32 rows) and writes FP32 to global memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -192,14 +194,168 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16 *__r
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
+// TMA-fed variant. Each 64-column chunk of K arrives as eight 2-D tensor-map boxes of
+// 8 columns x rows (16-byte rows), one per group of 8 K columns, so that a box is a
+// column of 8 x 16-byte core matrices: the same no-swizzle K-major layout as above with
+// LBO = rows * 16 B between core matrices along K and SBO = 128 B between 8-row groups.
+// STAGES chunks are in flight: thread 0 issues the copies (cp.async.bulk.tensor; an
+// mbarrier per stage counts their bytes), thread 32 issues the MMAs of a stage once its
+// bytes have landed and commits them to the stage's "empty" mbarrier, which the copy of
+// the chunk STAGES later waits for. Every wait is bounded.
+constexpr int STAGES = 3;
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128) gemm_bf16_tma_kernel(const __grid_constant__ CUtensorMap ta,
+                                                            const __grid_constant__ CUtensorMap tb, float *C, int ldc,
+                                                            int M, int N, int K, int BN, int kslice, int *err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int stage_a = BM * BK * 2, stage_b = BN * BK * 2;
+  const uint32_t sa0 = smem_u32(smem), sb0 = sa0 + STAGES * stage_a;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int bn = (N - n0) < BN ? (N - n0) : BN;
+  const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+  const int nchunks = (ke - kb + BK - 1) / BK;
+  C += (size_t)blockIdx.z * M * ldc;
+  const uint32_t ncols = 256;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(&done), 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+  if (threadIdx.x == 0) {
+    // copies: chunk c into stage c % STAGES once the MMAs of chunk c - STAGES are done
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % STAGES, u = c / STAGES;
+      if (c >= STAGES && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((u - 1) & 1))) {
+        abort_sh = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, (uint32_t)(stage_a + stage_b));
+      const int k = kb + c * BK;
+      for (int g = 0; g < BK / 8; ++g) {
+        tma_load_2d(sa0 + s * stage_a + g * (BM * 16), &ta, k + 8 * g, m0, fb);
+        tma_load_2d(sb0 + s * stage_b + g * (BN * 16), &tb, k + 8 * g, n0, fb);
+      }
+    }
+  } else if (threadIdx.x == 32) {
+    const uint32_t idesc = instr_desc(BM, bn);
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % STAGES, u = c / STAGES;
+      if (*(volatile int *)&abort_sh || !mbar_wait(smem_u32(&full[s]), (uint32_t)(u & 1))) {
+        abort_sh = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int k = kb + c * BK;
+      const int ksteps = (ke - k) < BK ? (ke - k) / 16 : BK / 16;
+      for (int t = 0; t < ksteps; ++t) {
+        // K step t: core-matrix columns 2t and 2t+1 of the stage (boxes 2t and 2t+1)
+        const uint64_t ad = smem_desc(sa0 + s * stage_a + 2 * t * (BM * 16), BM * 16, 128);
+        const uint64_t bd = smem_desc(sb0 + s * stage_b + 2 * t * (BN * 16), BN * 16, 128);
+        const uint32_t acc = (c > 0 || t > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty[s]))
+                   : "memory");
+    }
+    // completion of every MMA issued (also after an abort, before the accumulator is freed)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&done))
+                 : "memory");
+  }
+  if (!mbar_wait(smem_u32(&done), 0u)) {
+    abort_sh = 1;
+    if (lane == 0) atomicExch(err, 1);
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (!abort_sh) {
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < bn; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+          "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+          "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < bn) C[(size_t)row * ldc + n0 + c0 + j] = __uint_as_float(r[j]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
 }  // namespace mlp
 
-// C = A . B^T; requirements checked by the caller-facing entry point.
+// cuTensorMapEncodeTiled from the driver (through the runtime), or null if unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
 int gemm_splits(int K, int splits) {
   const int kslice = ((K + splits - 1) / splits + mlp::BK - 1) / mlp::BK * mlp::BK;
   return (K + kslice - 1) / kslice;
 }
 
+// C = A . B^T; requirements checked by the caller-facing entry point. The TMA-fed kernel
+// when the driver provides tensor maps, else the kernel that stages with ordinary loads.
 int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc, int M, int N, int K, int *err,
               void *st_, int splits) {
   cudaStream_t st = (cudaStream_t)st_;
@@ -209,6 +365,30 @@ int gemm_bf16(const void *A, int lda, const void *B, int ldb, float *C, int ldc,
   int BN = N <= mlp::MAX_BN ? N : 128;
   for (const int w : {128, 64})
     if (BN > w && gm * ((N + BN - 1) / BN) * gz < 64) BN = w;
+  const int kslice_t = ((K + splits - 1) / splits + mlp::BK - 1) / mlp::BK * mlp::BK;
+  if (PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder()) {
+    CUtensorMap ta, tb;
+    const cuuint64_t da[2] = {(cuuint64_t)K, (cuuint64_t)M}, db[2] = {(cuuint64_t)K, (cuuint64_t)N};
+    const cuuint64_t sa[1] = {(cuuint64_t)lda * 2}, sb[1] = {(cuuint64_t)ldb * 2};
+    const cuuint32_t ba[2] = {8, (cuuint32_t)mlp::BM}, bb[2] = {8, (cuuint32_t)BN}, es[2] = {1, 1};
+    if (enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(A), da, sa, ba, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+            CUDA_SUCCESS &&
+        enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(B), db, sb, bb, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+            CUDA_SUCCESS) {
+      const size_t smem_t = (size_t)mlp::STAGES * ((size_t)mlp::BM * mlp::BK * 2 + (size_t)BN * mlp::BK * 2);
+      static bool attr_t = false;
+      if (!attr_t) {
+        cudaFuncSetAttribute(mlp::gemm_bf16_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(mlp::STAGES * (mlp::BM + mlp::MAX_BN) * mlp::BK * 2));
+        attr_t = true;
+      }
+      dim3 grid((unsigned)gm, (unsigned)((N + BN - 1) / BN), (unsigned)((K + kslice_t - 1) / kslice_t));
+      mlp::gemm_bf16_tma_kernel<<<grid, 128, smem_t, st>>>(ta, tb, C, ldc, M, N, K, BN, kslice_t, err);
+      return (int)cudaGetLastError();
+    }
+  }
   const size_t smem = (size_t)mlp::BM * mlp::BK * 2 + (size_t)BN * mlp::BK * 2;
   static bool attr = false;
   if (!attr) {
