@@ -3,13 +3,15 @@
 // kt_gemm_bf16: C[M][N] (FP32) = A[M][K] . B[N][K]^T with A, B in BF16, row-major,
 // both K-contiguous. One CTA of 128 threads computes a 128 x BN tile (BN <= 256, a
 // multiple of 16): the K dimension is staged through shared memory 64 columns at a
-// time in the canonical no-swizzle K-major layout of the tensor core (8 x 16-byte
-// core matrices; LBO = 128 B between core matrices along K, SBO = 1024 B between
-// 8-row groups), one thread issues tcgen05.mma (kind::f16, M = 128, N = BN, K = 16
-// per instruction) into a TMEM accumulator, tcgen05.commit arrives on an mbarrier,
-// and every wait on that mbarrier is bounded (on timeout the kernel records an
-// error flag and stops issuing). The epilogue reads TMEM with tcgen05.ld (each
-// warp its 32 lanes = 32 rows) and writes FP32 to global memory.
+// time in the no-swizzle K-major layout of the tensor core (8 x 16-byte core
+// matrices), one thread issues tcgen05.mma (kind::f16, M = 128, N = BN, K = 16 per
+// instruction) into a TMEM accumulator, tcgen05.commit arrives on mbarriers, and every
+// wait on an mbarrier is bounded (on timeout the kernel records an error flag and
+// stops issuing). The epilogue reads TMEM with tcgen05.ld (each warp its 32 lanes =
+// 32 rows) and writes FP32 to global memory. Two kernels: gemm_bf16_tma_kernel feeds
+// three stages by TMA (the default), gemm_bf16_kernel stages one chunk at a time with
+// ordinary loads (LBO = 128 B along K, SBO = 1024 B between 8-row groups) when the
+// driver offers no tensor-map encoder.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
