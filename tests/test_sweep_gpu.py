@@ -347,3 +347,30 @@ def test_cached_delayed_acceptance_matches_uncached():
     assert out[0][1] == out[1][1]
     assert out[0][1]["stage1_rejected"] > 0 and out[0][1]["insert_accepted"] > 0
     assert np.abs(out[0][2] - out[1][2]).max() < 1e-9
+
+
+@pytest.mark.parametrize("precision", [kt.KT_FP64, kt.KT_FP32_KRYLOV])
+def test_cached_sweep_long_run_weights_stay_exact(precision):
+    """2,000 cached steps of 256 five-orbital chains at beta = 50 (thousands of accepted moves
+    per chain's cache): the tracked trace of every chain equals a from-scratch evaluation of
+    its final configuration (1e-9 FP64, 2e-5 FP32), so the cache accumulates no error."""
+    nw, beta = 256, 50.0
+    spec, table, seqs = _thermal_five_orbital(nw, beta, seed=17)
+    gm = engine.model_from_spec(spec, precision=precision)
+    sw = engine.Sweep(gm, table, beta, nw, k_cap=128, n_bins=10, cache_ops=512)
+    sw.set_configs(seqs)
+    g = torch.Generator(device="cuda").manual_seed(19)
+    for _ in range(4):
+        sw.run(torch.rand((500, nw, 6), dtype=torch.float64, device="cuda", generator=g))
+    cnt = sw.counters()
+    assert cnt["trace_errors"] == 0 and cnt["insert_accepted"] + cnt["remove_accepted"] > 100 * nw
+    st = {k: v.cpu().numpy() for k, v in sw.state().items()}
+    lens = st["lens"]
+    final = workloads.Sequences(np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
+                                np.concatenate([st["tau"][i, :lens[i]] for i in range(nw)]),
+                                np.concatenate([st["flavor"][i, :lens[i]] for i in range(nw)]),
+                                np.concatenate([st["dagger"][i, :lens[i]] for i in range(nw)]))
+    s, l, stt = (t.cpu().numpy() for t in engine.trace(gm, engine.DeviceSeqs.from_host(final)))
+    assert (stt == kt.KT_OK).all() and (s == st["trace_sign"]).all()
+    tol = 1e-9 if precision == kt.KT_FP64 else 2e-5
+    assert np.abs(l - st["trace_logabs"]).max() <= tol, float(np.abs(l - st["trace_logabs"]).max())
