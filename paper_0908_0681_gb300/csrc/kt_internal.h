@@ -111,7 +111,8 @@ struct CacheView {
   int32_t *sfblk, *sbblk;
   int32_t *f, *gr;    // [n_items]
   int4 *plan;         // [n_items] this step: {y, x_new, m, flags}: bit 0 store states, bit 1 unit run,
-                      // bit 2 cache build (both units cover the whole sequence)
+                      // bit 2 cache build (both units cover the whole sequence), bit 3 the halves
+                      // meet at beta/2 (measurement)
 };
 
 // Cached mode: stretches of at least this many operators are scheduled first.
@@ -162,6 +163,11 @@ int launch_cached_pipeline(const DevModel &m, int precision, int kernel_dmax, co
                            const MoveView &moves, const int8_t *cur_sign, const double *cur_logabs, int8_t *sign,
                            double *logv, int32_t *status, const Workspace &ws, const CacheView &cache, bool write,
                            kt_stats *stats, void *stream);
+// Traces and observables at beta/2 of the current configurations (the kt_measure
+// layout of the workspace and of obs) from the cache, extending it (plan flag 8).
+int launch_cached_measure(const DevModel &m, int precision, int kernel_dmax, const SeqView &seq, int8_t *sign,
+                          double *logv, int32_t *status, double *obs, const Workspace &ws, const CacheView &cache,
+                          void *stream);
 // Store every forward and backward state of the current configurations (plan flags
 // bit 2: whole sequences, no overlap) and mark them valid.
 int launch_cache_build(const DevModel &m, int precision, int kernel_dmax, const SeqView &seq, const Workspace &ws,

@@ -835,6 +835,63 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
 #undef Y_
 }
 
+// Observables of one item at the meeting time beta/2, from this unit's vector (shared
+// memory) and the other half's (global, `other`): <O> = sum_r o(x_r) bwd_r fwd_r /
+// sum_r bwd_r fwd_r for the diagonal observables (n_f, double occupancy), and S^2 applied
+// to this unit's vector dotted with the other half.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ __forceinline__ void measure_epilogue(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, const Workspace &ws,
+                                                 int item, const VT *other, double ov) {
+  constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
+  const int gl = u.gl;
+  const unsigned gm = u.gm;
+  const int nf = M.nf, nl = nf + M.n_orb + 1;
+  const int off = __ldg(M.blk_off + u.b);
+  VT pr[R];
+  int xr[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = gl + G * j;
+    pr[j] = VT(0);
+    xr[j] = 0;
+    if (r < u.dim) {
+      pr[j] = u.Q(0, r) * __ldcg(other + r);
+      xr[j] = __ldg(M.st_bits + off + r);
+    }
+  }
+  const double iov = 1.0 / ov;
+  for (int k = 0; k < nl - 1; ++k) {
+    const int sh = k < nf ? k : 2 * (k - nf);
+    const int msk = k < nf ? 1 : 3;
+    GroupDot<VT, G> d;
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (((xr[j] >> sh) & msk) == msk) d.add(pr[j], VT(1));
+    const double v = d.value(gm) * iov;
+    if (gl == 0) ws.item_obs[(size_t)item * nl + k] = v;
+  }
+  {
+    // S^2: sum_r other_r (S^2 own)_r, S^2 applied to this unit's vector in shared memory
+    const int s2w = __ldg(M.blk_s2w + u.b), s2o = __ldg(M.blk_s2ell + u.b);
+    GroupDot<VT, G> d;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = gl + G * j;
+      if (r < u.dim) {
+        VT a = VT(__ldg(M.s2_diag + off + r)) * u.Q(0, r);
+        for (int k = 0; k < s2w; ++k) {
+          const unsigned e = __ldg(M.s2_ell + s2o + k * u.dim + r);
+          if (e != 0xFFFFu) a += (e & 0x8000u) ? -u.Q(0, e & 0x7fffu) : u.Q(0, e & 0x7fffu);
+        }
+        d.add(a, __ldcg(other + r));
+      }
+    }
+    const double v = d.value(gm) * iov;
+    if (gl == 0) ws.item_obs[(size_t)item * nl + nl - 1] = v;
+  }
+  if (gl == 0) ws.item_blk[item] = u.b;
+}
+
 // Work units: every alive (walker, kept state) item is split at the middle of
 // its sequence into a forward unit (ops 0 .. m-1 acting on |n>, Sec. III step 3
 // "forward") and a backward unit (the adjoints of ops K-1 .. m acting on <n|,
@@ -967,55 +1024,7 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
       if (oinfo >= 0 && (oinfo >> 24) > st) st = oinfo >> 24;
       const double L = Lh + Lo + (zero ? 0.0 : log(fabs(ov)));
       if (!zero && !isfinite(L)) st = KT_ENUMERIC;
-      if (meas && !zero) {
-        // <O> of this item for the diagonal observables at beta/2:
-        // sum_r o(x_r) bwd_r fwd_r / sum_r bwd_r fwd_r
-        const int nf = M.nf, nl = nf + M.n_orb + 1;
-        const int off = __ldg(M.blk_off + u.b);
-        VT pr[R];
-        int xr[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int r = gl + G * j;
-          pr[j] = VT(0);
-          xr[j] = 0;
-          if (r < u.dim) {
-            pr[j] = u.Q(0, r) * __ldcg(hvec + (size_t)oslot * vstride + r);
-            xr[j] = __ldg(M.st_bits + off + r);
-          }
-        }
-        const double iov = 1.0 / ov;
-        for (int k = 0; k < nl - 1; ++k) {
-          const int sh = k < nf ? k : 2 * (k - nf);
-          const int msk = k < nf ? 1 : 3;
-          GroupDot<VT, G> d;
-#pragma unroll
-          for (int j = 0; j < R; ++j)
-            if (((xr[j] >> sh) & msk) == msk) d.add(pr[j], VT(1));
-          const double v = d.value(gm) * iov;
-          if (gl == 0) ws.item_obs[(size_t)item * nl + k] = v;
-        }
-        {
-          // S^2: sum_r other_r (S^2 own)_r, S^2 applied to this unit's vector in shared memory
-          const int s2w = __ldg(M.blk_s2w + u.b), s2o = __ldg(M.blk_s2ell + u.b);
-          GroupDot<VT, G> d;
-#pragma unroll
-          for (int j = 0; j < R; ++j) {
-            const int r = gl + G * j;
-            if (r < u.dim) {
-              VT a = VT(__ldg(M.s2_diag + off + r)) * u.Q(0, r);
-              for (int k = 0; k < s2w; ++k) {
-                const unsigned e = __ldg(M.s2_ell + s2o + k * u.dim + r);
-                if (e != 0xFFFFu) a += (e & 0x8000u) ? -u.Q(0, e & 0x7fffu) : u.Q(0, e & 0x7fffu);
-              }
-              d.add(a, __ldcg(hvec + (size_t)oslot * vstride + r));
-            }
-          }
-          const double v = d.value(gm) * iov;
-          if (gl == 0) ws.item_obs[(size_t)item * nl + nl - 1] = v;
-        }
-        if (gl == 0) ws.item_blk[item] = u.b;
-      }
+      if (meas && !zero) measure_epilogue(M, u, ws, item, hvec + (size_t)oslot * vstride, ov);
       if (gl == 0) {
         ws.item_sign[item] = zero ? 0 : (ov > 0.0 ? 1 : -1);
         ws.item_log[item] = zero ? -INFINITY : L;
@@ -1102,6 +1111,7 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
   const int vstride = M.d_max, dv = C.dv;
   VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
   const size_t P1 = (size_t)C.P + 1;
+  const bool meas = ws.item_obs != nullptr;  // observables at beta/2 (plans with flag 8)
 
   for (;;) {
     int uix = 0;
@@ -1129,6 +1139,7 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
     // its adjoint; a last step without op takes the interval down to op m-1.
     const bool fwd = half == 0;
     const bool build = (pl.w & 4) != 0;  // cache build: each half covers the whole sequence
+    const bool at_half = (pl.w & 8) != 0;  // measurement: the halves meet at beta/2
     const int start = fwd ? y : x;
     const bool from_kept = fwd ? (y == 0) : (x == Kn);
     double t = fwd ? (y == 0 ? 0.0 : cur.get(y - 1).t) : (x == Kn ? M.beta : cur.get(x).t);
@@ -1145,8 +1156,9 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
                              eb + (fwd ? start : Kn - start), dv, u);
     }
     const int n_ops = build ? Kn : (fwd ? m - y : x - m);
-    const int n_steps = fwd || build ? n_ops : n_ops + 1;
-    const double tf = m >= 1 ? cur.get(m - 1).t : 0.0;
+    // the last step of a half without an operator: the interval to the meeting time
+    const int n_steps = build ? n_ops : (fwd && !at_half ? n_ops : n_ops + 1);
+    const double tf = at_half ? 0.5 * M.beta : (m >= 1 ? cur.get(m - 1).t : 0.0);
     for (int s = 0; s < n_steps; ++s) {
       const bool has_op = s < n_ops;
       const int i = fwd ? y + s : x - 1 - s;
@@ -1165,13 +1177,18 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
       if (has_op && cached) {
         // forward slot i+1 / backward reverse slot K-i; outside the window the state is
         // valid for the current configuration too and goes to the cache itself
-        const bool out = build || (fwd ? i + 1 <= lo : i >= hi);
+        const bool out = build || at_half || (fwd ? i + 1 <= lo : i >= hi);
         const size_t e = eb + (fwd ? i + 1 : Kn - i);
         VT *vec = (VT *)(fwd ? (out ? C.fvec : C.sfvec) : (out ? C.bvec : C.sbvec));
         double2 *lg = fwd ? (out ? C.flog : C.sflog) : (out ? C.blog : C.sblog);
         int32_t *bk = fwd ? (out ? C.fblk : C.sfblk) : (out ? C.bblk : C.sbblk);
         store_entry(vec, lg, bk, e, dv, u, vanished);
       }
+    }
+    // a measurement stores states of the current configuration: the valid range grows
+    if (at_half && cached && gl == 0 && u.status == KT_OK) {
+      if (fwd) C.f[item] = max(C.f[item], m);
+      else C.gr[item] = max(C.gr[item], Kn - m);
     }
     // publish this half; the second to finish forms the overlap (not for a build)
     if (!build) {
@@ -1214,6 +1231,7 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
         if (oinfo >= 0 && (oinfo >> 24) > st) st = oinfo >> 24;
         const double L = Lh + Lo + (zero ? 0.0 : log(fabs(ov)));
         if (!zero && !isfinite(L)) st = KT_ENUMERIC;
+        if (meas && !zero) measure_epilogue(M, u, ws, item, hvec + (size_t)oslot * vstride, ov);
         if (gl == 0) {
           ws.item_sign[item] = zero ? 0 : (ov > 0.0 ? 1 : -1);
           ws.item_log[item] = zero ? -INFINITY : L;

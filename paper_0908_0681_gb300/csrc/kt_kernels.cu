@@ -224,6 +224,53 @@ __global__ void build_plan_kernel(DevModel M, SeqView S, Workspace ws, CacheView
   }
 }
 
+// Observables at beta/2 of the current configurations from the cache: the forward half
+// of an item covers the operators before beta/2 from its last valid cached state, the
+// backward half those after it from its first valid cached state, and they meet at
+// beta/2 (flag 8); the states they pass are stored (they belong to the current
+// configuration) and extend the valid ranges.
+__global__ void measure_plan_kernel(DevModel M, SeqView S, Workspace ws, CacheView C, kt_stats *stats) {
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nk = M.n_kept;
+  if (item >= S.n * nk) return;
+  const int w = item / nk, q = item - w * nk;
+  ws.item_sign[item] = 0;
+  ws.item_status[item] = KT_OK;
+  ws.item_log[item] = -INFINITY;
+  ws.pair_flag[item] = 0;
+  C.plan[item] = make_int4(0, 0, 0, 0);
+  if (ws.wstatus[w] != KT_OK) return;
+  const int o = __ldg(S.offsets + w), K = ws.desc[w].w;
+  const int b0 = __ldg(M.kept_blk + q);
+  int b = b0;
+  for (int i = 0; i < K && b >= 0; ++i) {
+    const Op op = load_op(S, o + i);
+    b = __ldg(M.blk_target + ((size_t)b * M.nf + op.f) * 2 + op.dag);
+  }
+  const bool alive = (b == b0);
+  const int m = lower_bound(S.tau + o, K, 0.5 * M.beta);
+  const bool cached = K <= C.P;
+  int y = 0, x = K;
+  if (cached) {
+    const int f = C.f[item], gr = C.gr[item];
+    y = m < f ? m : f;
+    x = max(m, K - gr);
+  }
+  C.plan[item] = make_int4(y, x, m, (cached ? 1 : 0) | (alive ? 2 : 0) | 8);
+  if (alive) {
+    atomicAdd(&ws.counters[0], 1);
+    if (x - y >= KT_LONG_STRETCH) {
+      ws.worklist[atomicAdd(&ws.counters[2], 1)] = item;
+    } else {
+      ws.worklist[S.n * nk - 1 - atomicAdd(&ws.counters[3], 1)] = item;
+    }
+  }
+  if (stats) {
+    atomicAdd(&stats->items, 1ull);
+    if (alive) atomicAdd(&stats->items_alive, 1ull);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 4. reduction over kept states, ratio
 // ---------------------------------------------------------------------------
@@ -407,6 +454,26 @@ int launch_cache_build(const DevModel &M, int precision, int kd, const SeqView &
   rc = (precision == KT_FP64) ? dispatch_items_cached_f64(kd, M, S, MoveView{}, ws, C, nullptr, st)
                               : dispatch_items_cached_f32(kd, M, S, MoveView{}, ws, C, nullptr, st);
   if (rc) return rc;
+  return (int)cudaGetLastError();
+}
+
+int launch_cached_measure(const DevModel &M, int precision, int kd, const SeqView &S, int8_t *sign, double *logv,
+                          int32_t *status, double *obs, const Workspace &ws, const CacheView &C, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = S.n;
+  cudaGetLastError();
+  prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, MoveView{}, 0, nullptr, ws, nullptr);
+  const long long items = (long long)n * M.n_kept;
+  if (items > 0) {
+    measure_plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, ws, C, nullptr);
+    int rc = (int)cudaGetLastError();
+    if (rc) return rc;
+    rc = (precision == KT_FP64) ? dispatch_items_cached_f64(kd, M, S, MoveView{}, ws, C, nullptr, st)
+                                : dispatch_items_cached_f32(kd, M, S, MoveView{}, ws, C, nullptr, st);
+    if (rc) return rc;
+  }
+  reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, 0, nullptr, nullptr, ws, sign, logv, status);
+  measure_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, ws, obs);
   return (int)cudaGetLastError();
 }
 

@@ -843,6 +843,10 @@ kt::SeqView seq_view(const kt_sweep *s) {
 int current_traces(kt_sweep *s, int8_t *sg, double *lg, int32_t *st, double *obs, cudaStream_t stream) {
   const kt::DevModel &M = *s->mv.dev;
   const kt::Workspace w = kt::carve_workspace(s->ws, s->v.nw, M.n_kept, M.d_max, obs ? M.nf + M.n_orb + 1 : 0);
+  // measurements of a cached sweep start from the cached states nearest to beta/2
+  if (obs && s->cache_mem)
+    return kt::launch_cached_measure(M, s->mv.precision, s->mv.kernel_dmax, seq_view(s), sg, lg, st, obs, w, s->cache,
+                                     stream);
   return kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, seq_view(s), nullptr, nullptr,
                              nullptr, sg, lg, st, nullptr, w, stream, nullptr, obs);
 }

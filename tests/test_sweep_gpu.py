@@ -304,11 +304,13 @@ def test_cached_five_orbital_chains_match_uncached(precision):
     gm = engine.model_from_spec(spec, precision=precision)
     runs = {}
     for c in (0, 512):
-        sw = engine.Sweep(gm, table, beta, nw, k_cap=128, n_bins=20, cache_ops=c)
+        sw = engine.Sweep(gm, table, beta, nw, k_cap=128, n_bins=20, cache_ops=c, measure_obs=True)
         sw.set_configs(seqs)
         sw.run(u, meas_every=10)
         runs[c] = (sw, {k: v.cpu().numpy() for k, v in sw.state().items()}, sw.counters())
     (a, sa, ca), (b, sb, cb) = runs[0], runs[512]
+    # the beta/2 observables of the cached sweep come from its cached states
+    oa, ob = a.accumulators()["obs_sum"].cpu().numpy(), b.accumulators()["obs_sum"].cpu().numpy()
     assert ca["trace_errors"] == 0 and cb["trace_errors"] == 0
     assert cb["insert_accepted"] + cb["remove_accepted"] > nw * steps // 10
     same = np.array([sa["lens"][i] == sb["lens"][i] and
@@ -316,9 +318,11 @@ def test_cached_five_orbital_chains_match_uncached(precision):
     if precision == kt.KT_FP64:
         assert same.all()
         assert np.abs(sa["trace_logabs"] - sb["trace_logabs"]).max() < 1e-9
+        assert np.abs(oa - ob).max() <= 1e-8 * max(1.0, np.abs(oa).max())
     else:
         assert same.mean() >= 0.95
         assert np.abs(sa["trace_logabs"][same] - sb["trace_logabs"][same]).max() < 1e-4
+        assert np.abs(oa[same] - ob[same]).max() <= 1e-4 * max(1.0, np.abs(oa).max())
         om, _ = model_pair(spec, kt.KT_FP64)
         hyb = Hyb(table, beta)
         cfg = b.configs()
