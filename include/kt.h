@@ -330,8 +330,9 @@ void kt_ratio_cache_destroy(kt_ratio_cache *c);
  * backward state after it (split in the middle, forward and backward concurrently),
  * writing the states it passes: positions outside the window extend the valid
  * prefix or suffix at once, positions inside it are kept aside and committed only if
- * the move is accepted. The Markov chain and its uniforms are unchanged; the ratios
- * differ from the full evaluation by rounding only. Memory: 4 * n_walkers * n_kept *
+ * the move is accepted. The observables at beta/2 (measure_obs) start from the cached
+ * states nearest beta/2 and extend the cache. The Markov chain and its uniforms are
+ * unchanged; the ratios and observables differ from the full evaluation by rounding only. Memory: 4 * n_walkers * n_kept *
  * (cache_ops + 1) * (d_max * element size + 20) bytes.
  */
 typedef struct kt_sweep kt_sweep;
