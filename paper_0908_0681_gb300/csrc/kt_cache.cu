@@ -92,8 +92,9 @@ kt_status kt_ratio_cache_build(kt_ratio_cache *c, const kt_seq_batch *b, void *s
 kt_status kt_trace_ratio_cached(kt_ratio_cache *c, const kt_seq_batch *cur, const int8_t *cur_sign,
                                 const double *cur_logabs, const kt_move_batch *moves, int8_t *sign, double *logratio,
                                 int32_t *status, kt_stats *stats, void *stream) {
-  if (!c || !cur || cur->n != c->n || !cur->offsets || !moves || !moves->kind || !moves->flavor || !moves->t_dag ||
-      !moves->t_ann || !moves->rem_idx || !cur_sign || !cur_logabs || !sign || !logratio || !status)
+  if (!c || !cur || cur->n != c->n || !cur->offsets || !cur->tau || !cur->flavor || !cur->dagger || !moves ||
+      !moves->kind || !moves->flavor || !moves->t_dag || !moves->t_ann || !moves->rem_idx || !cur_sign || !cur_logabs ||
+      !sign || !logratio || !status)
     return KT_EINVAL;
   const kt::DevModel &M = *c->mv.dev;
   const kt::SeqView sv{cur->n, cur->offsets, cur->tau, cur->flavor, cur->dagger};
