@@ -14,12 +14,18 @@
 //                first-interval factor, each c / c^+ is a gather with a
 //                Jordan-Wigner sign, and every inner interval is a Lanczos
 //                approximation of exp(-dtau (H - E0)) v (Sec. III step 5):
-//                matrix-free SpMV on the block, FP64 dot products and norms,
-//                a three-term recurrence, and the FP64 exponential of the
-//                small tridiagonal matrix, with the Krylov dimension chosen
-//                per interval by an a-posteriori error estimate.
+//                matrix-free SpMV on the block, FP64-accurate dot products and
+//                norms (FP64, or double-float on the FP32 path), a three-term
+//                recurrence, and the exponential of the small tridiagonal
+//                matrix, with the Krylov dimension chosen per interval by an
+//                a-posteriori error estimate.
 //   4. reduce  - one thread per walker: signed log-sum-exp over kept states
 //                (step 7-8) and, for a ratio, division by the current trace.
+//
+// Cached pipelines (the partial-state cache, CacheView): plan_kernel replaces
+// prune for ratios (the stretch between valid cached states), build_plan_kernel
+// fills the cache for fixed configurations, measure_plan_kernel prepares the
+// observables at beta/2 from the cache; items_cached_kernel runs their units.
 #include <cuda_runtime.h>
 
 #include <math.h>
