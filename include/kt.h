@@ -264,8 +264,9 @@ kt_status kt_trace_ratio_static(kt_model *m, const kt_seq_batch *cur, const int8
  * evaluates from scratch a walker whose length differs from the build, but cannot see
  * other changes. Walkers longer than max_ops operators, before or after their update,
  * are evaluated from scratch too.
- * Device memory: 2 * n_walkers * n_kept * (max_ops + 1) * (d_max * element size + 20)
- * bytes plus a kt_trace workspace; errors KT_EINVAL (bad arguments, n != n_walkers),
+ * Device memory: 4 * n_walkers * n_kept * (max_ops + 1) * (d_max * element size + 20)
+ * bytes (the cache and the tentative states of kt_ratio_cache_propose) plus a kt_trace
+ * workspace; errors KT_EINVAL (bad arguments, n != n_walkers),
  * KT_ENOMEM, KT_ECUDA. Calls are enqueued on the stream; build and ratio calls on one
  * cache must not overlap.
  */
@@ -276,6 +277,20 @@ kt_status kt_ratio_cache_build(kt_ratio_cache *c, const kt_seq_batch *cur, void 
 kt_status kt_trace_ratio_cached(kt_ratio_cache *c, const kt_seq_batch *cur, const int8_t *cur_sign,
                                 const double *cur_logabs, const kt_move_batch *moves, int8_t *sign,
                                 double *logratio, int32_t *status, kt_stats *stats, void *stream);
+/* For external Markov chains on the cached configurations: kt_ratio_cache_propose gives
+ * kt_trace_ratio_cached's results and also keeps the states inside each update's window
+ * aside (the states outside it, valid for both configurations, extend the cache at
+ * once). Then kt_ratio_cache_commit, with accepted (DEVICE int8 [n], nonzero = the
+ * walker's update was accepted) and the status array of that propose call, makes the
+ * cache describe the edited configuration of every accepted walker and the unchanged one
+ * of the others. The caller edits its sequences the same way before the next call: an
+ * insertion places c^+ at t_dag and c at t_ann, each after the operators at equal times
+ * (if t_dag == t_ann the c goes first); a removal drops the operator at rem_idx and the
+ * next operator of its flavor, cyclically. One propose, then one commit, per step. */
+kt_status kt_ratio_cache_propose(kt_ratio_cache *c, const kt_seq_batch *cur, const int8_t *cur_sign,
+                                 const double *cur_logabs, const kt_move_batch *moves, int8_t *sign,
+                                 double *logratio, int32_t *status, kt_stats *stats, void *stream);
+kt_status kt_ratio_cache_commit(kt_ratio_cache *c, const int8_t *accepted, const int32_t *status, void *stream);
 /* No-op on NULL. Not stream-ordered: call it after the cache's work has completed. */
 void kt_ratio_cache_destroy(kt_ratio_cache *c);
 

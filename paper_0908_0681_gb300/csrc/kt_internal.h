@@ -163,6 +163,11 @@ int launch_cached_pipeline(const DevModel &m, int precision, int kernel_dmax, co
                            const MoveView &moves, const int8_t *cur_sign, const double *cur_logabs, int8_t *sign,
                            double *logv, int32_t *status, const Workspace &ws, const CacheView &cache, bool write,
                            kt_stats *stats, void *stream);
+// After the accept decision of a step with stored states: accepted moves (accepted[w]
+// nonzero) take their tentative window states into the cache, rejected ones extend the
+// valid ranges (rstatus: the ratio statuses of the step). words = 32-bit words per vector.
+int launch_cache_commit(const CacheView &C, int n, int nk, const int4 *desc, const int32_t *wstatus,
+                        const int8_t *accepted, const int32_t *rstatus, int words, void *stream);
 // Traces and observables at beta/2 of the current configurations (the kt_measure
 // layout of the workspace and of obs) from the cache, extending it (plan flag 8).
 int launch_cached_measure(const DevModel &m, int precision, int kernel_dmax, const SeqView &seq, int8_t *sign,

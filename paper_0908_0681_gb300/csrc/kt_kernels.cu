@@ -277,6 +277,75 @@ __global__ void measure_plan_kernel(DevModel M, SeqView S, Workspace ws, CacheVi
   }
 }
 
+// After the accept decision of a cached step, one warp per (walker, kept state)
+// item: an accepted move makes its tentative states (scratch) the cache's and the
+// valid ranges meet at m; a rejected one keeps the cache and only extends the valid
+// ranges by the states written outside the window; a pruned item (zero in the new
+// configuration) keeps the unchanged prefix and suffix if the move is accepted.
+__global__ void cache_commit_kernel(CacheView C, int n, int nk, const int4 *__restrict__ desc,
+                                    const int32_t *__restrict__ wstatus, const int8_t *__restrict__ accepted,
+                                    const int32_t *__restrict__ rstatus, int words) {
+  const int lane = threadIdx.x & 31;
+  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (item >= n * nk) return;
+  const int w = item / nk;
+  if (wstatus[w] != KT_OK) return;  // no update evaluated (a null or invalid move)
+  const int4 pl = C.plan[item];
+  const bool acc = accepted[w] != 0;
+  if (!(pl.w & 1)) {
+    if (acc && lane == 0) {
+      C.f[item] = 0;
+      C.gr[item] = 0;
+    }
+    return;
+  }
+  const int4 d = desc[w];
+  int lo, hi;
+  edit_window(d, lo, hi);
+  const int Kn = d.w, Ko = d.x == 0 ? Kn - 2 : Kn + 2;
+  const int y = pl.x, x = pl.y, m = pl.z;
+  if (!(pl.w & 2)) {
+    if (acc && lane == 0) {
+      C.f[item] = min(C.f[item], lo);
+      C.gr[item] = min(C.gr[item], Ko - (hi - (Kn - Ko)));
+    }
+    return;
+  }
+  if (!acc) {
+    if (lane == 0 && rstatus[w] == KT_OK) {
+      C.f[item] = max(C.f[item], min(m, lo));
+      C.gr[item] = max(C.gr[item], Kn - max(m, hi));
+    }
+    return;
+  }
+  const size_t eb = (size_t)item * ((size_t)C.P + 1);
+  const uint32_t *sfv = (const uint32_t *)C.sfvec, *sbv = (const uint32_t *)C.sbvec;
+  uint32_t *fv = (uint32_t *)C.fvec, *bv = (uint32_t *)C.bvec;
+  // forward slots (max(y, lo), m] and backward reverse slots of positions [m, min(x, hi))
+  const int f0 = max(y, lo) + 1, nfw = m - f0 + 1;
+  const int r0 = Kn - min(x, hi) + 1, nbw = (Kn - m) - r0 + 1;
+  for (int k = lane; k < nfw * words; k += 32) {
+    const size_t e = eb + f0 + k / words;
+    fv[e * words + k % words] = sfv[e * words + k % words];
+  }
+  for (int k = lane; k < nbw * words; k += 32) {
+    const size_t e = eb + r0 + k / words;
+    bv[e * words + k % words] = sbv[e * words + k % words];
+  }
+  for (int k = lane; k < nfw; k += 32) {
+    C.fblk[eb + f0 + k] = C.sfblk[eb + f0 + k];
+    C.flog[eb + f0 + k] = C.sflog[eb + f0 + k];
+  }
+  for (int k = lane; k < nbw; k += 32) {
+    C.bblk[eb + r0 + k] = C.sbblk[eb + r0 + k];
+    C.blog[eb + r0 + k] = C.sblog[eb + r0 + k];
+  }
+  if (lane == 0) {
+    C.f[item] = m;
+    C.gr[item] = Kn - m;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 4. reduction over kept states, ratio
 // ---------------------------------------------------------------------------
@@ -480,6 +549,15 @@ int launch_cached_measure(const DevModel &M, int precision, int kd, const SeqVie
   }
   reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, 0, nullptr, nullptr, ws, sign, logv, status);
   measure_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, n, ws, obs);
+  return (int)cudaGetLastError();
+}
+
+int launch_cache_commit(const CacheView &C, int n, int nk, const int4 *desc, const int32_t *wstatus,
+                        const int8_t *accepted, const int32_t *rstatus, int words, void *stream) {
+  const long long nitems = (long long)n * nk;
+  if (nitems == 0) return 0;
+  cache_commit_kernel<<<(unsigned)((nitems * 32 + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      C, n, nk, desc, wstatus, accepted, rstatus, words);
   return (int)cudaGetLastError();
 }
 

@@ -593,74 +593,6 @@ __global__ void sweep_obs_accumulate_kernel(SweepView S) {
   if (isfinite(v)) S.obs_sum[t] += (double)S.w_sign[w] * v;
 }
 
-// After the accept decision of a cached-mode step, one warp per (walker, kept state)
-// item: an accepted move makes its tentative states (scratch) the cache's and the
-// valid ranges meet at m; a rejected one keeps the cache and only extends the valid
-// ranges by the states written outside the window; a pruned item (zero in the new
-// configuration) keeps the unchanged prefix and suffix if the move is accepted.
-__global__ void sweep_cache_commit_kernel(SweepView S, CacheView C, const int4 *__restrict__ desc,
-                                          const int32_t *__restrict__ wstatus, int nk, int words) {
-  const int lane = threadIdx.x & 31;
-  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (item >= S.nw * nk) return;
-  const int w = item / nk;
-  if (!S.p_valid[w] || wstatus[w] != KT_OK) return;
-  const int4 pl = C.plan[item];
-  const bool acc = S.p_acc[w] != 0;
-  if (!(pl.w & 1)) {
-    if (acc && lane == 0) {
-      C.f[item] = 0;
-      C.gr[item] = 0;
-    }
-    return;
-  }
-  const int4 d = desc[w];
-  int lo, hi;
-  edit_window(d, lo, hi);
-  const int Kn = d.w, Ko = d.x == 0 ? Kn - 2 : Kn + 2;
-  const int y = pl.x, x = pl.y, m = pl.z;
-  if (!(pl.w & 2)) {
-    if (acc && lane == 0) {
-      C.f[item] = min(C.f[item], lo);
-      C.gr[item] = min(C.gr[item], Ko - (hi - (Kn - Ko)));
-    }
-    return;
-  }
-  if (!acc) {
-    if (lane == 0 && S.r_status[w] == KT_OK) {
-      C.f[item] = max(C.f[item], min(m, lo));
-      C.gr[item] = max(C.gr[item], Kn - max(m, hi));
-    }
-    return;
-  }
-  const size_t eb = (size_t)item * ((size_t)C.P + 1);
-  const uint32_t *sfv = (const uint32_t *)C.sfvec, *sbv = (const uint32_t *)C.sbvec;
-  uint32_t *fv = (uint32_t *)C.fvec, *bv = (uint32_t *)C.bvec;
-  // forward slots (max(y, lo), m] and backward reverse slots of positions [m, min(x, hi))
-  const int f0 = max(y, lo) + 1, nfw = m - f0 + 1;
-  const int r0 = Kn - min(x, hi) + 1, nbw = (Kn - m) - r0 + 1;
-  for (int k = lane; k < nfw * words; k += 32) {
-    const size_t e = eb + f0 + k / words;
-    fv[e * words + k % words] = sfv[e * words + k % words];
-  }
-  for (int k = lane; k < nbw * words; k += 32) {
-    const size_t e = eb + r0 + k / words;
-    bv[e * words + k % words] = sbv[e * words + k % words];
-  }
-  for (int k = lane; k < nfw; k += 32) {
-    C.fblk[eb + f0 + k] = C.sfblk[eb + f0 + k];
-    C.flog[eb + f0 + k] = C.sflog[eb + f0 + k];
-  }
-  for (int k = lane; k < nbw; k += 32) {
-    C.bblk[eb + r0 + k] = C.sbblk[eb + r0 + k];
-    C.blog[eb + r0 + k] = C.sblog[eb + r0 + k];
-  }
-  if (lane == 0) {
-    C.f[item] = m;
-    C.gr[item] = Kn - m;
-  }
-}
-
 __global__ void sweep_init_kernel(SweepView S, const int8_t *sg, const double *lg) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= S.nw) return;
@@ -1016,8 +948,7 @@ static kt_status run_steps(kt_sweep *s, int32_t n_steps, const double *uniforms,
     kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, u, ustride, w.desc, mode == 1);
     if (s->cache_mem) {
       const long long nitems = (long long)v.nw * M.n_kept;
-      kt::sweep_cache_commit_kernel<<<(unsigned)((nitems * 32 + 255) / 256), 256, 0, st>>>(
-          v, s->cache, w.desc, w.wstatus, M.n_kept, s->cache_words);
+      kt::launch_cache_commit(s->cache, v.nw, M.n_kept, w.desc, w.wstatus, v.p_acc, v.r_status, s->cache_words, st);
     }
     if (meas_every > 0 && (step + 1) % meas_every == 0) {
       kt::sweep_measure_kernel<<<grid, wpb * 32, 0, st>>>(v);

@@ -145,6 +145,22 @@ class RatioCache:
         kt.kt_trace_ratio_cached(self.h, seqs.batch(), cur_sign, cur_logabs, moves.batch(), *out, stats)
         return out
 
+    def propose(self, seqs: DeviceSeqs, cur_sign: torch.Tensor, cur_logabs: torch.Tensor, moves: DeviceMoves,
+                out=None):
+        """As ratio(), keeping each update's window states aside for commit()."""
+        n = seqs.n
+        dev = seqs.offsets.device
+        if out is None:
+            out = (torch.empty(n, dtype=torch.int8, device=dev), torch.empty(n, dtype=torch.float64, device=dev),
+                   torch.empty(n, dtype=torch.int32, device=dev))
+        kt.kt_ratio_cache_propose(self.h, seqs.batch(), cur_sign, cur_logabs, moves.batch(), *out)
+        return out
+
+    def commit(self, accepted: torch.Tensor, status: torch.Tensor) -> None:
+        """accepted: int8 device tensor (nonzero = accepted); status: the propose() statuses.
+        The caller then edits its sequences of the accepted walkers as the library does."""
+        kt.kt_ratio_cache_commit(self.h, accepted, status)
+
 
 def binning_analysis(x) -> dict:
     """Standard error of the mean of correlated measurements by binning.

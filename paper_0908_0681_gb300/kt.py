@@ -93,7 +93,8 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_mlp_set_params", "kt_mlp_get_params", "kt_mlp_forward", "kt_mlp_backward", "kt_mlp_get_grads",
                  "kt_mlp_adam", "kt_mlp_error", "kt_mlp_destroy", "kt_sweep_feature_size", "kt_sweep_collect",
                  "kt_sweep_set_surrogate", "kt_sweep_run_da", "kt_sweep_set_stats", "kt_ratio_cache_create",
-                 "kt_ratio_cache_build", "kt_trace_ratio_cached", "kt_ratio_cache_destroy"]
+                 "kt_ratio_cache_build", "kt_trace_ratio_cached", "kt_ratio_cache_destroy", "kt_ratio_cache_propose",
+                 "kt_ratio_cache_commit"]
 
 KT_SWEEP_NCOUNTERS = 10
 KT_MLP_HIDDEN = 256
@@ -155,6 +156,9 @@ def load():
     lib.kt_ratio_cache_build.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp]
     lib.kt_trace_ratio_cached.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
                                           vp, vp, vp, vp, vp]
+    lib.kt_ratio_cache_propose.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, ctypes.POINTER(kt_move_batch),
+                                           vp, vp, vp, vp, vp]
+    lib.kt_ratio_cache_commit.argtypes = [vp, vp, vp, vp]
     lib.kt_ratio_cache_destroy.argtypes = [vp]
     lib.kt_ratio_cache_destroy.restype = None
     lib.kt_sweep_get_state.argtypes = [vp, ctypes.POINTER(kt_sweep_state), vp]
@@ -356,6 +360,18 @@ def kt_trace_ratio_cached(c: KtRatioCache, cur: kt_seq_batch, cur_sign, cur_loga
     _check(load().kt_trace_ratio_cached(c.handle, ctypes.byref(cur), _ptr(cur_sign), _ptr(cur_logabs),
                                         ctypes.byref(moves), _ptr(sign), _ptr(logratio), _ptr(status), _ptr(stats),
                                         _stream_handle(stream)), "kt_trace_ratio_cached")
+
+
+def kt_ratio_cache_propose(c: KtRatioCache, cur: kt_seq_batch, cur_sign, cur_logabs, moves: kt_move_batch, sign,
+                           logratio, status, stats=None, stream=None) -> None:
+    _check(load().kt_ratio_cache_propose(c.handle, ctypes.byref(cur), _ptr(cur_sign), _ptr(cur_logabs),
+                                         ctypes.byref(moves), _ptr(sign), _ptr(logratio), _ptr(status), _ptr(stats),
+                                         _stream_handle(stream)), "kt_ratio_cache_propose")
+
+
+def kt_ratio_cache_commit(c: KtRatioCache, accepted, status, stream=None) -> None:
+    _check(load().kt_ratio_cache_commit(c.handle, _ptr(accepted), _ptr(status), _stream_handle(stream)),
+           "kt_ratio_cache_commit")
 
 
 def kt_sweep_set_stats(s: KtSweep, stats) -> None:

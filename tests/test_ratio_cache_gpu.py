@@ -216,3 +216,48 @@ def test_stale_lengths_fall_back_to_full_evaluation(three):
     assert ok.sum() >= 10
     assert (res[0][ok] == full[0][ok]).all() and (res[0][zero] == 0).all()
     assert np.abs(res[1][ok] - full[1][ok]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_external_chain_with_propose_and_commit(prec):
+    """An external Markov chain on the trace alone (accept when u < |T_new / T_old|) driven
+    through kt_ratio_cache_propose / kt_ratio_cache_commit, its sequences edited on the host
+    with the library's edit rules: every step's cached ratios equal kt_trace_ratio's on the
+    same configurations (FP64 2e-10, FP32 2e-5), over many accepted moves."""
+    from oracle.oracle import edit
+    w = workloads.five_orbital()
+    n = 64
+    seqs = workloads.generate_sequences(w, n, seed=12)
+    m = engine.model_from_spec(w.model, precision=prec)
+    d = engine.DeviceSeqs.from_host(seqs)
+    cs, cl, cst = engine.trace(m, d)
+    assert (cs.cpu().numpy() != 0).all()
+    cache = engine.RatioCache(m, n, 512)
+    cache.build(d)
+    rng = np.random.default_rng(3)
+    ops = [list(zip(*[a.tolist() for a in seqs.walker(i)])) for i in range(n)]
+    accepted_total = 0
+    for step in range(40):
+        cur = workloads.Sequences(np.concatenate([[0], np.cumsum([len(o) for o in ops])]).astype(np.int32),
+                                  np.array([t for o in ops for (t, f, g) in o], np.float64),
+                                  np.array([f for o in ops for (t, f, g) in o], np.uint8),
+                                  np.array([g for o in ops for (t, f, g) in o], np.uint8))
+        d = engine.DeviceSeqs.from_host(cur)
+        mv = workloads.generate_moves(w, cur, seed=3000 + step)
+        dm = engine.DeviceMoves.from_host(mv)
+        c = [t.cpu().numpy() for t in cache.propose(d, cs, cl, dm)]
+        f = [t.cpu().numpy() for t in engine.trace_ratio(m, d, cs, cl, dm)]
+        ok = (c[2] == kt.KT_OK) & (f[2] == kt.KT_OK)
+        assert (c[2] == f[2]).all(), step
+        nz = ok & (f[0] != 0) & (c[0] != 0)
+        assert (c[0][ok & (f[0] != 0)] == f[0][ok & (f[0] != 0)]).all(), step
+        assert np.abs(c[1][nz] - f[1][nz]).max(initial=0.0) <= PAIR_TOL[prec], step
+        acc = nz & (np.log(rng.uniform(size=n)) < f[1])
+        accepted_total += int(acc.sum())
+        cache.commit(torch.as_tensor(acc.astype(np.int8), device="cuda"), torch.as_tensor(c[2], device="cuda"))
+        for i in np.nonzero(acc)[0]:
+            ops[i] = edit(ops[i], int(mv.kind[i]), int(mv.flavor[i]), float(mv.t_dag[i]), float(mv.t_ann[i]),
+                          int(mv.rem_idx[i]))
+        cs = torch.as_tensor(np.where(acc, c[0] * cs.cpu().numpy(), cs.cpu().numpy()).astype(np.int8), device="cuda")
+        cl = torch.as_tensor(np.where(acc, cl.cpu().numpy() + f[1], cl.cpu().numpy()), device="cuda")
+    assert accepted_total >= 200
