@@ -712,7 +712,11 @@ def main():
                 "flops_per_launch": f32_per_launch, "items_ms_per_launch": items_ms,
                 "stage_ms_per_step": {k: v / max(nl32, 1) for k, v in stage32.items()},
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock (sampled)",
-                "fp64_peak_tflops": peak64}
+                "fp64_peak_tflops": peak64,
+                # the kernel is bound by its longest serial chain, not by a pipe: the step time
+                # of its longest walker evaluated alone is the floor (bench key latency_floor)
+                "latency_floor_ms": max(latency_floor["single_walker_ms"]),
+                "frac_of_latency_floor": max(latency_floor["single_walker_ms"]) / (tot32 / a.steps)}
 
     sweep = sweep_bench(dev, a.sweep_steps, a.sweep_beta, seed=100 + rank) if a.sweep_steps > 0 else None
 
