@@ -1,11 +1,13 @@
 """A small, fixed invocation of the engine for profiler captures.
 
     python -m paper_0908_0681_gb300.profile_case [--workload five_orbital] [--walkers 4096]
-           [--precision fp32|fp64] [--launches 3]
+           [--precision fp32|fp64] [--launches 3] [--cached]
 
 Builds the model, computes the current traces once (kt_trace) and then runs
 `launches` trace-ratio calls (kt_trace_ratio) on rounds of moves with seeds
-1000 + r. Everything stays on the device; the process exits 0 on success.
+1000 + r. With --cached the ratios come from the partial-state cache of the same
+configurations (kt_ratio_cache_build once, then kt_trace_ratio_cached). Everything
+stays on the device; the process exits 0 on success.
 """
 from __future__ import annotations
 
@@ -26,6 +28,7 @@ def main():
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--flags", type=int, default=0)
     p.add_argument("--group-lanes", type=int, default=0, help="lanes per item (0: the model default)")
+    p.add_argument("--cached", action="store_true", help="ratios from the partial-state cache")
     a = p.parse_args()
     import torch
 
@@ -41,11 +44,18 @@ def main():
     d = engine.DeviceSeqs.from_host(seqs)
     ws = engine.workspace(m, seqs.n)
     cs, cl, st = engine.trace(m, d, ws=ws)
+    cache = None
+    if a.cached:
+        cache = engine.RatioCache(m, seqs.n, max_ops=512)
+        cache.build(d)
     for r in range(a.launches):
-        s, lr, st2 = engine.trace_ratio(m, d, cs, cl, moves[r], ws=ws)
+        if cache is not None:
+            s, lr, st2 = cache.ratio(d, cs, cl, moves[r])
+        else:
+            s, lr, st2 = engine.trace_ratio(m, d, cs, cl, moves[r], ws=ws)
     torch.cuda.synchronize()
     bad = int((st != 0).sum().item()) + int((st2 != 0).sum().item())
-    print(f"profile_case {a.workload} walkers={a.walkers} precision={a.precision} launches={a.launches} "
+    print(f"profile_case {a.workload} walkers={a.walkers} precision={a.precision} launches={a.launches} cached={a.cached} "
           f"info={kt.kt_model_query(m)} non_ok={bad}")
     return 0 if bad == 0 else 1
 
