@@ -261,3 +261,34 @@ def test_external_chain_with_propose_and_commit(prec):
         cs = torch.as_tensor(np.where(acc, c[0] * cs.cpu().numpy(), cs.cpu().numpy()).astype(np.int8), device="cuda")
         cl = torch.as_tensor(np.where(acc, cl.cpu().numpy() + f[1], cl.cpu().numpy()), device="cuda")
     assert accepted_total >= 200
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_batch_cached_ratios_sampled(prec):
+    """The benchmark's 4,096-walker batch and moves, with ratios from the partial-state cache
+    (the bench's cached_ratio configuration): every walker against the full GPU evaluation,
+    and 48 sampled walkers one by one against the oracle."""
+    w = workloads.five_orbital()
+    seqs = workloads.generate_sequences(w, 4096, seed=1)
+    moves = workloads.generate_moves(w, seqs, seed=1000)
+    m = engine.model_from_spec(w.model, precision=prec)
+    d = engine.DeviceSeqs.from_host(seqs)
+    cs, cl, cst = engine.trace(m, d)
+    assert (cst.cpu().numpy() == kt.KT_OK).all() and (cs.cpu().numpy() != 0).all()
+    cache = engine.RatioCache(m, seqs.n, max_ops=512)
+    cache.build(d)
+    dm = engine.DeviceMoves.from_host(moves)
+    c = [t.cpu().numpy() for t in cache.ratio(d, cs, cl, dm)]
+    f = [t.cpu().numpy() for t in engine.trace_ratio(m, d, cs, cl, dm)]
+    assert (c[2] == kt.KT_OK).all() and (f[2] == kt.KT_OK).all()
+    assert (c[0] == f[0]).all()
+    nz = c[0] != 0
+    assert np.abs(c[1][nz] - f[1][nz]).max() <= PAIR_TOL[prec]
+    idx = np.random.default_rng(1).choice(4096, 48, replace=False)
+    sub = seqs.subset(idx)
+    o64, ox = parity.oracle_pair(w.model)
+    cls, sx, lx = parity.oracle_traces(o64, ox, sub)
+    ncls, nsx, nlx = parity.oracle_ratios(o64, ox, sub, sx, lx, moves.subset(idx))
+    reg = ncls == 2
+    err = np.abs(np.expm1(c[1][idx][reg] - (nlx - lx)[reg]))
+    assert err.max() <= 2 * parity.RTOL[prec], err.max()
