@@ -1,0 +1,47 @@
+"""The ctypes structures of the binding match include/kt.h field by field: a C program
+compiled against the header prints sizeof and offsetof of every structure and field, and
+the binding's ctypes layout must give the same numbers (CPU only; needs gcc)."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import pytest
+
+from paper_0908_0681_gb300 import kt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+STRUCTS = ["kt_model_params", "kt_model_info", "kt_stats", "kt_seq_batch", "kt_move_batch", "kt_sweep_params",
+           "kt_sweep_state", "kt_sweep_accum"]
+
+
+def _c_layout(tmp_path):
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kt.h"', 'int main(void) {']
+    for name in STRUCTS:
+        cls = getattr(kt, name)
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return dict((k, int(v)) for k, v in (line.split() for line in out.splitlines()))
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    c = _c_layout(tmp_path)
+    for name in STRUCTS:
+        cls = getattr(kt, name)
+        assert ctypes.sizeof(cls) == c[name], name
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == c[f"{name}.{field}"], (name, field)
+
+
+def test_stats_words_cover_the_structure():
+    assert ctypes.sizeof(kt.kt_stats) == 8 * kt.STATS_WORDS
