@@ -402,3 +402,35 @@ def test_seven_orbital_cached_chains_match_uncached():
     oa, ob = out[0][2]["obs_sum"], out[1][2]["obs_sum"]
     # columns that the oracle leaves undefined beyond five orbitals are still computed on the GPU
     assert np.abs(oa - ob).max() <= 1e-8 * max(1.0, np.abs(oa).max())
+
+
+def test_cached_sweep_restart_invalidates_the_cache():
+    """set_configs in the middle of a cached run: the cache is invalidated and rebuilt from the
+    new configurations, so the chains continue exactly as uncached ones do (FP64)."""
+    w = workloads.three_orbital()
+    spec = w.model
+    gm = engine.model_from_spec(spec, precision=kt.KT_FP64)
+    om = model_pair(spec, kt.KT_FP64)[0]
+    table = workloads.semicircular_hybridization(spec.beta, 6, n_tau=2000)
+    hyb = Hyb(table, spec.beta)
+    cand = workloads.generate_sequences(w, 400, seed=19)
+    keep = [i for i in range(cand.n)
+            if max([sum(1 for t, f, d in zip(*[a.tolist() for a in cand.walker(i)]) if f == g and d == 1)
+                    for g in range(6)] + [0]) <= 8
+            and weight(om, hyb, list(zip(*[a.tolist() for a in cand.walker(i)])))[0] != 0][:16]
+    assert len(keep) == 16
+    restart = cand.subset(keep)
+    u1 = torch.as_tensor(workloads.sweep_uniforms(120, 16, seed=20), device="cuda")
+    u2 = torch.as_tensor(workloads.sweep_uniforms(120, 16, seed=21), device="cuda")
+    out = []
+    for c in (0, 128):
+        sw = engine.Sweep(gm, table, spec.beta, 16, k_cap=16, n_bins=10, measure_obs=True, cache_ops=c)
+        sw.run(u1, meas_every=10)
+        sw.set_configs(restart)
+        sw.run(u2, meas_every=10)
+        out.append((sw.configs(), sw.counters(), sw.state()["trace_logabs"].cpu().numpy(),
+                    sw.accumulators()["obs_sum"].cpu().numpy()))
+    assert out[0][0] == out[1][0]
+    assert out[0][1] == out[1][1]
+    assert np.abs(out[0][2] - out[1][2]).max() < 1e-9
+    assert np.abs(out[0][3] - out[1][3]).max() <= 1e-8 * max(1.0, np.abs(out[0][3]).max())
