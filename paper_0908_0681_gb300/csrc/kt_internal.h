@@ -73,9 +73,7 @@ struct MoveView {
 
 // Workspace layout (device), sized for n walkers and n_kept kept states.
 struct Workspace {
-  int32_t *counters;   // [4]: 0 = number of alive items, 1 = next item to claim; cached mode:
-                       // 2 = items with long stretches (worklist from the front), 3 = the others
-                       // (worklist from the back)
+  int32_t *counters;   // [4]: 0 = number of alive items, 1 = next unit to claim, 2-3 spare
   int4 *desc;          // [n] per-walker edit descriptor {kind, p1, p2, K_new}
   int32_t *wstatus;    // [n] per-walker status from validation
   int32_t *worklist;   // [n * n_kept] alive items (walker * n_kept + kept)
@@ -114,9 +112,6 @@ struct CacheView {
                       // bit 2 cache build (both units cover the whole sequence), bit 3 the halves
                       // meet at beta/2 (measurement)
 };
-
-// Cached mode: stretches of at least this many operators are scheduled first.
-#define KT_LONG_STRETCH 48
 
 // Edited window of a move in the new sequence: positions [lo, hi_new) differ from
 // the old sequence, positions < lo equal it, positions >= hi_new are old ones shifted

@@ -915,10 +915,14 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
   const bool meas = ws.item_obs != nullptr;
 
   for (;;) {
-    int uix = 0;
-    if (gl == 0) uix = atomicAdd(&ws.counters[1], 1);
-    uix = __shfl_sync(gm, uix, grp * G);
-    if (uix >= n_units) break;
+    int c = 0;
+    if (gl == 0) c = atomicAdd(&ws.counters[1], 1);
+    c = __shfl_sync(gm, c, grp * G);
+    if (c >= n_units) break;
+    // units in the worklist order (longest sequences first): of every four consecutive
+    // claims, one takes the next unit from the long end and three from the short end
+    const int b = c >> 2, j = c & 3;
+    const int uix = j == 0 ? b : n_units - 1 - (3 * b + j - 1);
     const int it = uix >> 1, half = uix & 1;
     const int item = ws.worklist[it];
     const int w = item / nk, q = item - w * nk;
@@ -1105,21 +1109,24 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
   const unsigned gm = (G == 32) ? FULL : (((1u << G) - 1u) << (grp * G));
   WarpTile<VT, G, DMAX, PMAX> &tile = reinterpret_cast<WarpTile<VT, G, DMAX, PMAX> *>(smem_raw)[wib];
   const VT *__restrict__ tkept = Tab<VT>::kept(M);
-  const int n_units = 2 * ws.counters[0], n_long = ws.counters[2];
+  const int n_units = 2 * ws.counters[0];
   const int nk = M.n_kept;
-  const int last = S.n * nk - 1;
   const int vstride = M.d_max, dv = C.dv;
   VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
   const size_t P1 = (size_t)C.P + 1;
   const bool meas = ws.item_obs != nullptr;  // observables at beta/2 (plans with flag 8)
 
   for (;;) {
-    int uix = 0;
-    if (gl == 0) uix = atomicAdd(&ws.counters[1], 1);
-    uix = __shfl_sync(gm, uix, grp * G);
-    if (uix >= n_units) break;
+    int c = 0;
+    if (gl == 0) c = atomicAdd(&ws.counters[1], 1);
+    c = __shfl_sync(gm, c, grp * G);
+    if (c >= n_units) break;
+    // the worklist is ordered longest stretch first: one unit of every four consecutive
+    // claims from the long end, three from the short end
+    const int b = c >> 2, j = c & 3;
+    const int uix = j == 0 ? b : n_units - 1 - (3 * b + j - 1);
     const int it = uix >> 1, half = uix & 1;
-    const int item = ws.worklist[it < n_long ? it : last - (it - n_long)];
+    const int item = ws.worklist[it];
     const int w = item / nk, q = item - w * nk;
     const Cursor cur = make_cursor(S, mv, true, ws.desc, w);
     const int Kn = cur.d.w;

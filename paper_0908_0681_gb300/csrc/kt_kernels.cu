@@ -194,15 +194,7 @@ __global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, Ca
   }
   const int m = y + (x - y) / 2;
   C.plan[item] = make_int4(y, x, m, (cached && write ? 1 : 0) | (alive ? 2 : 0));
-  if (alive) {
-    // longest stretches first: they bound the launch, the short ones fill in around them
-    atomicAdd(&ws.counters[0], 1);
-    if (x - y >= KT_LONG_STRETCH) {
-      ws.worklist[atomicAdd(&ws.counters[2], 1)] = item;
-    } else {
-      ws.worklist[S.n * nk - 1 - atomicAdd(&ws.counters[3], 1)] = item;
-    }
-  }
+  if (alive) ws.worklist[atomicAdd(&ws.counters[0], 1)] = item;
   if (stats) {
     atomicAdd(&stats->items, 1ull);
     if (alive) atomicAdd(&stats->items_alive, 1ull);
@@ -224,10 +216,7 @@ __global__ void build_plan_kernel(DevModel M, SeqView S, Workspace ws, CacheView
   C.f[item] = ok ? K : 0;
   C.gr[item] = ok ? K : 0;
   C.plan[item] = make_int4(0, K, 0, ok ? 1 | 2 | 4 : 0);
-  if (ok) {
-    atomicAdd(&ws.counters[0], 1);
-    ws.worklist[atomicAdd(&ws.counters[2], 1)] = item;
-  }
+  if (ok) ws.worklist[atomicAdd(&ws.counters[0], 1)] = item;
 }
 
 // Observables at beta/2 of the current configurations from the cache: the forward half
@@ -263,14 +252,7 @@ __global__ void measure_plan_kernel(DevModel M, SeqView S, Workspace ws, CacheVi
     x = max(m, K - gr);
   }
   C.plan[item] = make_int4(y, x, m, (cached ? 1 : 0) | (alive ? 2 : 0) | 8);
-  if (alive) {
-    atomicAdd(&ws.counters[0], 1);
-    if (x - y >= KT_LONG_STRETCH) {
-      ws.worklist[atomicAdd(&ws.counters[2], 1)] = item;
-    } else {
-      ws.worklist[S.n * nk - 1 - atomicAdd(&ws.counters[3], 1)] = item;
-    }
-  }
+  if (alive) ws.worklist[atomicAdd(&ws.counters[0], 1)] = item;
   if (stats) {
     atomicAdd(&stats->items, 1ull);
     if (alive) atomicAdd(&stats->items_alive, 1ull);
@@ -344,6 +326,48 @@ __global__ void cache_commit_kernel(CacheView C, int n, int nk, const int4 *__re
     C.f[item] = m;
     C.gr[item] = Kn - m;
   }
+}
+
+// Alive items ordered by the operators their two units propagate, longest first: the
+// length of the walker's (edited) sequence, or with a cache plan the stretch [y, x) between
+// valid cached states. A counting sort in one block, using the half-item info array as
+// scratch (the items kernels write it only later). The items kernels then hand every group
+// of four claims one unit from the long end and three from the short end, so that a long
+// unit shares its warp with short ones, which finish early and leave it alone.
+__global__ void __launch_bounds__(1024) order_kernel(DevModel M, Workspace ws, const int4 *__restrict__ plan) {
+  constexpr int NB = 1024;
+  __shared__ int cnt[NB];
+  const int t = threadIdx.x, nk = M.n_kept;
+  const int n = ws.counters[0];
+  int32_t *tmp = ws.half_info;
+  cnt[t] = 0;
+  __syncthreads();
+  auto key = [&](int item) {
+    if (plan) {
+      const int4 p = plan[item];
+      return p.y - p.x;
+    }
+    return ws.desc[item / nk].w;
+  };
+  for (int i = t; i < n; i += NB) atomicAdd(&cnt[NB - 1 - min(key(ws.worklist[i]) >> 2, NB - 1)], 1);
+  __syncthreads();
+  // exclusive scan of the bin counts (bin 0 = the longest sequences)
+  const int c = cnt[t];
+  __syncthreads();
+  for (int o = 1; o < NB; o <<= 1) {
+    const int v = t >= o ? cnt[t - o] : 0;
+    __syncthreads();
+    cnt[t] += v;
+    __syncthreads();
+  }
+  cnt[t] -= c;
+  __syncthreads();
+  for (int i = t; i < n; i += NB) {
+    const int item = ws.worklist[i];
+    tmp[atomicAdd(&cnt[NB - 1 - min(key(item) >> 2, NB - 1)], 1)] = item;
+  }
+  __syncthreads();
+  for (int i = t; i < n; i += NB) ws.worklist[i] = tmp[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -478,7 +502,10 @@ int launch_pipeline(const DevModel &M, int precision, int kd, int G, const SeqVi
   prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, mv, has_moves, cur_sign, ws, stats);
   mark(1);
   const long long items = (long long)n * M.n_kept;
-  if (items > 0) prune_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, has_moves, ws, stats);
+  if (items > 0) {
+    prune_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, has_moves, ws, stats);
+    order_kernel<<<1, 1024, 0, st>>>(M, ws, nullptr);
+  }
   mark(2);
   int rc = (int)cudaGetLastError();
   if (rc) return rc;
@@ -503,7 +530,10 @@ int launch_cached_pipeline(const DevModel &M, int precision, int kd, const SeqVi
   cudaGetLastError();
   prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, mv, 1, cur_sign, ws, stats);
   const long long items = (long long)n * M.n_kept;
-  if (items > 0) plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, ws, C, write ? 1 : 0, stats);
+  if (items > 0) {
+    plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, ws, C, write ? 1 : 0, stats);
+    order_kernel<<<1, 1024, 0, st>>>(M, ws, C.plan);
+  }
   int rc = (int)cudaGetLastError();
   if (rc) return rc;
   if (items > 0) {
@@ -524,6 +554,7 @@ int launch_cache_build(const DevModel &M, int precision, int kd, const SeqView &
   const long long items = (long long)n * M.n_kept;
   if (items == 0) return (int)cudaGetLastError();
   build_plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, ws, C);
+  order_kernel<<<1, 1024, 0, st>>>(M, ws, C.plan);
   int rc = (int)cudaGetLastError();
   if (rc) return rc;
   rc = (precision == KT_FP64) ? dispatch_items_cached_f64(kd, M, S, MoveView{}, ws, C, nullptr, st)
@@ -541,6 +572,7 @@ int launch_cached_measure(const DevModel &M, int precision, int kd, const SeqVie
   const long long items = (long long)n * M.n_kept;
   if (items > 0) {
     measure_plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, ws, C, nullptr);
+    order_kernel<<<1, 1024, 0, st>>>(M, ws, C.plan);
     int rc = (int)cudaGetLastError();
     if (rc) return rc;
     rc = (precision == KT_FP64) ? dispatch_items_cached_f64(kd, M, S, MoveView{}, ws, C, nullptr, st)
