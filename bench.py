@@ -757,7 +757,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "sweep": sweep,
             "clocks": clocks,
-            "gpu_launches": 4 * a.steps,
+            # prep, prune, order, items and reduce per ratio call
+            "gpu_launches": 5 * a.steps,
             "kernel_source_sha": sha,
         }
         print(json.dumps(line), flush=True)

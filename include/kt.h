@@ -515,8 +515,8 @@ kt_status kt_autotune(kt_model *m, const kt_seq_batch *batch, int8_t *sign, doub
 /* Per-stage timing with CUDA events (profiling aid, not part of the method).
  * After kt_timing_begin(m, max_launches), each of the next max_launches trace
  * or trace-ratio calls on m records CUDA events on its own stream around its
- * four kernels: 0 validation/edit, 1 structural pruning, 2 Krylov items,
- * 3 reduction. kt_timing_end waits for those events, writes the summed
+ * four stages: 0 validation/edit, 1 structural pruning and the ordering of the
+ * surviving items by length (two kernels), 2 Krylov items, 3 reduction. kt_timing_end waits for those events, writes the summed
  * durations in milliseconds to ms_per_stage[4] and the number of recorded calls
  * to *launches, and stops recording. Calls beyond max_launches run untimed.
  * Not thread-safe: do not share a model between host threads while timing. */
