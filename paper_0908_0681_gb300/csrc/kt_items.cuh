@@ -914,13 +914,21 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
   VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
   const bool meas = ws.item_obs != nullptr;
 
+  // claim numbers: every lane group's first one is fixed, dealing consecutive numbers to
+  // warp 0 of every CTA, then warp 1 of every CTA, and so on, so that the longest units
+  // (the lowest numbers) land on different SMs; later ones come from the queue
+  const int slots = (int)(gridDim.x * blockDim.x) / G;
+  int first = (wib * (int)gridDim.x + (int)blockIdx.x) * (32 / G) + grp;
   for (;;) {
-    int c = 0;
-    if (gl == 0) c = atomicAdd(&ws.counters[1], 1);
-    c = __shfl_sync(gm, c, grp * G);
+    int c = first;
+    first = -1;
+    if (c < 0) {
+      if (gl == 0) c = slots + atomicAdd(&ws.counters[1], 1);
+      c = __shfl_sync(gm, c, grp * G);
+    }
     if (c >= n_units) break;
     // units in the worklist order (longest sequences first): of every four consecutive
-    // claims, one takes the next unit from the long end and three from the short end
+    // claim numbers, one takes the next unit from the long end and three from the short end
     const int b = c >> 2, j = c & 3;
     const int uix = j == 0 ? b : n_units - 1 - (3 * b + j - 1);
     const int it = uix >> 1, half = uix & 1;
@@ -1116,13 +1124,19 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
   const size_t P1 = (size_t)C.P + 1;
   const bool meas = ws.item_obs != nullptr;  // observables at beta/2 (plans with flag 8)
 
+  // claim numbers as in items_kernel: a fixed first one per lane group, then the queue
+  const int slots = (int)(gridDim.x * blockDim.x) / G;
+  int first = (wib * (int)gridDim.x + (int)blockIdx.x) * (32 / G) + grp;
   for (;;) {
-    int c = 0;
-    if (gl == 0) c = atomicAdd(&ws.counters[1], 1);
-    c = __shfl_sync(gm, c, grp * G);
+    int c = first;
+    first = -1;
+    if (c < 0) {
+      if (gl == 0) c = slots + atomicAdd(&ws.counters[1], 1);
+      c = __shfl_sync(gm, c, grp * G);
+    }
     if (c >= n_units) break;
     // the worklist is ordered longest stretch first: one unit of every four consecutive
-    // claims from the long end, three from the short end
+    // claim numbers from the long end, three from the short end
     const int b = c >> 2, j = c & 3;
     const int uix = j == 0 ? b : n_units - 1 - (3 * b + j - 1);
     const int it = uix >> 1, half = uix & 1;
