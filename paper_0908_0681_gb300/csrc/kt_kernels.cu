@@ -342,14 +342,18 @@ __global__ void __launch_bounds__(1024) order_kernel(DevModel M, Workspace ws, c
   int32_t *tmp = ws.half_info;
   cnt[t] = 0;
   __syncthreads();
-  auto key = [&](int item) {
+  // bin of an item (bin 0 = the longest); keys are >= 0 by construction, clamped anyway
+  auto bin = [&](int item) {
+    int k;
     if (plan) {
       const int4 p = plan[item];
-      return p.y - p.x;
+      k = p.y - p.x;
+    } else {
+      k = ws.desc[item / nk].w;
     }
-    return ws.desc[item / nk].w;
+    return NB - 1 - min(max(k, 0) >> 2, NB - 1);
   };
-  for (int i = t; i < n; i += NB) atomicAdd(&cnt[NB - 1 - min(key(ws.worklist[i]) >> 2, NB - 1)], 1);
+  for (int i = t; i < n; i += NB) atomicAdd(&cnt[bin(ws.worklist[i])], 1);
   __syncthreads();
   // exclusive scan of the bin counts (bin 0 = the longest sequences)
   const int c = cnt[t];
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(1024) order_kernel(DevModel M, Workspace ws, c
   __syncthreads();
   for (int i = t; i < n; i += NB) {
     const int item = ws.worklist[i];
-    tmp[atomicAdd(&cnt[NB - 1 - min(key(item) >> 2, NB - 1)], 1)] = item;
+    tmp[atomicAdd(&cnt[bin(item)], 1)] = item;
   }
   __syncthreads();
   for (int i = t; i < n; i += NB) ws.worklist[i] = tmp[i];
