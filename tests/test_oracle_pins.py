@@ -12,7 +12,7 @@ from itertools import combinations
 import numpy as np
 import pytest
 
-from oracle.oracle import Model, Params, SeqBatch, classify, edit
+from oracle.oracle import Model, Params, SeqBatch, classify, edit, ratio
 from tests import brute
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_degeneracies.json")))
@@ -387,3 +387,86 @@ def test_edit_insert_and_remove():
     assert edit(ops, 1, 0, 0, 0, 2) == [(1.0, 1, 0), (3.0, 1, 1)]   # wraps: the c at 2, then the c^+ at 0
     assert edit(ops, 1, 0, 0, 0, 1) is None   # index 1 is not of flavor 0
     assert edit([(0.5, 0, 1), (1.0, 0, 1)], 1, 0, 0, 0, 0) is None   # successor of the same type
+
+
+def _gap_pair(rng, ops, f, beta):
+    """Two times in one gap between cyclically consecutive flavor-f operators, in cyclic
+    order: an inserted pair there is adjacent in flavor f, so removing its first operator
+    (with its cyclic successor) undoes the insertion."""
+    ts = sorted(t for t, g, _ in ops if g == f)
+    if not ts:
+        a, b = np.sort(rng.uniform(0, beta, 2))
+        return float(a), float(b)
+    k = int(rng.integers(len(ts)))
+    lo, hi = ts[k], (ts[k + 1] if k + 1 < len(ts) else ts[0] + beta)
+    a, b = np.sort(rng.uniform(lo, hi, 2))
+    return float(a % beta), float(b % beta)
+
+
+def _move(kind, f, t_dag=0.0, t_ann=0.0, rem_idx=0):
+    return {"kind": [kind], "flavor": [f], "t_dag": [t_dag], "t_ann": [t_ann], "rem_idx": [rem_idx]}
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_ratio_insert_then_remove_is_identity(n):
+    """Trace ratio (Sec. II local updates): inserting a pair and removing it again gives
+    back the sequence, and the two ratios multiply to one (signs and log-ratios)."""
+    rng = np.random.default_rng(40 + n)
+    beta = 5.0
+    m = Model(Params(n, 4.0, 1.0, mu=mu_half(n, 4.0, 1.0), beta=beta, trunc_eps=1e-8))
+    checked = 0
+    for _ in range(30):
+        ops = _random_ops(rng, n, beta, 2)
+        f = int(rng.integers(2 * n))
+        a, b = _gap_pair(rng, ops, f, beta)
+        d_first = int(rng.integers(2))  # the operator at a: c^+ (segment) or c (anti-segment)
+        t_dag, t_ann = (a, b) if d_first else (b, a)
+        new = edit(ops, 0, f, t_dag, t_ann, 0)
+        idx = new.index((a, f, d_first))
+        assert edit(new, 1, f, 0.0, 0.0, idx) == ops
+        cur = SeqBatch.from_lists([ops])
+        cs, cl, _ = m.trace(cur)
+        s1, lr1, ns, nl = ratio(m, cur, cs, cl, _move(0, f, t_dag, t_ann))
+        s2, lr2, bs, bl = ratio(m, SeqBatch.from_lists([new]), ns, nl, _move(1, f, rem_idx=idx))
+        assert bs[0] == cs[0] and (cs[0] == 0 or bl[0] == cl[0])
+        if cs[0] == 0:
+            assert s1[0] == 0 and math.isnan(lr1[0])
+            continue
+        if ns[0] == 0:
+            assert s1[0] == 0 and lr1[0] == -math.inf and s2[0] == 0 and math.isnan(lr2[0])
+            continue
+        checked += 1
+        assert s1[0] * s2[0] == 1
+        assert s1[0] == cs[0] * ns[0]
+        assert lr1[0] + lr2[0] == 0.0
+    assert checked >= 8
+
+
+def test_ratio_matches_full_space_brute_force():
+    """Trace ratio T_new / T_cur against the full-space Kronecker/expm traces (2 orbitals,
+    untruncated); numerically-zero traces (FP64 and long double disagree) are skipped."""
+    n, beta = 2, 4.0
+    rng = np.random.default_rng(77)
+    U, J, mu = 4.0, 1.0, mu_half(2, 4.0, 1.0)
+    m = Model(Params(n, U, J, mu=mu, beta=beta, trunc_eps=0.0))
+    mx = Model(Params(n, U, J, mu=mu, beta=beta, trunc_eps=0.0), "ext")
+    Hf = brute.hamiltonian(n, U, J, U - 2 * J, mu, np.zeros(n))
+    checked = 0
+    for _ in range(40):
+        ops = _random_ops(rng, n, beta, 2)
+        f = int(rng.integers(2 * n))
+        t_dag, t_ann = (float(t) for t in rng.uniform(0, beta, 2))
+        new = edit(ops, 0, f, t_dag, t_ann, 0)
+        cur = SeqBatch.from_lists([ops])
+        cs, cl, _ = m.trace(cur)
+        s, lr, ns, nl = ratio(m, cur, cs, cl, _move(0, f, t_dag, t_ann))
+        ok = [classify([x], [y], [xx], [yy])[0] == 2
+              for (x, y), (xx, yy) in (((cs[0], cl[0]), one(mx, ops)[:2]), ((ns[0], nl[0]), one(mx, new)[:2]))]
+        if not all(ok):
+            continue
+        Tc, _ = brute.trace_all_states(Hf, beta, ops, n)
+        Tn, _ = brute.trace_all_states(Hf, beta, new, n)
+        checked += 1
+        assert s[0] == int(np.sign(Tn * Tc))
+        assert abs(lr[0] - math.log(abs(Tn / Tc))) < 1e-9
+    assert checked >= 10
