@@ -113,3 +113,83 @@ def test_workspace_size_grows_with_walkers():
     m = kt.kt_model_create(3, 4.0, 1.0, 5.0, 10.0, flags=kt.KT_HOST_ONLY)
     a, b = kt.kt_workspace_size(m, 10), kt.kt_workspace_size(m, 1000)
     assert 0 < a < b
+
+
+def test_entry_points_reject_bad_arguments_without_touching_a_device():
+    """Every documented argument check that comes before any CUDA call: null handles and
+    outputs, host-only models, out-of-range sizes and shapes return KT_EINVAL; destroying a
+    null handle is a no-op."""
+    lib = kt.load()
+    NULL = None
+    i32 = ctypes.c_int32
+
+    def call(name, *args):
+        return getattr(lib, name)(*args)
+
+    m = kt.kt_model_create(2, 4.0, 1.0, 2.0, 5.0, flags=kt.KT_HOST_ONLY)
+    mh = m.handle
+    b = kt.kt_seq_batch(1, None, None, None, None)
+    mv = kt.kt_move_batch(None, None, None, None, None)
+    out = ctypes.c_void_p()
+    bad = kt.KT_EINVAL
+    # traces and ratios on a host-only model
+    assert call("kt_trace_ratio", mh, ctypes.byref(b), NULL, NULL, ctypes.byref(mv), NULL, NULL, NULL, NULL, NULL,
+                ctypes.c_size_t(0), NULL) == bad
+    assert call("kt_trace_ratio_static", mh, ctypes.byref(b), NULL, NULL, ctypes.byref(mv), NULL, NULL, NULL, NULL,
+                NULL) == bad
+    assert call("kt_measure", mh, ctypes.byref(b), NULL, NULL, NULL, NULL, NULL, NULL, ctypes.c_size_t(0), NULL) == bad
+    assert call("kt_autotune", mh, ctypes.byref(b), NULL, NULL, NULL, NULL, ctypes.c_size_t(0), NULL,
+                ctypes.byref(i32())) == bad
+    assert call("kt_timing_begin", mh, i32(4)) == bad
+    assert call("kt_timing_end", NULL, NULL, NULL) == bad
+    assert call("kt_model_set_tiling", mh, i32(3)) == bad
+    assert call("kt_model_query", NULL, NULL) == bad
+    assert call("kt_workspace_size", mh, i32(-1), ctypes.byref(ctypes.c_size_t())) == bad
+    assert call("kt_measure_workspace_size", mh, i32(-1), ctypes.byref(ctypes.c_size_t())) == bad
+    # partial-state cache
+    assert call("kt_ratio_cache_create", mh, i32(4), i32(16), ctypes.byref(out)) == bad
+    assert call("kt_ratio_cache_create", NULL, i32(4), i32(16), ctypes.byref(out)) == bad
+    assert call("kt_ratio_cache_create", mh, i32(0), i32(16), ctypes.byref(out)) == bad
+    assert call("kt_ratio_cache_create", mh, i32(4), i32(0), ctypes.byref(out)) == bad
+    assert call("kt_ratio_cache_build", NULL, ctypes.byref(b), NULL) == bad
+    for name in ("kt_trace_ratio_cached", "kt_ratio_cache_propose"):
+        assert call(name, NULL, ctypes.byref(b), NULL, NULL, ctypes.byref(mv), NULL, NULL, NULL, NULL, NULL) == bad
+    assert call("kt_ratio_cache_commit", NULL, NULL, NULL, NULL) == bad
+    call("kt_ratio_cache_destroy", NULL)
+    # sweeps
+    hyb = np.zeros(4 * 11)
+    p = kt.kt_sweep_params(4, 8, 10, hyb.ctypes.data, 20, 0, 0)
+    assert call("kt_sweep_create", mh, ctypes.byref(p), ctypes.byref(out)) == bad
+    assert call("kt_sweep_create", NULL, ctypes.byref(p), ctypes.byref(out)) == bad
+    assert call("kt_sweep_run", NULL, i32(1), NULL, i32(0), NULL) == bad
+    assert call("kt_sweep_run_da", NULL, i32(1), NULL, i32(0), NULL) == bad
+    assert call("kt_sweep_collect", NULL, i32(1), NULL, NULL, NULL, NULL, i32(0), NULL) == bad
+    assert call("kt_sweep_set_configs", NULL, NULL) == bad
+    assert call("kt_sweep_set_stats", NULL, NULL) == bad
+    assert call("kt_sweep_set_surrogate", NULL, NULL) == bad
+    assert call("kt_sweep_get_state", NULL, NULL, NULL) == bad
+    assert call("kt_sweep_get_accumulators", NULL, NULL, NULL) == bad
+    assert call("kt_sweep_counters", NULL, NULL) == bad
+    assert call("kt_sweep_reset_accumulators", NULL, NULL) == bad
+    assert call("kt_sweep_feature_size", NULL, NULL) == bad
+    call("kt_sweep_destroy", NULL)
+    # surrogate network and the tensor-core product: shapes must be multiples of 16
+    assert call("kt_mlp_create", i32(16), i32(8), ctypes.byref(out)) == bad
+    assert call("kt_mlp_create", i32(15), i32(16), ctypes.byref(out)) == bad
+    assert call("kt_mlp_create", i32(16), i32(16), NULL) == bad
+    assert call("kt_mlp_num_params", NULL, NULL) == bad
+    assert call("kt_mlp_set_params", NULL, NULL) == bad
+    assert call("kt_mlp_get_params", NULL, NULL) == bad
+    assert call("kt_mlp_get_grads", NULL, NULL) == bad
+    assert call("kt_mlp_forward", NULL, NULL, i32(16), NULL, NULL) == bad
+    assert call("kt_mlp_backward", NULL, NULL, NULL, i32(16), NULL, NULL) == bad
+    assert call("kt_mlp_adam", NULL, ctypes.c_float(1e-3), NULL) == bad
+    assert call("kt_mlp_error", NULL, NULL) == bad
+    call("kt_mlp_destroy", NULL)
+    A = np.zeros(64, np.uint16)
+    C = np.zeros(64, np.float32)
+    err = i32()
+    for M_, N_, K_ in ((0, 16, 16), (1, 8, 16), (1, 16, 8), (1, 24, 16)):
+        assert call("kt_gemm_bf16", ctypes.c_void_p(A.ctypes.data), i32(16), ctypes.c_void_p(A.ctypes.data), i32(16),
+                    ctypes.c_void_p(C.ctypes.data), i32(16), i32(M_), i32(N_), i32(K_), ctypes.byref(err), NULL) == bad
+    call("kt_model_destroy", NULL)
