@@ -337,7 +337,7 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   std::vector<uint16_t> st_bits(N);
   std::vector<double> st_diag64(N);
   for (int b = 0; b < B; ++b) {
-    const int d = blk_dim[b], w = blk_nnz[b];
+    const int d = blk_dim[b];
     for (int r = 0; r < d; ++r) {
       const uint32_t x = members[b][r];
       st_bits[blk_off[b] + r] = (uint16_t)x;

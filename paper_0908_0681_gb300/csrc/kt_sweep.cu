@@ -947,7 +947,6 @@ static kt_status run_steps(kt_sweep *s, int32_t n_steps, const double *uniforms,
     if (mode == 2) kt::sweep_record_kernel<<<grid, wpb * 32, 0, st>>>(v, feat, targ, count, cap);
     kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, u, ustride, w.desc, mode == 1);
     if (s->cache_mem) {
-      const long long nitems = (long long)v.nw * M.n_kept;
       kt::launch_cache_commit(s->cache, v.nw, M.n_kept, w.desc, w.wstatus, v.p_acc, v.r_status, s->cache_words, st);
     }
     if (meas_every > 0 && (step + 1) % meas_every == 0) {
