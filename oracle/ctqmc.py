@@ -1,7 +1,7 @@
 """Plain CT-HYB Markov chain of the hybridization expansion (test infrastructure only).
 
-Only the tests and the CPU-baseline leg of the benchmark import this module; the
-product library never calls it. Every weight is computed from scratch from its
+Only the tests and the smoke check import this module; the product library never
+calls it. Every weight is computed from scratch from its
 definition; nothing is updated incrementally.
 
 Weight of a configuration (Sec. II, Eq. (weight_strong) with a hybridization that is
