@@ -45,3 +45,29 @@ def test_ctypes_structures_match_the_header(tmp_path):
 
 def test_stats_words_cover_the_structure():
     assert ctypes.sizeof(kt.kt_stats) == 8 * kt.STATS_WORDS
+
+
+def test_constants_match_the_header(tmp_path):
+    """Status codes, precision and flag values, and the sizes the binding hard-codes, are the
+    header's (a C program prints them)."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    names = kt.STATUS_NAMES + ["KT_FP64", "KT_FP32_KRYLOV", "KT_DENSITY_ONLY", "KT_SECTOR_BLOCKS", "KT_HOST_ONLY",
+                               "KT_P_HIST", "KT_SWEEP_NCOUNTERS", "KT_MLP_HIDDEN", "KT_STATIC_SCRATCH_BYTES"]
+    lines = ['#include <stdio.h>', '#include "kt.h"', 'int main(void) {']
+    lines += [f'  printf("{n} %lld\\n", (long long)({n}));' for n in names]
+    lines += [f'  printf("NOBS{n} %lld\\n", (long long)KT_MEASURE_NOBS({n}));' for n in (3, 5, 7)]
+    lines += ['  return 0;', '}']
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    c = dict((k, int(v)) for k, v in (line.split() for line in out.splitlines()))
+    for code, n in enumerate(kt.STATUS_NAMES):
+        assert c[n] == code == getattr(kt, n), n
+    for n in names[len(kt.STATUS_NAMES):]:
+        assert c[n] == getattr(kt, n), n
+    for n in (3, 5, 7):
+        assert c[f"NOBS{n}"] == kt.measure_nobs(n)
