@@ -8,6 +8,7 @@ here uses sectors, ranks or the oracle's code.
 """
 from __future__ import annotations
 
+import math
 from functools import reduce
 
 import numpy as np
@@ -93,3 +94,40 @@ def trace_all_states_mp(H, beta, ops_seq, n_orb, dps=40):
         t_prev = mp.mpf(t)
     M = prop(mp.mpf(beta) - t_prev) * M
     return sum(M[i, i] for i in range(n)), E0
+
+
+def kept_projector(H, beta, trunc_eps, deg_tol=1e-9):
+    """Projector on the kept multiplets of the full-space H (truncation type (i) of Sec. II):
+    eigenvalues are grouped into multiplets of neighbours within deg_tol * max(1, |E|), and
+    whole multiplets whose lowest member has exp(-beta (E - E0)) >= trunc_eps are kept.
+    Returns (P, number of kept states)."""
+    E, V = np.linalg.eigh(H)
+    E0 = E[0]
+    keep = 0
+    i = 0
+    while i < len(E):
+        j = i + 1
+        while j < len(E) and E[j] - E[j - 1] <= deg_tol * max(1.0, abs(E[j])):
+            j += 1
+        if math.exp(-beta * (E[i] - E0)) < trunc_eps:
+            break
+        keep = j
+        i = j
+    Vk = V[:, :keep]
+    return Vk @ Vk.T, keep
+
+
+def trace_projected(H, beta, ops_seq, n_orb, P):
+    """T~ = e^{beta E0} Tr[P e^{-(beta-t_K)H} O_K ... O_1 e^{-t_1 H}] with full-space
+    scaling-and-squaring exponentials of H - E0 (P commutes with H)."""
+    c = fermion_ops(n_orb)
+    E0 = np.linalg.eigvalsh(H).min()
+    Hs = H - E0 * np.eye(len(H))
+    M = P.copy()
+    t_prev = 0.0
+    for (t, f, d) in ops_seq:
+        M = scipy.linalg.expm(-(t - t_prev) * Hs) @ M
+        M = (c[f].T if d else c[f]) @ M
+        t_prev = t
+    M = scipy.linalg.expm(-(beta - t_prev) * Hs) @ M
+    return float(np.trace(M)), E0

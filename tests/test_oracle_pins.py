@@ -272,6 +272,54 @@ def test_brute_force_full_space(n):
     assert checked >= 10
 
 
+def _gap_threshold(H, beta, n_multiplets, deg_tol=1e-9):
+    """A trunc_eps that keeps exactly the lowest n_multiplets multiplets of the full-space H,
+    set in the middle (geometrically) of the gap to the next one."""
+    E = np.linalg.eigvalsh(H)
+    lows = [0]
+    for i in range(1, len(E)):
+        if E[i] - E[i - 1] > deg_tol * max(1.0, abs(E[i])):
+            lows.append(i)
+    a, b = E[lows[n_multiplets - 1]] - E[0], E[lows[n_multiplets]] - E[0]
+    return math.exp(-beta * 0.5 * (a + b))
+
+
+@pytest.mark.parametrize("n,n_mult", [(2, 3), (3, 4), (3, 7)])
+def test_truncated_trace_full_space_projector(n, n_mult):
+    """Truncation type (i) of Sec. II with spin flip and pair hopping on: the truncated trace
+    with operators equals Tr[P e^{-(beta-t_K)H} O_K ... O_1 e^{-t_1 H}], P the projector on the
+    kept multiplets of the full-space Kronecker H (numpy eigh, whole multiplets) and every
+    propagator a full-space scaling-and-squaring exponential. Nothing here uses the oracle's
+    sectors, eigensolver or kept-state list."""
+    rng = np.random.default_rng(300 + 10 * n + n_mult)
+    U, J, beta = 4.0, 1.0, 4.0
+    mu = mu_half(n, U, J) + 0.6
+    delta = rng.uniform(-0.3, 0.3, n)
+    Hf = brute.hamiltonian(n, U, J, U - 2 * J, mu, delta)
+    eps = _gap_threshold(Hf, beta, n_mult)
+    P, n_keep = brute.kept_projector(Hf, beta, eps)
+    assert 1 < n_keep < 4 ** n
+    m = Model(Params(n, U, J, mu=mu, delta=tuple(delta), beta=beta, trunc_eps=eps))
+    mx = Model(Params(n, U, J, mu=mu, delta=tuple(delta), beta=beta, trunc_eps=eps), "ext")
+    assert m.nkept == n_keep
+    # the kept set really has multiplets (spin degeneracy survives the crystal field)
+    assert n_keep > n_mult
+    checked = 0
+    for _ in range(40):
+        ops = _random_ops(rng, n, beta, 3)
+        Tb, E0b = brute.trace_projected(Hf, beta, ops, n, P)
+        s, la, lt = one(m, ops)
+        sx, lax, ltx = one(mx, ops)
+        assert abs(E0b - m.E0) < 1e-12 * max(1.0, abs(E0b))
+        if classify([s], [lt], [sx], [ltx])[0] != 2:
+            assert abs(Tb) < 1e-10 * n_keep
+            continue
+        checked += 1
+        assert s == int(np.sign(Tb))
+        assert abs(lt - math.log(abs(Tb))) < 1e-9
+    assert checked >= 10
+
+
 def test_brute_force_extended_precision_classes():
     """Conditioning classes agree with a 40-digit full-space computation (2 orbitals)."""
     n = 2
