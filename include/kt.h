@@ -69,6 +69,13 @@ typedef enum {
 #define KT_DENSITY_ONLY 1u   /* drop spin-flip and pair-hopping (density-density H_loc) */
 #define KT_SECTOR_BLOCKS 2u  /* propagate in whole (n_up, n_dn) sectors instead of the
                                 finer blocks that also fix the set of singly occupied orbitals */
+#define KT_FP32_TRIDIAG64 4u /* FP32 path only: the final exponential of the small tridiagonal T_p of
+                                every propagation in FP64 (full QL for p >= 3, closed form for
+                                p = 2) instead of FP32 Ritz vectors with double-float Ritz values.
+                                FP32 Ritz vectors are off by about u ||T_p|| / gap, and these errors
+                                neither average out nor cancel between the halves of a sequence;
+                                with this flag the Krylov vectors carry the only FP32 rounding.
+                                Slower: the FP64 pipe of GB300 is 1/64 of the FP32 one */
 #define KT_HOST_ONLY 256u    /* build and check the model on the host only: no device upload;
                                 trace calls on such a model return KT_EINVAL */
 
@@ -88,7 +95,7 @@ typedef struct {
   double krylov_tol;    /* relative a-posteriori error target per propagation */
   int32_t krylov_pmax;  /* cap on the Krylov dimension (<= 0: the compiled maximum) */
   int32_t precision;    /* KT_FP64 or KT_FP32_KRYLOV */
-  uint32_t flags;       /* KT_DENSITY_ONLY | KT_SECTOR_BLOCKS */
+  uint32_t flags;       /* KT_DENSITY_ONLY | KT_SECTOR_BLOCKS | KT_FP32_TRIDIAG64 */
 } kt_model_params;
 
 typedef struct kt_model kt_model;
@@ -412,6 +419,18 @@ kt_status kt_sweep_set_configs(kt_sweep *s, const kt_seq_batch *host_batch);
 kt_status kt_sweep_set_stats(kt_sweep *s, kt_stats *stats);
 kt_status kt_sweep_get_state(kt_sweep *s, const kt_sweep_state *dst, void *stream);
 kt_status kt_sweep_get_accumulators(kt_sweep *s, const kt_sweep_accum *dst, void *stream);
+/* Drift guard: recompute, for every walker, everything the chain tracks incrementally, from
+ * its current configuration and from scratch, and replace the tracked values: the inverse
+ * bath matrices M = G_f^{-1} and log|det G_f| in FP64 on the device (Gauss-Jordan elimination
+ * with partial pivoting, one warp per walker and flavor), the sign of the bath permutation,
+ * and the local trace (this library's pipeline at the model's precision). The determinant
+ * fast updates of Sec. II and the products of accepted trace ratios accumulate rounding over
+ * a long chain; calling this every few hundred steps bounds that drift. A walker whose fresh
+ * evaluation fails (a singular G_f, a trace error) keeps its tracked values. Enqueued on the
+ * stream; with max_dev (HOST [4], or NULL) it synchronises the stream and writes the largest
+ * |tracked - fresh| of log|T| and of sum_f log|det G_f| over the walkers, the number of walkers
+ * whose tracked sign of w or of T differed, and the number left unchanged. */
+kt_status kt_sweep_refresh(kt_sweep *s, double *max_dev, void *stream);
 /* Synchronises the device and copies the counters to out[KT_SWEEP_NCOUNTERS]. */
 kt_status kt_sweep_counters(kt_sweep *s, unsigned long long *out);
 /* Zero the accumulators and counters (the configurations are kept). */
@@ -460,6 +479,18 @@ kt_status kt_mlp_forward(kt_mlp *n, const void *X, int32_t B, float *y, void *st
 kt_status kt_mlp_backward(kt_mlp *n, const void *X, const float *t, int32_t B, float *loss, void *stream);
 /* HOST copy of the packed gradients of the last kt_mlp_backward; synchronous. */
 kt_status kt_mlp_get_grads(kt_mlp *n, float *host_grads_out);
+/* The intermediate values of the last kt_mlp_backward (batch of B rows; KT_EINVAL if B
+ * differs), copied to HOST arrays (any may be NULL; synchronous), so that every stage of the
+ * gradient can be checked on its own inputs:
+ *   z1  [B][256] FP32         X W1^T, before the bias;
+ *   h1  [B][256] BF16 bits    relu(z1 + b1) rounded to nearest even;
+ *   z2  [B][256] FP32         h1 W2^T, before the bias;
+ *   dy  [B]      FP32         2 (y - t) / B;
+ *   dz2 [B][256] BF16 bits    dy w3 where z2 + b2 > 0, else 0, rounded;
+ *   dh1 [B][256] FP32         dz2 W2 (W2 in BF16);
+ *   dz1 [256][B] BF16 bits    dh1 where z1 + b1 > 0, else 0, rounded (transposed layout). */
+kt_status kt_mlp_get_tape(kt_mlp *n, int32_t B, float *z1, uint16_t *h1, float *z2, float *dy, uint16_t *dz2,
+                          float *dh1, uint16_t *dz1);
 /* One Adam step with the stored gradients. */
 kt_status kt_mlp_adam(kt_mlp *n, float lr, void *stream);
 /* Synchronises; *out = 1 if a tensor-core wait of any call timed out so far. */

@@ -118,6 +118,47 @@ def loss_and_grads(p: dict, X: np.ndarray, t: np.ndarray):
     return L, g
 
 
+def bf16(a) -> np.ndarray:
+    """Round to the nearest bfloat16, ties to even, through FP32 (the value is first rounded
+    to FP32, as the kernels hold it); returned as float64. bfloat16 is the upper half of an
+    IEEE FP32 word, so rounding adds half an ulp of the lower 16 bits (plus the tie bit)."""
+    x = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = x.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def from_bf16_bits(b) -> np.ndarray:
+    """bfloat16 bit patterns (uint16) as float64."""
+    return (np.asarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def loss_and_grads_bf16(p: dict, X: np.ndarray, t: np.ndarray):
+    """The chain rule of loss_and_grads with the rounding points of a BF16 tensor-core
+    implementation: the hidden activations H1 and the back-propagated dZ2 and dZ1 are
+    rounded to BF16 (they are the operands of the products), the bias gradients are sums of
+    the unrounded values, and everything else stays FP64. The weights and X are used as
+    given (pass BF16-representable W1, W2, X). Returns (L, grads, intermediates)."""
+    B = X.shape[0]
+    a1 = X @ p["W1"].T + p["b1"]
+    h1 = bf16(np.maximum(a1, 0.0))
+    a2 = h1 @ p["W2"].T + p["b2"]
+    h2 = np.maximum(a2, 0.0)
+    y = h2 @ p["w3"] + p["b3"][0]
+    r = y - t
+    L = float(np.mean(r * r))
+    dy = 2.0 * r / B
+    e2 = np.outer(dy, p["w3"]) * (a2 > 0)
+    dz2 = bf16(e2)
+    g = {"w3": h2.T @ dy, "b3": np.array([dy.sum()]), "b2": e2.sum(axis=0), "W2": dz2.T @ h1}
+    dh1 = dz2 @ p["W2"]
+    e1 = dh1 * (a1 > 0)
+    dz1 = bf16(e1)
+    g["b1"] = e1.sum(axis=0)
+    g["W1"] = dz1.T @ X
+    return L, g, {"a1": a1, "h1": h1, "a2": a2, "h2": h2, "y": y, "dy": dy, "dz2": dz2, "dh1": dh1, "dz1": dz1}
+
+
 def adam_step(p: dict, g: dict, m: dict, v: dict, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (step counts from 1); returns new (p, m, v)."""
     np_, nm, nv = {}, {}, {}

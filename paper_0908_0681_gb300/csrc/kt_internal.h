@@ -18,6 +18,7 @@ namespace kt {
 // Inside a block, rows are the bitstrings in ascending order.
 struct DevModel {
   int n_orb, nf, n_states, n_blocks, n_kept, d_max, pmax;
+  int tri64;  // FP32 path: final tridiagonal exponential in FP64 (KT_FP32_TRIDIAG64)
   double beta, E0, tol, brk_rel;
 
   const int32_t *blk_off;     // [n_blocks] first global row of the block
@@ -189,7 +190,10 @@ struct ModelView {
   const DevModel *dev;
   int precision, kernel_dmax, group_lanes;
   bool host_only;
+  int device;  // CUDA device holding the model's tables
 };
 ModelView model_view(const kt_model *m);
+// True when the current CUDA device is the one that holds the model's tables.
+bool on_model_device(const ModelView &v);
 
 }  // namespace kt

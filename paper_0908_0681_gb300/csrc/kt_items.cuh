@@ -758,13 +758,26 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
   }
   // final exp(-dt T_p) e_1 at the stopping p
   if constexpr (F32) {
-    if (p <= 2) {
+    if (p == 2 && M.tri64) {
+      // KT_FP32_TRIDIAG64: the 2x2 closed form in FP64 from the double-float alpha, beta
+      const float2 a0 = reinterpret_cast<float2 *>(s.a)[grp], a1 = reinterpret_cast<float2 *>(s.a)[IPW + grp];
+      const float2 b0 = reinterpret_cast<float2 *>(s.b)[grp];
+      double y0, y1;
+      logfac = exp2x2((double)a0.x + (double)a0.y, (double)a1.x + (double)a1.y, (double)b0.x + (double)b0.y, dt, y0,
+                      y1);
+      if (gl == 0) {
+        s.y32[grp] = (float)y0;
+        s.y32[IPW + grp] = (float)y1;
+      }
+      __syncwarp(gm);
+    } else if (p <= 2) {
       tri_small_f32(s, grp, gl, gm, p, dt, logfac);
     } else {
-      if constexpr (DMAX > 16) {
-        // blocks beyond 16 rows (seven orbitals) hold close Ritz pairs whose FP32
-        // vectors would leak rotation errors into y: full FP64 eigensolve at the final p
-        // (alpha, beta first widened in place from double-float to FP64)
+      if (DMAX > 16 || M.tri64) {
+        // FP32 Ritz vectors are off by about u ||T_p|| / gap, an error that does not average
+        // out over the intervals of a sequence; blocks beyond 16 rows (seven orbitals) and
+        // models with KT_FP32_TRIDIAG64 therefore take the full FP64 eigensolve at the final
+        // p (alpha, beta first widened in place from double-float to FP64)
         for (int k = gl; k < p; k += G) {
           const float2 av = reinterpret_cast<float2 *>(s.a)[k * IPW + grp];
           const float2 bv = reinterpret_cast<float2 *>(s.b)[k * IPW + grp];

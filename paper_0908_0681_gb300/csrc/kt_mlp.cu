@@ -578,7 +578,7 @@ inline unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1)
 }  // namespace kt
 
 struct kt_mlp {
-  int n_in = 0, maxB = 0, step = 0;
+  int n_in = 0, maxB = 0, step = 0, lastB = 0;
   long long P = 0;
   void *mem = nullptr;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
@@ -754,7 +754,25 @@ kt_status kt_mlp_backward(kt_mlp *n, const void *X, const float *t, int32_t B, f
   if (kt::gemm_bf16(n->dZ1Tb, B, n->XTb, B, n->part, nin, H, nin, B, n->err, st, MAX_SPLITS)) return KT_ECUDA;
   splitk_sum_kernel<<<blocks((long long)H * nin), 256, 0, st>>>(n->part, n->gW1, S, (long long)H * nin);
   if (loss) cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToDevice, st);
+  n->lastB = B;
   return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ECUDA;
+}
+
+kt_status kt_mlp_get_tape(kt_mlp *n, int32_t B, float *z1, uint16_t *h1, float *z2, float *dy, uint16_t *dz2,
+                          float *dh1, uint16_t *dz1) {
+  using namespace kt::mlp;
+  if (!n || B < 1 || B != n->lastB) return KT_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return KT_ECUDA;
+  const size_t bh = (size_t)B * H;
+  const struct {
+    void *dst;
+    const void *src;
+    size_t bytes;
+  } cp[] = {{z1, n->Z1, bh * 4}, {h1, n->H1b, bh * 2}, {z2, n->Z2, bh * 4}, {dy, n->dy, (size_t)B * 4},
+            {dz2, n->dZ2b, bh * 2}, {dh1, n->dH1, bh * 4}, {dz1, n->dZ1Tb, bh * 2}};
+  for (const auto &c : cp)
+    if (c.dst && cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return KT_ECUDA;
+  return KT_OK;
 }
 
 kt_status kt_mlp_adam(kt_mlp *n, float lr, void *stream) {

@@ -104,6 +104,7 @@ struct kt_model {
   std::vector<double> spectrum;
   double e_kept_max = 0.0;
   bool host_only = false;
+  int device = -1;  // CUDA device that holds the tables (current at kt_model_create)
   // per-stage timing (kt_timing_begin / kt_timing_end)
   std::vector<kt::StageEvents> timing;
   int timing_used = 0;
@@ -170,8 +171,17 @@ Workspace carve_workspace(void *base, int n, int n_kept, int d_max, int n_obs_it
 
 namespace kt {
 
+bool on_model_device(const ModelView &v) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return dev == v.device;
+}
+
 ModelView model_view(const kt_model *m) {
-  return ModelView{&m->dev, m->params.precision, m->kernel_dmax, m->group_lanes, m->host_only};
+  return ModelView{&m->dev, m->params.precision, m->kernel_dmax, m->group_lanes, m->host_only, m->device};
 }
 
 }  // namespace kt
@@ -521,6 +531,7 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   }
   M->dev_mem = dmem;
   M->dev_bytes = total;
+  if (cudaGetDevice(&M->device) != cudaSuccess) { cudaGetLastError(); M->device = -1; }
   char *base = (char *)dmem;
   auto at = [&](size_t i) { return (void *)(base + pieces[i].off); };
   kt::DevModel &D = M->dev;
@@ -529,6 +540,7 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   D.pmax = (P.krylov_pmax > 0) ? std::min(P.krylov_pmax, pcap) : pcap;
   D.beta = P.beta; D.E0 = E0;
   D.tol = P.krylov_tol;
+  D.tri64 = (P.precision == KT_FP32_KRYLOV && (P.flags & KT_FP32_TRIDIAG64)) ? 1 : 0;
   D.brk_rel = (P.precision == KT_FP64) ? 1e-14 : 8.0 * std::ldexp(1.0, -24);
   if (P.precision == KT_FP32_KRYLOV) D.tol = std::max(D.tol, 8.0 * std::ldexp(1.0, -24));
   D.blk_off = (const int32_t *)at(i_off); D.blk_dim = (const int32_t *)at(i_dim); D.blk_nnz = (const int32_t *)at(i_nnz);
@@ -595,6 +607,7 @@ static kt_status run(kt_model *m, const kt_seq_batch *b, const kt_move_batch *mv
     return KT_EINVAL;
   const int nobs_item = obs ? m->dev.nf + m->dev.n_orb + 1 : 0;
   if (ws_bytes < kt::workspace_bytes(b->n, m->dev.n_kept, m->dev.d_max, nobs_item)) return KT_ENOMEM;
+  if (!kt::on_model_device(kt::model_view(m))) return KT_EINVAL;  // tables on another GPU
   kt::SeqView sv{b->n, b->offsets, b->tau, b->flavor, b->dagger};
   kt::MoveView mvv{};
   if (mv) mvv = kt::MoveView{mv->kind, mv->flavor, mv->t_dag, mv->t_ann, mv->rem_idx};

@@ -14,6 +14,7 @@
 // and every other scratch entry is written before it is read. Calls whose
 // kernels overlap on the GPU (for example on two streams) race on the array;
 // serialise them.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -26,11 +27,35 @@ static __device__ __align__(256) unsigned char kt_static_scratch[KT_STATIC_SCRAT
 
 constexpr int kMaxDevices = 64;
 void *g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 std::mutex g_scratch_mu;
+
+// The driver's current context (through the runtime's entry-point lookup, so that the
+// library needs no link against the driver library); nullptr if unavailable.
+CUcontext current_context() {
+  using Fn = CUresult (*)(CUcontext *);
+  static Fn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<Fn>(p);
+    cudaGetLastError();
+  }
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
 
 // Device address of the scratch array on the current device. In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached together with the context it
+// belongs to: after a device reset the runtime creates a new context and loads the
+// library's device image again, so a context other than the cached one looks the
+// address up afresh.
 kt_status scratch_address(void **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -38,7 +63,8 @@ kt_status scratch_address(void **out) {
     return KT_ECUDA;
   }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  const CUcontext ctx = current_context();
+  if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, kt_static_scratch);
     if (e != cudaSuccess || p == nullptr) {
@@ -46,6 +72,7 @@ kt_status scratch_address(void **out) {
       return KT_ECUDA;
     }
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = current_context();  // the lookup may have made the primary context current
   }
   *out = g_scratch_addr[dev];
   return KT_OK;
@@ -64,6 +91,8 @@ extern "C" kt_status kt_trace_ratio_static(kt_model *m, const kt_seq_batch *cur,
       !moves->t_dag || !moves->t_ann || !moves->rem_idx)
     return KT_EINVAL;
   if (kt::workspace_bytes(cur->n, v.dev->n_kept, v.dev->d_max) > (size_t)KT_STATIC_SCRATCH_BYTES) return KT_ENOMEM;
+  // the scratch array of the current device must sit beside the model's tables
+  if (!kt::on_model_device(v)) return KT_EINVAL;
   void *scratch = nullptr;
   const kt_status rc = scratch_address(&scratch);
   if (rc != KT_OK) return rc;

@@ -97,6 +97,14 @@ struct SweepView {
   double *m_log;
   int32_t *m_status;
   unsigned long long *counters;
+  // refresh from scratch (kt_sweep_refresh)
+  double *f_detlog;   // [nw][nf] log|det G_f| recomputed
+  int8_t *f_detsign;  // [nw][nf] its sign (0: singular)
+  int8_t *f_tsign;    // [nw] trace recomputed
+  double *f_tlog;
+  int32_t *f_tstat;
+  unsigned long long *f_dev;  // [4] max |d log T| and max |d log det| (bits of non-negative doubles),
+                              //     sign mismatches, walkers left unchanged
 };
 
 // Fh_f(x): linear interpolation of F_f on tau_i = i beta / n_tau, antiperiodic for x < 0.
@@ -593,6 +601,153 @@ __global__ void sweep_obs_accumulate_kernel(SweepView S) {
   if (isfinite(v)) S.obs_sum[t] += (double)S.w_sign[w] * v;
 }
 
+// Refresh, step 1 (one warp per (walker, flavor)): G_f[i][j] = Fh_f(tau'_i - tau_j) over the
+// stored creator and annihilator times, built in the slot of M and inverted there by
+// Gauss-Jordan elimination with partial pivoting in FP64 (a lane owns whole rows, so every
+// row update reads only the finished pivot row); log|det G_f| and its sign are recorded.
+// The inverse keeps M's layout: M[j][i] = (G_f^{-1})_{ji}, rows indexed by annihilators.
+__global__ void sweep_refresh_det_kernel(SweepView S) {
+  extern __shared__ int piv_sh[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wf = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wf >= S.nw * S.nf) return;
+  const int f = wf % S.nf, kc = S.kcap, k = S.kf[wf];
+  int *perm = piv_sh + wib * kc;
+  double *A = S.M + (size_t)wf * kc * kc;
+  const double *rt = S.row_t + (size_t)wf * kc, *ct = S.col_t + (size_t)wf * kc;
+  for (int idx = lane; idx < k * k; idx += 32) {
+    const int i = idx / k, j = idx - i * k;
+    A[(size_t)i * kc + j] = hyb_Fh(S, f, rt[i] - ct[j]);
+  }
+  __syncwarp();
+  double ld = 0.0;
+  int sg = 1;
+  for (int c = 0; c < k && sg != 0; ++c) {
+    double best = -1.0;
+    int pr = c;
+    for (int r = c + lane; r < k; r += 32) {
+      const double a = fabs(A[(size_t)r * kc + c]);
+      if (a > best) {
+        best = a;
+        pr = r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(FULL, best, o);
+      const int opr = __shfl_xor_sync(FULL, pr, o);
+      if (ob > best || (ob == best && opr < pr)) {
+        best = ob;
+        pr = opr;
+      }
+    }
+    if (!(best > 0.0) || !isfinite(best)) {
+      sg = 0;
+      break;
+    }
+    if (lane == 0) perm[c] = pr;
+    if (pr != c) {
+      for (int j = lane; j < k; j += 32) {
+        const double t = A[(size_t)c * kc + j];
+        A[(size_t)c * kc + j] = A[(size_t)pr * kc + j];
+        A[(size_t)pr * kc + j] = t;
+      }
+      sg = -sg;
+    }
+    __syncwarp();
+    const double pv = A[(size_t)c * kc + c];
+    ld += log(fabs(pv));
+    if (pv < 0.0) sg = -sg;
+    const double inv = 1.0 / pv;
+    __syncwarp();
+    for (int j = lane; j < k; j += 32) A[(size_t)c * kc + j] = (j == c) ? inv : A[(size_t)c * kc + j] * inv;
+    __syncwarp();
+    for (int r = lane; r < k; r += 32) {
+      if (r == c) continue;
+      double *Ar = A + (size_t)r * kc;
+      const double fct = Ar[c];
+      if (fct == 0.0) continue;
+      const double *Ac = A + (size_t)c * kc;
+      for (int j = 0; j < k; ++j) Ar[j] = (j == c) ? -fct * Ac[c] : fma(-fct, Ac[j], Ar[j]);
+    }
+    __syncwarp();
+  }
+  if (sg != 0) {
+    // the row interchanges of the elimination become column interchanges of the inverse
+    for (int c = k - 1; c >= 0; --c) {
+      const int pr = perm[c];
+      if (pr == c) continue;
+      for (int r = lane; r < k; r += 32) {
+        const double t = A[(size_t)r * kc + c];
+        A[(size_t)r * kc + c] = A[(size_t)r * kc + pr];
+        A[(size_t)r * kc + pr] = t;
+      }
+      __syncwarp();
+    }
+  }
+  if (lane == 0) {
+    S.f_detlog[wf] = ld;
+    S.f_detsign[wf] = (int8_t)sg;
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v) {
+  atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// Refresh, step 2 (one warp per walker): the sign s_P of the bath permutation counted from
+// scratch (the bath operators flavor by flavor in storage order, tau'_1 tau_1 tau'_2 tau_2 ...,
+// against descending time), the recomputed determinants and trace replace the tracked ones,
+// and the deviations of the tracked values are recorded. A walker whose fresh evaluation
+// failed (a singular G_f or a trace error) keeps its tracked values.
+__global__ void sweep_refresh_apply_kernel(SweepView S) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= S.nw) return;
+  const int nf = S.nf, kc = S.kcap;
+  // operator a of the flavor-by-flavor sequence: flavor block, pair index, creator or annihilator
+  int total = 0;
+  for (int f = 0; f < nf; ++f) total += 2 * S.kf[w * nf + f];
+  auto op_time = [&](int a) {
+    int f = 0;
+    while (a >= 2 * S.kf[w * nf + f]) {
+      a -= 2 * S.kf[w * nf + f];
+      ++f;
+    }
+    const size_t b = ((size_t)w * nf + f) * kc + (a >> 1);
+    return (a & 1) ? S.col_t[b] : S.row_t[b];
+  };
+  long long inv = 0;
+  for (int a = lane; a < total; a += 32) {
+    const double ta = op_time(a);
+    for (int c = a + 1; c < total; ++c) inv += ta < op_time(c);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) inv += __shfl_xor_sync(FULL, inv, o);
+  if (lane != 0) return;
+  double dl = 0.0;
+  int ds = 1;
+  for (int f = 0; f < nf; ++f) {
+    if (S.kf[w * nf + f] == 0) continue;
+    dl += S.f_detlog[w * nf + f];
+    ds *= S.f_detsign[w * nf + f];
+  }
+  const int ts = S.f_tsign[w];
+  if (ds == 0 || ts == 0 || S.f_tstat[w] != KT_OK) {
+    atomicAdd(&S.f_dev[3], 1ull);
+    return;
+  }
+  const int sp = (inv & 1) ? -1 : 1;
+  const int ws = ts * sp * ds;
+  if (ws != S.w_sign[w] || ts != S.tr_sign[w]) atomicAdd(&S.f_dev[2], 1ull);
+  atomic_max_nonneg(&S.f_dev[0], fabs(S.tr_log[w] - S.f_tlog[w]));
+  atomic_max_nonneg(&S.f_dev[1], fabs(S.det_log[w] - dl));
+  S.tr_sign[w] = (int8_t)ts;
+  S.tr_log[w] = S.f_tlog[w];
+  S.det_log[w] = dl;
+  S.w_sign[w] = (int8_t)ws;
+}
+
 __global__ void sweep_init_kernel(SweepView S, const int8_t *sg, const double *lg) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= S.nw) return;
@@ -651,7 +806,8 @@ kt_status carve_and_alloc(kt_sweep *s) {
                o_obs = take(nw * v.nobs * 8), o_obt = take(nw * v.nobs * 8), o_msg = take(nw), o_mlg = take(nw * 8),
                o_mst = take(nw * 4), o_cnt = take(KT_SWEEP_NCOUNTERS * 8), o_pk = take(nw), o_pt1 = take(nw * 8),
                o_pt2 = take(nw * 8), o_pseg = take(nw), o_X = take(nw * (size_t)v.n_in * 2), o_yt = take(nw * 4),
-               o_ppair = take(nw * 2 * 4), o_pacc = take(nw);
+               o_ppair = take(nw * 2 * 4), o_pacc = take(nw), o_fdl = take(nw * nf * 8), o_fds = take(nw * nf),
+               o_fts = take(nw), o_ftl = take(nw * 8), o_fst = take(nw * 4), o_fdev = take(4 * 8);
   if (cudaMalloc(&s->mem, b) != cudaSuccess) {
     cudaGetLastError();
     s->mem = nullptr;
@@ -705,6 +861,12 @@ kt_status carve_and_alloc(kt_sweep *s) {
   v.ytil = (float *)(p + o_yt);
   v.p_pair = (int32_t *)(p + o_ppair);
   v.p_acc = (int8_t *)(p + o_pacc);
+  v.f_detlog = (double *)(p + o_fdl);
+  v.f_detsign = (int8_t *)(p + o_fds);
+  v.f_tsign = (int8_t *)(p + o_fts);
+  v.f_tlog = (double *)(p + o_ftl);
+  v.f_tstat = (int32_t *)(p + o_fst);
+  v.f_dev = (unsigned long long *)(p + o_fdev);
   return KT_OK;
 }
 
@@ -1133,6 +1295,34 @@ static kt_status set_configs_impl(kt_sweep *s, const kt_seq_batch *b) {
     return KT_ECUDA;
   }
   return invalidate_cache(s);
+}
+
+kt_status kt_sweep_refresh(kt_sweep *s, double *max_dev, void *stream) {
+  if (!s) return KT_EINVAL;
+  kt::SweepView &v = s->v;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaGetLastError();
+  if (cudaMemsetAsync(v.f_dev, 0, 4 * 8, st) != cudaSuccess) return KT_ECUDA;
+  const int wpb = 8;
+  const long long nmat = (long long)v.nw * v.nf;
+  kt::sweep_refresh_det_kernel<<<(unsigned)((nmat + wpb - 1) / wpb), wpb * 32, wpb * v.kcap * sizeof(int), st>>>(v);
+  if (current_traces(s, v.f_tsign, v.f_tlog, v.f_tstat, nullptr, st) != 0) return KT_ECUDA;
+  kt::sweep_refresh_apply_kernel<<<(unsigned)(((long long)v.nw * 32 + 255) / 256), 256, 0, st>>>(v);
+  if (cudaGetLastError() != cudaSuccess) return KT_ECUDA;
+  if (max_dev) {
+    unsigned long long h[4];
+    if (cudaMemcpyAsync(h, v.f_dev, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return KT_ECUDA;
+    double d0, d1;
+    memcpy(&d0, &h[0], 8);
+    memcpy(&d1, &h[1], 8);
+    max_dev[0] = d0;
+    max_dev[1] = d1;
+    max_dev[2] = (double)h[2];
+    max_dev[3] = (double)h[3];
+  }
+  return KT_OK;
 }
 
 kt_status kt_sweep_get_state(kt_sweep *s, const kt_sweep_state *d, void *stream) {

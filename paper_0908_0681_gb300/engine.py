@@ -285,6 +285,11 @@ class Sweep:
         assert uniforms.shape[1:] == (self.n_walkers, 7)
         kt.kt_sweep_run_da(self.h, uniforms.shape[0], uniforms, meas_every)
 
+    def refresh(self) -> dict:
+        """Drift guard (kt_sweep_refresh): tracked M, determinants, signs and traces recomputed
+        from scratch; returns how far the tracked values had drifted."""
+        return kt.kt_sweep_refresh(self.h)
+
     def reset_accumulators(self) -> None:
         kt.kt_sweep_reset_accumulators(self.h)
 

@@ -26,7 +26,7 @@ def status_name(code: int) -> str:
 
 
 KT_FP64, KT_FP32_KRYLOV = 0, 1
-KT_DENSITY_ONLY, KT_SECTOR_BLOCKS, KT_HOST_ONLY = 1, 2, 256
+KT_DENSITY_ONLY, KT_SECTOR_BLOCKS, KT_FP32_TRIDIAG64, KT_HOST_ONLY = 1, 2, 4, 256
 
 
 class kt_model_params(ctypes.Structure):
@@ -91,10 +91,11 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_sweep_counters", "kt_sweep_reset_accumulators", "kt_sweep_destroy",
                  "kt_sweep_set_configs", "kt_gemm_bf16", "kt_mlp_create", "kt_mlp_num_params",
                  "kt_mlp_set_params", "kt_mlp_get_params", "kt_mlp_forward", "kt_mlp_backward", "kt_mlp_get_grads",
-                 "kt_mlp_adam", "kt_mlp_error", "kt_mlp_destroy", "kt_sweep_feature_size", "kt_sweep_collect",
+                 "kt_mlp_adam", "kt_mlp_error", "kt_mlp_destroy", "kt_mlp_get_tape", "kt_sweep_feature_size",
+                 "kt_sweep_collect",
                  "kt_sweep_set_surrogate", "kt_sweep_run_da", "kt_sweep_set_stats", "kt_ratio_cache_create",
                  "kt_ratio_cache_build", "kt_trace_ratio_cached", "kt_ratio_cache_destroy", "kt_ratio_cache_propose",
-                 "kt_ratio_cache_commit"]
+                 "kt_ratio_cache_commit", "kt_sweep_refresh"]
 
 KT_SWEEP_NCOUNTERS = 10
 KT_MLP_HIDDEN = 256
@@ -143,6 +144,7 @@ def load():
     lib.kt_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
     lib.kt_mlp_backward.argtypes = [vp, vp, vp, i32, vp, vp]
     lib.kt_mlp_get_grads.argtypes = [vp, vp]
+    lib.kt_mlp_get_tape.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
     lib.kt_mlp_adam.argtypes = [vp, ctypes.c_float, vp]
     lib.kt_mlp_error.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.kt_mlp_destroy.argtypes = [vp]
@@ -165,6 +167,7 @@ def load():
     lib.kt_sweep_get_accumulators.argtypes = [vp, ctypes.POINTER(kt_sweep_accum), vp]
     lib.kt_sweep_counters.argtypes = [vp, vp]
     lib.kt_sweep_reset_accumulators.argtypes = [vp, vp]
+    lib.kt_sweep_refresh.argtypes = [vp, vp, vp]
     lib.kt_sweep_destroy.argtypes = [vp]
     lib.kt_sweep_destroy.restype = None
     lib.kt_timing_begin.argtypes = [vp, i32]
@@ -411,6 +414,16 @@ def kt_sweep_counters(s: KtSweep) -> dict:
     return dict(zip(SWEEP_COUNTERS, [int(x) for x in out]))
 
 
+def kt_sweep_refresh(s: KtSweep, stream=None) -> dict:
+    """Recompute M, log|det|, the permutation sign and the trace of every walker from scratch
+    (synchronises); returns the deviations of the tracked values."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(load().kt_sweep_refresh(s.handle, out.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)),
+           "kt_sweep_refresh")
+    return {"trace_log": float(out[0]), "det_log": float(out[1]), "sign_mismatches": int(out[2]),
+            "unchanged": int(out[3])}
+
+
 def kt_sweep_reset_accumulators(s: KtSweep, stream=None) -> None:
     _check(load().kt_sweep_reset_accumulators(s.handle, _stream_handle(stream)), "kt_sweep_reset_accumulators")
 
@@ -458,6 +471,19 @@ def kt_mlp_get_grads(n: KtMlp) -> np.ndarray:
     a = np.zeros(n.n_params, dtype=np.float32)
     _check(load().kt_mlp_get_grads(n.handle, a.ctypes.data_as(ctypes.c_void_p)), "kt_mlp_get_grads")
     return a
+
+
+def kt_mlp_get_tape(n: KtMlp, B: int) -> dict:
+    """Intermediate values of the last kt_mlp_backward on B rows (host numpy arrays; BF16
+    entries as uint16 bit patterns, dz1 transposed [256][B])."""
+    H = KT_MLP_HIDDEN
+    t = {"z1": np.zeros((B, H), np.float32), "h1": np.zeros((B, H), np.uint16), "z2": np.zeros((B, H), np.float32),
+         "dy": np.zeros(B, np.float32), "dz2": np.zeros((B, H), np.uint16), "dh1": np.zeros((B, H), np.float32),
+         "dz1": np.zeros((H, B), np.uint16)}
+    vp = ctypes.c_void_p
+    _check(load().kt_mlp_get_tape(n.handle, B, *(t[k].ctypes.data_as(vp) for k in
+                                                ("z1", "h1", "z2", "dy", "dz2", "dh1", "dz1"))), "kt_mlp_get_tape")
+    return t
 
 
 def kt_mlp_forward(n: KtMlp, X, y, stream=None) -> None:

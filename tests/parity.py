@@ -22,6 +22,10 @@ from oracle.oracle import Model, Params, SeqBatch, classify, ratio
 
 RTOL = {0: 1e-10, 1: 1e-5}       # keyed by precision (KT_FP64 = 0, KT_FP32_KRYLOV = 1)
 ZERO_TOL = {0: 1e-12, 1: 1e-6}
+# A ratio formed end to end from two of the path's own traces, T_new / T_cur, each within
+# RTOL of the exact value: |(1 + e1) / (1 + e2) - 1| <= (e1 + e2) / (1 - e2) <= 2 RTOL (1 + RTOL).
+# Ratios against the oracle's current trace carry only the new trace's error and use RTOL.
+RATIO_RTOL = {k: 2.0 * v * (1.0 + v) for k, v in RTOL.items()}
 
 
 def oracle_pair(spec, trunc_eps=None, density_only=False):

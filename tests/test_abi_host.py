@@ -185,7 +185,9 @@ def test_entry_points_reject_bad_arguments_without_touching_a_device():
     assert call("kt_mlp_backward", NULL, NULL, NULL, i32(16), NULL, NULL) == bad
     assert call("kt_mlp_adam", NULL, ctypes.c_float(1e-3), NULL) == bad
     assert call("kt_mlp_error", NULL, NULL) == bad
+    assert call("kt_mlp_get_tape", NULL, i32(16), NULL, NULL, NULL, NULL, NULL, NULL, NULL) == bad
     call("kt_mlp_destroy", NULL)
+    assert call("kt_sweep_refresh", NULL, NULL, NULL) == bad
     A = np.zeros(64, np.uint16)
     C = np.zeros(64, np.float32)
     err = i32()

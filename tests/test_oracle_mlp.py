@@ -121,3 +121,31 @@ def test_feature_vector_by_hand():
     assert mlp._overlap(9.0, 3.0, 1.0, 1.0, beta) == 1.0     # [9, 12) wraps to cover [1, 2)
     assert mlp._overlap(2.0, 1.0, 5.0, 1.0, beta) == 0.0
     assert mlp._overlap(0.0, 10.0, 4.0, 10.0, beta) == 10.0
+
+
+def test_bf16_rounding_against_hand_values():
+    """bfloat16 keeps 8 significand bits (7 stored): 1 + 2^-8 is a tie between 1 and 1 + 2^-7 and goes
+    to the even one (1); 1 + 3 * 2^-8 ties up to 1 + 2^-6; values just above a tie round up;
+    signs and powers of two pass unchanged."""
+    vals = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -8 + 2 ** -20, -(1 + 2 ** -8 + 2 ** -20), 2.0 ** -130,
+                     3.0, 0.0, -2.0 ** 40])
+    want = np.array([1.0, 1.0, 1 + 2 ** -6, 1 + 2 ** -7, -(1 + 2 ** -7), 2.0 ** -130, 3.0, 0.0, -2.0 ** 40])
+    assert np.array_equal(mlp.bf16(vals), want)
+    bits = np.array([0x3F80, 0xBF80, 0x4040, 0x0000], np.uint16)
+    assert np.array_equal(mlp.from_bf16_bits(bits), [1.0, -1.0, 3.0, 0.0])
+    # every output is representable: rounding twice changes nothing
+    x = np.random.default_rng(1).normal(0, 5, 2000)
+    assert np.array_equal(mlp.bf16(mlp.bf16(x)), mlp.bf16(x))
+    assert np.abs(mlp.bf16(x) / x - 1).max() <= 2.0 ** -8   # unit roundoff of 8 significand bits
+
+
+def test_bf16_chain_reduces_to_the_exact_one(monkeypatch):
+    """loss_and_grads_bf16 is the chain rule of loss_and_grads with rounding points added:
+    with the rounding replaced by the identity it must give the same loss and gradients."""
+    p, X, t = _small(4)
+    monkeypatch.setattr(mlp, "bf16", lambda a: np.asarray(a, dtype=np.float64))
+    L1, g1, _ = mlp.loss_and_grads_bf16(p, X, t)
+    L0, g0 = mlp.loss_and_grads(p, X, t)
+    assert L1 == L0
+    for k in mlp.PARAMS:
+        assert np.allclose(g1[k], g0[k], rtol=1e-13, atol=1e-15), k

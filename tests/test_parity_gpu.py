@@ -106,7 +106,7 @@ def test_five_orbital_ratios(five, prec):
 
 def test_five_orbital_ratio_end_to_end_fp32(five):
     """Ratios against the GPU's own current traces (as a sampler uses them), FP32 path:
-    within 2 x 1e-5 relative of the oracle ratio (two FP32 traces enter)."""
+    within parity.RATIO_RTOL of the oracle ratio (two FP32 traces, each within 1e-5, enter)."""
     w, seqs, o64, ox, cls, sx, lx = five
     moves = workloads.generate_moves(w, seqs, seed=1002)
     m = engine.model_from_spec(w.model, precision=kt.KT_FP32_KRYLOV)
@@ -117,7 +117,7 @@ def test_five_orbital_ratio_end_to_end_fp32(five):
     reg = ncls == 2
     assert (s[reg] == (nsx * sx)[reg]).all()
     err = np.abs(np.expm1(lr[reg] - (nlx - lx)[reg]))
-    assert err.max() <= 2e-5, err.max()
+    assert err.max() <= parity.RATIO_RTOL[kt.KT_FP32_KRYLOV], err.max()
 
 
 def test_sector_blocks_agree(five):
@@ -216,28 +216,49 @@ def test_invalid_moves():
     assert (st == kt.KT_EZEROWEIGHT).all() and (s == 0).all()
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_full_batch_sampled(prec):
-    """The benchmark's 4,096-walker batch in its launch configuration; 48 sampled walkers
-    are checked one by one against the oracle."""
+def _full_batch(prec, flags=0):
+    """The benchmark's 4,096-walker batch in its launch configuration: GPU current traces,
+    then ratios against them; the oracle (FP64 and its long-double twin) evaluates every
+    walker's current and edited sequence."""
     w = workloads.five_orbital()
     seqs = workloads.generate_sequences(w, 4096, seed=1)
     moves = workloads.generate_moves(w, seqs, seed=1000)
-    m = engine.model_from_spec(w.model, precision=prec)
+    m = engine.model_from_spec(w.model, precision=prec, flags=flags)
     cs, cl, cst = gpu_trace(m, seqs)
     s, lr, st = gpu_ratio(m, seqs, cs, cl, moves)
     assert (cst == kt.KT_OK).all() and (st == kt.KT_OK).all()
     assert (cs != 0).all()
-    idx = np.random.default_rng(0).choice(4096, 48, replace=False)
-    sub = seqs.subset(idx)
     o64, ox = parity.oracle_pair(w.model)
-    cls, sx, lx = parity.oracle_traces(o64, ox, sub)
-    parity.compare(cls, sx, lx, cs[idx], cl[idx], prec, ox.nkept, w.model.beta * ox.E0, "full batch traces")
-    submv = workloads.Moves(moves.kind[idx], moves.flavor[idx], moves.t_dag[idx], moves.t_ann[idx], moves.rem_idx[idx])
-    ncls, nsx, nlx = parity.oracle_ratios(o64, ox, sub, sx, lx, submv)
+    cls, sx, lx = parity.oracle_traces(o64, ox, seqs)
+    ncls, nsx, nlx = parity.oracle_ratios(o64, ox, seqs, sx, lx, moves)
+    return w, ox, cs, cl, s, lr, cls, sx, lx, ncls, nsx, nlx
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_batch_every_walker(prec):
+    """Every walker of the benchmark batch: traces within RTOL of the oracle, and the ratios a
+    sampler forms from two of the path's own traces within RATIO_RTOL, signs exact."""
+    w, ox, cs, cl, s, lr, cls, sx, lx, ncls, nsx, nlx = _full_batch(prec)
+    r = parity.compare(cls, sx, lx, cs, cl, prec, ox.nkept, w.model.beta * ox.E0, "full batch traces")
+    assert r["regular"] == 4096
     reg = ncls == 2
-    err = np.abs(np.expm1(lr[idx][reg] - (nlx - lx)[reg]))
-    assert err.max() <= 2 * parity.RTOL[prec], err.max()
+    assert (s[reg] == (nsx * sx)[reg]).all() and (s[ncls == 0] == 0).all()
+    err = np.abs(np.expm1(lr[reg] - (nlx - lx)[reg]))
+    assert err.max() <= parity.RATIO_RTOL[prec], err.max()
+
+
+def test_full_batch_fp64_tridiagonal_ratios_within_1e5():
+    """KT_FP32_TRIDIAG64 (FP32 Krylov vectors, FP64 tridiagonal exponential): every ratio of
+    the benchmark batch, formed end to end from two of the path's own traces, is within 1e-5
+    of the oracle's, and every trace within 5e-6."""
+    w, ox, cs, cl, s, lr, cls, sx, lx, ncls, nsx, nlx = _full_batch(kt.KT_FP32_KRYLOV, kt.KT_FP32_TRIDIAG64)
+    reg = cls == 2
+    assert (cs[reg] == sx[reg]).all()
+    assert np.abs(np.expm1(cl[reg] - lx[reg])).max() <= 5e-6
+    reg = ncls == 2
+    assert (s[reg] == (nsx * sx)[reg]).all()
+    err = np.abs(np.expm1(lr[reg] - (nlx - lx)[reg]))
+    assert err.max() <= 1e-5, err.max()
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -277,15 +298,23 @@ def test_autotune_picks_a_compiled_tiling(five):
 @pytest.fixture(scope="module")
 def seven():
     w = workloads.seven_orbital()
-    seqs = workloads.generate_sequences(w, 48, seed=1)
+    seqs = workloads.generate_sequences(w, 256, seed=1)   # the full seven-orbital batch
     o64, ox = parity.oracle_pair(w.model)
     cls, sx, lx = parity.oracle_traces(o64, ox, seqs)
     return w, seqs, o64, ox, cls, sx, lx
 
 
-@pytest.mark.parametrize("prec", PRECS)
+SEVEN_FP32_FLOOR = pytest.mark.xfail(
+    reason="stated shortfall: FP32 Krylov vectors carry a rounding floor of about u dtau ||H_b - s_b|| per "
+           "interval; at seven orbitals a few walkers of 256 exceed 1e-5 (up to about 2.6e-5); the FP64 path "
+           "meets 1e-10", strict=False)
+
+
+@pytest.mark.parametrize("prec", [kt.KT_FP64, pytest.param(kt.KT_FP32_KRYLOV, marks=SEVEN_FP32_FLOOR)])
 def test_seven_orbital_traces_and_ratios(seven, prec):
-    """7-orbital f-shell model (16,384 states, blocks up to 35 rows, N_tr = 63)."""
+    """7-orbital f-shell model (16,384 states, blocks up to 35 rows, N_tr = 63), the full batch
+    of 256 walkers: traces, ratios against the oracle's current traces (RTOL) and ratios
+    against the path's own current traces (RATIO_RTOL)."""
     w, seqs, o64, ox, cls, sx, lx = seven
     m = engine.model_from_spec(w.model, precision=prec)
     info = kt.kt_model_query(m)
@@ -303,6 +332,12 @@ def test_seven_orbital_traces_and_ratios(seven, prec):
     idx = np.nonzero(reg)[0]
     parity.compare(ncls[idx], nsx[idx] * cur_s[idx], nlx[idx] - lx[idx], rs[idx], rl[idx], prec, ox.nkept,
                    w.model.beta * ox.E0 + lx[idx], "7-orbital ratios")
+    # as a sampler forms them: against the path's own current traces
+    es, el, est = gpu_ratio(m, seqs, s, l, moves)
+    both = reg & (ncls == 2)
+    assert (est[reg] == kt.KT_OK).all() and (es[both] == (nsx * sx)[both]).all()
+    err = np.abs(np.expm1(el[both] - (nlx - lx)[both]))
+    assert err.max() <= parity.RATIO_RTOL[prec], err.max()
 
 
 def test_seven_orbital_energy_window_1e4():
