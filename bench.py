@@ -44,6 +44,7 @@ N_ROUNDS = 200
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2  # 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz x 2 flops)
+MEASURED_FP32_TFLOPS = 66.9  # FP32 FMA-chain microbenchmark on this GPU type (every lane of a full grid)
 
 
 def args_():
@@ -58,6 +59,10 @@ def args_():
     p.add_argument("--sweep-steps", type=int, default=1000,
                    help="timed Metropolis steps of the CT-HYB sweep line (0 skips it)")
     p.add_argument("--sweep-beta", type=float, default=50.0)
+    p.add_argument("--sweep-other-steps", type=int, default=500,
+                   help="timed steps of the lighter sweep lines at beta 10 and 100")
+    p.add_argument("--no-other-betas", action="store_true", help="skip the beta 10 and 100 sweep lines")
+    p.add_argument("--no-seven", action="store_true", help="skip the seven-orbital sub-dict of the default run")
     p.add_argument("--workload", choices=["five_orbital", "seven_orbital"], default="five_orbital",
                    help="five_orbital (4,096 walkers, the headline) or seven_orbital (256 walkers)")
     p.add_argument("--trunc-eps", type=float, default=None,
@@ -175,7 +180,10 @@ def make_workload(rank: int, rounds: int, name: str = "five_orbital", trunc_eps:
 
 
 def cpu_baseline(w, seqs, moves_list, gpu_ratio_round0, seconds: float):
-    """Time the oracle (as it stands) on a bounded sample of the same workload on the host cores."""
+    """Time the oracle (as it stands) on a bounded sample of the same workload on the host cores.
+    gpu_ratio_round0: {name: (sign, logratio)} of GPU paths on the first timed round, each formed
+    against that path's own current traces; their largest relative errors against the oracle's
+    ratios (against the oracle's current traces) are reported."""
     import numpy as np
     from oracle.oracle import Model, Params, SeqBatch, classify, ratio
 
@@ -194,17 +202,19 @@ def cpu_baseline(w, seqs, moves_list, gpu_ratio_round0, seconds: float):
         sgn, lr, ns, nl = ratio(o, sb, cs, cl, mv)
         t_used += time.perf_counter() - t0
         evals += seqs.n
-        if r == 0 and gpu_ratio_round0 is not None:
-            gs, gl = gpu_ratio_round0
+        if r == 0 and gpu_ratio_round0:
             ok = (sgn != 0) & np.isfinite(lr)
-            errs = np.abs(np.expm1(gl[ok] - lr[ok])).tolist()
-            sign_ok = bool((gs == sgn).all())
+            errs = {name: float(np.abs(np.expm1(gl[ok] - lr[ok])).max()) for name, (gs, gl) in gpu_ratio_round0.items()}
+            sign_ok = {name: bool((gs == sgn).all()) for name, (gs, gl) in gpu_ratio_round0.items()}
         r += 1
     out = {"value": evals / t_used, "unit": UNIT, "cores": int(o.threads_used), "kind": "oracle",
            "sample": f"{r} round(s) x {seqs.n} walkers of the same workload (FP64 dense-block oracle, OpenMP)"}
     if errs:
-        out["max_rel_err_fp32_vs_oracle"] = float(max(errs))
+        out["max_rel_err_fp32_vs_oracle"] = errs.get("fp32")
+        out["max_rel_err_vs_oracle"] = errs
         out["signs_equal"] = sign_ok
+        out["error_definition"] = ("round 0, all walkers: |T_new/T_cur - 1| relative to the oracle ratio, the GPU ratio "
+                                   "formed against the GPU path's own current traces")
     return out
 
 
@@ -248,6 +258,174 @@ def reference_arm(a):
 
 
 CACHE_OPS = 512   # partial-state cache length of the cached sweeps (operators per walker)
+
+
+def chain_estimates(acc, n_orb: int, beta: float, n_bins: int):
+    """Per-chain estimates from sweep accumulators: double occupancy (mean over orbitals),
+    expansion order (sum over flavors), n_f [chains][flavors] and G(tau) [chains][bins] (mean
+    over flavors), each divided by the chain's sign sum."""
+    ssum = acc["sign_sum"]
+    obs = acc["obs_sum"] / ssum[:, None]
+    return {"docc": obs[:, 2 * n_orb: 3 * n_orb].mean(1), "order": acc["order_sum"].sum(1) / ssum,
+            "n_f": obs[:, :2 * n_orb], "G_tau": acc["g_tau"].mean(1) * (n_bins / beta ** 2) / ssum[:, None]}
+
+
+def efficiencies(est, secs: float):
+    """Statistical efficiency 1 / (variance across independent chains x wall time) of every
+    observable (n_f per flavor, G(tau) per bin)."""
+    var = {k: v.var(axis=0, ddof=1) for k, v in est.items()}
+    return {k: (1.0 / (v * secs)) for k, v in var.items()}
+
+
+def speedups(ea, eb):
+    """Speedups at equal statistical error of path a over path b: ratios of efficiencies, for
+    n_f and G(tau) the smallest over flavors and bins (and the median over bins)."""
+    import numpy as np
+    out = {"docc": float(ea["docc"] / eb["docc"]), "order": float(ea["order"] / eb["order"])}
+    rf = np.asarray(ea["n_f"] / eb["n_f"])
+    rg = np.asarray(ea["G_tau"] / eb["G_tau"])
+    out["n_f_min_over_flavors"] = float(rf.min())
+    out["G_tau_min_over_bins"] = float(rg.min())
+    out["G_tau_median_over_bins"] = float(np.median(rg))
+    return out
+
+
+def sweep_beta_light(dev, beta: float, steps: int, seed: int):
+    """CT-HYB sweeps of the five-orbital model at another beta (1,024 chains, semicircular bath):
+    chains from Poisson(6) starts thermalise untimed with FP32 traces; from the same state
+    `steps` steps are timed for FP32, FP32 with the partial-state cache and FP64 traces, measuring
+    every 50 steps. Efficiencies at equal error cover double occupancy, the order, every n_f and
+    G(tau) on every bin. The step's roofline fraction counts the trace pipeline's algorithmic
+    Krylov flops (kt_stats.flops_alg over 50 untimed steps) against the FP32 peak."""
+    import numpy as np
+    import torch
+
+    from paper_0908_0681_gb300 import engine, kt, workloads
+
+    nw, therm, meas, n_bins = 1024, 1500, 50, 200
+    w = workloads.five_orbital()
+    spec = workloads.five_orbital_sweep(beta).model
+    gen = workloads.Workload(w.name, spec, start=w.start, order=w.order, lam=w.lam, cap=w.cap,
+                             pattern_singles=w.pattern_singles)
+    cand = workloads.generate_sequences(gen, 2 * nw, seed=seed)
+    table = workloads.semicircular_hybridization(beta, 2 * spec.n_orb, n_tau=2000)
+    g = torch.Generator(device=dev).manual_seed(seed)
+    models = {"fp32": engine.model_from_spec(spec, precision=kt.KT_FP32_KRYLOV),
+              "fp64": engine.model_from_spec(spec, precision=kt.KT_FP64)}
+    sg, _, _ = engine.trace(models["fp32"], engine.DeviceSeqs.from_host(cand, dev))
+    ok = np.nonzero(sg.cpu().numpy() != 0)[0][:nw]
+    base = engine.Sweep(models["fp32"], table, beta, nw, k_cap=128, n_bins=n_bins, measure_obs=True)
+    base.set_configs(cand.subset(ok))
+    for _ in range(0, therm, 500):
+        base.run(torch.rand((500, nw, 6), dtype=torch.float64, device=dev, generator=g))
+    st = {k: v.cpu().numpy() for k, v in base.state().items()}
+    lens = st["lens"]
+    thermal = workloads.Sequences(np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
+                                  np.concatenate([st["tau"][i, :lens[i]] for i in range(nw)]),
+                                  np.concatenate([st["flavor"][i, :lens[i]] for i in range(nw)]),
+                                  np.concatenate([st["dagger"][i, :lens[i]] for i in range(nw)]))
+    del base
+    steps = max(meas, steps - steps % meas)
+    u = torch.rand((steps, nw, 6), dtype=torch.float64, device=dev, generator=g)
+    mhz = 2070.0
+    peak32 = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    out, eff = {}, {}
+    for name, model, cache in (("fp32", models["fp32"], 0), ("fp32_cached", models["fp32"], CACHE_OPS),
+                               ("fp64", models["fp64"], 0)):
+        sw = engine.Sweep(model, table, beta, nw, k_cap=128, n_bins=n_bins, measure_obs=True, cache_ops=cache)
+        sw.set_configs(thermal)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sw.run(u, meas_every=meas)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        cnt = sw.counters()
+        acc = {k: v.cpu().numpy() for k, v in sw.accumulators().items()}
+        est = chain_estimates(acc, spec.n_orb, beta, n_bins)
+        eff[name] = efficiencies(est, ms / 1000.0)
+        stt = sw.state()
+        K = stt["lens"].double().mean().item()
+        wst = engine.new_stats(dev)
+        sw.set_stats(wst)
+        sw.run(u[:50])
+        sw.set_stats(None)
+        wk = kt.stats_from_tensor(wst)
+        flops_step = wk["flops_alg"] / 50
+        props = nw * steps / (ms / 1000.0)
+        out[name] = {"proposals_per_s": props, "ms_per_step": ms / steps, "sweeps_per_s": props / K,
+                     "mean_ops_per_chain": K, "mean_order_per_flavor": stt["order"].double().mean().item(),
+                     "acceptance": (cnt["insert_accepted"] + cnt["remove_accepted"]) / (nw * steps),
+                     "mean_sign": float(acc["sign_sum"].sum() / (nw * cnt["measurements"])) if cnt["measurements"] else None,
+                     "trace_errors": cnt["trace_errors"], "docc": float(est["docc"].mean()),
+                     "n_f": float(est["n_f"].mean()), "order": float(est["order"].mean()),
+                     "krylov_intervals_per_proposal": wk["intervals"] / (50 * nw),
+                     "roofline": {"bound": "alu", "achieved": flops_step / (ms / steps / 1000.0) / 1e12,
+                                  "peak": peak32, "unit": "TFLOP/s",
+                                  "frac": flops_step / (ms / steps / 1000.0) / 1e12 / peak32,
+                                  "definition": "algorithmic Krylov flops of the step's trace ratios / step time"}}
+        del sw
+    sp = {f"{a_}_over_{b_}": speedups(eff[a_], eff[b_]) for a_, b_ in (("fp32", "fp64"), ("fp32_cached", "fp64"),
+                                                                        ("fp32_cached", "fp32"))}
+    return {"workload": f"five_orbital_sweep_beta{beta:g}_1024_chains", "beta": beta, "thermalisation_steps": therm,
+            "measure_every": meas, "steps": steps, **out, "speedup_at_equal_error": sp}
+
+
+def seven_bench(dev, K: int):
+    """The seven-orbital batch (256 walkers, N_tr = 63, beta 40): FP32-Krylov and FP64
+    trace-ratio evaluations per second (L2 flushed before every step) and the largest relative
+    error of each path's ratios, formed against its own current traces, against the oracle's
+    ratios on the first round."""
+    import numpy as np
+    import torch
+
+    from oracle.oracle import Model, Params, SeqBatch, ratio
+    from paper_0908_0681_gb300 import engine, kt
+
+    w, seqs, moves = make_workload(0, K + 3, "seven_orbital")
+    spec = w.model
+    n = seqs.n
+    d = engine.DeviceSeqs.from_host(seqs, dev)
+    dm = [engine.DeviceMoves.from_host(m, dev) for m in moves]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    res, round0 = {}, {}
+    for name, prec in (("fp32", kt.KT_FP32_KRYLOV), ("fp64", kt.KT_FP64)):
+        m = engine.model_from_spec(spec, precision=prec)
+        ws = engine.workspace(m, n, dev)
+        cs, cl, _ = engine.trace(m, d, ws=ws)
+        o = (torch.empty(n, dtype=torch.int8, device=dev), torch.empty(n, dtype=torch.float64, device=dev),
+             torch.empty(n, dtype=torch.int32, device=dev))
+        kt.kt_trace_ratio(m, d.batch(), cs, cl, dm[0].batch(), *o, None, ws, stream)
+        torch.cuda.synchronize()
+        round0[name] = (o[0].cpu().numpy(), o[1].cpu().numpy())
+        for k in range(3):
+            kt.kt_trace_ratio(m, d.batch(), cs, cl, dm[k % len(dm)].batch(), *o, None, ws, stream)
+        tot = 0.0
+        for k in range(K):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            kt.kt_trace_ratio(m, d.batch(), cs, cl, dm[(3 + k) % len(dm)].batch(), *o, None, ws, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        res[name] = {"value": n * K / (tot / 1000.0), "unit": UNIT, "ms_per_step": tot / K}
+    P = Params(spec.n_orb, spec.U, spec.J, Up=spec.up, mu=spec.mu, delta=spec.delta, beta=spec.beta,
+               trunc_eps=spec.trunc_eps, deg_tol=spec.deg_tol)
+    om = Model(P)
+    sb = SeqBatch(seqs.offsets, seqs.tau, seqs.flavor, seqs.dagger)
+    ocs, ocl, _ = om.trace(sb)
+    osg, olr, _, _ = ratio(om, sb, ocs, ocl, moves[0].as_dict())
+    okr = (osg != 0) & np.isfinite(olr)
+    for name, (gs, gl) in round0.items():
+        res[name]["max_rel_err_vs_oracle"] = float(np.abs(np.expm1(gl[okr] - olr[okr])).max())
+        res[name]["signs_equal"] = bool((gs == osg).all())
+        res[name]["walkers_above_1e-5"] = int((np.abs(np.expm1(gl[okr] - olr[okr])) > 1e-5).sum())
+    return {"workload": f"seven_orbital_{n}_walkers", "metric": METRIC_7, "steps": K, "n_kept": om.nkept,
+            "error_definition": "round 0, all walkers, ratio against the path's own current traces vs the FP64 oracle",
+            **res, "speedup_fp32_over_fp64": res["fp32"]["value"] / res["fp64"]["value"]}
 
 
 def sweep_bench(dev, steps: int, beta: float, seed: int):
@@ -316,6 +494,9 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
 
     out = {}
     per_chain = {}
+    effs = {}
+    mhz = 2070.0
+    peak32 = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     steps = max(meas, steps - steps % meas)   # whole measurement blocks
     n_blocks = steps // meas
     u_plain = uni(steps, 6)      # the FP32 and FP64 plain runs share their uniforms
@@ -361,6 +542,16 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         order = acc["order_sum"].sum(1) / ssum
         gmid = (acc["g_tau"][:, :, 95:105].mean(2) * (200 / beta ** 2) / ssum[:, None]).mean(1)
         K = stt["lens"].double().mean().item()
+        effs[name] = efficiencies(chain_estimates(acc, spec.n_orb, beta, 200), ms / 1000.0)
+        # algorithmic Krylov flops of the trace pipeline per step (50 untimed steps)
+        wst = engine.new_stats(dev)
+        sw.set_stats(wst)
+        if mode == "da":
+            sw.run_da(u[:50])
+        else:
+            sw.run(u[:50])
+        sw.set_stats(None)
+        flops_step = kt.stats_from_tensor(wst)["flops_alg"] / 50
         del sw
         per_chain[name] = {"docc": docc, "order": order, "G_beta_half": gmid,
                            "n_f": obs[:, :2 * spec.n_orb].mean(1), "S2": obs[:, 3 * spec.n_orb],
@@ -379,7 +570,11 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
                      "n_f": float(obs[:, :2 * spec.n_orb].mean()), "S2": float(obs[:, 3 * spec.n_orb].mean()),
                      "eff": {"docc": 1.0 / (docc.var(ddof=1) * secs), "order": 1.0 / (order.var(ddof=1) * secs),
                              "G_beta_half": 1.0 / (gmid.var(ddof=1) * secs)},
-                     "error_bars_binning": binning}
+                     "error_bars_binning": binning,
+                     "roofline": {"bound": "alu", "achieved": flops_step / (ms / n_t / 1000.0) / 1e12, "peak": peak32,
+                                  "unit": "TFLOP/s", "frac": flops_step / (ms / n_t / 1000.0) / 1e12 / peak32,
+                                  "flops_alg_per_step": flops_step,
+                                  "definition": "algorithmic Krylov flops of the step's trace ratios / step time"}}
     # FP32 against FP64 on the same uniforms: chains whose final configurations agree took
     # the same decisions all along, so their accumulators differ only by the trace arithmetic
     a32, a64 = per_chain["fp32"], per_chain["fp64"]
@@ -473,7 +668,12 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
             "bath": "semicircular DOS, bandwidth 4, 2000 tau points", "thermalisation_steps": therm,
             "measure_every": meas, **out,
             "speedup_fp32_over_fp64": out["fp32"]["proposals_per_s"] / out["fp64"]["proposals_per_s"],
-            "speedup_at_equal_error": speed, "throughput_8192_chains": thr, "fp32_vs_fp64_same_uniforms": err32,
+            "speedup_at_equal_error": speed,
+            "speedup_at_equal_error_all_observables": {
+                f"{a_}_over_{b_}": speedups(effs[a_], effs[b_])
+                for a_, b_ in (("fp32", "fp64"), ("fp32_da", "fp64"), ("fp32_da", "fp32"), ("fp32_cached", "fp64"),
+                               ("fp32_da_cached", "fp64"), ("fp32_cached", "fp32"), ("fp64_cached", "fp64"))},
+            "throughput_8192_chains": thr, "fp32_vs_fp64_same_uniforms": err32,
             "cached_vs_uncached_identical_paths": cache_same, "cache_ops": CACHE_OPS,
             "surrogate": {"training_samples": int(X.shape[0]), "collect_s": t_collect, "train_s": t_train,
                           "epochs": len(hist), "loss_per_epoch": hist, "rms_residual_log_ratio": resid,
@@ -565,6 +765,15 @@ def main():
 
     K64 = a.fp64_steps if a.fp64_steps > 0 else min(a.steps, 100)
     ms64, stage64, _ = timed_loop(m64, cur64, K64, a.warmup)
+
+    # FP32 Krylov vectors with the final tridiagonal exponential in FP64 (KT_FP32_TRIDIAG64)
+    m32t = engine.model_from_spec(w.model, precision=kt.KT_FP32_KRYLOV, flags=kt.KT_FP32_TRIDIAG64)
+    tuned["fp32_tridiag64"] = kt.kt_autotune(m32t, dseq.batch(), out_s, out_l, out_st, ws)
+    cur32t = current(m32t)
+    for k in range(a.warmup):
+        step(m32t, cur32t, k)
+    Kt = min(a.steps, 100)
+    ms32t, _, _ = timed_loop(m32t, cur32t, Kt, a.warmup)
 
     # Latency floor: the walkers with the longest edited sequences of the last timed round,
     # each evaluated alone (a batch of one: no other work on the GPU). The batch cannot finish
@@ -695,6 +904,10 @@ def main():
 
     value, (tot32, tot64, e2e_ms) = aggregate([sum(ms32), sum(ms64), e2e_ms], n, a.steps, world, reduce_max)
     value64 = world * n * K64 / (tot64 / 1000.0)
+    value32t = n * Kt / (sum(ms32t) / 1000.0)
+    tridiag = {"value": value32t, "unit": UNIT, "ms_per_step": sum(ms32t) / Kt, "steps": Kt,
+               "speedup_over_fp64": value32t / value64, "flag": "KT_FP32_TRIDIAG64",
+               "precision": "FP32 Krylov vectors, FP64 tridiagonal exponential (QL for p >= 3, closed form p = 2)"}
     e2e_value = world * n / (e2e_ms / 1000.0)
 
     # roofline of the dominant kernel (Krylov items)
@@ -703,15 +916,21 @@ def main():
     mhz = clocks.get("sm_max_mhz") or 2070.0
     peak32 = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     peak64 = SM_COUNT_GB300 * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
-    f32_per_launch = st["flops_vec"] / a.steps
+    f32_per_launch = st["flops_alg"] / a.steps
     ach32 = f32_per_launch / (items_ms / 1000.0) / 1e12
     # The algorithmic work of the path is the Krylov vector arithmetic on the FP32 pipe;
     # its serial per-walker dependency chain (not a pipe) is what bounds the kernel.
     roofline = {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
                 "traffic": measured_traffic(sha), "kernel": "items_kernel", "pipe": "fp32",
-                "flops_per_launch": f32_per_launch, "items_ms_per_launch": items_ms,
+                "flops_per_launch": f32_per_launch,
+                "flops_definition": "sum over Krylov intervals of p (2 nnz(H_b) + 11 d_b) + 2 p d_b (kt_stats.flops_alg)",
+                "reorth_flops_per_launch": st["flops_reorth"] / a.steps,
+                "device_flops_vec_per_launch": st["flops_vec"] / a.steps,
+                "items_ms_per_launch": items_ms,
                 "stage_ms_per_step": {k: v / max(nl32, 1) for k, v in stage32.items()},
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock (sampled)",
+                "frac_of_measured_fp32_peak": ach32 / MEASURED_FP32_TFLOPS,
+                "measured_fp32_peak_tflops": MEASURED_FP32_TFLOPS,
                 "fp64_peak_tflops": peak64,
                 # the kernel is bound by its longest serial chain, not by a pipe: the step time
                 # of its longest walker evaluated alone is the floor (bench key latency_floor)
@@ -719,14 +938,22 @@ def main():
                 "frac_of_latency_floor": max(latency_floor["single_walker_ms"]) / (tot32 / a.steps)}
 
     sweep = sweep_bench(dev, a.sweep_steps, a.sweep_beta, seed=100 + rank) if a.sweep_steps > 0 else None
+    if sweep is not None and rank == 0 and not a.no_other_betas:
+        sweep["other_betas"] = {f"beta_{b:g}": sweep_beta_light(dev, b, a.sweep_other_steps, seed=300 + int(b))
+                                for b in (10.0, 100.0)}
+    seven = seven_bench(dev, min(a.steps, 40)) if (rank == 0 and a.workload == "five_orbital" and not a.no_seven) else None
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         # GPU ratios of the first timed round, for the sampled error statement
-        step(m32, cur32, a.warmup)
-        torch.cuda.synchronize()
-        g = (out_s.cpu().numpy(), out_l.cpu().numpy())
+        g = {}
+        for name, model, cur in (("fp32", m32, cur32), ("fp32_tridiag64", m32t, cur32t), ("fp64", m64, cur64)):
+            step(model, cur, a.warmup)
+            torch.cuda.synchronize()
+            g[name] = (out_s.cpu().numpy(), out_l.cpu().numpy())
         cpu = cpu_baseline(w, seqs, moves[a.warmup % n_rounds:] + moves[:a.warmup % n_rounds], g, a.cpu_seconds)
+        if "fp32_tridiag64" in cpu.get("max_rel_err_vs_oracle", {}):
+            tridiag["max_rel_err_vs_oracle"] = cpu["max_rel_err_vs_oracle"]["fp32_tridiag64"]
 
     if rank == 0:
         line = {
@@ -745,12 +972,14 @@ def main():
                          "speedup_fp32_over_fp64": value / value64},
             "work": {"items_alive_per_step": st["items_alive"] / a.steps, "intervals_per_step": st["intervals"] / a.steps,
                      "mean_krylov_dim": st["krylov_iters"] / max(st["intervals"], 1), "p_max": st["p_max"],
-                     "noconv": st["noconv"], "flops_vec_per_step": f32_per_launch,
+                     "noconv": st["noconv"], "flops_alg_per_step": f32_per_launch,
                      "nonzero_fraction": nonzero_frac,
                      "value_over_nonzero_proposals": value * nonzero_frac,
                      "p_hist_fp32": trim_hist(st["p_hist"]), "p_hist_fp64": trim_hist(st64["p_hist"]),
                      "mean_krylov_dim_fp64": st64["krylov_iters"] / max(st64["intervals"], 1)},
             "roofline": roofline,
+            "fp32_tridiag64": tridiag,
+            "seven_orbital": seven,
             "cached_ratio": cached_ratio,
             "latency_floor": latency_floor,
             "cpu_baseline": cpu,

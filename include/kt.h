@@ -132,6 +132,10 @@ typedef struct {
   unsigned long long flops_vec;      /* algorithmic vector flops (SpMV, dots, axpys, assembly) */
   unsigned long long flops_tri;      /* FP64 flops of the small tridiagonal exponentials */
   unsigned long long bytes_apply;    /* bytes moved by c / c^+ gathers */
+  unsigned long long flops_alg;      /* algorithmic Krylov flops: sum over intervals of
+                                        p (2 nnz(H_b) + 11 d_b) + 2 p d_b (nnz with the diagonal;
+                                        the three-term update, dots, norm and scaling; Q_p y) */
+  unsigned long long flops_reorth;   /* FP32 path: reorthogonalisation, sum of 2 p (p - 1) d_b */
   unsigned long long p_hist[KT_P_HIST]; /* propagations by stopping Krylov dimension p:
                                             bin p for p < KT_P_HIST - 1, the last bin p >= KT_P_HIST - 1 */
 } kt_stats;

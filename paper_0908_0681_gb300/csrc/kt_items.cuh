@@ -555,7 +555,7 @@ __device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
 }
 
 struct ItemAcc {
-  unsigned long long ops, intervals, iters, pmax, noconv, flops_vec, flops_tri, bytes_apply;
+  unsigned long long ops, intervals, iters, pmax, noconv, flops_vec, flops_tri, bytes_apply, flops_alg, flops_reorth;
 };
 
 // Per-group context of one work unit (half of a (walker, kept state) item).
@@ -840,7 +840,11 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
     }
     const int nnz_blk = gsum<G>(cnt, gm);
     u.acc.flops_vec += (unsigned long long)p * (2ull * nnz_blk + 9ull * dim) + 2ull * p * dim + 3ull * dim;
-    if (F32) u.acc.flops_vec += (unsigned long long)p * (p - 1) * 2ull * dim;  // reorthogonalisation
+    u.acc.flops_alg += (unsigned long long)p * (2ull * nnz_blk + 11ull * dim) + 2ull * p * dim;
+    if (F32) {  // reorthogonalisation
+      u.acc.flops_vec += (unsigned long long)p * (p - 1) * 2ull * dim;
+      u.acc.flops_reorth += (unsigned long long)p * (p - 1) * 2ull * dim;
+    }
   }
   return true;
 #undef A_
@@ -1066,6 +1070,8 @@ __global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveV
       stat_add(&stats->flops_vec, u.acc.flops_vec);
       stat_add(&stats->flops_tri, u.acc.flops_tri);
       stat_add(&stats->bytes_apply, u.acc.bytes_apply);
+      stat_add(&stats->flops_alg, u.acc.flops_alg);
+      stat_add(&stats->flops_reorth, u.acc.flops_reorth);
     }
     __syncwarp(gm);
   }
@@ -1282,6 +1288,8 @@ __global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S
       stat_add(&stats->flops_vec, u.acc.flops_vec);
       stat_add(&stats->flops_tri, u.acc.flops_tri);
       stat_add(&stats->bytes_apply, u.acc.bytes_apply);
+      stat_add(&stats->flops_alg, u.acc.flops_alg);
+      stat_add(&stats->flops_reorth, u.acc.flops_reorth);
     }
     __syncwarp(gm);
   }

@@ -46,7 +46,7 @@ class kt_model_info(ctypes.Structure):
 
 
 STATS_FIELDS = ["walkers", "items", "items_alive", "items_vanished", "ops_applied", "intervals", "krylov_iters",
-                "p_max", "noconv", "flops_vec", "flops_tri", "bytes_apply"]
+                "p_max", "noconv", "flops_vec", "flops_tri", "bytes_apply", "flops_alg", "flops_reorth"]
 
 
 KT_P_HIST = 32

@@ -43,3 +43,25 @@ def test_traffic_record_needs_the_current_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_traffic(sha) == 123
     assert bench.measured_traffic("0" * 16) is None
+
+
+def test_equal_error_speedups_per_observable():
+    """The speedup at equal statistical error is the ratio of 1 / (variance across chains x time):
+    halving the time doubles it for every observable; doubling the spread of one flavor's n_f
+    and of one G(tau) bin quarters the minimum over flavors and bins, not the others."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    nw, nf, nb = 256, 10, 20
+    acc = {"sign_sum": np.full(nw, 4.0), "obs_sum": rng.normal(1.0, 0.1, (nw, 3 * 5 + 1 + 36)),
+           "order_sum": rng.normal(2.0, 0.1, (nw, nf)), "g_tau": rng.normal(0.5, 0.05, (nw, nf, nb))}
+    est = bench.chain_estimates(acc, 5, 50.0, nb)
+    assert est["n_f"].shape == (nw, nf) and est["G_tau"].shape == (nw, nb)
+    assert np.allclose(est["docc"], acc["obs_sum"][:, 10:15].mean(1) / 4.0)
+    sp = bench.speedups(bench.efficiencies(est, 1.0), bench.efficiencies(est, 2.0))
+    assert all(abs(v - 2.0) < 1e-12 for v in sp.values())
+    wide = {k: v.copy() for k, v in est.items()}
+    wide["n_f"][:, 3] = 2.0 * (wide["n_f"][:, 3] - wide["n_f"][:, 3].mean())
+    wide["G_tau"][:, 7] = 2.0 * (wide["G_tau"][:, 7] - wide["G_tau"][:, 7].mean())
+    sp = bench.speedups(bench.efficiencies(wide, 1.0), bench.efficiencies(est, 1.0))
+    assert abs(sp["n_f_min_over_flavors"] - 0.25) < 1e-12 and abs(sp["G_tau_min_over_bins"] - 0.25) < 1e-12
+    assert sp["docc"] == 1.0 and abs(sp["G_tau_median_over_bins"] - 1.0) < 1e-12
