@@ -38,12 +38,14 @@ struct Tab<float> {
   static __device__ __forceinline__ const float *diag(const DevModel &M) { return M.st_diag32; }
   static __device__ __forceinline__ const float *val(const DevModel &M) { return M.ell_val32; }
   static __device__ __forceinline__ const float *kept(const DevModel &M) { return M.kept_vec32; }
+  static __device__ __forceinline__ const float *evec(const DevModel &M) { return M.blk_evec32; }
 };
 template <>
 struct Tab<double> {
   static __device__ __forceinline__ const double *diag(const DevModel &M) { return M.st_diag64; }
   static __device__ __forceinline__ const double *val(const DevModel &M) { return M.ell_val64; }
   static __device__ __forceinline__ const double *kept(const DevModel &M) { return M.kept_vec64; }
+  static __device__ __forceinline__ const double *evec(const DevModel &M) { return M.blk_evec64; }
 };
 
 template <int G, typename T>
@@ -616,6 +618,69 @@ __device__ bool apply_op(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, int f, i
   return true;
 }
 
+// FP32 path, exact Krylov stop (p = d_b, or an invariant subspace found by breakdown): the
+// Krylov space holds q_0 and is invariant under H_b, so the Lanczos result
+// V_p exp(-dt T_p) e_1 is exp(-dt (H_b - s_b)) q_0 itself. It is formed here from the block's
+// eigendecomposition (setup's FP64 Jacobi), which needs no eigensolve of T_p:
+// c_k = <v_k | q_0>, weights exp(-dt (lambda_k - lambda_min)) with lambda_min the lowest
+// eigenvalue whose component exceeds 4 u |q_0| (smaller components are rounding noise of
+// exact zeros, which the propagator would otherwise amplify, and are dropped), and
+// v = sum_k v_k c_k w_k into vv. TT is the type of the eigenvectors and of both sums: FP32,
+// or FP64 for models created with KT_FP32_TRIDIAG64. Returns -dt (lambda_min - s_b), the
+// scale taken out, in FP64.
+template <typename TT, typename VT, int G, int DMAX, int PMAX>
+__device__ __forceinline__ double exact_propagate32(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, int off, double dt,
+                                                    VT (&vv)[Unit<VT, G, DMAX, PMAX>::R]) {
+  constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
+  const int gl = u.gl, dim = u.dim;
+  const unsigned gm = u.gm;
+  const TT *__restrict__ V = Tab<TT>::evec(M) + __ldg(M.blk_evoff + u.b);
+  TT c[R];
+  TT n2 = 0;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int k = gl + G * j;
+    TT a = 0;
+    if (k < dim)
+      for (int r = 0; r < dim; ++r) a = fma(__ldg(V + k * dim + r), (TT)u.Q(0, r), a);
+    c[j] = a;
+    n2 = fma(a, a, n2);
+  }
+  n2 = gsum<G>(n2, gm);
+  // lowest significant eigenvalue: eigenvalues ascend within the block
+  const TT thr = n2 * (TT)((4 * 5.9604645e-8) * (4 * 5.9604645e-8));
+  int kmin = dim;
+#pragma unroll
+  for (int j = R - 1; j >= 0; --j) {
+    const int k = gl + G * j;
+    if (k < dim && c[j] * c[j] > thr) kmin = k;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(gm, kmin, o));
+  if (kmin >= dim) kmin = 0;
+  const double lmin = __ldg(M.st_eval64 + off + kmin);
+  const float dtf = (float)dt;
+  __syncwarp(gm);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int k = gl + G * j;
+    if (k < dim) {
+      const float dl = (float)(__ldg(M.st_eval64 + off + k) - lmin);
+      u.Q(1, k) = (c[j] * c[j] > thr) ? (float)c[j] * expf(-dtf * dl) : 0.f;
+    }
+  }
+  __syncwarp(gm);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = gl + G * j;
+    TT a = 0;
+    if (r < dim)
+      for (int k = 0; k < dim; ++k) a = fma(__ldg(V + k * dim + r), (TT)u.Q(1, k), a);
+    vv[j] = (VT)a;
+  }
+  return -dt * lmin;
+}
+
 // Step 5: q_0 <- exp(-dt (H_b - E0)) q_0 by Lanczos on H_b - s_b with the
 // a-posteriori stop; the scalars taken out go to the log-weight.
 // False if the propagated vector is exactly zero.
@@ -722,7 +787,11 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
     bool stop = exact;
     // a-posteriori checks at every p up to 4, then on a geometric schedule
     // (6, 8, 11, 15, 20, 27): each check costs an eigendecomposition of T_p
-    const bool check = p <= 4 || p == 6 || p == 8 || p == 11 || p == 15 || p == 20 || p == 27 || p == pcap;
+    // FP32 path, blocks of at most 16 rows: an interval two steps or less from exhausting its
+    // block is not checked; the exact stop that follows costs less than the eigensolve of a check
+    const bool near_exact = F32 && DMAX <= 16 && p >= 3 && dim <= pcap && dim - p <= 2;
+    const bool check = !near_exact &&
+                       (p <= 4 || p == 6 || p == 8 || p == 11 || p == 15 || p == 20 || p == 27 || p == pcap);
     if (!exact && check) {
       if constexpr (F32) {
         float yn, yl;
@@ -756,63 +825,72 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
     u.acc.noconv += 1;
     if (u.status == KT_OK) u.status = KT_ENOCONV;
   }
-  // final exp(-dt T_p) e_1 at the stopping p
-  if constexpr (F32) {
-    if (p == 2 && M.tri64) {
-      // KT_FP32_TRIDIAG64: the 2x2 closed form in FP64 from the double-float alpha, beta
-      const float2 a0 = reinterpret_cast<float2 *>(s.a)[grp], a1 = reinterpret_cast<float2 *>(s.a)[IPW + grp];
-      const float2 b0 = reinterpret_cast<float2 *>(s.b)[grp];
-      double y0, y1;
-      logfac = exp2x2((double)a0.x + (double)a0.y, (double)a1.x + (double)a1.y, (double)b0.x + (double)b0.y, dt, y0,
-                      y1);
-      if (gl == 0) {
-        s.y32[grp] = (float)y0;
-        s.y32[IPW + grp] = (float)y1;
-      }
-      __syncwarp(gm);
-    } else if (p <= 2) {
-      tri_small_f32(s, grp, gl, gm, p, dt, logfac);
-    } else {
-      if (DMAX > 16 || M.tri64) {
-        // FP32 Ritz vectors are off by about u ||T_p|| / gap, an error that does not average
-        // out over the intervals of a sequence; blocks beyond 16 rows (seven orbitals) and
-        // models with KT_FP32_TRIDIAG64 therefore take the full FP64 eigensolve at the final
-        // p (alpha, beta first widened in place from double-float to FP64)
-        for (int k = gl; k < p; k += G) {
-          const float2 av = reinterpret_cast<float2 *>(s.a)[k * IPW + grp];
-          const float2 bv = reinterpret_cast<float2 *>(s.b)[k * IPW + grp];
-          A_(k) = (double)av.x + (double)av.y;
-          B_(k) = (double)bv.x + (double)bv.y;
-        }
-        __syncwarp(gm);
-        if (!tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
-        for (int k = gl; k < p; k += G) s.y32[k * IPW + grp] = (float)Y_(k);
-        __syncwarp(gm);
-      } else {
-        if (exact) {
-          float yn, yl;
-          tri_check32(s, grp, gl, gm, p, dt, yn, yl);  // Ritz pairs of T_p (a check at p made them otherwise)
-        }
-        tri_final32(s, grp, gl, gm, p, dt, logfac);
-      }
-    }
-  } else {
-    if (exact && !tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
-  }
-  // v = sum_j y_j q_j, renormalised; what is taken out goes to the log-weight
+  // final exp(-dt T_p) e_1 at the stopping p, and v = sum_j y_j q_j (renormalised below;
+  // what is taken out goes to the log-weight)
   VT vv[R];
-#pragma unroll
-  for (int j = 0; j < R; ++j) {
-    const int r = gl + G * j;
-    VT a = VT(0);
-    if (r < dim) {
-      if constexpr (F32) {
-        for (int k = 0; k < p; ++k) a += s.y32[k * IPW + grp] * u.Q(k, r);
+  bool dense = false;
+  // exact stops of blocks beyond 16 rows (seven orbitals) keep the Lanczos final step: formed
+  // from the eigendecomposition there, their FP32 traces came out less accurate, not more
+  if constexpr (F32 && DMAX <= 16) dense = exact && p >= 2;
+  if (dense) {
+    if (M.tri64)
+      logfac = exact_propagate32<double>(M, u, off, dt, vv);
+    else
+      logfac = exact_propagate32<float>(M, u, off, dt, vv);
+  } else {
+    // final exp(-dt T_p) e_1 at the stopping p
+    if constexpr (F32) {
+      if (p == 2 && M.tri64) {
+        // KT_FP32_TRIDIAG64: the 2x2 closed form in FP64 from the double-float alpha, beta
+        const float2 a0 = reinterpret_cast<float2 *>(s.a)[grp], a1 = reinterpret_cast<float2 *>(s.a)[IPW + grp];
+        const float2 b0 = reinterpret_cast<float2 *>(s.b)[grp];
+        double y0, y1;
+        logfac = exp2x2((double)a0.x + (double)a0.y, (double)a1.x + (double)a1.y, (double)b0.x + (double)b0.y, dt, y0,
+                        y1);
+        if (gl == 0) {
+          s.y32[grp] = (float)y0;
+          s.y32[IPW + grp] = (float)y1;
+        }
+        __syncwarp(gm);
+      } else if (p <= 2) {
+        tri_small_f32(s, grp, gl, gm, p, dt, logfac);
       } else {
-        for (int k = 0; k < p; ++k) a += Y_(k) * u.Q(k, r);
+        if (DMAX > 16 || M.tri64) {
+          // FP32 Ritz vectors are off by about u ||T_p|| / gap, an error that does not average
+          // out over the intervals of a sequence; blocks beyond 16 rows (seven orbitals) and
+          // models with KT_FP32_TRIDIAG64 therefore take the full FP64 eigensolve at the final
+          // p (alpha, beta first widened in place from double-float to FP64)
+          for (int k = gl; k < p; k += G) {
+            const float2 av = reinterpret_cast<float2 *>(s.a)[k * IPW + grp];
+            const float2 bv = reinterpret_cast<float2 *>(s.b)[k * IPW + grp];
+            A_(k) = (double)av.x + (double)av.y;
+            B_(k) = (double)bv.x + (double)bv.y;
+          }
+          __syncwarp(gm);
+          if (!tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
+          for (int k = gl; k < p; k += G) s.y32[k * IPW + grp] = (float)Y_(k);
+          __syncwarp(gm);
+        } else {
+          tri_final32(s, grp, gl, gm, p, dt, logfac);  // Ritz pairs from the check that stopped at p
+        }
       }
+    } else {
+      if (exact && !tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
     }
-    vv[j] = a;
+    // v = sum_j y_j q_j
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = gl + G * j;
+      VT a = VT(0);
+      if (r < dim) {
+        if constexpr (F32) {
+          for (int k = 0; k < p; ++k) a += s.y32[k * IPW + grp] * u.Q(k, r);
+        } else {
+          for (int k = 0; k < p; ++k) a += Y_(k) * u.Q(k, r);
+        }
+      }
+      vv[j] = a;
+    }
   }
   if (!normalize_rows<VT, G, R>(vv, gl, dim, gm, u.Linv)) return false;
   u.Ladd += logfac - dt * (shift - M.E0);

@@ -500,6 +500,25 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   std::vector<float> st_diag32(st_diag64.begin(), st_diag64.end());
   std::vector<float> ell_val32(ell_val64.begin(), ell_val64.end());
   std::vector<float> kept_vec32(kept_vec64.begin(), kept_vec64.end());
+  // every block's eigendecomposition (exact Krylov stops of the FP32 path): eigenvalues
+  // minus the block shift per global row, eigenvectors one after another (vector k of block b
+  // at blk_evoff[b] + k d, component r at + r)
+  std::vector<double> st_eval64(N);
+  std::vector<float> st_eval32(N), blk_evec32;
+  std::vector<double> blk_evec64;
+  std::vector<int32_t> blk_evoff(B);
+  for (int b = 0; b < B; ++b) {
+    const int d = blk_dim[b];
+    blk_evoff[b] = (int32_t)blk_evec32.size();
+    for (int k = 0; k < d; ++k) {
+      st_eval64[blk_off[b] + k] = evals[b][k] - blk_shift[b];
+      st_eval32[blk_off[b] + k] = (float)st_eval64[blk_off[b] + k];
+      for (int r = 0; r < d; ++r) {
+        blk_evec64.push_back(evecs[b][(size_t)r * d + k]);
+        blk_evec32.push_back((float)evecs[b][(size_t)r * d + k]);
+      }
+    }
+  }
   struct Piece { const void *src; size_t bytes; size_t off; };
   std::vector<Piece> pieces;
   size_t total = 0;
@@ -517,7 +536,10 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
                i_kb = add(kept_blk.data(), NK * 4), i_ke = add(kept_e.data(), NK * 8), i_ko = add(kept_off.data(), NK * 4),
                i_kv64 = add(kept_vec64.data(), kept_vec64.size() * 8), i_kv32 = add(kept_vec32.data(), kept_vec32.size() * 4),
                i_s2d = add(s2_diag_blk.data(), N * 4), i_s2e = add(s2_ell.data(), s2_ell.size() * 2),
-               i_s2w = add(blk_s2w.data(), B * 4), i_s2o = add(blk_s2ell.data(), B * 4);
+               i_s2w = add(blk_s2w.data(), B * 4), i_s2o = add(blk_s2ell.data(), B * 4),
+               i_sev64 = add(st_eval64.data(), N * 8), i_sev32 = add(st_eval32.data(), N * 4),
+               i_evo = add(blk_evoff.data(), B * 4), i_evv = add(blk_evec32.data(), blk_evec32.size() * 4),
+               i_evv64 = add(blk_evec64.data(), blk_evec64.size() * 8);
   void *dmem = nullptr;
   if (cudaMalloc(&dmem, total) != cudaSuccess) { cudaGetLastError(); delete M; return KT_ENOMEM; }
   std::vector<char> host(total, 0);
@@ -551,6 +573,9 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   D.partner = (const uint16_t *)at(i_part);
   D.kept_blk = (const int32_t *)at(i_kb); D.kept_e = (const double *)at(i_ke); D.kept_off = (const int32_t *)at(i_ko);
   D.kept_vec64 = (const double *)at(i_kv64); D.kept_vec32 = (const float *)at(i_kv32);
+  D.st_eval64 = (const double *)at(i_sev64); D.st_eval32 = (const float *)at(i_sev32);
+  D.blk_evoff = (const int32_t *)at(i_evo); D.blk_evec32 = (const float *)at(i_evv);
+  D.blk_evec64 = (const double *)at(i_evv64);
   D.s2_diag = (const float *)at(i_s2d); D.s2_ell = (const uint16_t *)at(i_s2e);
   D.blk_s2w = (const int32_t *)at(i_s2w); D.blk_s2ell = (const int32_t *)at(i_s2o);
   *out = M;
