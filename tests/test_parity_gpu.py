@@ -304,13 +304,7 @@ def seven():
     return w, seqs, o64, ox, cls, sx, lx
 
 
-SEVEN_FP32_FLOOR = pytest.mark.xfail(
-    reason="stated shortfall: FP32 Krylov vectors carry a rounding floor of about u dtau ||H_b - s_b|| per "
-           "interval; at seven orbitals a few walkers of 256 exceed 1e-5 (up to about 2.6e-5); the FP64 path "
-           "meets 1e-10", strict=False)
-
-
-@pytest.mark.parametrize("prec", [kt.KT_FP64, pytest.param(kt.KT_FP32_KRYLOV, marks=SEVEN_FP32_FLOOR)])
+@pytest.mark.parametrize("prec", PRECS)
 def test_seven_orbital_traces_and_ratios(seven, prec):
     """7-orbital f-shell model (16,384 states, blocks up to 35 rows, N_tr = 63), the full batch
     of 256 walkers: traces, ratios against the oracle's current traces (RTOL) and ratios
