@@ -842,8 +842,9 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
     if constexpr (F32) {
       if (p == 2 && (DMAX > 16 || M.tri64)) {
         // the 2x2 closed form in FP64 from the double-float alpha, beta: with KT_FP32_TRIDIAG64,
-        // and on seven-orbital blocks, whose larger ||H_b - s_b|| makes the FP32 eigenvector
-        // components of the 2x2 step one of the two largest contributions to the trace error
+        // and in the instances for blocks beyond 16 rows (seven orbitals), where the FP32
+        // eigenvector components of the 2x2 step (error u ||T_2|| / gap) were the largest
+        // contribution to the trace error
         const float2 a0 = reinterpret_cast<float2 *>(s.a)[grp], a1 = reinterpret_cast<float2 *>(s.a)[IPW + grp];
         const float2 b0 = reinterpret_cast<float2 *>(s.b)[grp];
         double y0, y1;
