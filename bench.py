@@ -56,9 +56,11 @@ def args_():
     p.add_argument("--fp64-steps", type=int, default=0, help="steps for the FP64 comparator (default min(K, 100))")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
-    p.add_argument("--sweep-steps", type=int, default=1000,
+    p.add_argument("--sweep-steps", type=int, default=3000,
                    help="timed Metropolis steps of the CT-HYB sweep line (0 skips it)")
     p.add_argument("--sweep-beta", type=float, default=50.0)
+    p.add_argument("--da-tries", type=int, default=DA_TRIES,
+                   help="proposals per chain and call step of the multi-try delayed-acceptance sweep lines")
     p.add_argument("--sweep-other-steps", type=int, default=500,
                    help="timed steps of the lighter sweep lines at beta 10 and 100")
     p.add_argument("--no-other-betas", action="store_true", help="skip the beta 10 and 100 sweep lines")
@@ -265,35 +267,48 @@ def reference_arm(a):
 
 
 CACHE_OPS = 512   # partial-state cache length of the cached sweeps (operators per walker)
+DA_TRIES = 8      # proposals per chain and call step of the multi-try delayed-acceptance sweeps (--da-tries)
+THERM_DA_CALL_STEPS = 3000  # multi-try delayed-acceptance call steps at the end of the sweeps' thermalisation
 
 
 def chain_estimates(acc, n_orb: int, beta: float, n_bins: int):
     """Per-chain estimates from sweep accumulators: double occupancy (mean over orbitals),
-    expansion order (sum over flavors), n_f [chains][flavors] and G(tau) [chains][bins] (mean
-    over flavors), each divided by the chain's sign sum."""
+    expansion order (sum over flavors), n_f [chains][flavors] (flavor f = 2a + s), the orbital
+    occupations n_a = n_{a up} + n_{a dn} [chains][orbitals] and G(tau) [chains][bins] (mean over
+    flavors), each divided by the chain's sign sum."""
     ssum = acc["sign_sum"]
     obs = acc["obs_sum"] / ssum[:, None]
+    nf = obs[:, :2 * n_orb]
     return {"docc": obs[:, 2 * n_orb: 3 * n_orb].mean(1), "order": acc["order_sum"].sum(1) / ssum,
-            "n_f": obs[:, :2 * n_orb], "G_tau": acc["g_tau"].mean(1) * (n_bins / beta ** 2) / ssum[:, None]}
+            "n_f": nf, "n_orbital": nf[:, 0::2] + nf[:, 1::2],
+            "G_tau": acc["g_tau"].mean(1) * (n_bins / beta ** 2) / ssum[:, None]}
 
 
 def efficiencies(est, secs: float):
     """Statistical efficiency 1 / (variance across independent chains x wall time) of every
-    observable (n_f per flavor, G(tau) per bin)."""
+    observable (n_f per flavor, n_a per orbital, G(tau) per bin), and of G(tau) pooled over its
+    bins (1 / (sum of the bins' variances x wall time))."""
     var = {k: v.var(axis=0, ddof=1) for k, v in est.items()}
-    return {k: (1.0 / (v * secs)) for k, v in var.items()}
+    out = {k: (1.0 / (v * secs)) for k, v in var.items()}
+    out["G_tau_pooled"] = 1.0 / (float(var["G_tau"].sum()) * secs)
+    return out
 
 
 def speedups(ea, eb):
-    """Speedups at equal statistical error of path a over path b: ratios of efficiencies, for
-    n_f and G(tau) the smallest over flavors and bins (and the median over bins)."""
+    """Speedups at equal statistical error of path a over path b: ratios of efficiencies; for
+    n_f, n_a and G(tau) the smallest over flavors, orbitals and bins, the median over bins and
+    the ratio pooled over bins. A smallest ratio over many noisy ratios sits below their common
+    value (each ratio of two variances over 1,024 chains carries about 6% noise)."""
     import numpy as np
     out = {"docc": float(ea["docc"] / eb["docc"]), "order": float(ea["order"] / eb["order"])}
     rf = np.asarray(ea["n_f"] / eb["n_f"])
+    ro = np.asarray(ea["n_orbital"] / eb["n_orbital"])
     rg = np.asarray(ea["G_tau"] / eb["G_tau"])
     out["n_f_min_over_flavors"] = float(rf.min())
+    out["n_orbital_min_over_orbitals"] = float(ro.min())
     out["G_tau_min_over_bins"] = float(rg.min())
     out["G_tau_median_over_bins"] = float(np.median(rg))
+    out["G_tau_pooled"] = float(ea["G_tau_pooled"] / eb["G_tau_pooled"])
     return out
 
 
@@ -478,16 +493,13 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
               for name, prec in (("fp32", kt.KT_FP32_KRYLOV), ("fp64", kt.KT_FP64))}
     sg, _, _ = engine.trace(models["fp32"], engine.DeviceSeqs.from_host(cand, dev))
     ok = np.nonzero(sg.cpu().numpy() != 0)[0][:nw]
-    base = engine.Sweep(models["fp32"], table, beta, nw, k_cap=128, n_bins=200, measure_obs=True)
+    # thermalisation (untimed), with the partial-state cache: plain steps, the surrogate's
+    # training steps, then multi-try delayed-acceptance steps, the fastest route to many
+    # Metropolis steps per chain
+    base = engine.Sweep(models["fp32"], table, beta, nw, k_cap=128, n_bins=200, measure_obs=True, cache_ops=CACHE_OPS)
     base.set_configs(cand.subset(ok))
     for _ in range(0, therm, 500):
         base.run(uni(500, 6))
-    st = {k: v.cpu().numpy() for k, v in base.state().items()}
-    lens = st["lens"]
-    thermal = workloads.Sequences(np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
-                                  np.concatenate([st["tau"][i, :lens[i]] for i in range(nw)]),
-                                  np.concatenate([st["flavor"][i, :lens[i]] for i in range(nw)]),
-                                  np.concatenate([st["dagger"][i, :lens[i]] for i in range(nw)]))
     # the surrogate: training data from the chains themselves, then Adam on the tensor cores
     torch.cuda.synchronize()
     t0 = time.time()
@@ -497,7 +509,7 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     # targets clipped to where the acceptance test can go either way (the chain stays exact
     # for any surrogate; accuracy only matters near log ratio 0)
     t = t.clamp(-25.0, 10.0)
-    net = engine.Surrogate(base.n_features, max_batch=8192, seed=seed)
+    net = engine.Surrogate(base.n_features, max_batch=max(8192, DA_TRIES * nw), seed=seed)
     t0 = time.time()
     hist = net.train(X, t, epochs=10, batch=4096, lr=3e-3, seed=seed)
     hist += net.train(X, t, epochs=10, batch=4096, lr=1e-3, seed=seed + 1)
@@ -506,6 +518,19 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     pred = net.predict(X[:65536]).double()
     resid = float(torch.sqrt(torch.mean((pred - t[:65536].double()) ** 2)).item())
     spread = float(torch.std(t[:65536].double()).item())
+    n_train = int(X.shape[0])
+    del X, t
+    base.set_surrogate(net)
+    for _ in range(0, THERM_DA_CALL_STEPS, 500):
+        base.run_da_multi(torch.rand((500, nw, DA_TRIES, 7), dtype=torch.float64, device=dev, generator=g))
+    cth = base.counters()
+    therm_mh = cth["insert_proposed"] + cth["remove_proposed"]
+    st = {k: v.cpu().numpy() for k, v in base.state().items()}
+    lens = st["lens"]
+    thermal = workloads.Sequences(np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
+                                  np.concatenate([st["tau"][i, :lens[i]] for i in range(nw)]),
+                                  np.concatenate([st["flavor"][i, :lens[i]] for i in range(nw)]),
+                                  np.concatenate([st["dagger"][i, :lens[i]] for i in range(nw)]))
     del base
 
     out = {}
@@ -517,21 +542,34 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     n_blocks = steps // meas
     u_plain = uni(steps, 6)      # the FP32 and FP64 plain runs share their uniforms
     u_da = uni(steps, 7)         # and so do the delayed-acceptance runs
+    u_multi = None
     for name, model, mode, n_t, cache in (("fp32", models["fp32"], "plain", steps, 0),
                                           ("fp32_da", models["fp32"], "da", steps, 0),
+                                          ("fp32_da_multi", models["fp32"], "multi", steps, 0),
                                           ("fp64", models["fp64"], "plain", steps, 0),
                                           ("fp32_cached", models["fp32"], "plain", steps, CACHE_OPS),
                                           ("fp32_da_cached", models["fp32"], "da", steps, CACHE_OPS),
+                                          ("fp32_da_multi_cached", models["fp32"], "multi", steps, CACHE_OPS),
                                           ("fp64_cached", models["fp64"], "plain", steps, CACHE_OPS)):
         sw = engine.Sweep(model, table, beta, nw, k_cap=128, n_bins=200, measure_obs=True, cache_ops=cache)
         sw.set_configs(thermal)
-        if mode == "da":
+        if mode != "plain":
             sw.set_surrogate(net)
-        u = u_da if mode == "da" else u_plain
+        meas_m = meas
+        if mode == "multi":
+            # measure at the Metropolis-step spacing of the other lines: a call step is E[n]
+            # Metropolis steps, from the stage-1 pass rate p of the one-try line
+            pp = out["fp32_da"]["trace_evaluations_per_proposal"]
+            en = (1.0 - (1.0 - pp) ** DA_TRIES) / pp
+            meas_m = max(1, int(round(meas / en)))
+            n_t = n_blocks * 3 * meas_m
+            if u_multi is None or u_multi.shape[0] < n_t:
+                u_multi = torch.rand((n_t, nw, DA_TRIES, 7), dtype=torch.float64, device=dev, generator=g)
+        u = {"plain": u_plain, "da": u_da, "multi": u_multi[:n_t] if mode == "multi" else None}[mode]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        blocks = sw.run_blocks(u, meas, n_blocks, delayed=(mode == "da"))
+        blocks = sw.run_blocks(u, meas_m, n_blocks, delayed=(mode != "plain"))
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
@@ -562,7 +600,9 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         # algorithmic Krylov flops of the trace pipeline per step (50 untimed steps)
         wst = engine.new_stats(dev)
         sw.set_stats(wst)
-        if mode == "da":
+        if mode == "multi":
+            sw.run_da_multi(u[:50])
+        elif mode == "da":
             sw.run_da(u[:50])
         else:
             sw.run(u[:50])
@@ -572,15 +612,20 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         per_chain[name] = {"docc": docc, "order": order, "G_beta_half": gmid,
                            "n_f": obs[:, :2 * spec.n_orb].mean(1), "S2": obs[:, 3 * spec.n_orb],
                            "lens": stt["lens"].cpu().numpy(), "tau": stt["tau"].cpu().numpy()}
-        props = nw * n_t / (ms / 1000.0)
+        # Metropolis steps taken (a multi-try call step is 1 to DA_TRIES of them per chain)
+        n_mh = cnt["insert_proposed"] + cnt["remove_proposed"]
+        props = n_mh / (ms / 1000.0)
         secs = ms / 1000.0
-        out[name] = {"proposals_per_s": props, "ms_per_step": ms / n_t, "steps": n_t,
+        out[name] = {"proposals_per_s": props, "ms_per_step": ms / n_t, "steps": n_t, "measure_every": meas_m,
+                     "metropolis_steps_per_call_step": n_mh / (nw * n_t),
                      "sweeps_per_s": props / K, "mean_ops_per_chain": K,
                      "mean_order_per_flavor": stt["order"].double().mean().item(),
-                     "acceptance": (cnt["insert_accepted"] + cnt["remove_accepted"]) / (nw * n_t),
-                     "trace_evaluations_per_proposal": cnt["trace_evaluations"] / (nw * n_t),
-                     "stage1_rejected_per_proposal": cnt["stage1_rejected"] / (nw * n_t),
-                     "mean_sign": float(ssum.sum() / (nw * cnt["measurements"])) if cnt["measurements"] else None,
+                     "acceptance": (cnt["insert_accepted"] + cnt["remove_accepted"]) / n_mh,
+                     "trace_evaluations_per_proposal": cnt["trace_evaluations"] / n_mh,
+                     "stage1_rejected_per_proposal": cnt["stage1_rejected"] / n_mh,
+                     # multi-try sums carry the tries as weights, so their sign sum is no count
+                     "mean_sign": (float(ssum.sum() / (nw * cnt["measurements"]))
+                                   if cnt["measurements"] and mode != "multi" else None),
                      "trace_errors": cnt["trace_errors"], "refused_at_k_cap": cnt["refused_at_k_cap"],
                      "docc": float(docc.mean()), "G_beta_half": float(gmid.mean()),
                      "n_f": float(obs[:, :2 * spec.n_orb].mean()), "S2": float(obs[:, 3 * spec.n_orb].mean()),
@@ -606,10 +651,13 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         return int(sum(a["lens"][i] == b["lens"][i] and np.array_equal(a["tau"][i, :a["lens"][i]], b["tau"][i, :b["lens"][i]])
                        for i in range(nw)))
     cache_same = {f"{c}_vs_{p}": identical(c, p) for c, p in (("fp32_cached", "fp32"), ("fp32_da_cached", "fp32_da"),
+                                                            ("fp32_da_multi_cached", "fp32_da_multi"),
                                                             ("fp64_cached", "fp64"))}
     speed = {f"{a}_over_{b}": {k: out[a]["eff"][k] / out[b]["eff"][k] for k in out[a]["eff"]}
              for a, b in (("fp32", "fp64"), ("fp32_da", "fp64"), ("fp32_da", "fp32"), ("fp32_cached", "fp64"),
-                          ("fp32_da_cached", "fp64"), ("fp32_cached", "fp32"), ("fp64_cached", "fp64"))}
+                          ("fp32_da_cached", "fp64"), ("fp32_cached", "fp32"), ("fp64_cached", "fp64"),
+                          ("fp32_da_multi", "fp64"), ("fp32_da_multi", "fp32"), ("fp32_da_multi_cached", "fp64"),
+                          ("fp32_da_multi_cached", "fp32_cached"))}
     # throughput-bound batch: 8,192 chains (the 1,024-chain batch is bound by its longest chains)
     nbig, nsteps_big = 8192, max(steps // 4, 100)
     cand_big = workloads.generate_sequences(gen, int(1.3 * nbig), seed=seed + 1)
@@ -619,10 +667,15 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     def unib(n, k):
         return torch.rand((n, nbig, k), dtype=torch.float64, device=dev, generator=g)
 
-    big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200, measure_obs=True)
+    # the same network, with room for DA_TRIES proposals of every chain
+    net_big = engine.Surrogate(net.n_in, max_batch=DA_TRIES * nbig, params=net.params())
+    big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200, measure_obs=True, cache_ops=CACHE_OPS)
     big.set_configs(cand_big.subset(okb))
     for _ in range(0, therm, 500):
         big.run(unib(500, 6))
+    big.set_surrogate(net_big)
+    for _ in range(0, THERM_DA_CALL_STEPS // 3, 250):
+        big.run_da_multi(torch.rand((250, nbig, DA_TRIES, 7), dtype=torch.float64, device=dev, generator=g))
     stb = {k: v.cpu().numpy() for k, v in big.state().items()}
     lb = stb["lens"]
     thermal_big = workloads.Sequences(np.concatenate([[0], np.cumsum(lb)]).astype(np.int32),
@@ -632,43 +685,45 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     del big
     thr = {}
     ub = {6: unib(nsteps_big, 6), 7: unib(nsteps_big, 7)}
-    for mode in ("plain", "da", "plain_cached", "da_cached"):
+    meas_big_m = out["fp32_da_multi"]["measure_every"]
+    ub[(DA_TRIES, 7)] = torch.rand((nsteps_big, nbig, DA_TRIES, 7), dtype=torch.float64, device=dev, generator=g)
+    for mode in ("plain", "da", "da_multi", "plain_cached", "da_cached", "da_multi_cached"):
         big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200, measure_obs=True,
                            cache_ops=CACHE_OPS if mode.endswith("cached") else 0)
         big.set_configs(thermal_big)
+        multi = mode.startswith("da_multi")
         if mode.startswith("da"):
-            big.set_surrogate(net)
-        u = ub[7 if mode.startswith("da") else 6]
+            big.set_surrogate(net_big if multi else net)
+        u = ub[(DA_TRIES, 7)] if multi else ub[7 if mode.startswith("da") else 6]
+        run = big.run_da_multi if multi else (big.run_da if mode.startswith("da") else big.run)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        if mode.startswith("da"):
-            big.run_da(u, meas_every=meas)
-        else:
-            big.run(u, meas_every=meas)
+        run(u, meas_every=meas_big_m if multi else meas)
         e1.record()
         torch.cuda.synchronize()
         c1 = big.counters()
         ms = e0.elapsed_time(e1)
-        # trace-pipeline work of 50 more (untimed) steps
+        n_mh = c1["insert_proposed"] + c1["remove_proposed"]
+        # trace-pipeline work of 50 more (untimed) call steps
         wst = engine.new_stats(dev)
         big.set_stats(wst)
-        if mode.startswith("da"):
-            big.run_da(u[:50])
-        else:
-            big.run(u[:50])
+        run(u[:50])
         big.set_stats(None)
+        c2 = big.counters()
+        n_mh50 = c2["insert_proposed"] + c2["remove_proposed"] - n_mh
         wk = kt.stats_from_tensor(wst)
         ab = {k: v.cpu().numpy() for k, v in big.accumulators().items()}
         docc_b = (ab["obs_sum"] / ab["sign_sum"][:, None])[:, 2 * spec.n_orb: 3 * spec.n_orb].mean(1)
         order_b = ab["order_sum"].sum(1) / ab["sign_sum"]
-        thr[mode] = {"proposals_per_s": nbig * nsteps_big / (ms / 1000.0), "ms_per_step": ms / nsteps_big,
-                     "work_per_proposal": {"intervals": wk["intervals"] / (50 * nbig),
-                                           "ops_applied": wk["ops_applied"] / (50 * nbig),
-                                           "krylov_iters": wk["krylov_iters"] / (50 * nbig),
-                                           "items_alive": wk["items_alive"] / (50 * nbig)},
-                     "trace_evaluations_per_proposal": c1["trace_evaluations"] / (nbig * nsteps_big),
-                     "acceptance": (c1["insert_accepted"] + c1["remove_accepted"]) / (nbig * nsteps_big),
+        thr[mode] = {"proposals_per_s": n_mh / (ms / 1000.0), "ms_per_step": ms / nsteps_big,
+                     "metropolis_steps_per_call_step": n_mh / (nbig * nsteps_big),
+                     "work_per_proposal": {"intervals": wk["intervals"] / n_mh50,
+                                           "ops_applied": wk["ops_applied"] / n_mh50,
+                                           "krylov_iters": wk["krylov_iters"] / n_mh50,
+                                           "items_alive": wk["items_alive"] / n_mh50},
+                     "trace_evaluations_per_proposal": c1["trace_evaluations"] / n_mh,
+                     "acceptance": (c1["insert_accepted"] + c1["remove_accepted"]) / n_mh,
                      "eff": {"docc": 1.0 / (docc_b.var(ddof=1) * ms / 1000.0),
                              "order": 1.0 / (order_b.var(ddof=1) * ms / 1000.0)}}
         del big
@@ -676,28 +731,40 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
                speedup_da_over_plain=thr["da"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
                speedup_cached_over_plain=thr["plain_cached"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
                speedup_da_cached_over_plain=thr["da_cached"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
+               speedup_da_multi_over_plain=thr["da_multi"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
+               speedup_da_multi_cached_over_plain=(thr["da_multi_cached"]["proposals_per_s"]
+                                                  / thr["plain"]["proposals_per_s"]),
                speedup_at_equal_error_over_plain={m: {k: thr[m]["eff"][k] / thr["plain"]["eff"][k]
                                                          for k in ("docc", "order")}
-                                                      for m in ("da", "plain_cached", "da_cached")})
+                                                      for m in ("da", "da_multi", "plain_cached", "da_cached",
+                                                                "da_multi_cached")})
     return {"workload": f"five_orbital_sweep_beta{beta:g}_1024_chains", "metric": "Metropolis proposals/s (all chains)",
             "sweep_definition": "one sweep = as many proposals per chain as the chain holds operators on average",
             "bath": "semicircular DOS, bandwidth 4, 2000 tau points", "thermalisation_steps": therm,
+            "thermalisation": {"plain_steps": therm, "surrogate_training_steps": ncollect,
+                               "da_multi_call_steps": THERM_DA_CALL_STEPS,
+                               "metropolis_steps_per_chain": therm_mh / nw},
             "measure_every": meas, **out,
             "speedup_fp32_over_fp64": out["fp32"]["proposals_per_s"] / out["fp64"]["proposals_per_s"],
             "speedup_at_equal_error": speed,
             "speedup_at_equal_error_all_observables": {
                 f"{a_}_over_{b_}": speedups(effs[a_], effs[b_])
                 for a_, b_ in (("fp32", "fp64"), ("fp32_da", "fp64"), ("fp32_da", "fp32"), ("fp32_cached", "fp64"),
-                               ("fp32_da_cached", "fp64"), ("fp32_cached", "fp32"), ("fp64_cached", "fp64"))},
+                               ("fp32_da_cached", "fp64"), ("fp32_cached", "fp32"), ("fp64_cached", "fp64"),
+                               ("fp32_da_multi", "fp64"), ("fp32_da_multi", "fp32"), ("fp32_da_multi_cached", "fp64"),
+                               ("fp32_da_multi_cached", "fp32_cached"))},
+            "da_tries": DA_TRIES,
             "throughput_8192_chains": thr, "fp32_vs_fp64_same_uniforms": err32,
             "cached_vs_uncached_identical_paths": cache_same, "cache_ops": CACHE_OPS,
-            "surrogate": {"training_samples": int(X.shape[0]), "collect_s": t_collect, "train_s": t_train,
+            "surrogate": {"training_samples": n_train, "collect_s": t_collect, "train_s": t_train,
                           "epochs": len(hist), "loss_per_epoch": hist, "rms_residual_log_ratio": resid,
                           "target_std": spread, "network": "n_in-256-256-1 ReLU, BF16 tcgen05, FP32 accumulate"}}
 
 
 def main():
+    global DA_TRIES
     a = args_()
+    DA_TRIES = a.da_tries
     if a.impl == "reference":
         reference_arm(a)
         return

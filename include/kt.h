@@ -536,6 +536,33 @@ kt_status kt_sweep_set_surrogate(kt_sweep *s, kt_mlp *net);
  * Counters 8 (stage-1 rejections) and 9 (trace ratios evaluated) count them. */
 kt_status kt_sweep_run_da(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream);
 
+/* Multi-try delayed acceptance (the two-stage rule of kt_sweep_run_da, Christen & Fox).
+ * A proposal rejected at stage 1 is a Metropolis step that leaves the configuration as it
+ * is, so the next proposal starts from the same configuration. Each call step therefore
+ * draws up to `tries` proposals per walker from its current configuration (uniforms DEVICE
+ * [n_steps][n_walkers][tries][7], each try laid out as kt_sweep_run_da's seven), scores all
+ * of them with one surrogate inference, and takes the first that passes stage 1 through the
+ * trace pipeline and stage 2. The tries before it are stage-1 rejections (or null moves);
+ * the tries after it are not taken. A call step is thus 1 to `tries` Metropolis steps of
+ * the walker, every one judged by the exact two-stage rule.
+ *
+ * Measurement: because the number of Metropolis steps in a call step depends on the
+ * configuration, a measurement per call step would weight configurations by the inverse of
+ * their expected number of tries. Every meas_every-th call step therefore measures the
+ * configuration the walker starts it in (after stage 1, before stage 2) with the weight n,
+ * the number of tries the walker takes in that call step: the accumulators of
+ * kt_sweep_get_accumulators hold sums of n * sign * O, and sign_sum the sum of n * sign,
+ * whose ratio estimates <O> without that bias. With tries == 1, n == 1.
+ *
+ * Counters: 0/2 count the tries taken (proposals), 8 the stage-1 rejections among them.
+ * The surrogate (kt_sweep_set_surrogate) must accept batches of tries * n_walkers rows
+ * (KT_EINVAL otherwise); 1 <= tries <= KT_DA_MAX_TRIES. The first call with a larger
+ * `tries` than before allocates the proposal slots (about tries * n_walkers *
+ * (16 k_cap + 2 n_in + 120) bytes) and synchronises; KT_ENOMEM if that fails. */
+#define KT_DA_MAX_TRIES 16
+kt_status kt_sweep_run_da_multi(kt_sweep *s, int32_t n_steps, int32_t tries, const double *uniforms,
+                                int32_t meas_every, void *stream);
+
 /* Kernel tiling: every (walker, kept state) item of the Krylov stage is
  * processed by a group of group_lanes lanes of one warp (32 / group_lanes items
  * per warp). kt_model_set_tiling picks one of the compiled group sizes

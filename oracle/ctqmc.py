@@ -302,6 +302,109 @@ def chain(model: Model, hyb: Hyb, init, uniforms: np.ndarray, k_cap: int = 64, n
     return out
 
 
+def chain_da_multi(model: Model, hyb: Hyb, init, uniforms: np.ndarray, surrogate, k_cap: int = 64,
+                   n_bins: int = 50, meas_every: int = 0, observables: bool = False, trace=None):
+    """Multi-try delayed acceptance. uniforms [n_steps, n_walkers, tries, 7], each try's seven
+    as in chain(). A null move or a stage-1 rejection is a Metropolis step that keeps the
+    configuration, so per step every walker takes its tries in order from its configuration
+    until one passes stage 1; that one is judged at stage 2 and ends the step, and the later
+    tries are not taken. A step is thus n = 1 .. tries Metropolis steps of the walker.
+
+    Measurement weights: the step's off-diagonal transition probability from x to y is
+    c(x) K(x, y), with K the delayed-acceptance kernel and c(x) the expected number of tries
+    taken from x, so the step chain is stationary in w(x) / c(x). Every meas_every steps the
+    configuration each walker holds after stage 1 (before stage 2) is measured with the
+    weight n of that step's tries, an unbiased estimate of c(x): sums of n * sign * O, and
+    sign_sum = sum n * sign, whose ratio estimates <O> under w.
+
+    Returns a dict: accepted [n_steps, n_walkers] (1 accepted at stage 2, 0 rejected at stage
+    2 or a zero new weight, -2 no try passed stage 1), tries [n_steps, n_walkers] (n),
+    counts {"proposals", "insertions", "removals", "null", "stage1_rejected"} over the tries
+    taken, configs, sign / logw, and when meas_every > 0 the accumulators of chain()."""
+    beta = model.p.beta
+    nf = 2 * model.p.n_orb
+    n_steps, nw, T, _ = uniforms.shape
+    configs = [list(c) for c in init]
+    cur = [weight(model, hyb, c, trace) for c in configs]
+    acc = np.zeros((n_steps, nw), dtype=np.int8)
+    tries = np.zeros((n_steps, nw), dtype=np.int32)
+    counts = {"proposals": 0, "insertions": 0, "removals": 0, "null": 0, "stage1_rejected": 0}
+    g_acc = np.zeros((nw, nf, n_bins))
+    sign_sum = np.zeros(nw)
+    order_sum = np.zeros((nw, nf))
+    obs_sum = None
+    n_meas = 0
+    for step in range(n_steps):
+        passed = [None] * nw
+        for w in range(nw):
+            n = T
+            for t in range(T):
+                u = uniforms[step, w, t]
+                counts["proposals"] += 1
+                counts["insertions" if u[0] < 0.5 else "removals"] += 1
+                mv = propose(configs[w], u, nf, beta, k_cap)
+                if mv is None:
+                    counts["null"] += 1
+                    continue
+                new, lp, info = mv
+                bs_new, bl_new = bath_weight(hyb, new, nf)
+                if bs_new == 0:
+                    counts["null"] += 1
+                    continue
+                bs_old, bl_old = bath_weight(hyb, configs[w], nf)
+                lstage1 = float(surrogate(configs[w], *info)) + bl_new - bl_old + lp
+                if not (math.log(u[6]) if u[6] > 0 else -math.inf) < lstage1:
+                    counts["stage1_rejected"] += 1
+                    continue
+                n = t + 1
+                passed[w] = (new, lp, lstage1, u[5])
+                break
+            tries[step, w] = n
+        if meas_every and (step + 1) % meas_every == 0:
+            n_meas += 1
+            for w in range(nw):
+                s = cur[w][0] * float(tries[step, w])
+                sign_sum[w] += s
+                for f in range(nf):
+                    cre, ann = flavor_times(configs[w], f)
+                    order_sum[w, f] += s * len(cre)
+                    if not cre:
+                        continue
+                    M = np.linalg.inv(bath_matrix(hyb, f, cre, ann))
+                    for i, tc in enumerate(cre):
+                        for j, ta in enumerate(ann):
+                            x, v = ta - tc, M[j, i]
+                            if x < 0:
+                                x, v = x + beta, -v
+                            b = min(int(x / beta * n_bins), n_bins - 1)
+                            g_acc[w, f, b] += s * v
+            if observables:
+                val, _, _ = measure(model, SeqBatch.from_lists(configs))
+                sg = np.array([c[0] for c in cur], dtype=np.float64) * tries[step].astype(np.float64)
+                obs_sum = val * sg[:, None] if obs_sum is None else obs_sum + val * sg[:, None]
+        for w in range(nw):
+            if passed[w] is None:
+                acc[step, w] = -2
+                continue
+            new, lp, lstage1, u5 = passed[w]
+            nw_ = weight(model, hyb, new, trace)
+            if nw_[0] == 0:
+                continue
+            lr = nw_[1] - cur[w][1] + lp - lstage1
+            if (math.log(u5) if u5 > 0 else -math.inf) < lr:
+                configs[w] = new
+                cur[w] = nw_
+                acc[step, w] = 1
+    out = {"accepted": acc, "tries": tries, "counts": counts, "configs": configs,
+           "sign": np.array([c[0] for c in cur]), "logw": np.array([c[1] for c in cur]),
+           "trace_sign": np.array([c[2] for c in cur]), "trace_log": np.array([c[3] for c in cur])}
+    if meas_every:
+        out.update(g_acc=g_acc, sign_sum=sign_sum, order_sum=order_sum, n_meas=n_meas)
+        if observables:
+            out["obs_sum"] = obs_sum
+    return out
+
+
 def green_function(g_acc: np.ndarray, sign_sum: np.ndarray, beta: float) -> np.ndarray:
     """G_f(tau) at the bin centres from the accumulated estimator (summed over walkers)."""
     n_bins = g_acc.shape[-1]

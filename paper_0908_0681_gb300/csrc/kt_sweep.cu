@@ -160,8 +160,40 @@ __device__ int perm_count(const double *tau, const uint8_t *fl, int K, int f, do
   return c + (tdag < tann ? 1 : 0);
 }
 
-__global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni, int ustride) {
+// Multi-try delayed acceptance: per walker and step, T proposals drawn from the same
+// configuration, each with its own seven uniforms, stored slot by slot (slot t * nw + w).
+struct TryView {
+  int T;
+  int8_t *p_kind, *p_seg, *p_valid, *p_sign, *p_acc;
+  double *p_t1, *p_t2, *mv_tdag, *mv_tann, *p_lprop, *p_ldet, *p_lambda, *p_vec;
+  int32_t *p_pair, *mv_rem, *p_ij;
+  uint8_t *mv_kind, *mv_flv;
+  __nv_bfloat16 *X;
+  float *ytil;
+  unsigned long long *scratch_counters;  // the propose kernel's counters land here; the select kernel counts
+  int32_t *n_tries;   // [nw] Metropolis steps the walker took this step (tries up to and including the selected one)
+  double *u5;         // [nw] stage-2 uniform of the selected try
+};
+
+// The view of try t: the walker state of S, the proposal arrays of slot t.
+__host__ __device__ inline SweepView try_view(const SweepView &S, const TryView &Tv, int t) {
+  SweepView v = S;
+  const size_t o = (size_t)t * S.nw;
+  v.p_kind = Tv.p_kind + o; v.p_seg = Tv.p_seg + o; v.p_valid = Tv.p_valid + o; v.p_sign = Tv.p_sign + o;
+  v.p_acc = Tv.p_acc + o; v.p_t1 = Tv.p_t1 + o; v.p_t2 = Tv.p_t2 + o; v.mv_tdag = Tv.mv_tdag + o;
+  v.mv_tann = Tv.mv_tann + o; v.p_lprop = Tv.p_lprop + o; v.p_ldet = Tv.p_ldet + o; v.p_lambda = Tv.p_lambda + o;
+  v.p_vec = Tv.p_vec + o * 2 * S.kcap; v.p_pair = Tv.p_pair + 2 * o; v.mv_rem = Tv.mv_rem + o;
+  v.p_ij = Tv.p_ij + 2 * o; v.mv_kind = Tv.mv_kind + o; v.mv_flv = Tv.mv_flv + o;
+  v.X = Tv.X + o * S.n_in; v.ytil = Tv.ytil + o;
+  v.counters = Tv.scratch_counters;
+  return v;
+}
+
+// Tv.T > 0: multi-try launch, blockIdx.y = try (uniforms of try t at uni + 7 t).
+__global__ void sweep_propose_kernel(SweepView S0, const double *__restrict__ uni, int ustride, TryView Tv) {
   extern __shared__ double sh[];
+  const SweepView S = Tv.T ? try_view(S0, Tv, blockIdx.y) : S0;
+  if (Tv.T) uni += 7 * blockIdx.y;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int w = blockIdx.x * (blockDim.x >> 5) + wib;
   if (w >= S.nw) return;
@@ -328,7 +360,7 @@ __global__ void sweep_propose_kernel(SweepView S, const double *__restrict__ uni
   }
 }
 
-__global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni, int ustride,
+__global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ u5s, int u5stride,
                                     const int4 *__restrict__ desc, bool delayed) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -344,7 +376,7 @@ __global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni,
   if (tsg == 0) return;  // the new trace is zero
   // plain Metropolis: the whole ratio; delayed acceptance, stage 2: true over predicted trace ratio
   const double logR = delayed ? S.r_log[w] - (double)S.ytil[w] : S.r_log[w] + S.p_ldet[w] + S.p_lprop[w];
-  const double u5 = uni[(size_t)w * ustride + 5];
+  const double u5 = u5s[(size_t)w * u5stride];
   const bool accept = (u5 > 0.0 ? log(u5) : -INFINITY) < logR;
   if (!accept) return;
   if (lane == 0) S.p_acc[w] = 1;
@@ -457,8 +489,9 @@ __global__ void sweep_accept_kernel(SweepView S, const double *__restrict__ uni,
 
 // Feature vector of each proposal (see kt_sweep_feature_size): the configuration without
 // the move's pair (the base) and the pair. A removal's base skips the pair's operators.
-__global__ void sweep_features_kernel(SweepView S) {
+__global__ void sweep_features_kernel(SweepView S0, TryView Tv) {
   extern __shared__ float hsm[];
+  const SweepView S = Tv.T ? try_view(S0, Tv, blockIdx.y) : S0;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int w = blockIdx.x * (blockDim.x >> 5) + wib;
   if (w >= S.nw) return;
@@ -544,6 +577,86 @@ __global__ void sweep_stage1_kernel(SweepView S, const double *__restrict__ uni)
   }
 }
 
+// Stage 1 over the tries in order (one warp per walker): the first try that passes becomes
+// the step's move, copied into the walker's proposal arrays for the trace pipeline and the
+// accept kernel. Every try before it is a Metropolis step that leaves the configuration as
+// it is (rejected at stage 1, or a null move); the tries after it are never taken. A walker
+// none of whose tries passes keeps its configuration for T steps. Counters of the tries taken.
+__global__ void sweep_select_kernel(SweepView S, TryView Tv, const double *__restrict__ uni) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= S.nw) return;
+  const int nw = S.nw, T = Tv.T;
+  int sel = -1;
+  float ysel = 0.f;
+  if (lane == 0) {
+    unsigned long long c_ins = 0, c_rem = 0, c_null = 0, c_cap = 0, c_st1 = 0;
+    for (int t = 0; t < T; ++t) {
+      const size_t sl = (size_t)t * nw + w;
+      const int kind = Tv.p_kind[sl];
+      if (kind == 0) ++c_ins;
+      else ++c_rem;
+      if (!Tv.p_valid[sl]) {
+        ++c_null;
+        if (kind == 0 && S.kf[(size_t)w * S.nf + Tv.mv_flv[sl]] >= S.kcap) ++c_cap;
+        continue;
+      }
+      const float y = kind != 0 ? -Tv.ytil[sl] : Tv.ytil[sl];
+      const double lt = (double)y + Tv.p_ldet[sl] + Tv.p_lprop[sl];
+      const double u6 = uni[((size_t)w * T + t) * 7 + 6];
+      if ((u6 > 0.0 ? log(u6) : -INFINITY) < lt) {
+        sel = t;
+        ysel = y;
+        break;
+      }
+      ++c_st1;
+    }
+    Tv.n_tries[w] = sel < 0 ? T : sel + 1;
+    S.p_acc[w] = 0;
+    if (c_ins) atomicAdd(&S.counters[C_INS_PROP], c_ins);
+    if (c_rem) atomicAdd(&S.counters[C_REM_PROP], c_rem);
+    if (c_null) atomicAdd(&S.counters[C_NULL], c_null);
+    if (c_cap) atomicAdd(&S.counters[C_CAP], c_cap);
+    if (c_st1) atomicAdd(&S.counters[C_STAGE1], c_st1);
+  }
+  sel = __shfl_sync(FULL, sel, 0);
+  if (sel < 0) {
+    if (lane == 0) {
+      S.p_valid[w] = 0;
+      S.mv_kind[w] = 2;  // skipped by the trace pipeline
+    }
+    return;
+  }
+  const size_t sl = (size_t)sel * nw + w;
+  if (lane == 0) {
+    S.p_kind[w] = Tv.p_kind[sl];
+    S.p_t1[w] = Tv.p_t1[sl];
+    S.p_t2[w] = Tv.p_t2[sl];
+    S.p_seg[w] = Tv.p_seg[sl];
+    S.p_pair[2 * w] = Tv.p_pair[2 * sl];
+    S.p_pair[2 * w + 1] = Tv.p_pair[2 * sl + 1];
+    S.mv_kind[w] = Tv.mv_kind[sl];
+    S.mv_flv[w] = Tv.mv_flv[sl];
+    S.mv_tdag[w] = Tv.mv_tdag[sl];
+    S.mv_tann[w] = Tv.mv_tann[sl];
+    S.mv_rem[w] = Tv.mv_rem[sl];
+    S.p_valid[w] = 1;
+    S.p_sign[w] = Tv.p_sign[sl];
+    S.p_lprop[w] = Tv.p_lprop[sl];
+    S.p_ldet[w] = Tv.p_ldet[sl];
+    S.p_lambda[w] = Tv.p_lambda[sl];
+    S.p_ij[2 * w] = Tv.p_ij[2 * sl];
+    S.p_ij[2 * w + 1] = Tv.p_ij[2 * sl + 1];
+    S.ytil[w] = ysel;
+    Tv.u5[w] = uni[((size_t)w * T + sel) * 7 + 5];
+  }
+  if (Tv.p_kind[sl] == 0) {
+    const double *src = Tv.p_vec + sl * 2 * S.kcap;
+    double *dst = S.p_vec + (size_t)w * 2 * S.kcap;
+    for (int i = lane; i < 2 * S.kcap; i += 32) dst[i] = src[i];
+  }
+}
+
 // Training data: features and the insertion log trace ratio of every evaluated nonzero
 // ratio (log|T_new / T_old| for an insertion, its negative for a removal).
 __global__ void sweep_record_kernel(SweepView S, __nv_bfloat16 *feat, float *targ, int *count, int cap) {
@@ -561,11 +674,13 @@ __global__ void sweep_record_kernel(SweepView S, __nv_bfloat16 *feat, float *tar
   if (lane == 0) targ[slot] = (float)(S.p_kind[w] == 0 ? S.r_log[w] : -S.r_log[w]);
 }
 
-__global__ void sweep_measure_kernel(SweepView S) {
+// wt: per-walker weight of the measurement (NULL: 1), the Metropolis steps the walker spends
+// in the measured configuration in multi-try delayed acceptance
+__global__ void sweep_measure_kernel(SweepView S, const int32_t *__restrict__ wt) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= S.nw) return;
-  const double s = (double)S.w_sign[w];
+  const double s = (double)S.w_sign[w] * (wt ? (double)wt[w] : 1.0);
   const int nf = S.nf, kc = S.kcap, nb = S.n_bins;
   const double beta = S.beta;
   if (lane == 0) {
@@ -593,12 +708,12 @@ __global__ void sweep_measure_kernel(SweepView S) {
   }
 }
 
-__global__ void sweep_obs_accumulate_kernel(SweepView S) {
+__global__ void sweep_obs_accumulate_kernel(SweepView S, const int32_t *__restrict__ wt) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= S.nw * S.nobs) return;
   const int w = t / S.nobs;
   const double v = S.obs_tmp[t];
-  if (isfinite(v)) S.obs_sum[t] += (double)S.w_sign[w] * v;
+  if (isfinite(v)) S.obs_sum[t] += (double)S.w_sign[w] * (wt ? (double)wt[w] : 1.0) * v;
 }
 
 // Refresh, step 1 (one warp per (walker, flavor)): G_f[i][j] = Fh_f(tau'_i - tau_j) over the
@@ -782,6 +897,8 @@ struct kt_sweep {
   kt_stats *stats = nullptr;  // device counters of the trace pipeline (kt_sweep_set_stats)
   void *cache_mem = nullptr;
   int cache_words = 0;    // 32-bit words per cached vector
+  void *try_mem = nullptr;  // proposal slots of multi-try delayed acceptance
+  kt::TryView tv{};         // tv.T == 0: not allocated
 };
 
 namespace {
@@ -945,6 +1062,48 @@ int current_traces(kt_sweep *s, int8_t *sg, double *lg, int32_t *st, double *obs
                              nullptr, sg, lg, st, nullptr, w, stream, nullptr, obs);
 }
 
+// Proposal slots for T tries per walker (kt_sweep_run_da_multi); grown on demand.
+kt_status alloc_tries(kt_sweep *s, int T) {
+  if (s->tv.T >= T) return KT_OK;
+  if (s->try_mem) {
+    cudaFree(s->try_mem);
+    s->try_mem = nullptr;
+    s->tv = kt::TryView{};
+  }
+  const size_t n = (size_t)T * s->v.nw, kc = s->v.kcap, nw = s->v.nw;
+  size_t b = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = b;
+    b += kt::up256(bytes);
+    return at;
+  };
+  const size_t o_kind = take(n), o_seg = take(n), o_valid = take(n), o_sign = take(n), o_acc = take(n),
+               o_t1 = take(n * 8), o_t2 = take(n * 8), o_td = take(n * 8), o_ta = take(n * 8), o_lp = take(n * 8),
+               o_ld = take(n * 8), o_lam = take(n * 8), o_vec = take(n * 2 * kc * 8), o_pair = take(n * 2 * 4),
+               o_rem = take(n * 4), o_ij = take(n * 2 * 4), o_mk = take(n), o_mf = take(n),
+               o_X = take(n * (size_t)s->v.n_in * 2), o_y = take(n * 4), o_cnt = take(KT_SWEEP_NCOUNTERS * 8),
+               o_nt = take(nw * 4), o_u5 = take(nw * 8);
+  if (cudaMalloc(&s->try_mem, b) != cudaSuccess) {
+    cudaGetLastError();
+    s->try_mem = nullptr;
+    return KT_ENOMEM;
+  }
+  if (cudaMemset(s->try_mem, 0, b) != cudaSuccess) return KT_ECUDA;
+  char *p = (char *)s->try_mem;
+  kt::TryView &t = s->tv;
+  t.p_kind = (int8_t *)(p + o_kind); t.p_seg = (int8_t *)(p + o_seg); t.p_valid = (int8_t *)(p + o_valid);
+  t.p_sign = (int8_t *)(p + o_sign); t.p_acc = (int8_t *)(p + o_acc);
+  t.p_t1 = (double *)(p + o_t1); t.p_t2 = (double *)(p + o_t2); t.mv_tdag = (double *)(p + o_td);
+  t.mv_tann = (double *)(p + o_ta); t.p_lprop = (double *)(p + o_lp); t.p_ldet = (double *)(p + o_ld);
+  t.p_lambda = (double *)(p + o_lam); t.p_vec = (double *)(p + o_vec); t.p_pair = (int32_t *)(p + o_pair);
+  t.mv_rem = (int32_t *)(p + o_rem); t.p_ij = (int32_t *)(p + o_ij); t.mv_kind = (uint8_t *)(p + o_mk);
+  t.mv_flv = (uint8_t *)(p + o_mf); t.X = (__nv_bfloat16 *)(p + o_X); t.ytil = (float *)(p + o_y);
+  t.scratch_counters = (unsigned long long *)(p + o_cnt); t.n_tries = (int32_t *)(p + o_nt);
+  t.u5 = (double *)(p + o_u5);
+  t.T = T;
+  return KT_OK;
+}
+
 // Every walker to the empty configuration: weight = trace of the empty sequence.
 kt_status reset_empty(kt_sweep *s) {
   kt::SweepView &v = s->v;
@@ -1092,8 +1251,8 @@ static kt_status run_steps(kt_sweep *s, int32_t n_steps, const double *uniforms,
   const size_t shf = (size_t)wpb * v.nf * 34 * sizeof(float);
   for (int step = 0; step < n_steps; ++step) {
     const double *u = uniforms + (size_t)step * v.nw * ustride;
-    kt::sweep_propose_kernel<<<grid, wpb * 32, shm, st>>>(v, u, ustride);
-    if (mode != 0) kt::sweep_features_kernel<<<grid, wpb * 32, shf, st>>>(v);
+    kt::sweep_propose_kernel<<<grid, wpb * 32, shm, st>>>(v, u, ustride, kt::TryView{});
+    if (mode != 0) kt::sweep_features_kernel<<<grid, wpb * 32, shf, st>>>(v, kt::TryView{});
     if (mode == 1) {
       if (kt::mlp_forward(s->net, v.X, v.nw, v.ytil, false, st) != 0) return KT_ECUDA;
       kt::sweep_stage1_kernel<<<(v.nw + 255) / 256, 256, 0, st>>>(v, u);
@@ -1107,16 +1266,16 @@ static kt_status run_steps(kt_sweep *s, int32_t n_steps, const double *uniforms,
       return KT_ECUDA;
     }
     if (mode == 2) kt::sweep_record_kernel<<<grid, wpb * 32, 0, st>>>(v, feat, targ, count, cap);
-    kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, u, ustride, w.desc, mode == 1);
+    kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, u + 5, ustride, w.desc, mode == 1);
     if (s->cache_mem) {
       kt::launch_cache_commit(s->cache, v.nw, M.n_kept, w.desc, w.wstatus, v.p_acc, v.r_status, s->cache_words, st);
     }
     if (meas_every > 0 && (step + 1) % meas_every == 0) {
-      kt::sweep_measure_kernel<<<grid, wpb * 32, 0, st>>>(v);
+      kt::sweep_measure_kernel<<<grid, wpb * 32, 0, st>>>(v, nullptr);
       if (s->measure_obs) {
         if (current_traces(s, v.m_sign, v.m_log, v.m_status, v.obs_tmp, st) != 0) return KT_ECUDA;
         const int n = v.nw * v.nobs;
-        kt::sweep_obs_accumulate_kernel<<<(n + 255) / 256, 256, 0, st>>>(v);
+        kt::sweep_obs_accumulate_kernel<<<(n + 255) / 256, 256, 0, st>>>(v, nullptr);
       }
     }
   }
@@ -1130,6 +1289,62 @@ kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int
 kt_status kt_sweep_run_da(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream) {
   if (!s || !s->net) return KT_EINVAL;
   return run_steps(s, n_steps, uniforms, meas_every, stream, 1, nullptr, nullptr, nullptr, 0);
+}
+
+kt_status kt_sweep_run_da_multi(kt_sweep *s, int32_t n_steps, int32_t tries, const double *uniforms,
+                                int32_t meas_every, void *stream) {
+  if (!s || !s->net || n_steps < 0 || meas_every < 0 || tries < 1 || tries > KT_DA_MAX_TRIES) return KT_EINVAL;
+  if ((long long)kt::mlp_max_batch(s->net) < (long long)tries * s->v.nw) return KT_EINVAL;
+  if (n_steps == 0) return KT_OK;
+  if (!uniforms) return KT_EINVAL;
+  const kt_status ra = alloc_tries(s, tries);
+  if (ra != KT_OK) return ra;
+  cudaStream_t st = (cudaStream_t)stream;
+  kt::SweepView &v = s->v;
+  kt::TryView tv = s->tv;
+  tv.T = tries;
+  const kt::DevModel &M = *s->mv.dev;
+  const kt::Workspace w = kt::carve_workspace(s->ws, v.nw, M.n_kept, M.d_max, 0);
+  const kt::MoveView mvv{v.mv_kind, v.mv_flv, v.mv_tdag, v.mv_tann, v.mv_rem};
+  const kt::SeqView sv = seq_view(s);
+  const int wpb = 8;
+  const unsigned grid = (unsigned)((v.nw + wpb - 1) / wpb);
+  const size_t shm = (size_t)wpb * 2 * v.kcap * sizeof(double);
+  const size_t shf = (size_t)wpb * v.nf * 34 * sizeof(float);
+  const int ustride = 7 * tries;
+  cudaGetLastError();
+  for (int step = 0; step < n_steps; ++step) {
+    const double *u = uniforms + (size_t)step * v.nw * ustride;
+    // every try from the walker's current configuration (the configuration only changes at
+    // the end of the step), all scored by one surrogate inference
+    const dim3 grid_t(grid, (unsigned)tries);
+    kt::sweep_propose_kernel<<<grid_t, wpb * 32, shm, st>>>(v, u, ustride, tv);
+    kt::sweep_features_kernel<<<grid_t, wpb * 32, shf, st>>>(v, tv);
+    if (kt::mlp_forward(s->net, tv.X, tries * v.nw, tv.ytil, false, st) != 0) return KT_ECUDA;
+    kt::sweep_select_kernel<<<grid, wpb * 32, 0, st>>>(v, tv, u);
+    // measurement of the configuration the walker spent this step's tries in, weighted by them
+    if (meas_every > 0 && (step + 1) % meas_every == 0) {
+      kt::sweep_measure_kernel<<<grid, wpb * 32, 0, st>>>(v, tv.n_tries);
+      if (s->measure_obs) {
+        if (current_traces(s, v.m_sign, v.m_log, v.m_status, v.obs_tmp, st) != 0) return KT_ECUDA;
+        const int n = v.nw * v.nobs;
+        kt::sweep_obs_accumulate_kernel<<<(n + 255) / 256, 256, 0, st>>>(v, tv.n_tries);
+      }
+    }
+    if (s->cache_mem) {
+      if (kt::launch_cached_pipeline(M, s->mv.precision, s->mv.kernel_dmax, sv, mvv, v.tr_sign, v.tr_log, v.r_sign,
+                                     v.r_log, v.r_status, w, s->cache, true, s->stats, st) != 0)
+        return KT_ECUDA;
+    } else if (kt::launch_pipeline(M, s->mv.precision, s->mv.kernel_dmax, s->mv.group_lanes, sv, &mvv, v.tr_sign,
+                                   v.tr_log, v.r_sign, v.r_log, v.r_status, s->stats, w, st, nullptr) != 0) {
+      return KT_ECUDA;
+    }
+    kt::sweep_accept_kernel<<<grid, wpb * 32, 0, st>>>(v, tv.u5, 1, w.desc, true);
+    if (s->cache_mem) {
+      kt::launch_cache_commit(s->cache, v.nw, M.n_kept, w.desc, w.wstatus, v.p_acc, v.r_status, s->cache_words, st);
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? KT_OK : KT_ECUDA;
 }
 
 kt_status kt_sweep_collect(kt_sweep *s, int32_t n_steps, const double *uniforms, void *features, float *targets,
@@ -1384,6 +1599,7 @@ kt_status kt_sweep_reset_accumulators(kt_sweep *s, void *stream) {
 
 void kt_sweep_destroy(kt_sweep *s) {
   if (!s) return;
+  if (s->try_mem) cudaFree(s->try_mem);
   if (s->ws) cudaFree(s->ws);
   if (s->mem) cudaFree(s->mem);
   if (s->cache_mem) cudaFree(s->cache_mem);

@@ -285,6 +285,14 @@ class Sweep:
         assert uniforms.shape[1:] == (self.n_walkers, 7)
         kt.kt_sweep_run_da(self.h, uniforms.shape[0], uniforms, meas_every)
 
+    def run_da_multi(self, uniforms: torch.Tensor, meas_every: int = 0) -> None:
+        """Multi-try delayed-acceptance steps (kt_sweep_run_da_multi); uniforms float64
+        [n_steps, n_walkers, tries, 7]. Each step takes 1 to `tries` Metropolis steps per
+        walker; measurements are weighted by them."""
+        assert uniforms.dtype == torch.float64 and uniforms.is_cuda and uniforms.is_contiguous()
+        assert uniforms.dim() == 4 and uniforms.shape[1] == self.n_walkers and uniforms.shape[3] == 7
+        kt.kt_sweep_run_da_multi(self.h, uniforms.shape[0], uniforms.shape[2], uniforms, meas_every)
+
     def refresh(self) -> dict:
         """Drift guard (kt_sweep_refresh): tracked M, determinants, signs and traces recomputed
         from scratch; returns how far the tracked values had drifted."""
@@ -300,8 +308,9 @@ class Sweep:
         kt.kt_sweep_set_stats(self.h, stats)
 
     def run_blocks(self, uniforms: torch.Tensor, meas_every: int, n_blocks: int, delayed: bool = False) -> list:
-        """Run the steps as n_blocks consecutive equal blocks (plain, or delayed acceptance
-        with 7 uniforms per step) and return each block's own accumulator sums (device
+        """Run the steps as n_blocks consecutive equal blocks (plain; delayed acceptance
+        with 7 uniforms per step; multi-try delayed acceptance with [tries, 7] uniforms per
+        step) and return each block's own accumulator sums (device
         tensors), for binning analyses over time. The running accumulators and counters
         keep their totals; the per-block sums are differences of device snapshots, so no
         block waits for the host."""
@@ -310,7 +319,8 @@ class Sweep:
         step = n // n_blocks
         snaps = [self.accumulators()]
         for b in range(n_blocks):
-            (self.run_da if delayed else self.run)(uniforms[b * step:(b + 1) * step], meas_every)
+            fn = (self.run_da_multi if uniforms.dim() == 4 else self.run_da) if delayed else self.run
+            fn(uniforms[b * step:(b + 1) * step], meas_every)
             snaps.append(self.accumulators())
         return [{k: snaps[b + 1][k] - snaps[b][k] for k in snaps[0]} for b in range(n_blocks)]
 

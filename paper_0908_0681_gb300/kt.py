@@ -95,9 +95,10 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_sweep_collect",
                  "kt_sweep_set_surrogate", "kt_sweep_run_da", "kt_sweep_set_stats", "kt_ratio_cache_create",
                  "kt_ratio_cache_build", "kt_trace_ratio_cached", "kt_ratio_cache_destroy", "kt_ratio_cache_propose",
-                 "kt_ratio_cache_commit", "kt_sweep_refresh"]
+                 "kt_ratio_cache_commit", "kt_sweep_refresh", "kt_sweep_run_da_multi"]
 
 KT_SWEEP_NCOUNTERS = 10
+KT_DA_MAX_TRIES = 16
 KT_MLP_HIDDEN = 256
 SWEEP_COUNTERS = ["insert_proposed", "insert_accepted", "remove_proposed", "remove_accepted", "null_moves",
                   "refused_at_k_cap", "trace_errors", "measurements", "stage1_rejected", "trace_evaluations"]
@@ -153,6 +154,7 @@ def load():
     lib.kt_sweep_collect.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
     lib.kt_sweep_set_surrogate.argtypes = [vp, vp]
     lib.kt_sweep_run_da.argtypes = [vp, i32, vp, i32, vp]
+    lib.kt_sweep_run_da_multi.argtypes = [vp, i32, i32, vp, i32, vp]
     lib.kt_sweep_set_stats.argtypes = [vp, vp]
     lib.kt_ratio_cache_create.argtypes = [vp, i32, i32, ctypes.POINTER(vp)]
     lib.kt_ratio_cache_build.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp]
@@ -524,6 +526,11 @@ def kt_sweep_set_surrogate(s: KtSweep, net) -> None:
 def kt_sweep_run_da(s: KtSweep, n_steps: int, uniforms, meas_every: int = 0, stream=None) -> None:
     _check(load().kt_sweep_run_da(s.handle, int(n_steps), _ptr(uniforms), int(meas_every), _stream_handle(stream)),
            "kt_sweep_run_da")
+
+
+def kt_sweep_run_da_multi(s: KtSweep, n_steps: int, tries: int, uniforms, meas_every: int = 0, stream=None) -> None:
+    _check(load().kt_sweep_run_da_multi(s.handle, int(n_steps), int(tries), _ptr(uniforms), int(meas_every),
+                                        _stream_handle(stream)), "kt_sweep_run_da_multi")
 
 
 def kt_model_set_tiling(m: KtModel, group_lanes: int) -> None:

@@ -163,6 +163,7 @@ def test_entry_points_reject_bad_arguments_without_touching_a_device():
     assert call("kt_sweep_create", NULL, ctypes.byref(p), ctypes.byref(out)) == bad
     assert call("kt_sweep_run", NULL, i32(1), NULL, i32(0), NULL) == bad
     assert call("kt_sweep_run_da", NULL, i32(1), NULL, i32(0), NULL) == bad
+    assert call("kt_sweep_run_da_multi", NULL, i32(1), i32(4), NULL, i32(0), NULL) == bad
     assert call("kt_sweep_collect", NULL, i32(1), NULL, NULL, NULL, NULL, i32(0), NULL) == bad
     assert call("kt_sweep_set_configs", NULL, NULL) == bad
     assert call("kt_sweep_set_stats", NULL, NULL) == bad

@@ -55,7 +55,8 @@ def test_constants_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     names = kt.STATUS_NAMES + ["KT_FP64", "KT_FP32_KRYLOV", "KT_DENSITY_ONLY", "KT_SECTOR_BLOCKS", "KT_HOST_ONLY",
                                "KT_FP32_TRIDIAG64",
-                               "KT_P_HIST", "KT_SWEEP_NCOUNTERS", "KT_MLP_HIDDEN", "KT_STATIC_SCRATCH_BYTES"]
+                               "KT_P_HIST", "KT_SWEEP_NCOUNTERS", "KT_MLP_HIDDEN", "KT_STATIC_SCRATCH_BYTES",
+                               "KT_DA_MAX_TRIES"]
     lines = ['#include <stdio.h>', '#include "kt.h"', 'int main(void) {']
     lines += [f'  printf("{n} %lld\\n", (long long)({n}));' for n in names]
     lines += [f'  printf("NOBS{n} %lld\\n", (long long)KT_MEASURE_NOBS({n}));' for n in (3, 5, 7)]

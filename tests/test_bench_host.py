@@ -65,3 +65,10 @@ def test_equal_error_speedups_per_observable():
     sp = bench.speedups(bench.efficiencies(wide, 1.0), bench.efficiencies(est, 1.0))
     assert abs(sp["n_f_min_over_flavors"] - 0.25) < 1e-12 and abs(sp["G_tau_min_over_bins"] - 0.25) < 1e-12
     assert sp["docc"] == 1.0 and abs(sp["G_tau_median_over_bins"] - 1.0) < 1e-12
+    # orbital occupations sum the two spins of each orbital (flavor f = 2a + s)
+    assert est["n_orbital"].shape == (nw, 5)
+    assert np.allclose(est["n_orbital"][:, 2], est["n_f"][:, 4] + est["n_f"][:, 5])
+    # pooled over bins: one wider bin of twenty raises the summed variance, not four-fold
+    vb = est["G_tau"].var(axis=0, ddof=1)
+    want = vb.sum() / (vb.sum() + 3.0 * vb[7])
+    assert abs(sp["G_tau_pooled"] - want) < 1e-12 and 0.25 < sp["G_tau_pooled"] < 1.0

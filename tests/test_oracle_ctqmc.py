@@ -12,6 +12,10 @@
   U = 0): fixes the proposal probabilities, the acceptance rule and the G estimator
   of the whole chain (statistical, 5 standard errors over independent walkers).
 - The tabulated semicircular bath itself against an independent adaptive quadrature.
+- Multi-try delayed acceptance (chain_da_multi): with one try it is delayed acceptance
+  decision for decision; on a finite toy chain, the exact transition matrix of a step is
+  stationary in pi / c (c the expected tries), so tries-weighted measurements are exact and
+  unweighted ones are not; and at U = 0 the weighted G(tau) is the semicircular one.
 """
 import math
 
@@ -19,7 +23,7 @@ import numpy as np
 import pytest
 import scipy.integrate
 
-from oracle.ctqmc import Hyb, chain, green_function, weight
+from oracle.ctqmc import Hyb, chain, chain_da_multi, green_function, weight
 from oracle.oracle import Model, Params
 from paper_0908_0681_gb300 import workloads
 from tests import brute
@@ -189,3 +193,88 @@ def test_delayed_acceptance_keeps_the_distribution():
                       for b in range(nb)])
     assert np.all(np.abs(mean - exact) < 5 * err + 2e-3), (mean, exact, err)
     assert (out["accepted"] == -2).mean() > 0.05
+
+
+def _guess(beta):
+    def guess(ops, kind, flavor, t1, t2, seg):
+        d = (t2 - t1) % beta
+        return -0.3 * d if kind == 0 else 0.3 * d
+    return guess
+
+
+def test_multi_try_with_one_try_is_delayed_acceptance():
+    """One try per step takes exactly the delayed-acceptance chain's decisions."""
+    beta, nw, steps = 4.0, 6, 400
+    m = Model(Params(1, 2.0, 0.0, mu=1.0, beta=beta, trunc_eps=0.0))
+    hyb = Hyb(workloads.semicircular_hybridization(beta, 2, n_tau=400), beta)
+    u = np.random.default_rng(21).random((steps, nw, 7))
+    a = chain(m, hyb, [[] for _ in range(nw)], u, k_cap=64, surrogate=_guess(beta))
+    b = chain_da_multi(m, hyb, [[] for _ in range(nw)], u[:, :, None, :], _guess(beta), k_cap=64)
+    assert a["configs"] == b["configs"]
+    assert ((a["accepted"] == 1) == (b["accepted"] == 1)).all()
+    # chain() codes a null move -1 and a stage-1 rejection -2; with one try both are "no try passed"
+    assert ((a["accepted"] < 0) == (b["accepted"] == -2)).all()
+    assert (b["tries"] == 1).all()
+    assert b["counts"]["stage1_rejected"] == int((a["accepted"] == -2).sum()) > 0
+
+
+def _multi_try_step_matrix(pi, g, T):
+    """Exact transition matrix of one multi-try delayed-acceptance step on states 0..N-1:
+    uniform proposals to the other states, stage 1 min(1, e^{g(y) - g(x)}) (surrogate
+    log ratio g(y) - g(x), antisymmetric), stage 2 min(1, pi(y)/pi(x) e^{-(g(y) - g(x))}),
+    at most T tries, each rejected try keeping x. Returns (P, c) with c(x) the expected
+    number of tries taken from x."""
+    N = len(pi)
+    q = (np.ones((N, N)) - np.eye(N)) / (N - 1)
+    a1 = np.minimum(1.0, np.exp(g[None, :] - g[:, None]))
+    a2 = np.minimum(1.0, (pi[None, :] / pi[:, None]) * np.exp(-(g[None, :] - g[:, None])))
+    r = 1.0 - (q * a1).sum(1)                     # a try from x fails stage 1
+    c = np.array([sum(ri ** t for t in range(T)) for ri in r])
+    P = c[:, None] * q * a1 * a2
+    P[np.diag_indices(N)] = 0.0
+    P[np.diag_indices(N)] = 1.0 - P.sum(1)
+    return P, c
+
+
+def test_multi_try_weights_make_the_estimate_exact():
+    """The weighting rule of chain_da_multi, checked on a finite chain by linear algebra:
+    the step chain's stationary law mu is proportional to pi / c, so weighting each
+    measured state by its number of tries (mean c) recovers pi exactly, while the
+    unweighted step average is biased; one try (c = 1) needs no weight."""
+    rng = np.random.default_rng(3)
+    N = 6
+    pi = rng.random(N) + 0.1
+    pi /= pi.sum()
+    g = np.log(pi) + rng.normal(0, 0.8, N)       # an imperfect surrogate
+    for T in (1, 3, 8):
+        P, c = _multi_try_step_matrix(pi, g, T)
+        ev, V = np.linalg.eig(P.T)
+        mu = np.real(V[:, np.argmin(np.abs(ev - 1.0))])
+        mu /= mu.sum()
+        weighted = mu * c / (mu * c).sum()
+        assert np.abs(weighted - pi).max() < 1e-12, T
+        if T == 1:
+            assert np.abs(mu - pi).max() < 1e-12
+        else:
+            assert np.abs(mu - pi).max() > 1e-3, T
+
+
+def test_multi_try_delayed_acceptance_keeps_the_distribution():
+    """Four tries per step with the crude surrogate: the tries-weighted U = 0 Green's
+    function is the semicircular one, and steps take more than one Metropolis step on
+    average."""
+    beta, nw, steps, T = 4.0, 12, 1200, 4
+    m = Model(Params(1, 0.0, 0.0, mu=0.0, beta=beta, trunc_eps=0.0))
+    table = workloads.semicircular_hybridization(beta, 2, n_tau=400)
+    hyb = Hyb(table, beta)
+    u = np.random.default_rng(13).random((steps, nw, T, 7))
+    nb = 10
+    out = chain_da_multi(m, hyb, [[] for _ in range(nw)], u, _guess(beta), k_cap=64, n_bins=nb, meas_every=5)
+    g_w = (out["g_acc"] * (nb / beta ** 2) / out["sign_sum"][:, None, None]).mean(axis=1)
+    mean, err = g_w.mean(axis=0), g_w.std(axis=0, ddof=1) / math.sqrt(nw)
+    grid = np.linspace(0, beta, 401)
+    exact = np.array([-np.mean(np.interp(np.linspace(b * beta / nb, (b + 1) * beta / nb, 41), grid, table[0]))
+                      for b in range(nb)])
+    assert np.all(np.abs(mean - exact) < 5 * err + 2e-3), (mean, exact, err)
+    assert out["tries"].mean() > 1.3
+    assert out["counts"]["proposals"] == int(out["tries"].sum())
