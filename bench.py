@@ -268,7 +268,11 @@ def reference_arm(a):
 
 CACHE_OPS = 512   # partial-state cache length of the cached sweeps (operators per walker)
 DA_TRIES = 8      # proposals per chain and call step of the multi-try delayed-acceptance sweeps (--da-tries)
-THERM_DA_CALL_STEPS = 3000  # multi-try delayed-acceptance call steps at the end of the sweeps' thermalisation
+# multi-try delayed-acceptance call steps (with the partial-state cache) at the end of the
+# sweeps' thermalisation: about 8 10^4 Metropolis steps per chain, where the expansion order
+# has stopped drifting (shorter starts left it several standard errors above its equilibrium)
+THERM_DA_CALL_STEPS = 20000
+LONG_PLAIN_STEPS = 12000    # Metropolis steps per chain of the longer cached comparison
 
 
 def chain_estimates(acc, n_orb: int, beta: float, n_bins: int):
@@ -658,23 +662,57 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
                           ("fp32_da_cached", "fp64"), ("fp32_cached", "fp32"), ("fp64_cached", "fp64"),
                           ("fp32_da_multi", "fp64"), ("fp32_da_multi", "fp32"), ("fp32_da_multi_cached", "fp64"),
                           ("fp32_da_multi_cached", "fp32_cached"))}
+    # longer runs for the slow observables: with the cache, plain and multi-try delayed
+    # acceptance from the same equilibrium state over about 12,000 Metropolis steps per chain
+    # each, measured every ~50 Metropolis steps (the spin of the high-spin ground multiplet
+    # turns over slowly, so n_f needs runs of many thousand steps to resolve its variance)
+    long_run = {}
+    effs_long = {}
+    for name, mode in (("fp32_cached", "plain"), ("fp32_da_multi_cached", "multi")):
+        sw = engine.Sweep(models["fp32"], table, beta, nw, k_cap=128, n_bins=200, measure_obs=True, cache_ops=CACHE_OPS)
+        sw.set_configs(thermal)
+        meas_l = meas if mode == "plain" else out["fp32_da_multi"]["measure_every"]
+        chunk = (500 // meas_l) * meas_l
+        n_chunks = LONG_PLAIN_STEPS // chunk if mode == "plain" else -(-LONG_PLAIN_STEPS // (4 * chunk))
+        if mode == "multi":
+            sw.set_surrogate(net)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n_chunks):
+            if mode == "plain":
+                sw.run(uni(chunk, 6), meas_every=meas_l)
+            else:
+                sw.run_da_multi(torch.rand((chunk, nw, DA_TRIES, 7), dtype=torch.float64, device=dev, generator=g),
+                                meas_every=meas_l)
+        e1.record()
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1000.0
+        cnt = sw.counters()
+        acc = {k: v.cpu().numpy() for k, v in sw.accumulators().items()}
+        effs_long[name] = efficiencies(chain_estimates(acc, spec.n_orb, beta, 200), secs)
+        est = chain_estimates(acc, spec.n_orb, beta, 200)
+        long_run[name] = {"call_steps": n_chunks * chunk, "measure_every": meas_l, "seconds": secs,
+                          "metropolis_steps_per_chain": (cnt["insert_proposed"] + cnt["remove_proposed"]) / nw,
+                          "order": float(est["order"].mean()),
+                          "order_stderr": float(est["order"].std(ddof=1) / np.sqrt(nw)),
+                          "docc": float(est["docc"].mean()), "docc_stderr": float(est["docc"].std(ddof=1) / np.sqrt(nw))}
+        del sw
+    long_run["speedup_at_equal_error"] = speedups(effs_long["fp32_da_multi_cached"], effs_long["fp32_cached"])
     # throughput-bound batch: 8,192 chains (the 1,024-chain batch is bound by its longest chains)
     nbig, nsteps_big = 8192, max(steps // 4, 100)
-    cand_big = workloads.generate_sequences(gen, int(1.3 * nbig), seed=seed + 1)
-    sgb, _, _ = engine.trace(models["fp32"], engine.DeviceSeqs.from_host(cand_big, dev))
-    okb = np.nonzero(sgb.cpu().numpy() != 0)[0][:nbig]
 
     def unib(n, k):
         return torch.rand((n, nbig, k), dtype=torch.float64, device=dev, generator=g)
 
     # the same network, with room for DA_TRIES proposals of every chain
     net_big = engine.Surrogate(net.n_in, max_batch=DA_TRIES * nbig, params=net.params())
+    # start: the 1,024 thermalised configurations, each repeated nbig / nw times, decorrelated
+    # by 2,000 multi-try call steps (about 7,600 Metropolis steps, many autocorrelation times)
     big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200, measure_obs=True, cache_ops=CACHE_OPS)
-    big.set_configs(cand_big.subset(okb))
-    for _ in range(0, therm, 500):
-        big.run(unib(500, 6))
+    big.set_configs(thermal.subset(np.tile(np.arange(nw), nbig // nw)))
     big.set_surrogate(net_big)
-    for _ in range(0, THERM_DA_CALL_STEPS // 3, 250):
+    for _ in range(0, 2000, 250):
         big.run_da_multi(torch.rand((250, nbig, DA_TRIES, 7), dtype=torch.float64, device=dev, generator=g))
     stb = {k: v.cpu().numpy() for k, v in big.state().items()}
     lb = stb["lens"]
@@ -686,7 +724,9 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
     thr = {}
     ub = {6: unib(nsteps_big, 6), 7: unib(nsteps_big, 7)}
     meas_big_m = out["fp32_da_multi"]["measure_every"]
-    ub[(DA_TRIES, 7)] = torch.rand((nsteps_big, nbig, DA_TRIES, 7), dtype=torch.float64, device=dev, generator=g)
+    # the multi-try lines take as many Metropolis steps as the others (fewer call steps)
+    nsteps_big_m = max(50, int(round(nsteps_big / out["fp32_da_multi"]["metropolis_steps_per_call_step"])))
+    ub[(DA_TRIES, 7)] = torch.rand((nsteps_big_m, nbig, DA_TRIES, 7), dtype=torch.float64, device=dev, generator=g)
     for mode in ("plain", "da", "da_multi", "plain_cached", "da_cached", "da_multi_cached"):
         big = engine.Sweep(models["fp32"], table, beta, nbig, k_cap=128, n_bins=200, measure_obs=True,
                            cache_ops=CACHE_OPS if mode.endswith("cached") else 0)
@@ -716,8 +756,9 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
         ab = {k: v.cpu().numpy() for k, v in big.accumulators().items()}
         docc_b = (ab["obs_sum"] / ab["sign_sum"][:, None])[:, 2 * spec.n_orb: 3 * spec.n_orb].mean(1)
         order_b = ab["order_sum"].sum(1) / ab["sign_sum"]
-        thr[mode] = {"proposals_per_s": n_mh / (ms / 1000.0), "ms_per_step": ms / nsteps_big,
-                     "metropolis_steps_per_call_step": n_mh / (nbig * nsteps_big),
+        n_call = nsteps_big_m if multi else nsteps_big
+        thr[mode] = {"proposals_per_s": n_mh / (ms / 1000.0), "ms_per_step": ms / n_call, "call_steps": n_call,
+                     "metropolis_steps_per_call_step": n_mh / (nbig * n_call),
                      "work_per_proposal": {"intervals": wk["intervals"] / n_mh50,
                                            "ops_applied": wk["ops_applied"] / n_mh50,
                                            "krylov_iters": wk["krylov_iters"] / n_mh50,
@@ -728,6 +769,8 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
                              "order": 1.0 / (order_b.var(ddof=1) * ms / 1000.0)}}
         del big
     thr.update(chains=nbig, steps=nsteps_big, cache_ops=CACHE_OPS,
+               start=(f"the {nw} thermalised configurations, each repeated {nbig // nw} times, then 2,000 "
+                      f"multi-try delayed-acceptance call steps"),
                speedup_da_over_plain=thr["da"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
                speedup_cached_over_plain=thr["plain_cached"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
                speedup_da_cached_over_plain=thr["da_cached"]["proposals_per_s"] / thr["plain"]["proposals_per_s"],
@@ -755,6 +798,7 @@ def sweep_bench(dev, steps: int, beta: float, seed: int):
                                ("fp32_da_multi_cached", "fp32_cached"))},
             "da_tries": DA_TRIES,
             "throughput_8192_chains": thr, "fp32_vs_fp64_same_uniforms": err32,
+            "long_run_1024_chains": long_run,
             "cached_vs_uncached_identical_paths": cache_same, "cache_ops": CACHE_OPS,
             "surrogate": {"training_samples": n_train, "collect_s": t_collect, "train_s": t_train,
                           "epochs": len(hist), "loss_per_epoch": hist, "rms_residual_log_ratio": resid,

@@ -406,6 +406,15 @@ typedef struct {
  * must outlive the sweep) and set every walker to the empty configuration.
  * Synchronises. Errors: KT_EINVAL, KT_ENOMEM, KT_ECUDA. */
 kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out);
+/* Device bytes that kt_sweep_create(m, p) allocates, computed on the host from the same
+ * layouts, without touching the device. The total covers the chains (configurations,
+ * inverse bath matrices, about n_walkers * n_flavors * k_cap * (8 k_cap + 36) bytes),
+ * the partial-state cache when p->cache_ops > 0, and the trace-pipeline workspace. With
+ * tries > 0 it adds the proposal slots that kt_sweep_run_da_multi with that many tries
+ * allocates on its first call. p->hyb is not read; m may be a KT_HOST_ONLY model. Callers
+ * size k_cap, cache_ops and n_walkers from the device's free memory with it. KT_EINVAL for
+ * parameters kt_sweep_create would reject or tries outside 0 .. KT_DA_MAX_TRIES. */
+kt_status kt_sweep_memory_bytes(const kt_model *m, const kt_sweep_params *p, int32_t tries, size_t *bytes);
 /* n_steps Metropolis steps of every walker, measuring after every meas_every-th
  * step (0: never). Enqueued on the stream; returns launch errors only. */
 kt_status kt_sweep_run(kt_sweep *s, int32_t n_steps, const double *uniforms, int32_t meas_every, void *stream);

@@ -48,6 +48,11 @@ struct Tab<double> {
   static __device__ __forceinline__ const double *evec(const DevModel &M) { return M.blk_evec64; }
 };
 
+// Register budget of the items kernels: the FP32 warp tiles let two 256-thread CTAs share an
+// SM (at most 128 registers a thread); the FP64 tiles take more than half of the shared
+// memory, so one CTA per SM runs anyway and its threads may use the registers of two
+#define KT_MIN_CTAS(VT) (sizeof(VT) == 8 ? 1 : 2)
+
 template <int G, typename T>
 __device__ __forceinline__ T gsum(T v, unsigned mask) {
 #pragma unroll
@@ -997,7 +1002,7 @@ __device__ __forceinline__ void measure_epilogue(const DevModel &M, Unit<VT, G, 
 // publishes its normalised vector and log-weight to the workspace; whichever
 // finishes second forms the overlap <backward|forward>. No unit ever waits.
 template <typename VT, int G, int DMAX, int PMAX>
-__global__ void __launch_bounds__(256) items_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, Workspace ws,
+__global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, Workspace ws,
                                                     kt_stats *stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int R = (DMAX + G - 1) / G;
@@ -1208,7 +1213,7 @@ __device__ __forceinline__ bool load_entry(const DevModel &M, const VT *vec, con
 // cache when its position lies outside the edited window, else to the scratch
 // arrays. The halves meet as in items_kernel.
 template <typename VT, int G, int DMAX, int PMAX>
-__global__ void __launch_bounds__(256) items_cached_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws,
+__global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_cached_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws,
                                                            CacheView C, kt_stats *stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int R = (DMAX + G - 1) / G;

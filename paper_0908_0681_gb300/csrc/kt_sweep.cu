@@ -903,7 +903,8 @@ struct kt_sweep {
 
 namespace {
 
-kt_status carve_and_alloc(kt_sweep *s) {
+// dry != NULL: only the size of the allocation, in *dry.
+kt_status carve_and_alloc(kt_sweep *s, size_t *dry = nullptr) {
   kt::SweepView &v = s->v;
   const size_t nw = v.nw, nf = v.nf, kc = v.kcap, cap = v.cap;
   size_t b = 0;
@@ -925,6 +926,10 @@ kt_status carve_and_alloc(kt_sweep *s) {
                o_pt2 = take(nw * 8), o_pseg = take(nw), o_X = take(nw * (size_t)v.n_in * 2), o_yt = take(nw * 4),
                o_ppair = take(nw * 2 * 4), o_pacc = take(nw), o_fdl = take(nw * nf * 8), o_fds = take(nw * nf),
                o_fts = take(nw), o_ftl = take(nw * 8), o_fst = take(nw * 4), o_fdev = take(4 * 8);
+  if (dry) {
+    *dry = b;
+    return KT_OK;
+  }
   if (cudaMalloc(&s->mem, b) != cudaSuccess) {
     cudaGetLastError();
     s->mem = nullptr;
@@ -989,7 +994,7 @@ kt_status carve_and_alloc(kt_sweep *s) {
 
 // The partial-state cache: P + 1 slots per direction for every (walker, kept state)
 // item, cache and scratch, plus the valid ranges and the per-step plan.
-kt_status alloc_cache(kt_sweep *s, int P) {
+kt_status alloc_cache(kt_sweep *s, int P, size_t *dry = nullptr) {
   const kt::DevModel &M = *s->mv.dev;
   const size_t items = (size_t)s->v.nw * M.n_kept, slots = items * ((size_t)P + 1);
   const size_t esz = s->mv.precision == KT_FP64 ? 8 : 4, dv = (size_t)M.d_max;
@@ -1006,6 +1011,10 @@ kt_status alloc_cache(kt_sweep *s, int P) {
     o_blk[k] = take(slots * 4);
   }
   const size_t o_f = take(items * 4), o_gr = take(items * 4), o_plan = take(items * 16);
+  if (dry) {
+    *dry = b;
+    return KT_OK;
+  }
   if (cudaMalloc(&s->cache_mem, b) != cudaSuccess) {
     cudaGetLastError();
     s->cache_mem = nullptr;
@@ -1063,9 +1072,9 @@ int current_traces(kt_sweep *s, int8_t *sg, double *lg, int32_t *st, double *obs
 }
 
 // Proposal slots for T tries per walker (kt_sweep_run_da_multi); grown on demand.
-kt_status alloc_tries(kt_sweep *s, int T) {
-  if (s->tv.T >= T) return KT_OK;
-  if (s->try_mem) {
+kt_status alloc_tries(kt_sweep *s, int T, size_t *dry = nullptr) {
+  if (!dry && s->tv.T >= T) return KT_OK;
+  if (!dry && s->try_mem) {
     cudaFree(s->try_mem);
     s->try_mem = nullptr;
     s->tv = kt::TryView{};
@@ -1083,6 +1092,10 @@ kt_status alloc_tries(kt_sweep *s, int T) {
                o_rem = take(n * 4), o_ij = take(n * 2 * 4), o_mk = take(n), o_mf = take(n),
                o_X = take(n * (size_t)s->v.n_in * 2), o_y = take(n * 4), o_cnt = take(KT_SWEEP_NCOUNTERS * 8),
                o_nt = take(nw * 4), o_u5 = take(nw * 8);
+  if (dry) {
+    *dry = b;
+    return KT_OK;
+  }
   if (cudaMalloc(&s->try_mem, b) != cudaSuccess) {
     cudaGetLastError();
     s->try_mem = nullptr;
@@ -1171,31 +1184,54 @@ bool gauss_jordan(int k, std::vector<double> A, std::vector<double> &inv, double
 
 extern "C" {
 
-kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out) {
-  if (!m || !p || !out || !p->hyb) return KT_EINVAL;
-  *out = nullptr;
+static bool sweep_params_ok(const kt_sweep_params *p) {
+  return p->n_walkers >= 1 && p->k_cap >= 1 && p->k_cap <= 128 && p->n_tau >= 1 && p->n_bins >= 1 && p->cache_ops >= 0;
+}
+
+// The sizes and the model of a sweep, before any allocation.
+static void sweep_init_view(kt_sweep *s, kt_model *m, const kt_sweep_params *p) {
   const kt::ModelView mv = kt::model_view(m);
-  if (mv.host_only) return KT_EINVAL;
-  if (p->n_walkers < 1 || p->k_cap < 1 || p->k_cap > 128 || p->n_tau < 1 || p->n_bins < 1 || p->cache_ops < 0)
-    return KT_EINVAL;
-  const int nf = mv.dev->nf;
-  for (long long i = 0; i < (long long)nf * (p->n_tau + 1); ++i)
-    if (!std::isfinite(p->hyb[i])) return KT_EINVAL;
-  kt_sweep *s = new (std::nothrow) kt_sweep();
-  if (!s) return KT_ENOMEM;
   s->model = m;
   s->mv = mv;
   s->measure_obs = p->measure_obs != 0;
   kt::SweepView &v = s->v;
   v.nw = p->n_walkers;
-  v.nf = nf;
+  v.nf = mv.dev->nf;
   v.kcap = p->k_cap;
-  v.cap = 2 * nf * p->k_cap;
+  v.cap = 2 * v.nf * p->k_cap;
   v.n_tau = p->n_tau;
   v.n_bins = p->n_bins;
   v.nobs = KT_MEASURE_NOBS(mv.dev->n_orb);
-  v.n_in = (35 * nf + 3 + 15) / 16 * 16;
+  v.n_in = (35 * v.nf + 3 + 15) / 16 * 16;
   v.beta = mv.dev->beta;
+}
+
+kt_status kt_sweep_memory_bytes(const kt_model *m, const kt_sweep_params *p, int32_t tries, size_t *bytes) {
+  if (!m || !p || !bytes || tries < 0 || tries > KT_DA_MAX_TRIES || !sweep_params_ok(p)) return KT_EINVAL;
+  kt_sweep tmp;
+  sweep_init_view(&tmp, const_cast<kt_model *>(m), p);
+  const kt::DevModel &D = *tmp.mv.dev;
+  size_t a = 0, c = 0, t = 0;
+  carve_and_alloc(&tmp, &a);
+  if (p->cache_ops > 0) alloc_cache(&tmp, std::min(p->cache_ops, tmp.v.cap), &c);
+  if (tries > 0) alloc_tries(&tmp, tries, &t);
+  *bytes = a + c + t + kt::workspace_bytes(tmp.v.nw, D.n_kept, D.d_max, D.nf + D.n_orb + 1);
+  return KT_OK;
+}
+
+kt_status kt_sweep_create(kt_model *m, const kt_sweep_params *p, kt_sweep **out) {
+  if (!m || !p || !out || !p->hyb) return KT_EINVAL;
+  *out = nullptr;
+  const kt::ModelView mv = kt::model_view(m);
+  if (mv.host_only) return KT_EINVAL;
+  if (!sweep_params_ok(p)) return KT_EINVAL;
+  const int nf = mv.dev->nf;
+  for (long long i = 0; i < (long long)nf * (p->n_tau + 1); ++i)
+    if (!std::isfinite(p->hyb[i])) return KT_EINVAL;
+  kt_sweep *s = new (std::nothrow) kt_sweep();
+  if (!s) return KT_ENOMEM;
+  sweep_init_view(s, m, p);
+  kt::SweepView &v = s->v;
   kt_status rc = carve_and_alloc(s);
   if (rc == KT_OK && p->cache_ops > 0) rc = alloc_cache(s, std::min(p->cache_ops, v.cap));
   if (rc == KT_OK) {

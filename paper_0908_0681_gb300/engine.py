@@ -330,6 +330,27 @@ class Sweep:
         return acc["g_tau"].sum(0) * (self.n_bins / self.beta ** 2) / acc["sign_sum"].sum()
 
 
+def largest_cache_ops(model: kt.KtModel, n_walkers: int, budget_bytes: int, k_cap: int = 64, n_tau: int = 2000,
+                      n_bins: int = 100, measure_obs: bool = False, tries: int = 0) -> int:
+    """The longest partial-state cache (operators per walker, up to the sequence capacity
+    2 n_flavors k_cap) whose sweep fits in budget_bytes of device memory (for example a share of
+    torch.cuda.mem_get_info()[0]); 0 if only the uncached sweep fits, -1 if not even that."""
+    def need(c):
+        return kt.kt_sweep_memory_bytes(model, n_walkers, k_cap, n_tau, n_bins, measure_obs, c, tries)
+    if need(0) > budget_bytes:
+        return -1
+    lo, hi = 0, 2 * kt.kt_model_query(model)["n_flavors"] * k_cap
+    if need(hi) <= budget_bytes:
+        return hi
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if need(mid) <= budget_bytes:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
 class Surrogate:
     """The delayed-acceptance network (kt_mlp_*): predicts log|T_new / T_old| of a proposal."""
 

@@ -95,7 +95,7 @@ ABI_FUNCTIONS = ["kt_status_string", "kt_model_create", "kt_model_query", "kt_mo
                  "kt_sweep_collect",
                  "kt_sweep_set_surrogate", "kt_sweep_run_da", "kt_sweep_set_stats", "kt_ratio_cache_create",
                  "kt_ratio_cache_build", "kt_trace_ratio_cached", "kt_ratio_cache_destroy", "kt_ratio_cache_propose",
-                 "kt_ratio_cache_commit", "kt_sweep_refresh", "kt_sweep_run_da_multi"]
+                 "kt_ratio_cache_commit", "kt_sweep_refresh", "kt_sweep_run_da_multi", "kt_sweep_memory_bytes"]
 
 KT_SWEEP_NCOUNTERS = 10
 KT_DA_MAX_TRIES = 16
@@ -135,6 +135,7 @@ def load():
     lib.kt_measure_workspace_size.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_size_t)]
     lib.kt_measure.argtypes = [vp, ctypes.POINTER(kt_seq_batch), vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.kt_sweep_create.argtypes = [vp, ctypes.POINTER(kt_sweep_params), ctypes.POINTER(vp)]
+    lib.kt_sweep_memory_bytes.argtypes = [vp, ctypes.POINTER(kt_sweep_params), i32, ctypes.POINTER(ctypes.c_size_t)]
     lib.kt_sweep_run.argtypes = [vp, i32, vp, i32, vp]
     lib.kt_sweep_set_configs.argtypes = [vp, ctypes.POINTER(kt_seq_batch)]
     lib.kt_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp, vp]
@@ -336,6 +337,18 @@ class KtSweep:
         if h is not None and _lib is not None:
             _lib.kt_sweep_destroy(h)
             self.handle = None
+
+
+def kt_sweep_memory_bytes(model: KtModel, n_walkers: int, k_cap: int = 64, n_tau: int = 2000, n_bins: int = 100,
+                          measure_obs: bool = False, cache_ops: int = 0, tries: int = 0) -> int:
+    """Device bytes of a sweep with these parameters (kt_sweep_memory_bytes), plus the multi-try
+    proposal slots of `tries` tries."""
+    p = kt_sweep_params(int(n_walkers), int(k_cap), int(n_tau), None, int(n_bins), 1 if measure_obs else 0,
+                        int(cache_ops))
+    out = ctypes.c_size_t()
+    _check(load().kt_sweep_memory_bytes(model.handle, ctypes.byref(p), int(tries), ctypes.byref(out)),
+           "kt_sweep_memory_bytes")
+    return int(out.value)
 
 
 class KtRatioCache:

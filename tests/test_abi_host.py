@@ -164,6 +164,9 @@ def test_entry_points_reject_bad_arguments_without_touching_a_device():
     assert call("kt_sweep_run", NULL, i32(1), NULL, i32(0), NULL) == bad
     assert call("kt_sweep_run_da", NULL, i32(1), NULL, i32(0), NULL) == bad
     assert call("kt_sweep_run_da_multi", NULL, i32(1), i32(4), NULL, i32(0), NULL) == bad
+    sz = ctypes.c_size_t()
+    assert call("kt_sweep_memory_bytes", NULL, ctypes.byref(p), i32(0), ctypes.byref(sz)) == bad
+    assert call("kt_sweep_memory_bytes", mh, NULL, i32(0), ctypes.byref(sz)) == bad
     assert call("kt_sweep_collect", NULL, i32(1), NULL, NULL, NULL, NULL, i32(0), NULL) == bad
     assert call("kt_sweep_set_configs", NULL, NULL) == bad
     assert call("kt_sweep_set_stats", NULL, NULL) == bad
@@ -196,3 +199,33 @@ def test_entry_points_reject_bad_arguments_without_touching_a_device():
         assert call("kt_gemm_bf16", ctypes.c_void_p(A.ctypes.data), i32(16), ctypes.c_void_p(A.ctypes.data), i32(16),
                     ctypes.c_void_p(C.ctypes.data), i32(16), i32(M_), i32(N_), i32(K_), ctypes.byref(err), NULL) == bad
     call("kt_model_destroy", NULL)
+
+
+def test_sweep_memory_bytes_on_host_only_model():
+    """kt_sweep_memory_bytes needs no device: it grows with k_cap (the inverse bath matrices,
+    8 k_cap^2 bytes per flavor and walker), the partial-state cache adds the documented
+    4 n_walkers n_kept (cache_ops + 1) (d_max element + 20) bytes, multi-try slots grow with
+    the tries, and parameters kt_sweep_create rejects are rejected."""
+    from paper_0908_0681_gb300 import engine, workloads
+    spec = workloads.five_orbital_sweep().model
+    m = engine.model_from_spec(spec, flags=kt.KT_HOST_ONLY)
+    info = kt.kt_model_query(m)
+    nw, nf = 256, info["n_flavors"]
+    b64, b128 = kt.kt_sweep_memory_bytes(m, nw, 64), kt.kt_sweep_memory_bytes(m, nw, 128)
+    grow = b128 - b64
+    want = nw * nf * 8 * (128 ** 2 - 64 ** 2)
+    assert want <= grow <= want * 1.1, (grow, want)
+    P = 100
+    dc = kt.kt_sweep_memory_bytes(m, nw, 64, cache_ops=P) - b64
+    cache = 4 * nw * info["n_kept"] * (P + 1) * (info["d_max"] * 4 + 20)
+    assert cache <= dc <= cache + 64 * 1024, (dc, cache)
+    t4, t8 = (kt.kt_sweep_memory_bytes(m, nw, 64, tries=t) for t in (4, 8))
+    assert b64 < t4 < t8
+    with pytest.raises(RuntimeError):
+        kt.kt_sweep_memory_bytes(m, nw, 129)
+    with pytest.raises(RuntimeError):
+        kt.kt_sweep_memory_bytes(m, nw, 64, tries=kt.KT_DA_MAX_TRIES + 1)
+    assert engine.largest_cache_ops(m, nw, b64 - 1) == -1
+    assert engine.largest_cache_ops(m, nw, b64) == 0
+    c = engine.largest_cache_ops(m, nw, b64 + dc)
+    assert c >= P and kt.kt_sweep_memory_bytes(m, nw, 64, cache_ops=c) <= b64 + dc

@@ -525,3 +525,24 @@ def test_cached_sweep_restart_invalidates_the_cache():
     assert out[0][1] == out[1][1]
     assert np.abs(out[0][2] - out[1][2]).max() < 1e-9
     assert np.abs(out[0][3] - out[1][3]).max() <= 1e-8 * max(1.0, np.abs(out[0][3]).max())
+
+
+def test_memory_query_matches_the_allocation():
+    """kt_sweep_memory_bytes against the device memory kt_sweep_create takes (free memory
+    before and after, within the allocation granularity). A first small sweep loads the
+    kernels, so the measured difference is the sweep's own allocations."""
+    spec = workloads.five_orbital_sweep().model
+    gm = engine.model_from_spec(spec, precision=kt.KT_FP32_KRYLOV)
+    table = workloads.semicircular_hybridization(spec.beta, 10, n_tau=2000)
+    warm = engine.Sweep(gm, table, spec.beta, 8, k_cap=8, n_bins=10, measure_obs=True, cache_ops=16)
+    del warm
+    nw = 512
+    torch.cuda.synchronize()
+    f0 = torch.cuda.mem_get_info()[0]
+    sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=64, n_bins=50, measure_obs=True, cache_ops=256)
+    torch.cuda.synchronize()
+    used = f0 - torch.cuda.mem_get_info()[0]
+    want = kt.kt_sweep_memory_bytes(gm, nw, 64, 2000, 50, True, 256, 0)
+    assert want > 100 * 2 ** 20
+    assert abs(used - want) <= 8 * 2 ** 20 + 0.01 * want, (used, want)
+    assert sw.n_walkers == nw
