@@ -54,8 +54,10 @@ using namespace dev;
 // ---------------------------------------------------------------------------
 __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, const int8_t *cur_sign, Workspace ws,
                             kt_stats *stats) {
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w == 0) {
+  // one warp per walker: the lanes read consecutive operators (coalesced) and decide by ballot
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     ws.counters[0] = 0;
     ws.counters[1] = 0;
     ws.counters[2] = 0;
@@ -68,14 +70,25 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
   if (K < 0) {
     st = KT_EINVAL;
   } else if (!S.trusted) {
-    double prev = 0.0;
-    for (int k = 0; k < K; ++k) {
-      const double t = S.tau[o + k];
-      if (!(t >= prev) || !(t < M.beta) || S.flavor[o + k] >= M.nf || S.dagger[o + k] > 1) {
+    // times non-decreasing from 0 and below beta, flavors and daggers in range
+    double carry = 0.0;
+    for (int base = 0; base < K; base += 32) {
+      const int i = base + lane;
+      double t = 0.0;
+      int f = 0, g = 0;
+      if (i < K) {
+        t = __ldg(S.tau + o + i);
+        f = __ldg(S.flavor + o + i);
+        g = __ldg(S.dagger + o + i);
+      }
+      double prev = __shfl_up_sync(FULL, t, 1);
+      if (lane == 0) prev = carry;
+      const bool bad = i < K && (!(t >= prev) || !(t < M.beta) || f >= M.nf || g > 1);
+      if (__any_sync(FULL, bad)) {
         st = KT_EINVAL;
         break;
       }
-      prev = t;
+      carry = __shfl_sync(FULL, t, 31);
     }
   }
   if (has_moves && st == KT_OK) {
@@ -87,8 +100,16 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
       if (!(td >= 0.0 && td < M.beta && ta >= 0.0 && ta < M.beta)) {
         st = KT_EINVAL;
       } else {
+        // insertion points: the number of operators at or before each new time (the sorted
+        // sequence's upper bound)
         const double tA = td < ta ? td : ta, tB = td < ta ? ta : td;
-        const int pa = upper_bound(S.tau + o, K, tA), pb = upper_bound(S.tau + o, K, tB);
+        int pa = 0, pb = 0;
+        for (int base = 0; base < K; base += 32) {
+          const int i = base + lane;
+          const double t = i < K ? __ldg(S.tau + o + i) : 0.0;
+          pa += __popc(__ballot_sync(FULL, i < K && t <= tA));
+          pb += __popc(__ballot_sync(FULL, i < K && t <= tB));
+        }
         d = make_int4(0, pa, pb, K + 2);
       }
     } else if (kind == 1) {
@@ -96,13 +117,17 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
       if (r < 0 || r >= K || S.flavor[o + r] != f) {
         st = KT_EINVAL;
       } else {
+        // its partner: the next operator of the flavor after r, cyclically
         int j = -1;
-        for (int s = 1; s < K; ++s) {
-          const int c = (r + s) % K;
-          if (S.flavor[o + c] == f) {
-            j = c;
-            break;
-          }
+        for (int base = r + 1; base < K && j < 0; base += 32) {
+          const int i = base + lane;
+          const unsigned m = __ballot_sync(FULL, i < K && __ldg(S.flavor + o + i) == f);
+          if (m) j = base + __ffs(m) - 1;
+        }
+        for (int base = 0; base < r && j < 0; base += 32) {
+          const int i = base + lane;
+          const unsigned m = __ballot_sync(FULL, i < r && __ldg(S.flavor + o + i) == f);
+          if (m) j = base + __ffs(m) - 1;
         }
         if (j < 0 || S.dagger[o + j] == S.dagger[o + r]) {
           st = KT_EINVAL;
@@ -115,39 +140,70 @@ __global__ void prep_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, c
     }
     if (st == KT_OK && cur_sign[w] == 0) st = KT_EZEROWEIGHT;
   }
-  ws.desc[w] = d;
-  ws.wstatus[w] = st;
-  if (stats) atomicAdd(&stats->walkers, 1ull);
+  if (lane == 0) {
+    ws.desc[w] = d;
+    ws.wstatus[w] = st;
+    if (stats) atomicAdd(&stats->walkers, 1ull);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // 2. structural pruning
 // ---------------------------------------------------------------------------
+// Structural pruning of one walker by one warp: the block of each lane's kept state after the
+// first Kn operators of the walker's sequence, get(i) giving operator i (b = -1: a lane
+// without an item). 32 operators are read at a time, one per lane (coalesced), and operator
+// j reaches every lane by shuffle; a zero (b = -1) stays zero.
+template <typename Get>
+__device__ __forceinline__ int warp_block_walk(const DevModel &M, int b, int Kn, int lane, const Get &get) {
+  const size_t row = (size_t)2 * M.nf;
+  for (int base = 0; base < Kn; base += 32) {
+    int code = 0;
+    if (base + lane < Kn) {
+      const Op op = get(base + lane);
+      code = 2 * op.f + op.dag;
+    }
+    const int n = Kn - base < 32 ? Kn - base : 32;
+    for (int j = 0; j < n; ++j) {
+      const int cj = __shfl_sync(FULL, code, j);
+      if (b >= 0) b = __ldg(M.blk_target + (size_t)b * row + cj);
+    }
+  }
+  return b;
+}
+
 __global__ void prune_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, Workspace ws, kt_stats *stats) {
-  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per walker: 32 operators of the edited sequence are read at a time, one per
+  // lane, and every lane follows its kept states' blocks through them (operator j by shuffle)
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (w >= S.n) return;
   const int nk = M.n_kept;
-  if (item >= S.n * nk) return;
-  const int w = item / nk, q = item - w * nk;
-  ws.item_sign[item] = 0;
-  ws.item_status[item] = KT_OK;
-  ws.item_log[item] = -INFINITY;
-  ws.pair_flag[item] = 0;
+  for (int q = lane; q < nk; q += 32) {
+    const int item = w * nk + q;
+    ws.item_sign[item] = 0;
+    ws.item_status[item] = KT_OK;
+    ws.item_log[item] = -INFINITY;
+    ws.pair_flag[item] = 0;
+  }
   if (ws.wstatus[w] != KT_OK) return;
   const Cursor c = make_cursor(S, mv, has_moves != 0, ws.desc, w);
-  const int b0 = __ldg(M.kept_blk + q);
-  int b = b0;
-  for (int i = 0; i < c.d.w && b >= 0; ++i) {
-    const Op op = c.get(i);
-    b = __ldg(M.blk_target + ((size_t)b * M.nf + op.f) * 2 + op.dag);
+  const int Kn = c.d.w;
+  int n_alive = 0;
+  for (int q0 = 0; q0 < nk; q0 += 32) {
+    const int q = q0 + lane;
+    const int b0 = q < nk ? __ldg(M.kept_blk + q) : -1;
+    const int b = warp_block_walk(M, b0, Kn, lane, [&](int i) { return c.get(i); });
+    const bool alive = q < nk && b == b0;
+    if (alive) {
+      const int slot = atomicAdd(&ws.counters[0], 1);
+      ws.worklist[slot] = w * nk + q;
+    }
+    n_alive += __popc(__ballot_sync(FULL, alive));
   }
-  const bool alive = (b == b0);
-  if (alive) {
-    const int slot = atomicAdd(&ws.counters[0], 1);
-    ws.worklist[slot] = item;
-  }
-  if (stats) {
-    atomicAdd(&stats->items, 1ull);
-    if (alive) atomicAdd(&stats->items_alive, 1ull);
+  if (stats && lane == 0) {
+    atomicAdd(&stats->items, (unsigned long long)nk);
+    atomicAdd(&stats->items_alive, (unsigned long long)n_alive);
   }
 }
 
@@ -161,43 +217,50 @@ __global__ void prune_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, 
 // this call is stored).
 __global__ void plan_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws, CacheView C, int write,
                             kt_stats *stats) {
-  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per walker, lanes over its kept states (the walk of prune_kernel)
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (w >= S.n) return;
   const int nk = M.n_kept;
-  if (item >= S.n * nk) return;
-  const int w = item / nk, q = item - w * nk;
-  ws.item_sign[item] = 0;
-  ws.item_status[item] = KT_OK;
-  ws.item_log[item] = -INFINITY;
-  ws.pair_flag[item] = 0;
-  C.plan[item] = make_int4(0, 0, 0, 0);
+  for (int q = lane; q < nk; q += 32) {
+    const int item = w * nk + q;
+    ws.item_sign[item] = 0;
+    ws.item_status[item] = KT_OK;
+    ws.item_log[item] = -INFINITY;
+    ws.pair_flag[item] = 0;
+    C.plan[item] = make_int4(0, 0, 0, 0);
+  }
   if (ws.wstatus[w] != KT_OK) return;
   const Cursor c = make_cursor(S, mv, true, ws.desc, w);
-  const int b0 = __ldg(M.kept_blk + q);
-  int b = b0;
-  for (int i = 0; i < c.d.w && b >= 0; ++i) {
-    const Op op = c.get(i);
-    b = __ldg(M.blk_target + ((size_t)b * M.nf + op.f) * 2 + op.dag);
-  }
-  const bool alive = (b == b0);
   const int Kn = c.d.w, Ko = c.d.x == 0 ? Kn - 2 : Kn + 2;
-  // read-only use (fixed configurations): the cache was built for every operator of the
-  // current sequence, so a walker whose length differs from the build is evaluated in full
-  const bool cached = Kn <= C.P && Ko <= C.P && (write || C.f[item] == Ko);
   int lo, hi;
   edit_window(c.d, lo, hi);
-  int y = 0, x = Kn;
-  if (cached) {
-    const int f = C.f[item], gr = C.gr[item];
-    y = lo < f ? lo : f;
-    const int x_old = max(hi - (Kn - Ko), Ko - gr);
-    x = x_old + (Kn - Ko);
+  int n_alive = 0;
+  for (int q0 = 0; q0 < nk; q0 += 32) {
+    const int q = q0 + lane;
+    const int b0 = q < nk ? __ldg(M.kept_blk + q) : -1;
+    const int b = warp_block_walk(M, b0, Kn, lane, [&](int i) { return c.get(i); });
+    const bool alive = q < nk && b == b0;
+    n_alive += __popc(__ballot_sync(FULL, alive));
+    if (q >= nk) continue;
+    const int item = w * nk + q;
+    // read-only use (fixed configurations): the cache was built for every operator of the
+    // current sequence, so a walker whose length differs from the build is evaluated in full
+    const bool cached = Kn <= C.P && Ko <= C.P && (write || C.f[item] == Ko);
+    int y = 0, x = Kn;
+    if (cached) {
+      const int f = C.f[item], gr = C.gr[item];
+      y = lo < f ? lo : f;
+      const int x_old = max(hi - (Kn - Ko), Ko - gr);
+      x = x_old + (Kn - Ko);
+    }
+    const int m = y + (x - y) / 2;
+    C.plan[item] = make_int4(y, x, m, (cached && write ? 1 : 0) | (alive ? 2 : 0));
+    if (alive) ws.worklist[atomicAdd(&ws.counters[0], 1)] = item;
   }
-  const int m = y + (x - y) / 2;
-  C.plan[item] = make_int4(y, x, m, (cached && write ? 1 : 0) | (alive ? 2 : 0));
-  if (alive) ws.worklist[atomicAdd(&ws.counters[0], 1)] = item;
-  if (stats) {
-    atomicAdd(&stats->items, 1ull);
-    if (alive) atomicAdd(&stats->items_alive, 1ull);
+  if (stats && lane == 0) {
+    atomicAdd(&stats->items, (unsigned long long)nk);
+    atomicAdd(&stats->items_alive, (unsigned long long)n_alive);
   }
 }
 
@@ -225,37 +288,49 @@ __global__ void build_plan_kernel(DevModel M, SeqView S, Workspace ws, CacheView
 // beta/2 (flag 8); the states they pass are stored (they belong to the current
 // configuration) and extend the valid ranges.
 __global__ void measure_plan_kernel(DevModel M, SeqView S, Workspace ws, CacheView C, kt_stats *stats) {
-  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per walker, lanes over its kept states (the walk of prune_kernel)
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (w >= S.n) return;
   const int nk = M.n_kept;
-  if (item >= S.n * nk) return;
-  const int w = item / nk, q = item - w * nk;
-  ws.item_sign[item] = 0;
-  ws.item_status[item] = KT_OK;
-  ws.item_log[item] = -INFINITY;
-  ws.pair_flag[item] = 0;
-  C.plan[item] = make_int4(0, 0, 0, 0);
+  for (int q = lane; q < nk; q += 32) {
+    const int item = w * nk + q;
+    ws.item_sign[item] = 0;
+    ws.item_status[item] = KT_OK;
+    ws.item_log[item] = -INFINITY;
+    ws.pair_flag[item] = 0;
+    C.plan[item] = make_int4(0, 0, 0, 0);
+  }
   if (ws.wstatus[w] != KT_OK) return;
   const int o = __ldg(S.offsets + w), K = ws.desc[w].w;
-  const int b0 = __ldg(M.kept_blk + q);
-  int b = b0;
-  for (int i = 0; i < K && b >= 0; ++i) {
-    const Op op = load_op(S, o + i);
-    b = __ldg(M.blk_target + ((size_t)b * M.nf + op.f) * 2 + op.dag);
+  // m: the operators before beta/2 (the lower bound of the sorted times)
+  int m = 0;
+  for (int base = 0; base < K; base += 32) {
+    const int i = base + lane;
+    m += __popc(__ballot_sync(FULL, i < K && __ldg(S.tau + o + i) < 0.5 * M.beta));
   }
-  const bool alive = (b == b0);
-  const int m = lower_bound(S.tau + o, K, 0.5 * M.beta);
   const bool cached = K <= C.P;
-  int y = 0, x = K;
-  if (cached) {
-    const int f = C.f[item], gr = C.gr[item];
-    y = m < f ? m : f;
-    x = max(m, K - gr);
+  int n_alive = 0;
+  for (int q0 = 0; q0 < nk; q0 += 32) {
+    const int q = q0 + lane;
+    const int b0 = q < nk ? __ldg(M.kept_blk + q) : -1;
+    const int b = warp_block_walk(M, b0, K, lane, [&](int i) { return load_op(S, o + i); });
+    const bool alive = q < nk && b == b0;
+    n_alive += __popc(__ballot_sync(FULL, alive));
+    if (q >= nk) continue;
+    const int item = w * nk + q;
+    int y = 0, x = K;
+    if (cached) {
+      const int f = C.f[item], gr = C.gr[item];
+      y = m < f ? m : f;
+      x = max(m, K - gr);
+    }
+    C.plan[item] = make_int4(y, x, m, (cached ? 1 : 0) | (alive ? 2 : 0) | 8);
+    if (alive) ws.worklist[atomicAdd(&ws.counters[0], 1)] = item;
   }
-  C.plan[item] = make_int4(y, x, m, (cached ? 1 : 0) | (alive ? 2 : 0) | 8);
-  if (alive) ws.worklist[atomicAdd(&ws.counters[0], 1)] = item;
-  if (stats) {
-    atomicAdd(&stats->items, 1ull);
-    if (alive) atomicAdd(&stats->items_alive, 1ull);
+  if (stats && lane == 0) {
+    atomicAdd(&stats->items, (unsigned long long)nk);
+    atomicAdd(&stats->items_alive, (unsigned long long)n_alive);
   }
 }
 
@@ -503,11 +578,11 @@ int launch_pipeline(const DevModel &M, int precision, int kd, int G, const SeqVi
   MoveView mv = moves ? *moves : MoveView{};
   cudaGetLastError();
   mark(0);
-  prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, mv, has_moves, cur_sign, ws, stats);
+  prep_kernel<<<(n + 7) / 8, 256, 0, st>>>(M, S, mv, has_moves, cur_sign, ws, stats);
   mark(1);
   const long long items = (long long)n * M.n_kept;
   if (items > 0) {
-    prune_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, has_moves, ws, stats);
+    prune_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(M, S, mv, has_moves, ws, stats);
     order_kernel<<<1, 1024, 0, st>>>(M, ws, nullptr);
   }
   mark(2);
@@ -532,10 +607,10 @@ int launch_cached_pipeline(const DevModel &M, int precision, int kd, const SeqVi
   cudaStream_t st = (cudaStream_t)stream;
   const int n = S.n;
   cudaGetLastError();
-  prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, mv, 1, cur_sign, ws, stats);
+  prep_kernel<<<(n + 7) / 8, 256, 0, st>>>(M, S, mv, 1, cur_sign, ws, stats);
   const long long items = (long long)n * M.n_kept;
   if (items > 0) {
-    plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, mv, ws, C, write ? 1 : 0, stats);
+    plan_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(M, S, mv, ws, C, write ? 1 : 0, stats);
     order_kernel<<<1, 1024, 0, st>>>(M, ws, C.plan);
   }
   int rc = (int)cudaGetLastError();
@@ -554,7 +629,7 @@ int launch_cache_build(const DevModel &M, int precision, int kd, const SeqView &
   cudaStream_t st = (cudaStream_t)stream;
   const int n = S.n;
   cudaGetLastError();
-  prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, MoveView{}, 0, nullptr, ws, nullptr);
+  prep_kernel<<<(n + 7) / 8, 256, 0, st>>>(M, S, MoveView{}, 0, nullptr, ws, nullptr);
   const long long items = (long long)n * M.n_kept;
   if (items == 0) return (int)cudaGetLastError();
   build_plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, ws, C);
@@ -572,10 +647,10 @@ int launch_cached_measure(const DevModel &M, int precision, int kd, const SeqVie
   cudaStream_t st = (cudaStream_t)stream;
   const int n = S.n;
   cudaGetLastError();
-  prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(M, S, MoveView{}, 0, nullptr, ws, nullptr);
+  prep_kernel<<<(n + 7) / 8, 256, 0, st>>>(M, S, MoveView{}, 0, nullptr, ws, nullptr);
   const long long items = (long long)n * M.n_kept;
   if (items > 0) {
-    measure_plan_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(M, S, ws, C, nullptr);
+    measure_plan_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(M, S, ws, C, nullptr);
     order_kernel<<<1, 1024, 0, st>>>(M, ws, C.plan);
     int rc = (int)cudaGetLastError();
     if (rc) return rc;

@@ -1,13 +1,14 @@
 """A fixed invocation of the CT-HYB sweep for profiler captures.
 
     python -m paper_0908_0681_gb300.profile_sweep [--beta 50] [--chains 1024] [--steps 20]
-           [--therm 200] [--collect 100] [--mode plain|da|both] [--cache-ops 0] [--precision fp32|fp64]
-           [--k-cap 128]
+           [--therm 200] [--collect 100] [--mode plain|da|both|multi] [--tries 8] [--cache-ops 0]
+           [--precision fp32|fp64] [--k-cap 128]
 
 Five-orbital model with the semicircular bath (2,000 tau points); the chains start from
 Poisson(6) configurations (kt_sweep_set_configs) and thermalise `therm` steps. For
-`da`, a surrogate is trained for one epoch on `collect` steps of the chains' own ratios.
-Then `steps` plain and/or delayed-acceptance steps run, measuring every 10 steps, with
+`da` and `multi`, a surrogate is trained for one epoch on `collect` steps of the chains' own
+ratios. Then `steps` plain and/or delayed-acceptance steps (`multi`: call steps of up to
+`tries` stage-1 tries, kt_sweep_run_da_multi) run, measuring every 10 steps, with
 the partial-state cache when --cache-ops > 0. Prints the CUDA-event time per step and
 the trace pipeline's work per proposal. Exits 0 when no chain reported a trace error.
 """
@@ -28,7 +29,8 @@ def main():
     p.add_argument("--chains", type=int, default=1024)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--therm", type=int, default=200)
-    p.add_argument("--mode", choices=["plain", "da", "both"], default="both")
+    p.add_argument("--mode", choices=["plain", "da", "both", "multi"], default="both")
+    p.add_argument("--tries", type=int, default=8, help="stage-1 tries per call step of --mode multi")
     p.add_argument("--collect", type=int, default=100, help="steps of training data for the surrogate")
     p.add_argument("--cache-ops", type=int, default=0)
     p.add_argument("--k-cap", type=int, default=128)
@@ -62,17 +64,21 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
+        c0 = sw.counters()
         fn(u, meas_every=10)
         e1.record()
         torch.cuda.synchronize()
+        c1 = sw.counters()
         ms = e0.elapsed_time(e1) / u.shape[0]
+        mh = (c1["insert_proposed"] + c1["remove_proposed"] - c0["insert_proposed"] - c0["remove_proposed"]) / u.shape[0]
         st = engine.new_stats()
         sw.set_stats(st)
         fn(u[:10])
         sw.set_stats(None)
         w = kt.stats_from_tensor(st)
         per = {k: round(w[k] / (10 * nw), 3) for k in ("intervals", "ops_applied", "krylov_iters", "items_alive")}
-        print(f"  {fn.__name__}: {ms:.3f} ms/step, {nw / ms * 1e3:.0f} proposals/s, work per proposal {per}")
+        print(f"  {fn.__name__}: {ms:.3f} ms per call step, {mh / ms * 1e3:.0f} Metropolis steps/s, "
+              f"work per chain and call step {per}")
 
     if a.mode in ("plain", "both"):
         timed(sw.run, uni(a.steps, 6))
@@ -82,6 +88,13 @@ def main():
         net.train(X, t.clamp(-25.0, 10.0), epochs=1, batch=4096, lr=3e-3)
         sw.set_surrogate(net)
         timed(sw.run_da, uni(a.steps, 7))
+    if a.mode == "multi":
+        X, t = sw.collect(uni(a.collect, 6), capacity=a.collect * nw)
+        net = engine.Surrogate(sw.n_features, max_batch=max(4096, a.tries * nw), seed=1)
+        net.train(X, t.clamp(-25.0, 10.0), epochs=1, batch=4096, lr=3e-3)
+        sw.set_surrogate(net)
+        u = torch.rand((a.steps, nw, a.tries, 7), dtype=torch.float64, device="cuda", generator=g)
+        timed(sw.run_da_multi, u)
     torch.cuda.synchronize()
     c = sw.counters()
     print(f"profile_sweep beta={a.beta:g} chains={nw} steps={a.steps} mode={a.mode} cache_ops={a.cache_ops} "
