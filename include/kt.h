@@ -567,7 +567,8 @@ kt_status kt_sweep_run_da(kt_sweep *s, int32_t n_steps, const double *uniforms, 
  * The surrogate (kt_sweep_set_surrogate) must accept batches of tries * n_walkers rows
  * (KT_EINVAL otherwise); 1 <= tries <= KT_DA_MAX_TRIES. The first call with a larger
  * `tries` than before allocates the proposal slots (about tries * n_walkers *
- * (16 k_cap + 2 n_in + 120) bytes) and synchronises; KT_ENOMEM if that fails. */
+ * (16 k_cap + 2 n_in + 120) bytes, plus 2 bytes per operator slot of every walker for a
+ * next-same-flavor table) and synchronises; KT_ENOMEM if that fails. */
 #define KT_DA_MAX_TRIES 16
 kt_status kt_sweep_run_da_multi(kt_sweep *s, int32_t n_steps, int32_t tries, const double *uniforms,
                                 int32_t meas_every, void *stream);

@@ -172,6 +172,7 @@ struct TryView {
   float *ytil;
   unsigned long long *scratch_counters;  // the propose kernel's counters land here; the select kernel counts
   int32_t *n_tries;   // [nw] Metropolis steps the walker took this step (tries up to and including the selected one)
+  int16_t *nxt;       // [nw][cap] next operator of the same flavor (sweep_next_flavor_kernel)
   double *u5;         // [nw] stage-2 uniform of the selected try
 };
 
@@ -553,6 +554,98 @@ __global__ void sweep_features_kernel(SweepView S0, TryView Tv) {
       x = (float)(d / beta);
     } else if (i == 34 * nf + 2) {
       x = S.p_seg[w] ? 1.f : -1.f;
+    } else if (i < 35 * nf + 3) {
+      x = md > 0.0 ? (float)(occ[i - 34 * nf - 3] / md) : 0.f;
+    }
+    row[i] = __float2bfloat16_rn(x);
+  }
+}
+
+// Multi-try delayed acceptance, before the features: for every operator i of a walker, the
+// next operator of the same flavor after it, cyclically (-1 if i is its flavor's only one),
+// one warp per walker. The tries of a call step share the configuration, so this table is
+// built once and every try's features take O(K) instead of O(K^2 / n_flavors).
+__global__ void sweep_next_flavor_kernel(SweepView S, TryView Tv) {
+  const int lane = threadIdx.x & 31;
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (w >= S.nw) return;
+  const int o = S.offsets[w], K = S.lens[w];
+  const uint8_t *fl = S.flv + o;
+  int16_t *nxt = Tv.nxt + (size_t)w * S.cap;
+  for (int i = lane; i < K; i += 32) {
+    const int f = fl[i];
+    int j = -1;
+    for (int s2 = 1; s2 < K; ++s2) {
+      const int c = i + s2 < K ? i + s2 : i + s2 - K;
+      if (fl[c] == f) {
+        j = c;
+        break;
+      }
+    }
+    nxt[i] = (int16_t)j;
+  }
+}
+
+// Features of the tries (one warp per walker and try), with the values of
+// sweep_features_kernel: a removal try's base skips its own pair by following the walker's
+// next-same-flavor table past the pair's two operators.
+__global__ void sweep_features_multi_kernel(SweepView S, TryView Tv) {
+  extern __shared__ float hsm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (w >= S.nw) return;
+  const int nf = S.nf;
+  const double beta = S.beta;
+  const size_t sl = (size_t)blockIdx.y * S.nw + w;
+  float *hist = hsm + (size_t)wib * nf * 34;
+  double *occ = reinterpret_cast<double *>(hist + nf * 32);
+  for (int i = lane; i < nf * 32; i += 32) hist[i] = 0.f;
+  for (int i = lane; i < nf; i += 32) occ[i] = 0.0;
+  __syncwarp();
+  const double m0 = Tv.p_t1[sl];
+  double md = Tv.p_t2[sl] - m0;
+  if (md < 0.0) md += beta;
+  const int o = S.offsets[w], K = S.lens[w];
+  const double *tau = S.tau + o;
+  const uint8_t *fl = S.flv + o, *dg = S.dag + o;
+  const int16_t *nxt = Tv.nxt + (size_t)w * S.cap;
+  const int pa = Tv.p_pair[2 * sl], pb = Tv.p_pair[2 * sl + 1];
+  for (int i = lane; i < K; i += 32) {
+    if (dg[i] != 1 || i == pa || i == pb) continue;
+    const int f = fl[i];
+    int j = nxt[i];
+    while (j >= 0 && (j == pa || j == pb)) j = nxt[j];
+    if (j == i) j = -1;
+    if (j < 0) continue;
+    const double ti = tau[i], tj = tau[j];
+    const double l = tj > ti ? tj - ti : tj + beta - ti;
+    int b = (int)(l / beta * 32);
+    b = b > 31 ? 31 : b;
+    atomicAdd(&hist[f * 32 + b], 0.25f);
+    double ov = 0.0;
+    for (int k = -1; k <= 1; ++k) {
+      const double lo = fmax(ti, m0 + k * beta), hi = fmin(ti + l, m0 + md + k * beta);
+      ov += fmax(0.0, hi - lo);
+    }
+    if (ov > 0.0) atomicAdd(&occ[f], ov);
+  }
+  __syncwarp();
+  __nv_bfloat16 *row = Tv.X + sl * S.n_in;
+  const int fm = Tv.mv_flv[sl];
+  for (int i = lane; i < S.n_in; i += 32) {
+    float x = 0.f;
+    if (i < nf) {
+      x = (float)(S.kf[(size_t)w * nf + i] - (pa >= 0 && i == fm ? 1 : 0)) / 8.f;
+    } else if (i < 33 * nf) {
+      x = hist[i - nf];
+    } else if (i == 33 * nf) {
+      x = 0.f;
+    } else if (i <= 34 * nf) {
+      x = (i - 33 * nf - 1 == fm) ? 1.f : 0.f;
+    } else if (i == 34 * nf + 1) {
+      x = (float)(md / beta);
+    } else if (i == 34 * nf + 2) {
+      x = Tv.p_seg[sl] ? 1.f : -1.f;
     } else if (i < 35 * nf + 3) {
       x = md > 0.0 ? (float)(occ[i - 34 * nf - 3] / md) : 0.f;
     }
@@ -1091,7 +1184,7 @@ kt_status alloc_tries(kt_sweep *s, int T, size_t *dry = nullptr) {
                o_ld = take(n * 8), o_lam = take(n * 8), o_vec = take(n * 2 * kc * 8), o_pair = take(n * 2 * 4),
                o_rem = take(n * 4), o_ij = take(n * 2 * 4), o_mk = take(n), o_mf = take(n),
                o_X = take(n * (size_t)s->v.n_in * 2), o_y = take(n * 4), o_cnt = take(KT_SWEEP_NCOUNTERS * 8),
-               o_nt = take(nw * 4), o_u5 = take(nw * 8);
+               o_nt = take(nw * 4), o_u5 = take(nw * 8), o_nxt = take(nw * (size_t)s->v.cap * 2);
   if (dry) {
     *dry = b;
     return KT_OK;
@@ -1113,6 +1206,7 @@ kt_status alloc_tries(kt_sweep *s, int T, size_t *dry = nullptr) {
   t.mv_flv = (uint8_t *)(p + o_mf); t.X = (__nv_bfloat16 *)(p + o_X); t.ytil = (float *)(p + o_y);
   t.scratch_counters = (unsigned long long *)(p + o_cnt); t.n_tries = (int32_t *)(p + o_nt);
   t.u5 = (double *)(p + o_u5);
+  t.nxt = (int16_t *)(p + o_nxt);
   t.T = T;
   return KT_OK;
 }
@@ -1355,7 +1449,8 @@ kt_status kt_sweep_run_da_multi(kt_sweep *s, int32_t n_steps, int32_t tries, con
     // the end of the step), all scored by one surrogate inference
     const dim3 grid_t(grid, (unsigned)tries);
     kt::sweep_propose_kernel<<<grid_t, wpb * 32, shm, st>>>(v, u, ustride, tv);
-    kt::sweep_features_kernel<<<grid_t, wpb * 32, shf, st>>>(v, tv);
+    kt::sweep_next_flavor_kernel<<<grid, wpb * 32, 0, st>>>(v, tv);
+    kt::sweep_features_multi_kernel<<<grid_t, wpb * 32, shf, st>>>(v, tv);
     if (kt::mlp_forward(s->net, tv.X, tries * v.nw, tv.ytil, false, st) != 0) return KT_ECUDA;
     kt::sweep_select_kernel<<<grid, wpb * 32, 0, st>>>(v, tv, u);
     // measurement of the configuration the walker spent this step's tries in, weighted by them

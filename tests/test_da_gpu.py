@@ -238,3 +238,29 @@ def test_multi_try_five_orbital_statistics():
     assert np.all(np.abs(gp.mean(0) - gm_.mean(0)) < 5 * seg + 1e-4)
     seo = np.sqrt(obp.var(0, ddof=1) / nw + obm.var(0, ddof=1) / nw)
     assert np.all(np.abs(obp.mean(0) - obm.mean(0)) < 5 * seo + 1e-6), (obp.mean(0), obm.mean(0), seo)
+
+
+def test_multi_try_features_equal_single_try_features():
+    """The multi-try path builds its features per walker from a shared next-same-flavor table;
+    with one try and a network whose prediction depends on every feature (random weights), it
+    takes exactly the decisions of kt_sweep_run_da, whose features come from the per-proposal
+    kernel (the values are the same up to the order of floating-point additions)."""
+    spec, om, gm, table = three_orbital()
+    nw, steps = 64, 300
+    net = engine.Surrogate(ref.n_inputs(6), max_batch=nw, seed=5)
+    u = np.random.default_rng(57).random((steps, nw, 7))
+    res = []
+    for multi in (False, True):
+        sw = engine.Sweep(gm, table, spec.beta, nw, k_cap=64, n_bins=10)
+        sw.set_surrogate(net)
+        if multi:
+            sw.run_da_multi(torch.as_tensor(u[:, :, None, :].copy(), device="cuda"))
+        else:
+            sw.run_da(torch.as_tensor(u, device="cuda"))
+        res.append((sw.configs(), sw.counters()))
+    (ca, ka), (cb, kb) = res
+    assert ka["stage1_rejected"] > 0.1 * nw * steps
+    assert ca == cb
+    for k in ("insert_proposed", "remove_proposed", "insert_accepted", "remove_accepted", "stage1_rejected",
+              "trace_evaluations", "null_moves"):
+        assert ka[k] == kb[k], k
