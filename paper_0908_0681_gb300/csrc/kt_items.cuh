@@ -53,6 +53,12 @@ struct Tab<double> {
 // memory, so one CTA per SM runs anyway and its threads may use the registers of two
 #define KT_MIN_CTAS(VT) (sizeof(VT) == 8 ? 1 : 2)
 
+// Compile-time options of the items kernels (OPT): the code a launch does not need is not in
+// its instance, which keeps the hot loop's instructions together (a smaller kernel, fewer
+// instruction-fetch stalls). KT_OPT_TRI64: the FP64 tridiagonal steps of KT_FP32_TRIDIAG64
+// (FP32 path, blocks of at most 16 rows); KT_OPT_MEAS: the observables at beta/2.
+constexpr int KT_OPT_TRI64 = 1, KT_OPT_MEAS = 2;
+
 template <int G, typename T>
 __device__ __forceinline__ T gsum(T v, unsigned mask) {
 #pragma unroll
@@ -689,10 +695,11 @@ __device__ __forceinline__ double exact_propagate32(const DevModel &M, Unit<VT, 
 // Step 5: q_0 <- exp(-dt (H_b - E0)) q_0 by Lanczos on H_b - s_b with the
 // a-posteriori stop; the scalars taken out go to the log-weight.
 // False if the propagated vector is exactly zero.
-template <typename VT, int G, int DMAX, int PMAX>
+template <int OPT, typename VT, int G, int DMAX, int PMAX>
 __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double dt, kt_stats *stats) {
   const bool with_stats = stats != nullptr;
   constexpr bool F32 = sizeof(VT) == 4;
+  constexpr bool TRI64 = (OPT & KT_OPT_TRI64) != 0;
   constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
   constexpr int IPW = 32 / G;
   auto &s = u.s;
@@ -838,14 +845,14 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
   // from the eigendecomposition there, their FP32 traces came out less accurate, not more
   if constexpr (F32 && DMAX <= 16) dense = exact && p >= 2;
   if (dense) {
-    if (M.tri64)
+    if (TRI64)
       logfac = exact_propagate32<double>(M, u, off, dt, vv);
     else
       logfac = exact_propagate32<float>(M, u, off, dt, vv);
   } else {
     // final exp(-dt T_p) e_1 at the stopping p
     if constexpr (F32) {
-      if (p == 2 && (DMAX > 16 || M.tri64)) {
+      if (p == 2 && (DMAX > 16 || TRI64)) {
         // the 2x2 closed form in FP64 from the double-float alpha, beta: with KT_FP32_TRIDIAG64,
         // and in the instances for blocks beyond 16 rows (seven orbitals), where the FP32
         // eigenvector components of the 2x2 step (error u ||T_2|| / gap) were the largest
@@ -863,7 +870,7 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
       } else if (p <= 2) {
         tri_small_f32(s, grp, gl, gm, p, dt, logfac);
       } else {
-        if (DMAX > 16 || M.tri64) {
+        if (DMAX > 16 || TRI64) {
           // FP32 Ritz vectors are off by about u ||T_p|| / gap, an error that does not average
           // out over the intervals of a sequence; blocks beyond 16 rows (seven orbitals) and
           // models with KT_FP32_TRIDIAG64 therefore take the full FP64 eigensolve at the final
@@ -1001,7 +1008,7 @@ __device__ __forceinline__ void measure_epilogue(const DevModel &M, Unit<VT, G, 
 // "backward", including the interval between ops m-1 and m). Each unit
 // publishes its normalised vector and log-weight to the workspace; whichever
 // finishes second forms the overlap <backward|forward>. No unit ever waits.
-template <typename VT, int G, int DMAX, int PMAX>
+template <typename VT, int G, int DMAX, int PMAX, int OPT>
 __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_kernel(DevModel M, SeqView S, MoveView mv, int has_moves, Workspace ws,
                                                     kt_stats *stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1015,7 +1022,7 @@ __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_kernel(DevModel M,
   const int nk = M.n_kept;
   const int vstride = M.d_max;
   VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
-  const bool meas = ws.item_obs != nullptr;
+  constexpr bool meas = (OPT & KT_OPT_MEAS) != 0;  // ws.item_obs is set
 
   // claim numbers: every lane group's first one is fixed, dealing consecutive numbers to
   // warp 0 of every CTA, then warp 1 of every CTA, and so on, so that the longest units
@@ -1092,7 +1099,7 @@ __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_kernel(DevModel M,
         const double tn = last ? t_s : nx.t;
         const double dt = half == 0 ? tn - op.t : op.t - tn;
         if (!last) op = nx;
-        if (dt > 0.0 && !propagate(M, u, dt, stats)) {
+        if (dt > 0.0 && !propagate<OPT>(M, u, dt, stats)) {
           vanished = true;
           break;
         }
@@ -1212,7 +1219,7 @@ __device__ __forceinline__ bool load_entry(const DevModel &M, const VT *vec, con
 // the stretch that the cache does not cover). Each state passed is written to the
 // cache when its position lies outside the edited window, else to the scratch
 // arrays. The halves meet as in items_kernel.
-template <typename VT, int G, int DMAX, int PMAX>
+template <typename VT, int G, int DMAX, int PMAX, int OPT>
 __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_cached_kernel(DevModel M, SeqView S, MoveView mv, Workspace ws,
                                                            CacheView C, kt_stats *stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1227,7 +1234,7 @@ __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_cached_kernel(DevM
   const int vstride = M.d_max, dv = C.dv;
   VT *__restrict__ hvec = reinterpret_cast<VT *>(ws.half_vec);
   const size_t P1 = (size_t)C.P + 1;
-  const bool meas = ws.item_obs != nullptr;  // observables at beta/2 (plans with flag 8)
+  constexpr bool meas = (OPT & KT_OPT_MEAS) != 0;  // observables at beta/2 (plans with flag 8)
 
   // claim numbers as in items_kernel: a fixed first one per lane group, then the queue
   const int slots = (int)(gridDim.x * blockDim.x) / G;
@@ -1293,7 +1300,7 @@ __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_cached_kernel(DevM
       if (!vanished) {
         const double dt = fwd ? op.t - t : t - op.t;
         if (eigen) u.Ladd -= dt * Ek;
-        else if (dt > 0.0 && !propagate(M, u, dt, stats)) vanished = true;
+        else if (dt > 0.0 && !propagate<OPT>(M, u, dt, stats)) vanished = true;
         if (has_op) {
           if (!vanished && !apply_op(M, u, op.f, fwd ? op.dag : 1 - op.dag)) vanished = true;
           eigen = false;
@@ -1382,7 +1389,7 @@ __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_cached_kernel(DevM
 }
 
 // launch helpers
-template <typename VT, int G, int DMAX, int PMAX>
+template <typename VT, int G, int DMAX, int PMAX, int OPT>
 int launch_items(const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves, const Workspace &ws,
                  kt_stats *stats, cudaStream_t st) {
   using Tile = WarpTile<VT, G, DMAX, PMAX>;
@@ -1392,22 +1399,22 @@ int launch_items(const DevModel &M, const SeqView &S, const MoveView &mv, int ha
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
     const size_t smem = (size_t)wpb * sizeof(Tile);
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(items_kernel<VT, G, DMAX, PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(items_kernel<VT, G, DMAX, PMAX, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, items_kernel<VT, G, DMAX, PMAX>, wpb * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, items_kernel<VT, G, DMAX, PMAX, OPT>, wpb * 32, smem);
     if (per_sm < 1) per_sm = 1;
     cached_wpb = wpb;
     cached_grid = sms * per_sm;
   }
   const size_t smem = (size_t)cached_wpb * sizeof(Tile);
-  items_kernel<VT, G, DMAX, PMAX><<<cached_grid, cached_wpb * 32, smem, st>>>(M, S, mv, has_moves, ws, stats);
+  items_kernel<VT, G, DMAX, PMAX, OPT><<<cached_grid, cached_wpb * 32, smem, st>>>(M, S, mv, has_moves, ws, stats);
   return (int)cudaGetLastError();
 }
 
 
-template <typename VT, int G, int DMAX, int PMAX>
+template <typename VT, int G, int DMAX, int PMAX, int OPT>
 int launch_items_cached(const DevModel &M, const SeqView &S, const MoveView &mv, const Workspace &ws,
                         const CacheView &C, kt_stats *stats, cudaStream_t st) {
   using Tile = WarpTile<VT, G, DMAX, PMAX>;
@@ -1417,26 +1424,34 @@ int launch_items_cached(const DevModel &M, const SeqView &S, const MoveView &mv,
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
     const size_t smem = (size_t)wpb * sizeof(Tile);
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(items_cached_kernel<VT, G, DMAX, PMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(items_cached_kernel<VT, G, DMAX, PMAX, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, items_cached_kernel<VT, G, DMAX, PMAX>, wpb * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, items_cached_kernel<VT, G, DMAX, PMAX, OPT>, wpb * 32, smem);
     if (per_sm < 1) per_sm = 1;
     cached_wpb = wpb;
     cached_grid = sms * per_sm;
   }
   const size_t smem = (size_t)cached_wpb * sizeof(Tile);
-  items_cached_kernel<VT, G, DMAX, PMAX><<<cached_grid, cached_wpb * 32, smem, st>>>(M, S, mv, ws, C, stats);
+  items_cached_kernel<VT, G, DMAX, PMAX, OPT><<<cached_grid, cached_wpb * 32, smem, st>>>(M, S, mv, ws, C, stats);
   return (int)cudaGetLastError();
 }
 
+// The options a launch needs: KT_OPT_TRI64 only where the FP32 path's blocks have at most 16
+// rows (larger ones always take the FP64 steps), KT_OPT_MEAS when the observables are asked for.
+template <typename VT>
+int items_options(int kd, const DevModel &M, const Workspace &ws) {
+  return (sizeof(VT) == 4 && kd <= 16 && M.tri64 ? KT_OPT_TRI64 : 0) | (ws.item_obs ? KT_OPT_MEAS : 0);
+}
+
+// Launches without options: every compiled (rows, lane group) variant.
 template <typename VT>
 int dispatch_items(int kd, int G, const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves,
                    const Workspace &ws, kt_stats *stats, cudaStream_t st) {
 #define KT_CASE(D, P, GG) \
-  if (kd == D && G == GG) return launch_items<VT, GG, D, P>(M, S, mv, has_moves, ws, stats, st);
+  if (kd == D && G == GG) return launch_items<VT, GG, D, P, 0>(M, S, mv, has_moves, ws, stats, st);
   KT_FOR_VARIANTS(KT_CASE)
 #undef KT_CASE
   return (int)cudaErrorInvalidValue;

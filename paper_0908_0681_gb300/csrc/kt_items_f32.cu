@@ -1,10 +1,18 @@
-// FP32-Krylov instantiations of the Krylov items kernel.
+// FP32-Krylov instances of the Krylov items kernels without options; the instances with
+// options (KT_OPT_TRI64, KT_OPT_MEAS) are in kt_items_f32_opt.cu, compiled alongside.
 #include "kt_items.cuh"
 
 namespace kt {
 
+int dispatch_items_f32_opt(int kd, int G, int opt, const DevModel &M, const SeqView &S, const MoveView &mv,
+                           int has_moves, const Workspace &ws, kt_stats *stats, cudaStream_t st);
+int dispatch_items_cached_f32_opt(int kd, int opt, const DevModel &M, const SeqView &S, const MoveView &mv,
+                                  const Workspace &ws, const CacheView &C, kt_stats *stats, cudaStream_t st);
+
 int dispatch_items_f32(int kd, int G, const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves,
                        const Workspace &ws, kt_stats *stats, cudaStream_t st) {
+  const int opt = dev::items_options<float>(kd, M, ws);
+  if (opt) return dispatch_items_f32_opt(kd, G, opt, M, S, mv, has_moves, ws, stats, st);
   return dev::dispatch_items<float>(kd, G, M, S, mv, has_moves, ws, stats, st);
 }
 
@@ -12,10 +20,12 @@ int dispatch_items_f32(int kd, int G, const DevModel &M, const SeqView &S, const
 // of each row capacity.
 int dispatch_items_cached_f32(int kd, const DevModel &M, const SeqView &S, const MoveView &mv, const Workspace &ws,
                               const CacheView &C, kt_stats *stats, cudaStream_t st) {
+  const int opt = dev::items_options<float>(kd, M, ws);
+  if (opt) return dispatch_items_cached_f32_opt(kd, opt, M, S, mv, ws, C, stats, st);
   switch (kd) {
-    case 10: return dev::launch_items_cached<float, 8, 10, 10>(M, S, mv, ws, C, stats, st);
-    case 36: return dev::launch_items_cached<float, 16, 36, 24>(M, S, mv, ws, C, stats, st);
-    case 128: return dev::launch_items_cached<float, 32, 128, 40>(M, S, mv, ws, C, stats, st);
+    case 10: return dev::launch_items_cached<float, 8, 10, 10, 0>(M, S, mv, ws, C, stats, st);
+    case 36: return dev::launch_items_cached<float, 16, 36, 24, 0>(M, S, mv, ws, C, stats, st);
+    case 128: return dev::launch_items_cached<float, 32, 128, 40, 0>(M, S, mv, ws, C, stats, st);
   }
   return (int)cudaErrorInvalidValue;
 }
