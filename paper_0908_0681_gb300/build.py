@@ -18,8 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libkt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kt_kernels.cu", "kt_items_f32.cu", "kt_items_f32_opt.cu", "kt_items_f64.cu", "kt_items_f64_opt.cu", "kt_model.cpp",
-           "kt_static.cu", "kt_sweep.cu", "kt_mlp.cu", "kt_cache.cu"]
+SOURCES = ["kt_kernels.cu", "kt_items_f32.cu", "kt_items_f32_opt.cu", "kt_items_f32_stats.cu", "kt_items_f64.cu",
+           "kt_items_f64_opt.cu", "kt_items_f64_stats.cu", "kt_model.cpp", "kt_static.cu", "kt_sweep.cu", "kt_mlp.cu",
+           "kt_cache.cu"]
 
 
 def _nvcc() -> str:

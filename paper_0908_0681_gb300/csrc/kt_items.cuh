@@ -56,8 +56,9 @@ struct Tab<double> {
 // Compile-time options of the items kernels (OPT): the code a launch does not need is not in
 // its instance, which keeps the hot loop's instructions together (a smaller kernel, fewer
 // instruction-fetch stalls). KT_OPT_TRI64: the FP64 tridiagonal steps of KT_FP32_TRIDIAG64
-// (FP32 path, blocks of at most 16 rows); KT_OPT_MEAS: the observables at beta/2.
-constexpr int KT_OPT_TRI64 = 1, KT_OPT_MEAS = 2;
+// (FP32 path, blocks of at most 16 rows); KT_OPT_MEAS: the observables at beta/2;
+// KT_OPT_STATS: the work counters of kt_stats.
+constexpr int KT_OPT_TRI64 = 1, KT_OPT_MEAS = 2, KT_OPT_STATS = 4;
 
 template <int G, typename T>
 __device__ __forceinline__ T gsum(T v, unsigned mask) {
@@ -697,9 +698,9 @@ __device__ __forceinline__ double exact_propagate32(const DevModel &M, Unit<VT, 
 // False if the propagated vector is exactly zero.
 template <int OPT, typename VT, int G, int DMAX, int PMAX>
 __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double dt, kt_stats *stats) {
-  const bool with_stats = stats != nullptr;
   constexpr bool F32 = sizeof(VT) == 4;
   constexpr bool TRI64 = (OPT & KT_OPT_TRI64) != 0;
+  const bool with_stats = (OPT & KT_OPT_STATS) && stats != nullptr;
   constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
   constexpr int IPW = 32 / G;
   auto &s = u.s;
@@ -1153,7 +1154,7 @@ __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_kernel(DevModel M,
         ws.item_status[item] = st;
       }
     }
-    if (gl == 0 && stats) {
+    if ((OPT & KT_OPT_STATS) && gl == 0 && stats) {
       if (old == 1 && ws.item_sign[item] == 0) atomicAdd(&stats->items_vanished, 1ull);
       stat_add(&stats->ops_applied, u.acc.ops);
       stat_add(&stats->intervals, u.acc.intervals);
@@ -1372,7 +1373,7 @@ __global__ void __launch_bounds__(256, KT_MIN_CTAS(VT)) items_cached_kernel(DevM
         }
       }
     }
-    if (gl == 0 && stats) {
+    if ((OPT & KT_OPT_STATS) && gl == 0 && stats) {
       stat_add(&stats->ops_applied, u.acc.ops);
       stat_add(&stats->intervals, u.acc.intervals);
       stat_add(&stats->krylov_iters, u.acc.iters);
@@ -1440,10 +1441,12 @@ int launch_items_cached(const DevModel &M, const SeqView &S, const MoveView &mv,
 }
 
 // The options a launch needs: KT_OPT_TRI64 only where the FP32 path's blocks have at most 16
-// rows (larger ones always take the FP64 steps), KT_OPT_MEAS when the observables are asked for.
+// rows (larger ones always take the FP64 steps), KT_OPT_MEAS when the observables are asked for,
+// KT_OPT_STATS when the work is counted.
 template <typename VT>
-int items_options(int kd, const DevModel &M, const Workspace &ws) {
-  return (sizeof(VT) == 4 && kd <= 16 && M.tri64 ? KT_OPT_TRI64 : 0) | (ws.item_obs ? KT_OPT_MEAS : 0);
+int items_options(int kd, const DevModel &M, const Workspace &ws, const kt_stats *stats) {
+  return (sizeof(VT) == 4 && kd <= 16 && M.tri64 ? KT_OPT_TRI64 : 0) | (ws.item_obs ? KT_OPT_MEAS : 0) |
+         (stats ? KT_OPT_STATS : 0);
 }
 
 // Launches without options: every compiled (rows, lane group) variant.

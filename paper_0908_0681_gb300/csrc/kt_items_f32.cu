@@ -1,5 +1,6 @@
 // FP32-Krylov instances of the Krylov items kernels without options; the instances with
-// options (KT_OPT_TRI64, KT_OPT_MEAS) are in kt_items_f32_opt.cu, compiled alongside.
+// options are in kt_items_f32_opt.cu (KT_OPT_TRI64, KT_OPT_MEAS) and kt_items_f32_stats.cu
+// (KT_OPT_STATS), compiled alongside.
 #include "kt_items.cuh"
 
 namespace kt {
@@ -8,10 +9,15 @@ int dispatch_items_f32_opt(int kd, int G, int opt, const DevModel &M, const SeqV
                            int has_moves, const Workspace &ws, kt_stats *stats, cudaStream_t st);
 int dispatch_items_cached_f32_opt(int kd, int opt, const DevModel &M, const SeqView &S, const MoveView &mv,
                                   const Workspace &ws, const CacheView &C, kt_stats *stats, cudaStream_t st);
+int dispatch_items_f32_stats(int kd, int opt, const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves,
+                             const Workspace &ws, kt_stats *stats, cudaStream_t st);
+int dispatch_items_cached_f32_stats(int kd, int opt, const DevModel &M, const SeqView &S, const MoveView &mv,
+                                    const Workspace &ws, const CacheView &C, kt_stats *stats, cudaStream_t st);
 
 int dispatch_items_f32(int kd, int G, const DevModel &M, const SeqView &S, const MoveView &mv, int has_moves,
                        const Workspace &ws, kt_stats *stats, cudaStream_t st) {
-  const int opt = dev::items_options<float>(kd, M, ws);
+  const int opt = dev::items_options<float>(kd, M, ws, stats);
+  if (opt & dev::KT_OPT_STATS) return dispatch_items_f32_stats(kd, opt, M, S, mv, has_moves, ws, stats, st);
   if (opt) return dispatch_items_f32_opt(kd, G, opt, M, S, mv, has_moves, ws, stats, st);
   return dev::dispatch_items<float>(kd, G, M, S, mv, has_moves, ws, stats, st);
 }
@@ -20,7 +26,8 @@ int dispatch_items_f32(int kd, int G, const DevModel &M, const SeqView &S, const
 // of each row capacity.
 int dispatch_items_cached_f32(int kd, const DevModel &M, const SeqView &S, const MoveView &mv, const Workspace &ws,
                               const CacheView &C, kt_stats *stats, cudaStream_t st) {
-  const int opt = dev::items_options<float>(kd, M, ws);
+  const int opt = dev::items_options<float>(kd, M, ws, stats);
+  if (opt & dev::KT_OPT_STATS) return dispatch_items_cached_f32_stats(kd, opt, M, S, mv, ws, C, stats, st);
   if (opt) return dispatch_items_cached_f32_opt(kd, opt, M, S, mv, ws, C, stats, st);
   switch (kd) {
     case 10: return dev::launch_items_cached<float, 8, 10, 10, 0>(M, S, mv, ws, C, stats, st);
