@@ -893,7 +893,7 @@ def main():
     K64 = a.fp64_steps if a.fp64_steps > 0 else min(a.steps, 100)
     ms64, stage64, _ = timed_loop(m64, cur64, K64, a.warmup)
 
-    # FP32 Krylov vectors with the final tridiagonal exponential in FP64 (KT_FP32_TRIDIAG64)
+    # FP32 Krylov vectors with the final tridiagonal exponential to FP64 accuracy (KT_FP32_TRIDIAG64)
     m32t = engine.model_from_spec(w.model, precision=kt.KT_FP32_KRYLOV, flags=kt.KT_FP32_TRIDIAG64)
     tuned["fp32_tridiag64"] = kt.kt_autotune(m32t, dseq.batch(), out_s, out_l, out_st, ws)
     cur32t = current(m32t)
@@ -1034,7 +1034,9 @@ def main():
     value32t = n * Kt / (sum(ms32t) / 1000.0)
     tridiag = {"value": value32t, "unit": UNIT, "ms_per_step": sum(ms32t) / Kt, "steps": Kt,
                "speedup_over_fp64": value32t / value64, "flag": "KT_FP32_TRIDIAG64",
-               "precision": "FP32 Krylov vectors, FP64 tridiagonal exponential (QL for p >= 3, closed form p = 2)"}
+               "precision": "FP32 Krylov vectors, tridiagonal exponential to FP64 accuracy (p = 2 closed form "
+                            "in FP64; p >= 3 FP32 Ritz vectors with one double-float refinement step and FP64 "
+                            "weights, FP64 QL where Ritz values are too close)"}
     e2e_value = world * n / (e2e_ms / 1000.0)
 
     # roofline of the dominant kernel (Krylov items)

@@ -70,12 +70,18 @@ typedef enum {
 #define KT_SECTOR_BLOCKS 2u  /* propagate in whole (n_up, n_dn) sectors instead of the
                                 finer blocks that also fix the set of singly occupied orbitals */
 #define KT_FP32_TRIDIAG64 4u /* FP32 path only: the final exponential of the small tridiagonal T_p of
-                                every propagation in FP64 (full QL for p >= 3, closed form for
-                                p = 2) instead of FP32 Ritz vectors with double-float Ritz values.
-                                FP32 Ritz vectors are off by about u ||T_p|| / gap, and these errors
-                                neither average out nor cancel between the halves of a sequence;
-                                with this flag the Krylov vectors carry the only FP32 rounding.
-                                Slower: the FP64 pipe of GB300 is 1/64 of the FP32 one */
+                                every propagation to FP64 accuracy, rounded to FP32 once, instead
+                                of FP32 Ritz vectors with double-float Ritz values. FP32 Ritz
+                                vectors are off by about u ||T_p|| / gap, and these errors neither
+                                average out nor cancel between the halves of a sequence; with this
+                                flag the Krylov vectors carry the only FP32 rounding. p = 2: the
+                                closed form in FP64. p >= 3: the FP32 Ritz vectors refined by one
+                                step of Ogita and Aishima's iteration (Japan J. Indust. Appl. Math.
+                                35, 2018) in double-float, Ritz values recomputed from them and FP64
+                                weights; a T_p with Ritz values too close to refine takes a full
+                                FP64 QL. Exact stops: double-float sums over the block
+                                eigendecomposition. Slower than the default (the FP64 pipe of
+                                GB300 is 1/64 of the FP32 one) */
 #define KT_HOST_ONLY 256u    /* build and check the model on the host only: no device upload;
                                 trace calls on such a model return KT_EINVAL */
 

@@ -46,12 +46,13 @@ struct DevModel {
 
   // eigendecomposition of every block (setup's FP64 Jacobi): eigenvalue k of block b minus its
   // shift at global row blk_off[b] + k (ascending within the block), and its eigenvector at
-  // blk_evec32[blk_evoff[b] + k * d_b + r], r = 0 .. d_b - 1 (blk_evec64: the same in FP64)
+  // blk_evec32[blk_evoff[b] + k * d_b + r], r = 0 .. d_b - 1 (blk_evec32lo: fl32(v - fl32(v))
+  // of the FP64 component v, the low part of a double-float copy)
   const double *st_eval64;
   const float *st_eval32;
   const int32_t *blk_evoff;
   const float *blk_evec32;
-  const double *blk_evec64;
+  const float *blk_evec32lo;
 
   const int32_t *kept_blk;    // [n_kept]
   const double *kept_e;       // [n_kept] E - E0

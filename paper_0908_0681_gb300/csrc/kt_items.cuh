@@ -38,14 +38,12 @@ struct Tab<float> {
   static __device__ __forceinline__ const float *diag(const DevModel &M) { return M.st_diag32; }
   static __device__ __forceinline__ const float *val(const DevModel &M) { return M.ell_val32; }
   static __device__ __forceinline__ const float *kept(const DevModel &M) { return M.kept_vec32; }
-  static __device__ __forceinline__ const float *evec(const DevModel &M) { return M.blk_evec32; }
 };
 template <>
 struct Tab<double> {
   static __device__ __forceinline__ const double *diag(const DevModel &M) { return M.st_diag64; }
   static __device__ __forceinline__ const double *val(const DevModel &M) { return M.ell_val64; }
   static __device__ __forceinline__ const double *kept(const DevModel &M) { return M.kept_vec64; }
-  static __device__ __forceinline__ const double *evec(const DevModel &M) { return M.blk_evec64; }
 };
 
 // Register budget of the items kernels: the FP32 warp tiles let two 256-thread CTAs share an
@@ -476,14 +474,39 @@ __device__ void tri_check32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
 #undef S_
 }
 
+// exp(-x) for a double-float argument x = hi + lo (|lo| <= u |hi|): exp(-hi) (1 - lo), whose
+// relative error is that of expf, where expf of the rounded argument alone would carry u |x|.
+__device__ __forceinline__ float exp_neg_df(DF x) { return expf(-x.hi) * (1.f - x.lo); }
+__device__ __forceinline__ DF df_from(double v) {
+  DF r;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+
 // FP32-path final step (p >= 3): every Ritz value is recomputed in double-float
 // arithmetic (about 44 bits, on the FP32 pipe) as the Rayleigh quotient of its FP32 Ritz
 // vector with the double-float T_p (the error is quadratic in the vector's, ~1e-14);
 // lambda_min enters the log-weight. The relative weights exp(-dt (lambda_k - lambda_min))
 // in (0, 1] and y = sum_k s_k s_k[0] w_k / |s_k|^2 are formed in FP32 (one Ritz pair per
 // lane), the precision of the Krylov vectors they multiply. y lands in y32.
-template <typename VT, int G, int DMAX, int PMAX>
-__device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
+//
+// REFINE (models created with KT_FP32_TRIDIAG64): the FP32 Ritz vectors X first take one
+// step of Ogita and Aishima's refinement of a symmetric eigendecomposition (Japan J. Indust.
+// Appl. Math. 35 (2018) 1007): with R = I - X^T X and S = X^T T_p X in double-float,
+// X <- X (I + E), E_kk = R_kk / 2 and, for k != l, E_kl = (S_kl + lambda_l R_kl) /
+// (lambda_l - lambda_k). That reduces the vectors' error from u |T_p| / gap to its square.
+// The Ritz values are then recomputed from the refined vectors, the weights x_l[0] w_l
+// formed in FP64, and y = sum_l x_l x_l[0] w_l summed in double-float, so that y is rounded
+// to FP32 once, as from an FP64 eigensolve (weights rounded to FP32 first put a few ulps into
+// y, which the cancellations of a trace can amplify a hundredfold). A pair whose correction
+// would exceed 1e-4 (a gap within about 1e-3 |T_p|) is not refined by this step: its FP32
+// mixing angle u |T_p| / gap times the weights' difference dt gap leaves an error u |T_p| dt
+// in y whatever the gap, so an item with such a pair returns false without writing y, and
+// the caller takes the FP64 eigensolve instead.
+// Scratch: the FP64 Ritz-vector tile S, as float pairs. Without REFINE: always true.
+template <bool REFINE, typename VT, int G, int DMAX, int PMAX>
+__device__ bool tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, unsigned gm, int p, double dt,
                             double &logfac) {
   constexpr int IPW = 32 / G;
 #define AF_(k) reinterpret_cast<const float2 *>(s.a)[(k) * IPW + grp]
@@ -492,7 +515,8 @@ __device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
 #define X_(k) s.x32[(k) * IPW + grp]
 #define Y_(k) s.y32[(k) * IPW + grp]
 #define S_(k, i) s.S32[((k) * PMAX + (i)) * IPW + grp]
-  // lane-local Ritz pair k: double-float Rayleigh quotient
+#define W_(l, i) reinterpret_cast<float2 *>(s.S)[((l) * PMAX + (i)) * IPW + grp]
+  // lane-local Ritz pair k: double-float Rayleigh quotient (and, to refine, T_p s_k)
   DF lmin;
   lmin.hi = INFINITY;
   int kmin = 0;
@@ -517,6 +541,7 @@ __device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
         b.lo = BF_(i).y;
         ti = df_add(ti, df_mulf(b, snext));
       }
+      if (REFINE) W_(k, i) = make_float2(ti.hi, ti.lo);
       num = df_add(num, df_mulf(ti, scur));
       den.add_prod(scur, scur);
       sprev = scur;
@@ -545,27 +570,144 @@ __device__ void tri_final32(WarpTile<VT, G, DMAX, PMAX> &s, int grp, int gl, uns
   }
   __syncwarp(gm);
   const float dtf = (float)dt;
-  for (int k = gl; k < p; k += G) {
-    DF lk;
-    lk.hi = DF_(k).x;
-    lk.lo = DF_(k).y;
-    const DF diff = df_add(lk, df_neg(lmin));
-    X_(k) = expf(-dtf * diff.hi) * S_(k, 0) * X_(k);
-  }
-  __syncwarp(gm);
-  for (int i = gl; i < p; i += G) {
-    float acc = 0.f;
-    for (int k = 0; k < p; ++k) acc = fmaf(S_(k, i), X_(k), acc);
-    Y_(i) = acc;
+  if constexpr (REFINE) {
+    bool close = false;
+    for (int l = gl; l < p; l += G) {
+      DF t[PMAX];  // T_p x_l
+#pragma unroll
+      for (int i = 0; i < PMAX; ++i)
+        if (i < p) {
+          const float2 v = W_(l, i);
+          t[i].hi = v.x;
+          t[i].lo = v.y;
+        }
+      // column l of S and R (float: the off-diagonal entries are O(u), their sums exact)
+      for (int k = 0; k < p; ++k) {
+        DF sa, ra;
+#pragma unroll
+        for (int i = 0; i < PMAX; ++i)
+          if (i < p) {
+            const float x = S_(k, i);
+            sa.add_prod(x, t[i].hi);
+            sa.lo = fmaf(x, t[i].lo, sa.lo);
+            ra.add_prod(x, S_(l, i));
+          }
+        const float rkl = (k == l) ? (1.f - ra.hi) - ra.lo : -(ra.hi + ra.lo);
+        W_(l, k) = make_float2(k == l ? 0.f : sa.hi + sa.lo, rkl);
+      }
+      const float2 ll = DF_(l);
+      DF lam_l;
+      lam_l.hi = ll.x;
+      lam_l.lo = ll.y;
+      for (int k = 0; k < p; ++k) {
+        const float2 sr = W_(l, k);
+        float e = 0.5f * sr.y;
+        if (k != l) {
+          const float2 kk = DF_(k);
+          DF lam_k;
+          lam_k.hi = kk.x;
+          lam_k.lo = kk.y;
+          const DF gap = df_add(lam_l, df_neg(lam_k));
+          const float num = fmaf(lam_l.hi, sr.y, sr.x), dl = gap.hi + gap.lo;
+          // the same decision for E_kl and E_lk
+          if (fmaxf(fabsf(num), fabsf(fmaf(lam_k.hi, sr.y, sr.x))) <= 1e-4f * fabsf(dl))
+            e = num / dl;
+          else
+            close = true;
+        }
+        W_(l, k).x = e;
+      }
+      // correction c_l = X E[:, l] into W(l, .).y
+      for (int i = 0; i < p; ++i) {
+        float c = 0.f;
+        for (int k = 0; k < p; ++k) c = fmaf(S_(k, i), W_(l, k).x, c);
+        W_(l, i).y = c;
+      }
+      // Ritz value of the refined vector x' = x + c: the Rayleigh quotient of x is biased by
+      // about gap |x - v|^2 (upwards for the lowest), a bias that adds up over the intervals
+      // of a sequence. With r = T x - lambda x (exact in double-float) and |x'| = 1 + O(u^2),
+      // lambda' - lambda = 2 c^T r + c^T (T - lambda) c, in X(l) until every lane is done
+      float dlam = 0.f, cprev = 0.f, ccur = W_(l, 0).y;
+#pragma unroll
+      for (int i = 0; i < PMAX; ++i)
+        if (i < p) {
+          const float cnext = (i + 1 < p) ? W_(l, i + 1).y : 0.f;
+          const DF ri = df_add(t[i], df_neg(df_mulf(lam_l, S_(l, i))));
+          float tc = (AF_(i).x - lam_l.hi) * ccur;
+          if (i > 0) tc = fmaf(BF_(i - 1).x, cprev, tc);
+          if (i + 1 < p) tc = fmaf(BF_(i).x, cnext, tc);
+          dlam = fmaf(ccur, fmaf(2.f, ri.hi + ri.lo, tc), dlam);
+          cprev = ccur;
+          ccur = cnext;
+        }
+      X_(l) = dlam;
+    }
+    if (__any_sync(gm, close)) return false;
+    // lowest refined Ritz value over the group, then x'_l[0] w_l
+    DF lmin2;
+    lmin2.hi = INFINITY;
+    for (int l = gl; l < p; l += G) {
+      DF lam;
+      lam.hi = DF_(l).x;
+      lam.lo = DF_(l).y;
+      lam = df_add(lam, df_norm(X_(l), 0.f));
+      if (df_lt(lam, lmin2)) lmin2 = lam;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      DF ol;
+      ol.hi = __shfl_xor_sync(gm, lmin2.hi, o);
+      ol.lo = __shfl_xor_sync(gm, lmin2.lo, o);
+      if (df_lt(ol, lmin2)) lmin2 = ol;
+    }
+    lmin = lmin2;
+    // x'_l[0] w_l in FP64 (one exp per Ritz pair), kept as a double-float pair in x32 / e32
+    for (int l = gl; l < p; l += G) {
+      DF lam;
+      lam.hi = DF_(l).x;
+      lam.lo = DF_(l).y;
+      lam = df_add(lam, df_norm(X_(l), 0.f));
+      const DF diff = df_add(lam, df_neg(lmin));
+      const double zw = ((double)S_(l, 0) + (double)W_(l, 0).y) * exp(-dt * ((double)diff.hi + (double)diff.lo));
+      const float hi = (float)zw;
+      X_(l) = hi;
+      s.e32[l * IPW + grp] = (float)(zw - (double)hi);
+    }
+    __syncwarp(gm);
+    for (int i = gl; i < p; i += G) {
+      DF acc;
+      for (int l = 0; l < p; ++l) {
+        const float wh = X_(l), wl = s.e32[l * IPW + grp], x = S_(l, i);
+        acc.add_prod(x, wh);
+        acc.lo = fmaf(x, wl, fmaf(W_(l, i).y, wh, acc.lo));
+      }
+      Y_(i) = acc.hi + acc.lo;
+    }
+  } else {
+    for (int k = gl; k < p; k += G) {
+      DF lk;
+      lk.hi = DF_(k).x;
+      lk.lo = DF_(k).y;
+      const DF diff = df_add(lk, df_neg(lmin));
+      X_(k) = expf(-dtf * diff.hi) * S_(k, 0) * X_(k);
+    }
+    __syncwarp(gm);
+    for (int i = gl; i < p; i += G) {
+      float acc = 0.f;
+      for (int k = 0; k < p; ++k) acc = fmaf(S_(k, i), X_(k), acc);
+      Y_(i) = acc;
+    }
   }
   logfac = -dt * ((double)lmin.hi + (double)lmin.lo);
   __syncwarp(gm);
+  return true;
 #undef AF_
 #undef BF_
 #undef DF_
 #undef X_
 #undef Y_
 #undef S_
+#undef W_
 }
 
 struct ItemAcc {
@@ -637,30 +779,29 @@ __device__ bool apply_op(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, int f, i
 // c_k = <v_k | q_0>, weights exp(-dt (lambda_k - lambda_min)) with lambda_min the lowest
 // eigenvalue whose component exceeds 4 u |q_0| (smaller components are rounding noise of
 // exact zeros, which the propagator would otherwise amplify, and are dropped), and
-// v = sum_k v_k c_k w_k into vv. TT is the type of the eigenvectors and of both sums: FP32,
-// or FP64 for models created with KT_FP32_TRIDIAG64. Returns -dt (lambda_min - s_b), the
-// scale taken out, in FP64.
-template <typename TT, typename VT, int G, int DMAX, int PMAX>
+// v = sum_k v_k c_k w_k into vv, all in FP32 (exact_propagate_df: the same with double-float
+// sums). Returns -dt (lambda_min - s_b), the scale taken out, in FP64.
+template <typename VT, int G, int DMAX, int PMAX>
 __device__ __forceinline__ double exact_propagate32(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, int off, double dt,
                                                     VT (&vv)[Unit<VT, G, DMAX, PMAX>::R]) {
   constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
   const int gl = u.gl, dim = u.dim;
   const unsigned gm = u.gm;
-  const TT *__restrict__ V = Tab<TT>::evec(M) + __ldg(M.blk_evoff + u.b);
-  TT c[R];
-  TT n2 = 0;
+  const float *__restrict__ V = M.blk_evec32 + __ldg(M.blk_evoff + u.b);
+  float c[R];
+  float n2 = 0.f;
 #pragma unroll
   for (int j = 0; j < R; ++j) {
     const int k = gl + G * j;
-    TT a = 0;
+    float a = 0.f;
     if (k < dim)
-      for (int r = 0; r < dim; ++r) a = fma(__ldg(V + k * dim + r), (TT)u.Q(0, r), a);
+      for (int r = 0; r < dim; ++r) a = fmaf(__ldg(V + k * dim + r), u.Q(0, r), a);
     c[j] = a;
-    n2 = fma(a, a, n2);
+    n2 = fmaf(a, a, n2);
   }
   n2 = gsum<G>(n2, gm);
   // lowest significant eigenvalue: eigenvalues ascend within the block
-  const TT thr = n2 * (TT)((4 * 5.9604645e-8) * (4 * 5.9604645e-8));
+  const float thr = n2 * (float)((4 * 5.9604645e-8) * (4 * 5.9604645e-8));
   int kmin = dim;
 #pragma unroll
   for (int j = R - 1; j >= 0; --j) {
@@ -678,17 +819,83 @@ __device__ __forceinline__ double exact_propagate32(const DevModel &M, Unit<VT, 
     const int k = gl + G * j;
     if (k < dim) {
       const float dl = (float)(__ldg(M.st_eval64 + off + k) - lmin);
-      u.Q(1, k) = (c[j] * c[j] > thr) ? (float)c[j] * expf(-dtf * dl) : 0.f;
+      u.Q(1, k) = (c[j] * c[j] > thr) ? c[j] * expf(-dtf * dl) : 0.f;
     }
   }
   __syncwarp(gm);
 #pragma unroll
   for (int j = 0; j < R; ++j) {
     const int r = gl + G * j;
-    TT a = 0;
+    float a = 0.f;
     if (r < dim)
-      for (int k = 0; k < dim; ++k) a = fma(__ldg(V + k * dim + r), (TT)u.Q(1, k), a);
-    vv[j] = (VT)a;
+      for (int k = 0; k < dim; ++k) a = fmaf(__ldg(V + k * dim + r), u.Q(1, k), a);
+    vv[j] = a;
+  }
+  return -dt * lmin;
+}
+
+// The exact stop of exact_propagate32 with both eigenvector sums in double-float on the FP32
+// pipe (eigenvectors as fl32 pairs, products exact by FMA; about 44 significant bits, the
+// accuracy of FP64 sums at a fraction of their cost on GB300, whose FP64 pipe is 1/64 of the
+// FP32 one) and double-float weight arguments: models created with KT_FP32_TRIDIAG64.
+template <typename VT, int G, int DMAX, int PMAX>
+__device__ __forceinline__ double exact_propagate_df(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, int off, double dt,
+                                                     VT (&vv)[Unit<VT, G, DMAX, PMAX>::R]) {
+  constexpr int R = Unit<VT, G, DMAX, PMAX>::R;
+  const int gl = u.gl, dim = u.dim;
+  const unsigned gm = u.gm;
+  const int eo = __ldg(M.blk_evoff + u.b);
+  const float *__restrict__ Vh = M.blk_evec32 + eo;
+  const float *__restrict__ Vl = M.blk_evec32lo + eo;
+  float c[R];
+  float n2 = 0.f;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int k = gl + G * j;
+    DF a;
+    if (k < dim)
+      for (int r = 0; r < dim; ++r) {
+        const float q = u.Q(0, r);
+        a.add_prod(__ldg(Vh + k * dim + r), q);
+        a.lo = fmaf(__ldg(Vl + k * dim + r), q, a.lo);
+      }
+    c[j] = a.hi + a.lo;
+    n2 = fmaf(c[j], c[j], n2);
+  }
+  n2 = gsum<G>(n2, gm);
+  const float thr = n2 * (float)((4 * 5.9604645e-8) * (4 * 5.9604645e-8));
+  int kmin = dim;
+#pragma unroll
+  for (int j = R - 1; j >= 0; --j) {
+    const int k = gl + G * j;
+    if (k < dim && c[j] * c[j] > thr) kmin = k;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(gm, kmin, o));
+  if (kmin >= dim) kmin = 0;
+  const double lmin = __ldg(M.st_eval64 + off + kmin);
+  const DF dtd = df_from(dt);
+  __syncwarp(gm);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int k = gl + G * j;
+    if (k < dim) {
+      const DF x = df_mul(dtd, df_from(__ldg(M.st_eval64 + off + k) - lmin));
+      u.Q(1, k) = (c[j] * c[j] > thr) ? c[j] * exp_neg_df(x) : 0.f;
+    }
+  }
+  __syncwarp(gm);
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int r = gl + G * j;
+    DF a;
+    if (r < dim)
+      for (int k = 0; k < dim; ++k) {
+        const float w = u.Q(1, k);
+        a.add_prod(__ldg(Vh + k * dim + r), w);
+        a.lo = fmaf(__ldg(Vl + k * dim + r), w, a.lo);
+      }
+    vv[j] = a.hi + a.lo;
   }
   return -dt * lmin;
 }
@@ -847,9 +1054,9 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
   if constexpr (F32 && DMAX <= 16) dense = exact && p >= 2;
   if (dense) {
     if (TRI64)
-      logfac = exact_propagate32<double>(M, u, off, dt, vv);
+      logfac = exact_propagate_df(M, u, off, dt, vv);
     else
-      logfac = exact_propagate32<float>(M, u, off, dt, vv);
+      logfac = exact_propagate32(M, u, off, dt, vv);
   } else {
     // final exp(-dt T_p) e_1 at the stopping p
     if constexpr (F32) {
@@ -871,11 +1078,16 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
       } else if (p <= 2) {
         tri_small_f32(s, grp, gl, gm, p, dt, logfac);
       } else {
-        if (DMAX > 16 || TRI64) {
+        // Ritz pairs from the check that stopped at p; refined with KT_FP32_TRIDIAG64
+        bool done = false;
+        if constexpr (DMAX <= 16) done = tri_final32<TRI64>(s, grp, gl, gm, p, dt, logfac);
+        if (!(DMAX <= 16 && !TRI64) && !done) {
           // FP32 Ritz vectors are off by about u ||T_p|| / gap, an error that does not average
-          // out over the intervals of a sequence; blocks beyond 16 rows (seven orbitals) and
-          // models with KT_FP32_TRIDIAG64 therefore take the full FP64 eigensolve at the final
-          // p (alpha, beta first widened in place from double-float to FP64)
+          // out over the intervals of a sequence; blocks beyond 16 rows (seven orbitals), and
+          // the items with close Ritz values that KT_FP32_TRIDIAG64 does not refine, therefore
+          // take the full FP64 eigensolve at the final p (alpha, beta first widened in place
+          // from double-float to FP64). Exact stops beyond 16 rows come without a check at p,
+          // so there are no FP32 Ritz pairs to refine.
           for (int k = gl; k < p; k += G) {
             const float2 av = reinterpret_cast<float2 *>(s.a)[k * IPW + grp];
             const float2 bv = reinterpret_cast<float2 *>(s.b)[k * IPW + grp];
@@ -886,8 +1098,6 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
           if (!tri_exp64(s, grp, gl, gm, p, dt, logfac)) u.status = KT_ENUMERIC;
           for (int k = gl; k < p; k += G) s.y32[k * IPW + grp] = (float)Y_(k);
           __syncwarp(gm);
-        } else {
-          tri_final32(s, grp, gl, gm, p, dt, logfac);  // Ritz pairs from the check that stopped at p
         }
       }
     } else {

@@ -504,8 +504,7 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   // minus the block shift per global row, eigenvectors one after another (vector k of block b
   // at blk_evoff[b] + k d, component r at + r)
   std::vector<double> st_eval64(N);
-  std::vector<float> st_eval32(N), blk_evec32;
-  std::vector<double> blk_evec64;
+  std::vector<float> st_eval32(N), blk_evec32, blk_evec32lo;
   std::vector<int32_t> blk_evoff(B);
   for (int b = 0; b < B; ++b) {
     const int d = blk_dim[b];
@@ -514,8 +513,9 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
       st_eval64[blk_off[b] + k] = evals[b][k] - blk_shift[b];
       st_eval32[blk_off[b] + k] = (float)st_eval64[blk_off[b] + k];
       for (int r = 0; r < d; ++r) {
-        blk_evec64.push_back(evecs[b][(size_t)r * d + k]);
-        blk_evec32.push_back((float)evecs[b][(size_t)r * d + k]);
+        const double x = evecs[b][(size_t)r * d + k];
+        blk_evec32.push_back((float)x);
+        blk_evec32lo.push_back((float)(x - (double)(float)x));
       }
     }
   }
@@ -539,7 +539,7 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
                i_s2w = add(blk_s2w.data(), B * 4), i_s2o = add(blk_s2ell.data(), B * 4),
                i_sev64 = add(st_eval64.data(), N * 8), i_sev32 = add(st_eval32.data(), N * 4),
                i_evo = add(blk_evoff.data(), B * 4), i_evv = add(blk_evec32.data(), blk_evec32.size() * 4),
-               i_evv64 = add(blk_evec64.data(), blk_evec64.size() * 8);
+               i_evvlo = add(blk_evec32lo.data(), blk_evec32lo.size() * 4);
   void *dmem = nullptr;
   if (cudaMalloc(&dmem, total) != cudaSuccess) { cudaGetLastError(); delete M; return KT_ENOMEM; }
   std::vector<char> host(total, 0);
@@ -575,7 +575,7 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   D.kept_vec64 = (const double *)at(i_kv64); D.kept_vec32 = (const float *)at(i_kv32);
   D.st_eval64 = (const double *)at(i_sev64); D.st_eval32 = (const float *)at(i_sev32);
   D.blk_evoff = (const int32_t *)at(i_evo); D.blk_evec32 = (const float *)at(i_evv);
-  D.blk_evec64 = (const double *)at(i_evv64);
+  D.blk_evec32lo = (const float *)at(i_evvlo);
   D.s2_diag = (const float *)at(i_s2d); D.s2_ell = (const uint16_t *)at(i_s2e);
   D.blk_s2w = (const int32_t *)at(i_s2w); D.blk_s2ell = (const int32_t *)at(i_s2o);
   *out = M;
