@@ -932,6 +932,25 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
     qc[j] = (r < dim) ? u.Q(0, r) : VT(0);
     qp[j] = VT(0);
   }
+  // Blocks of at most 16 rows: the ELL column indices of the lane's rows, read once per
+  // interval rather than at every Lanczos step (a block's pattern is the same at every step;
+  // setup merges repeated columns, so a row has at most d_b - 1 < DMAX entries), as col + 1
+  // in bytes, four to a register. The load that heads each product's chain is then gone.
+  constexpr bool PACK = DMAX <= 16;
+  constexpr int NW = PACK ? (DMAX + 2) / 4 : 1;
+  uint32_t cpk[R][NW];
+  if constexpr (PACK) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int r = gl + G * j;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) cpk[j][w] = 0u;
+      if (r < dim)
+#pragma unroll
+        for (int k = 0; k < DMAX - 1; ++k)
+          if (k < wid) cpk[j][k >> 2] |= (uint32_t)(__ldg(M.ell_col + ell + k * dim + r) + 1) << (8 * (k & 3));
+    }
+  }
   double logfac = 0.0;
   VT bprev = VT(0);
   int p = 0;
@@ -945,9 +964,18 @@ __device__ bool propagate(const DevModel &M, Unit<VT, G, DMAX, PMAX> &u, double 
       VT a = VT(0);
       if (r < dim) {
         a = __ldg(tdiag + off + r) * qc[j];
-        for (int k = 0; k < wid; ++k) {
-          const int col = __ldg(M.ell_col + ell + k * dim + r);
-          if (col >= 0) a += __ldg(tval + ell + k * dim + r) * u.Q(jj, col);
+        if constexpr (PACK) {
+#pragma unroll
+          for (int k = 0; k < DMAX - 1; ++k)
+            if (k < wid) {
+              const int col = (int)((cpk[j][k >> 2] >> (8 * (k & 3))) & 0xffu) - 1;
+              if (col >= 0) a += __ldg(tval + ell + k * dim + r) * u.Q(jj, col);
+            }
+        } else {
+          for (int k = 0; k < wid; ++k) {
+            const int col = __ldg(M.ell_col + ell + k * dim + r);
+            if (col >= 0) a += __ldg(tval + ell + k * dim + r) * u.Q(jj, col);
+          }
         }
         da.add(a, qc[j]);
       }

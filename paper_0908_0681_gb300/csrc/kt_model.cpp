@@ -315,7 +315,18 @@ kt_status kt_model_create(const kt_model_params *pp, kt_model **out) {
   std::vector<double> blk_shift(B), blk_norm(B);
   std::vector<std::vector<std::pair<int, double>>> rows(N);  // row r of global state: (col rank, value)
   for (uint32_t x = 0; x < (uint32_t)N; ++x)
-    for (auto &e : offd[x]) rows[e.first].push_back({rank_of[x], e.second});  // H[y][x]
+    for (auto &e : offd[x]) {  // H[y][x]; two terms reaching the same column share its entry
+      auto &row = rows[e.first];
+      const int col = rank_of[x];
+      bool merged = false;
+      for (auto &f : row)
+        if (f.first == col) {
+          f.second += e.second;
+          merged = true;
+          break;
+        }
+      if (!merged) row.push_back({col, e.second});
+    }
   int nnz_max = 0, n_ell = 0;
   for (int b = 0; b < B; ++b) {
     const int d = blk_dim[b];
