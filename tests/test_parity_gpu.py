@@ -248,9 +248,9 @@ def test_full_batch_every_walker(prec):
 
 
 def test_full_batch_fp64_tridiagonal_ratios_within_1e5():
-    """KT_FP32_TRIDIAG64 (FP32 Krylov vectors, FP64 tridiagonal exponential): every ratio of
-    the benchmark batch, formed end to end from two of the path's own traces, is within 1e-5
-    of the oracle's, and every trace within 5e-6."""
+    """KT_FP32_TRIDIAG64 (FP32 Krylov vectors, tridiagonal exponential to FP64 accuracy):
+    every ratio of the benchmark batch, formed end to end from two of the path's own traces,
+    is within 1e-5 of the oracle's, and every trace within 5e-6."""
     w, ox, cs, cl, s, lr, cls, sx, lx, ncls, nsx, nlx = _full_batch(kt.KT_FP32_KRYLOV, kt.KT_FP32_TRIDIAG64)
     reg = cls == 2
     assert (cs[reg] == sx[reg]).all()
