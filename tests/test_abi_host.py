@@ -93,6 +93,24 @@ def test_block_structure_counts():
         assert kt.kt_model_query(ms)["d_max"] == math.comb(n, n // 2) ** 2
 
 
+def test_ell_width_closed_form():
+    """Off-diagonal entries per row of H_loc (the ELL width nnz_max): a state with s singly
+    occupied orbitals, u of them spin up, e empty and D doubly occupied orbitals has u (s - u)
+    spin-flip and e D pair-hopping neighbours, all distinct states. Rows with fewer entries
+    than the block capacity is what the items kernels of blocks up to 16 rows rely on when they
+    keep a row's column indices in registers."""
+    for n in (1, 2, 3, 4, 5):
+        expect = max(u * (s - u) + e * (n - s - e) for s in range(n + 1) for u in range(s + 1)
+                     for e in range(n - s + 1))
+        for flags in (0, kt.KT_SECTOR_BLOCKS):
+            info = kt.kt_model_query(kt.kt_model_create(n, 4.0, 1.0, 2.0, 5.0, flags=kt.KT_HOST_ONLY | flags))
+            assert info["nnz_max"] == expect, (n, flags)
+            assert info["nnz_max"] < info["kernel_dmax"]
+        dd = kt.kt_model_query(kt.kt_model_create(n, 4.0, 1.0, 2.0, 5.0,
+                                                  flags=kt.KT_HOST_ONLY | kt.KT_DENSITY_ONLY))
+        assert dd["nnz_max"] == 0
+
+
 def test_five_orbital_paper_degeneracies_host():
     """The product's own setup reproduces N_tr = 6, 31, 25 near the level crossing (Sec. IV.C)."""
     U, J = 6.0, 1.0
